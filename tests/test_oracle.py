@@ -1,0 +1,276 @@
+"""Pins for the CPU oracle (no GPU): the oracle is checked against things other
+than itself -- brute-force enumeration of every simple cycle, Karp's
+independent recurrence, hand-computed closed forms (tests/golden), the
+structure of Fig. 1, the LP-dual certificate (Eq. 1, Prop. 2.1), Prop. 2.2,
+and invariances of the cycle mean (shift, scale, duality, relabelling,
+monotonicity).  A dropped term, a wrong sign or index, or a transposed operand
+in Howard's evaluation or improvement step changes the value or the cycle on
+some of these thousands of graphs."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from golden_io import closed_forms, fig1, relabel
+
+
+def _frac(num, den):
+    return Fraction(int(num), int(den))
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_howard_matches_brute_force_and_karp_on_tiny_graphs(mode):
+    rng = np.random.default_rng(1111062700 + (mode == "min"))
+    for trial in range(1500):
+        n = int(rng.integers(1, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=bool(trial % 3 == 0),
+                              mode=mode)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, mode)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode)
+        k = oracle.karp(g.row_ptr, g.col_idx, g.w, mode)
+        assert h.value == b.value == k, (trial, n)
+        # Howard's critical cycle is one of the optimal simple cycles, listed
+        # from its smallest vertex
+        assert tuple(int(e) for e in h.cycle) in b.optimal, (trial, h.cycle, b.optimal)
+        rc, bad = oracle.certificate(g.row_ptr, g.col_idx, g.w, mode, h.eta_p, h.eta_q, h.V,
+                                     h.num, h.den, h.cycle)
+        assert rc == 0, (trial, rc, bad)
+
+
+def test_howard_on_wide_weights_matches_brute_force():
+    rng = np.random.default_rng(7)
+    for trial in range(300):
+        n = int(rng.integers(2, 8))
+        g = synth.tiny_random(rng, n, max_extra=4, wlo=-2**31 + 1, whi=2**31 - 1)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, "max")
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, "max")
+        assert h.value == b.value
+        assert tuple(int(e) for e in h.cycle) in b.optimal
+
+
+def test_brute_force_counts_cycles_of_complete_digraph():
+    # K_4 with self-loops: simple cycles = 4 loops + C(4,2)*1 + C(4,3)*2 + C(4,4)*6 = 4+6+8+6
+    edges = [(i, j, 1) for i in range(4) for j in range(4)]
+    g = synth.from_edges(4, edges)
+    b = oracle.brute(g.row_ptr, g.col_idx, g.w)
+    assert b.ncycles == 24
+    assert b.value == 1 and len(b.optimal) == 24
+
+
+# --------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("cf", closed_forms(), ids=lambda c: c.name)
+def test_closed_forms(cf):
+    g = cf.graph
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert (h.num, h.den) == (cf.num, cf.den)
+    assert oracle.karp(g.row_ptr, g.col_idx, g.w, g.mode) == _frac(cf.num, cf.den)
+    if cf.cycle is not None:
+        assert tuple(int(e) for e in h.cycle) == cf.cycle
+
+
+def test_single_ring_closed_form_any_size():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 64, 1000):
+        w = rng.integers(-1000, 1000, size=n)
+        g = synth.from_edges(n, [(i, (i + 1) % n, int(w[i])) for i in range(n)])
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+        assert h.value == Fraction(int(w.sum()), n)
+        assert list(h.cycle) == list(range(n))
+
+
+def test_fig1_sccs_and_prop_2_2():
+    f = fig1()
+    k, comp = oracle.tarjan_scc(f.graph_max.row_ptr, f.graph_max.col_idx)
+    assert k == 4
+    groups = {}
+    for v, c in enumerate(comp):
+        groups.setdefault(int(c), set()).add(f.names[v])
+    assert sorted(map(sorted, groups.values())) == sorted(map(sorted, f.sccs))
+    for g, val, cyc in ((f.graph_max, f.max_value, f.max_cycle),
+                        (f.graph_min, f.min_value, f.min_cycle)):
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        assert (h.num, h.den) == val
+        assert tuple(int(e) for e in h.cycle) == cyc
+        # Prop. 2.2: optimum over G = optimum over the optimal cycle means of its SCCs
+        best = None
+        for members in groups.values():
+            ids = sorted(f.names.index(x) for x in members)
+            sub = [(ids.index(s), ids.index(int(g.col_idx[e])), int(g.w[e]))
+                   for s in ids for e in range(g.row_ptr[s], g.row_ptr[s + 1])
+                   if int(g.col_idx[e]) in ids]
+            if not sub:
+                continue  # single vertex without a self-loop has no cycle
+            sg = synth.from_edges(len(ids), sub, g.mode)
+            if (np.diff(sg.row_ptr) == 0).any():
+                continue
+            v = oracle.brute(sg.row_ptr, sg.col_idx, sg.w, g.mode).value
+            best = v if best is None else (max(best, v) if g.mode == "max" else min(best, v))
+        assert best == _frac(*val)
+
+
+def test_prop_2_2_random_non_strongly_connected():
+    rng = np.random.default_rng(11)
+    for trial in range(200):
+        n = int(rng.integers(2, 9))
+        g = synth.tiny_random(rng, n, max_extra=2, wlo=-20, whi=20)
+        k, comp = oracle.tarjan_scc(g.row_ptr, g.col_idx)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+        best = None
+        for c in range(k):
+            ids = [v for v in range(n) if comp[v] == c]
+            sub = [(ids.index(s), ids.index(int(g.col_idx[e])), int(g.w[e]))
+                   for s in ids for e in range(g.row_ptr[s], g.row_ptr[s + 1])
+                   if comp[g.col_idx[e]] == c]
+            if not sub:
+                continue
+            deg = np.bincount([s for s, _, _ in sub], minlength=len(ids))
+            if (deg == 0).any():
+                continue
+            sg = synth.from_edges(len(ids), sub)
+            v = oracle.karp(sg.row_ptr, sg.col_idx, sg.w)
+            best = v if best is None else max(best, v)
+        assert h.value == best
+
+
+# ------------------------------------------------------------------ invariants
+def _graph_with(g, w):
+    return synth.Graph(g.row_ptr, g.col_idx, np.asarray(w, dtype=np.int32), g.mode)
+
+
+def test_invariants_shift_scale_duality_relabel_monotone():
+    rng = np.random.default_rng(5)
+    for trial in range(200):
+        n = int(rng.integers(1, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-50, whi=50)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+        lam, cyc = h.value, tuple(h.cycle)
+        # shift: lambda(w + c) = lambda(w) + c, same cycle
+        c = int(rng.integers(-100, 100))
+        hs = oracle.howard(g.row_ptr, g.col_idx, g.w + c)
+        assert hs.value == lam + c and tuple(hs.cycle) == cyc
+        # scale: lambda(k w) = k lambda(w), same cycle
+        k = int(rng.integers(1, 50))
+        hk = oracle.howard(g.row_ptr, g.col_idx, g.w * k)
+        assert hk.value == lam * k and tuple(hk.cycle) == cyc
+        # duality: min(w) = -max(-w), same cycle
+        hm = oracle.howard(g.row_ptr, g.col_idx, -g.w, "min")
+        assert hm.value == -lam and tuple(hm.cycle) == cyc
+        # relabelling does not change the value
+        perm = rng.permutation(n)
+        r = relabel(g, perm)
+        assert oracle.howard(r.row_ptr, r.col_idx, r.w).value == lam
+        # adding an edge never lowers the maximum
+        s, t = int(rng.integers(0, n)), int(rng.integers(0, n))
+        edges = [(v, int(g.col_idx[e]), int(g.w[e])) for v in range(n)
+                 for e in range(g.row_ptr[v], g.row_ptr[v + 1])]
+        edges.append((s, t, int(rng.integers(-50, 50))))
+        g2 = synth.from_edges(n, edges)
+        assert oracle.howard(g2.row_ptr, g2.col_idx, g2.w).value >= lam
+
+
+# ----------------------------------------------------------------- certificate
+def test_certificate_rejects_planted_mistakes():
+    """Plant mistakes in an oracle answer; the certificate must catch each."""
+    rng = np.random.default_rng(9)
+    caught = {1: 0, 2: 0, 5: 0, 6: 0}
+    for trial in range(300):
+        n = int(rng.integers(3, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=True)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+        args = (g.row_ptr, g.col_idx, g.w, "max")
+        assert oracle.certificate(*args, h.eta_p, h.eta_q, h.V, h.num, h.den, h.cycle)[0] == 0
+        # a value that is too small: the optimal cycle then violates (b) or (d)
+        rc = oracle.certificate(*args, h.eta_p, h.eta_q, h.V, h.num - 1, h.den, h.cycle)[0]
+        assert rc in (5, 6)
+        caught[rc if rc in caught else 5] += 1
+        # a potential perturbed at one vertex breaks a reduced-weight inequality
+        # unless that vertex's constraints all have slack; try every vertex
+        broke = False
+        for v in range(n):
+            V2 = h.V.copy()
+            V2[v] += 1
+            rc = oracle.certificate(*args, h.eta_p, h.eta_q, V2, h.num, h.den, h.cycle)[0]
+            if rc:
+                assert rc == 2
+                broke = True
+        assert broke  # at least the critical cycle's vertices are tight
+        # claim a larger mean at one vertex only: (a) fails on an edge into it
+        # or (d) fails
+        v = int(rng.integers(0, n))
+        ep = h.eta_p.copy()
+        ep[v] += h.eta_q[v]
+        rc = oracle.certificate(*args, ep, h.eta_q, h.V, h.num, h.den, h.cycle)[0]
+        assert rc in (1, 2, 6)
+    assert caught[5] + caught[6] == 300
+
+
+def test_certificate_rejects_non_cycles():
+    cf = {c.name: c for c in closed_forms()}["k3"]
+    g = cf.graph
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+    args = (g.row_ptr, g.col_idx, g.w, "max", h.eta_p, h.eta_q, h.V, h.num, h.den)
+    assert oracle.certificate(*args, h.cycle)[0] == 0
+    assert oracle.certificate(*args, np.array([3], np.int32))[0] == 3       # not closed
+    assert oracle.certificate(*args, np.array([3, 4], np.int32))[0] == 3    # not chained
+    assert oracle.certificate(*args, np.array([3, 5, 3, 5], np.int32))[0] == 3  # longer than n
+    assert oracle.certificate(*args, np.array([0, 2], np.int32))[0] == 5    # wrong mean
+    sl = {c.name: c for c in closed_forms()}["selfloop"].graph
+    hs = oracle.howard(sl.row_ptr, sl.col_idx, sl.w)
+    a2 = (sl.row_ptr, sl.col_idx, sl.w, "max", hs.eta_p, hs.eta_q, hs.V, hs.num, hs.den)
+    assert oracle.certificate(*a2, np.array([2], np.int32))[0] == 0
+    assert oracle.certificate(*a2, np.array([2, 2], np.int32))[0] == 4     # not simple
+
+
+# ------------------------------------------------------------- error handling
+def test_oracle_rejects_bad_input():
+    g = synth.from_edges(3, [(0, 1, 1), (1, 0, 1), (2, 0, 1)])
+    with pytest.raises(oracle.OracleError):
+        oracle.howard(g.row_ptr, g.col_idx, np.array([1, 1, -2**31], np.int32))
+    rp = np.array([0, 1, 1, 2], np.int32)   # vertex 1 has no out-edge
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.howard(rp, np.array([1, 0], np.int32), np.array([1, 1], np.int32))
+    assert ei.value.code == -3
+    with pytest.raises(oracle.OracleError):
+        oracle.howard(np.array([0, 1], np.int32), np.array([5], np.int32),
+                      np.array([1], np.int32))
+
+
+def test_iteration_cap_reports_not_converged():
+    g = synth.ring10k()
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.howard(g.row_ptr, g.col_idx, g.w, "max", max_iter=1)
+    assert ei.value.code == -5
+
+
+# ------------------------------------------------------------- workload sizes
+@pytest.mark.slow
+def test_karp_equals_howard_on_ring10k():
+    g = synth.ring10k()
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert oracle.karp(g.row_ptr, g.col_idx, g.w, g.mode) == h.value
+    rc, _ = oracle.certificate(g.row_ptr, g.col_idx, g.w, g.mode, h.eta_p, h.eta_q, h.V,
+                               h.num, h.den, h.cycle)
+    assert rc == 0
+
+
+def test_karp_equals_howard_on_small_batch_members():
+    graphs = synth.batch_graphs(G=12, nmin=100, nmax=600)
+    for g in graphs:
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        assert oracle.karp(g.row_ptr, g.col_idx, g.w, g.mode) == h.value
+
+
+def test_gradient_is_one_over_cycle_length():
+    cf = {c.name: c for c in closed_forms()}["ring5"]
+    g = cf.graph
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w)
+    grad = oracle.gradient(g.m, h.cycle)
+    assert np.allclose(grad, 1 / 5)
+    # finite difference on the closed form: +1 on any ring edge adds 1/5
+    for e in range(g.m):
+        w2 = g.w.copy()
+        w2[e] += 1
+        assert oracle.howard(g.row_ptr, g.col_idx, w2).value - h.value == Fraction(1, 5)
