@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 optimal-cycle-mean solver.
+
+One step = one complete solve (initial policy, every Howard iteration of
+evaluation + improvement sweep, critical-cycle extraction) of the workload,
+with its CSR graph already resident in HBM.  The metric is edge-iterations
+per second: m * (number of improvement sweeps) / solve time, summed over all
+GPUs for multi-GPU runs (each GPU solves its own replica: one graph does not
+shard, so N > 1 is replicas only).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference     # the CPU oracle on the same workload
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "edge-iters/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _workloads():
+    return {
+        "product4": (synth.product4,
+                     "state-space product of 4 processes x 38-state rings + 2 chords/state, "
+                     "BFS-numbered, 2,085,136 states, w U[0,1000], max"),
+        "ring10k": (synth.ring10k, "ring + U{0..4} uniform extra edges, n=10,000, w U[1,100], max"),
+        "locality32m": (synth.locality32m,
+                        "locality graph n=2^25, deg 4/16/64, targets i+1+|N(0,4096)|, "
+                        "w U[-1000,1000], min"),
+        "diff1m": (synth.diff1m_base, "ring + U{0..7} extra edges, n=2^20, w 1024*U[0,1000], max"),
+    }
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.15)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands
+# --------------------------------------------------------------------------
+
+def run_reference(args, g, desc):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    iters = args.ref_iters
+    ms = []
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        try:
+            oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode, max_iter=iters)
+        except oracle.OracleError as e:
+            if e.code != -5:
+                raise
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            ms.append(dt * 1e3)
+    t_step = sum(ms) / len(ms) / 1e3
+    value = g.m * iters / t_step
+    sample = (f"first {iters} Howard iterations (evaluation + improvement sweep each) of the "
+              f"oracle on the full {args.workload} graph, per step")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edge-iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "n": g.n, "m": g.m, "mode": g.mode},
+        "cpu_baseline": {"value": value, "unit": "edge-iters/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edge-iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def algorithmic_bytes(cls: str, n: int, m: int, st_total: dict, launches: int) -> float:
+    """Bytes a kernel class must move at least, summed over its launches.
+
+    sweep:  row_ptr 4(n+1) + col_idx/w 8m + target records 16n (each once) +
+            own policy 4n per sweep, + 12 B per switched vertex (pi, succ, w_pi)
+    detect: per worklist item 40 B (list 4, own state 8, target state 8,
+            previous window min 4+4, new state 8, list out 4)
+    value:  per worklist item 56 B (list 4, own 16, target 16, new 16, list 4)
+    """
+    if cls == "sweep":
+        return launches * (4.0 * (n + 1) + 8.0 * m + 20.0 * n) + 12.0 * st_total["switched"]
+    if cls == "detect":
+        return 40.0 * st_total["detect_items"]
+    if cls == "value":
+        return 56.0 * st_total["value_items"]
+    if cls == "materialise":
+        return launches * 36.0 * n
+    return 0.0
+
+
+CLASSES = ["init", "sweep", "detect", "value", "cycles", "materialise", "extract"]
+
+
+def run_ours(args, g, desc):
+    import ctypes
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1111_0627_gb300 as ocm
+    from paper_1111_0627_gb300 import _native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _native.load()
+    stream = torch.cuda.current_stream(dev)
+
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col_idx).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    ws = ocm.make_workspace(g.n, g.m, dev)
+    cyc = torch.empty(g.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def solve():
+        return ocm.solve(rp, col, w, g.mode, workspace=ws, cycle_out=cyc, stream=stream)
+
+    for _ in range(args.warmup):
+        sol = solve()
+    sweeps = sol.stats["iterations"] + 1
+    units = g.m * sweeps                    # edge-iterations per solve
+
+    # ---- timed region: inputs resident, L2 flushed before every step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clocks:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            s = solve()
+            ev[k][1].record(stream)
+            launches += s.stats["launches"]
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * units / (total_ms / 1e3)
+
+    # ---- kernel-class durations (events around each launch), same workload
+    prof_steps = max(1, min(args.steps, 5))
+    lib.ocm_profile_enable(1)
+    lib.ocm_profile_collect(None, None)
+    st_total = {"switched": 0, "detect_items": 0, "value_items": 0}
+    for k in range(prof_steps):
+        flush.fill_(k & 0xFF)
+        s = solve()
+        for key in st_total:
+            st_total[key] += s.stats[key]
+    ms_arr = (ctypes.c_double * 7)()
+    n_arr = (ctypes.c_int64 * 7)()
+    lib.ocm_profile_collect(ms_arr, n_arr)
+    lib.ocm_profile_enable(0)
+    classes = {c: {"ms_total": ms_arr[i], "launches": int(n_arr[i])} for i, c in enumerate(CLASSES)}
+    peak, peak_kind = _peaks()
+    for c, d in classes.items():
+        b = algorithmic_bytes(c, g.n, g.m, st_total, d["launches"])
+        d["algorithmic_bytes"] = b
+        d["gbs"] = (b / (d["ms_total"] / 1e3) / 1e9) if d["ms_total"] > 0 and b > 0 else None
+    dom = max(classes, key=lambda c: classes[c]["ms_total"])
+    sweep = classes["sweep"]
+    d = classes[dom]
+    achieved = d["gbs"]
+    roofline = {"bound": "hbm", "kernel": dom,
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_kind": peak_kind,
+                "avg_launch_us": d["ms_total"] * 1e3 / max(d["launches"], 1),
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(d["launches"], 1)}
+    share = {c: round(v["ms_total"] / max(sum(x["ms_total"] for x in classes.values()), 1e-12), 4)
+             for c, v in classes.items()}
+
+    # ---- end to end through the public API with host buffers
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_col = torch.from_numpy(g.col_idx).pin_memory()
+    h_w = torch.from_numpy(g.w).pin_memory()
+    h_cyc = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    d_rp, d_col, d_w = torch.empty_like(rp), torch.empty_like(col), torch.empty_like(w)
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(e2e_steps)]
+    d2h = 0
+    barrier()
+    for k in range(e2e_steps):
+        flush.fill_(k & 0xFF)
+        e_ev[k][0].record(stream)
+        d_rp.copy_(h_rp, non_blocking=True)
+        d_col.copy_(h_col, non_blocking=True)
+        d_w.copy_(h_w, non_blocking=True)
+        s = ocm.solve(d_rp, d_col, d_w, g.mode, workspace=ws, cycle_out=cyc, stream=stream)
+        L = s.cycle.numel()
+        h_cyc[:L].copy_(s.cycle, non_blocking=True)
+        e_ev[k][1].record(stream)
+        d2h = 4 * L + 16
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps * units / (float(t.item()) / 1e3)
+
+    # ---- CPU baseline: the oracle as it stands, rank 0 at N = 1
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        dt = time.perf_counter() - t0
+        cpu = {"value": g.m * (h.iterations + 1) / dt, "unit": "edge-iters/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"one complete oracle solve of the same {args.workload} graph "
+                         f"({h.iterations + 1} sweeps, {dt:.1f} s, single-threaded)"}
+        assert (h.num, h.den) == (sol.num, sol.den), "oracle and GPU disagree"
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "edge-iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "n": g.n, "m": g.m,
+                       "mode": g.mode, "sweeps_per_solve": sweeps,
+                       "lambda": f"{sol.num}/{sol.den}", "critical_cycle_len": int(sol.cycle.numel()),
+                       "l2": "flushed before every timed step (256 MiB write, outside the timing)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "step_ms_median": statistics.median(step_ms),
+                       "step_ms_min": min(step_ms)},
+            "roofline": roofline,
+            "kernel_share": share,
+            "kernels": {c: {"ms_per_solve": v["ms_total"] / prof_steps,
+                            "launches_per_solve": v["launches"] / prof_steps,
+                            "gbs": v["gbs"]} for c, v in classes.items()},
+            "sweep_gbs": sweep["gbs"],
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "edge-iters/s",
+                    "h2d_bytes_per_step": 4 * (g.n + 1) + 8 * g.m, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "stats": sol.stats,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="product4", choices=sorted(_workloads()))
+    ap.add_argument("--ref-iters", type=int, default=2,
+                    help="Howard iterations per reference (oracle) step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    make, desc = _workloads()[args.workload]
+    g = make()
+    if args.impl == "reference":
+        return run_reference(args, g, desc)
+    return run_ours(args, g, desc)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * ocm.h -- C ABI of the GB300 optimal-cycle-mean solver.
+ *
+ * Problem (Barnat, Bauch, Brim, Ceska, "Computing Optimal Cycle Mean in
+ * Parallel on CUDA", Sec. 2.1): for a digraph G = (V, E) with integer edge
+ * weights w, the mean of a cycle C is w(C)/|C|.  The solver returns the
+ * maximum (OCM_MAX) or minimum (OCM_MIN) cycle mean lambda* as an exact
+ * reduced rational num/den, and a critical cycle attaining it.
+ *
+ * Method: Howard's policy iteration (Sec. 2.4, Alg. 1), decomposed into
+ * data-parallel primitives as in Sec. 3 (Alg. 2): an improvement sweep over
+ * the CSR edges (Alg. 2 SPFPassIter), cycle detection in the policy graph,
+ * per-cycle means, and value propagation along policy edges (Alg. 3).  The
+ * primitives here are hand-written sm_103a kernels of this library's own
+ * design: pointer jumping replaces the paper's elimination / connectGpi /
+ * valuePropagate fixpoints, and every policy cycle keeps its own exact mean
+ * (multichain policy iteration) instead of rebuilding the policy graph around
+ * one chosen cycle.  All arithmetic is integer, so results are bit-exact and
+ * deterministic.
+ *
+ * Graph format (Sec. 2.3, Fig. 2b: arrays A_i and A_t): CSR with
+ *   row_ptr[n+1]  int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = m;
+ *   col_idx[m]    int32 targets, 0 <= col_idx[e] < n;
+ *   w[m]          int32 weights, w[e] != INT32_MIN.
+ * Edge e leaves vertex v iff row_ptr[v] <= e < row_ptr[v+1].  Every vertex
+ * must have at least one out-edge.  Self-loops and parallel edges are allowed;
+ * strong connectivity is NOT required (lambda* is then the optimum over all
+ * cycles of G, as in Prop. 2.2).  Exactness bound: 2 * n^2 * max|w| < 2^62.
+ *
+ * Conventions for every entry point:
+ *   - array pointers are CUDA device memory unless marked "host";
+ *   - the caller owns all memory; the library allocates no device memory,
+ *     keeps no pointer after return, and works only on the given stream
+ *     (a cudaStream_t passed as void*, NULL = the legacy default stream);
+ *   - on any error the outputs are left untouched and a negative OCM_ERR_*
+ *     code is returned (ocm_status_string gives a message);
+ *   - results are deterministic: the same input gives the same bits.
+ */
+#ifndef OCM_H_
+#define OCM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define OCM_OK 0
+#define OCM_ERR_INVALID_ARG (-1)   /* null pointer, n or m out of range, bad mode   */
+#define OCM_ERR_BAD_CSR (-2)       /* row_ptr not monotone / wrong ends, col out of range */
+#define OCM_ERR_NO_OUT_EDGE (-3)   /* a vertex has no out-edge                      */
+#define OCM_ERR_OVERFLOW (-4)      /* w = INT32_MIN, or 2 n^2 max|w| >= 2^62         */
+#define OCM_ERR_NOT_CONVERGED (-5) /* iteration cap reached                         */
+#define OCM_ERR_TIMEOUT (-6)       /* a bounded device-side wait gave up            */
+#define OCM_ERR_WORKSPACE (-7)     /* workspace missing, too small or misaligned    */
+#define OCM_ERR_CUDA (-8)          /* a CUDA runtime call failed                    */
+#define OCM_ERR_INTERNAL (-9)      /* an internal consistency check failed          */
+
+/* optimisation sense */
+#define OCM_MAX 0
+#define OCM_MIN 1
+
+/* Optional inputs/outputs of ocm_solve.  Zero-initialise, then set fields.
+ * The per-vertex outputs describe the final policy in the MAXIMISING sense of
+ * s*w, s = +1 for OCM_MAX and -1 for OCM_MIN: eta_num[v]/eta_den[v] is the
+ * (reduced) mean of the policy cycle that v reaches, and potential[v] is the
+ * value V(v) = eta_den[v] * (s*w-weight of v's policy path to that cycle's
+ * smallest vertex) - eta_num[v] * (its length).  Together they certify
+ * optimality as the LP dual of Eq. (1): for every edge e = (v, t),
+ * eta(t) <= eta(v), and when equal, q*s*w(e) - p + V(t) - V(v) <= 0.       */
+typedef struct ocm_options {
+    int32_t max_iters;   /* improvement steps before OCM_ERR_NOT_CONVERGED; <= 0: 4n + 64 */
+    int32_t flags;       /* reserved, must be 0                                     */
+    int64_t *eta_num;    /* optional device [n]                                     */
+    int32_t *eta_den;    /* optional device [n]                                     */
+    int64_t *potential;  /* optional device [n]                                     */
+    int32_t *policy;     /* optional device [n]: final policy edge of each vertex   */
+} ocm_options;
+
+/* Counters of one solve (host struct, filled when a pointer is given). */
+typedef struct ocm_stats {
+    int32_t iterations;     /* improvement sweeps that changed the policy           */
+    int32_t cycles;         /* cycles in the final policy graph                     */
+    int32_t detect_rounds;  /* pointer-jumping rounds of cycle detection, all iters */
+    int32_t value_rounds;   /* pointer-jumping rounds of value propagation, all iters */
+    int64_t switched;       /* vertex policy switches summed over iterations        */
+    int64_t launches;       /* kernels launched by this call                        */
+    int64_t detect_items;   /* worklist items processed by cycle-detection rounds   */
+    int64_t value_items;    /* worklist items processed by value-propagation rounds */
+} ocm_stats;
+
+/* Bytes of device workspace ocm_solve needs for a graph with n vertices and m
+ * edges (256-byte aligned base required).  Returns 0 if n or m is out of
+ * range.  The workspace holds the policy, per-vertex values, pointer-jumping
+ * buffers and per-cycle records; its contents are scratch between calls.    */
+size_t ocm_workspace_size(int32_t n, int32_t m);
+
+/*
+ * ocm_solve -- optimal cycle mean of one graph.
+ *   row_ptr, col_idx, w : device CSR as described above (read only)
+ *   n, m                : vertex and edge counts, 1 <= n, 1 <= m < 2^31
+ *   mode                : OCM_MAX or OCM_MIN
+ *   num, den            : host; lambda* = *num / *den, *den > 0, gcd(|num|, den) = 1
+ *   cycle_out           : device [n]; receives the critical cycle as CSR edge
+ *                         indices in cycle order, starting with the policy edge
+ *                         of the cycle's smallest vertex (Alg. 1 MinVertex)
+ *   cycle_len           : host; number of edges written to cycle_out
+ *   workspace, ws_bytes : device scratch of at least ocm_workspace_size(n, m) bytes
+ *   stream              : cudaStream_t as void*
+ *   opt                 : NULL for defaults
+ *   stats               : host, NULL to skip
+ * Synchronises the stream before returning (the scalars are host values).
+ * Among several optimal cycles, the returned one is fixed by the iteration:
+ * the policy cycle of largest mean whose smallest vertex is smallest.
+ */
+int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
+              int32_t m, int mode, int64_t *num, int32_t *den, int32_t *cycle_out,
+              int32_t *cycle_len, void *workspace, size_t ws_bytes, void *stream,
+              const ocm_options *opt, ocm_stats *stats);
+
+/*
+ * ocm_backward -- gradient of lambda* with respect to the edge weights.
+ * While the critical cycle C* stays optimal, lambda* = w(C*)/|C*| is linear in
+ * the weights of C*, so the derivative of lambda* by w(e) = 1/|C*| for e in C* and 0 otherwise
+ * (the same in both senses).  Writes grad_w[e] = grad_lambda[0] * that value.
+ *   cycle_edges : device [cycle_len], distinct edge indices in [0, m)
+ *   grad_lambda : device [1] float, upstream gradient
+ *   grad_w      : device [m] float, fully overwritten
+ * Asynchronous on `stream`.
+ */
+int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *grad_lambda,
+                 int32_t m, float *grad_w, void *stream);
+
+/* Instrumentation for benchmarks (not needed to solve).  While enabled,
+ * every kernel launch of ocm_solve is bracketed by CUDA events recorded on
+ * the solve's stream, grouped by class:
+ *   0 initial policy + CSR checks, 1 improvement sweep, 2 cycle detection
+ *   rounds, 3 value propagation rounds, 4 per-cycle means and ranks,
+ *   5 value materialisation, 6 critical-cycle extraction and outputs.
+ * ocm_profile_enable returns the previous setting.  ocm_profile_collect waits
+ * for the recorded events, adds their durations (ms) and launch counts per
+ * class into ms_out[0..6] and launches_out[0..6] (host arrays, either may be
+ * NULL), forgets them, and returns the number of classes (7).  Not
+ * thread-safe: use from one host thread.                                    */
+#define OCM_PROFILE_CLASSES 7
+int ocm_profile_enable(int on);
+int ocm_profile_collect(double *ms_out, int64_t *launches_out);
+
+/* Text for a status code (static storage). */
+const char *ocm_status_string(int status);
+
+/* ABI version: 100 * major + minor. */
+int ocm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCM_H_ */

@@ -1,0 +1,303 @@
+// api.cu -- the C ABI declared in include/ocm.h: argument and CSR validation,
+// workspace layout, the host loop of Howard's iteration (Alg. 2's host code,
+// restructured: evaluate -> sweep -> stop when no vertex switched), the
+// extraction of the critical cycle, and the backward scatter.
+#include <climits>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ocm {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+size_t carve_workspace(void *base, int n, Workspace *ws) {
+    char *b = static_cast<char *>(base);
+    size_t off = 0;
+    const size_t N = static_cast<size_t>(n);
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off, 256);
+        void *p = b ? b + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    Workspace w{};
+    w.pi = static_cast<int *>(take(4 * N));
+    w.succ = static_cast<int *>(take(4 * N));
+    w.wpi = static_cast<int *>(take(4 * N));
+    w.rec = static_cast<Rec *>(take(sizeof(Rec) * N));
+    w.jm[0] = static_cast<JM *>(take(sizeof(JM) * N));
+    w.jm[1] = static_cast<JM *>(take(sizeof(JM) * N));
+    w.aprev = static_cast<int *>(take(4 * N));
+    w.rep = static_cast<int *>(take(4 * N));
+    w.jls[0] = static_cast<JLS *>(take(sizeof(JLS) * N));
+    w.jls[1] = static_cast<JLS *>(take(sizeof(JLS) * N));
+    for (int i = 0; i < 3; ++i) w.list[i] = static_cast<int *>(take(4 * N));
+    w.cyc_root = static_cast<int *>(take(4 * N));
+    w.cyc_p = static_cast<long long *>(take(8 * N));
+    w.cyc_q = static_cast<int *>(take(4 * N));
+    w.cyc_L = static_cast<int *>(take(4 * N));
+    w.cyc_key = static_cast<long long *>(take(8 * N));
+    w.cyc_rank = static_cast<int *>(take(4 * N));
+    w.cid_of_root = static_cast<int *>(take(4 * N));
+    w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
+    if (ws) *ws = w;
+    return align_up(off, 256);
+}
+
+__global__ void ctrl_init_kernel(Ctrl *c) {
+    Ctrl z;
+    memset(&z, 0, sizeof z);
+    z.bad_index = INT_MAX;
+    *c = z;
+}
+
+__global__ void __launch_bounds__(kThreads)
+zero_float_kernel(float *g, int m) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) g[i] = 0.0f;
+}
+
+__global__ void __launch_bounds__(kThreads)
+cycle_grad_kernel(const int *cyc, int L, const float *gl, float *g, int m) {
+    float val = __fdiv_rn(gl[0], (float)L);
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += stride) {
+        int e = cyc[i];
+        if ((unsigned)e < (unsigned)m) g[e] = val;
+    }
+}
+
+void launch_backward(const int *cycle_edges, int cycle_len, const float *grad_lambda, int m,
+                     float *grad_w, cudaStream_t st) {
+    int blocks = (m + kThreads - 1) / kThreads;
+    if (blocks > 8192) blocks = 8192;
+    zero_float_kernel<<<blocks, kThreads, 0, st>>>(grad_w, m);
+    int b2 = (cycle_len + kThreads - 1) / kThreads;
+    if (b2 > 4096) b2 = 4096;
+    if (b2 < 1) b2 = 1;
+    cycle_grad_kernel<<<b2, kThreads, 0, st>>>(cycle_edges, cycle_len, grad_lambda, grad_w, m);
+}
+
+// ---------------------------------------------------------- profiling --
+namespace {
+struct ProfPair {
+    int cls;
+    cudaEvent_t a, b;
+};
+bool g_prof_on = false;
+std::vector<cudaEvent_t> g_prof_free;
+std::vector<ProfPair> g_prof_done;
+cudaEvent_t g_prof_open = nullptr;
+double g_prof_ms[kProfCount];
+long long g_prof_n[kProfCount];
+
+cudaEvent_t prof_event() {
+    if (!g_prof_free.empty()) {
+        cudaEvent_t e = g_prof_free.back();
+        g_prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+void prof_begin(int cls, cudaStream_t st) {
+    (void)cls;
+    if (!g_prof_on) return;
+    g_prof_open = prof_event();
+    if (g_prof_open) cudaEventRecord(g_prof_open, st);
+}
+
+void prof_end(int cls, cudaStream_t st) {
+    if (!g_prof_on || !g_prof_open) return;
+    cudaEvent_t b = prof_event();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    g_prof_done.push_back(ProfPair{cls, g_prof_open, b});
+    g_prof_open = nullptr;
+}
+
+static int persistent_grid() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1024;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 1024;
+    return sms * 8;   // 8 resident 256-thread CTAs per SM
+}
+
+static int map_err_bits(int err) {
+    if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
+    if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
+    if (err & kErrWeightMin) return OCM_ERR_OVERFLOW;
+    if (err) return OCM_ERR_INTERNAL;
+    return OCM_OK;
+}
+
+static int read_ctrl(const Ctrl *dev, Ctrl *host, cudaStream_t st) {
+    if (cudaMemcpyAsync(host, dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return OCM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return OCM_ERR_CUDA;
+    return OCM_OK;
+}
+
+}  // namespace ocm
+
+using namespace ocm;
+
+extern "C" {
+
+size_t ocm_workspace_size(int32_t n, int32_t m) {
+    if (n < 1 || m < 1) return 0;
+    return carve_workspace(nullptr, n, nullptr);
+}
+
+const char *ocm_status_string(int status) {
+    switch (status) {
+        case OCM_OK: return "ok";
+        case OCM_ERR_INVALID_ARG: return "invalid argument";
+        case OCM_ERR_BAD_CSR: return "malformed CSR (row_ptr or col_idx)";
+        case OCM_ERR_NO_OUT_EDGE: return "a vertex has no out-edge";
+        case OCM_ERR_OVERFLOW: return "weights out of the exact range (INT32_MIN or 2 n^2 max|w| >= 2^62)";
+        case OCM_ERR_NOT_CONVERGED: return "iteration cap reached";
+        case OCM_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+        case OCM_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case OCM_ERR_CUDA: return "CUDA runtime error";
+        case OCM_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int ocm_version(void) { return 100; }
+
+int ocm_profile_enable(int on) {
+    int prev = g_prof_on ? 1 : 0;
+    g_prof_on = on != 0;
+    return prev;
+}
+
+int ocm_profile_collect(double *ms_out, int64_t *launches_out) {
+    for (const ProfPair &p : g_prof_done) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_prof_ms[p.cls] += ms;
+            g_prof_n[p.cls] += 1;
+        }
+        g_prof_free.push_back(p.a);
+        g_prof_free.push_back(p.b);
+    }
+    g_prof_done.clear();
+    for (int c = 0; c < kProfCount; ++c) {
+        if (ms_out) ms_out[c] = g_prof_ms[c];
+        if (launches_out) launches_out[c] = g_prof_n[c];
+        g_prof_ms[c] = 0.0;
+        g_prof_n[c] = 0;
+    }
+    return kProfCount;
+}
+
+int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
+              int32_t m, int mode, int64_t *num, int32_t *den, int32_t *cycle_out,
+              int32_t *cycle_len, void *workspace, size_t ws_bytes, void *stream,
+              const ocm_options *opt, ocm_stats *stats) {
+    if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
+    if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
+    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
+    if (!workspace) return OCM_ERR_WORKSPACE;
+    const size_t need = ocm_workspace_size(n, m);
+    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return OCM_ERR_WORKSPACE;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Workspace ws;
+    carve_workspace(workspace, n, &ws);
+    const int sign = (mode == OCM_MAX) ? 1 : -1;
+    const int grid = persistent_grid();
+    long long launches = 0;
+    Ctrl h;
+
+    // 1. row_ptr must be sane before any kernel trusts it
+    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl);
+    launch_check_row_ptr(row_ptr, n, m, ws.ctrl, st);
+    launches += 2;
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    int rc = read_ctrl(ws.ctrl, &h, st);
+    if (rc) return rc;
+    if (h.err) return map_err_bits(h.err);
+
+    // 2. initial policy (the paper's first pass from val = 0, lambda = 0),
+    //    which also validates col_idx and w and measures max|w|
+    launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, st);
+    launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    rc = read_ctrl(ws.ctrl, &h, st);
+    if (rc) return rc;
+    if (h.err) return map_err_bits(h.err);
+    {
+        // exactness bound: 2 n^2 max|w| < 2^62 keeps every value, key and
+        // cross product of the iteration inside int64
+        unsigned __int128 bound = (unsigned __int128)2 * (unsigned)n * (unsigned)n * (unsigned)h.maxabsw;
+        if (bound >= ((unsigned __int128)1 << 62)) return OCM_ERR_OVERFLOW;
+    }
+    const long long N2 = (long long)n * (long long)n;
+    const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
+
+    // 3. Howard iteration: evaluate the policy, sweep, stop when stable
+    long long it = 0, switched = 0;
+    for (;;) {
+        launches += launch_evaluate(n, N2, ws, grid, st);
+        launch_sweep(row_ptr, col_idx, w, sign, n, ws, st);
+        launches += 1;
+        if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+        rc = read_ctrl(ws.ctrl, &h, st);
+        if (rc) return rc;
+        if (h.err) return map_err_bits(h.err);
+        switched += h.switched;
+        if (!h.changed) break;
+        if (++it >= max_iters) return OCM_ERR_NOT_CONVERGED;
+    }
+
+    // 4. critical cycle of the final policy
+    const int Lstar = h.res_len;
+    if (Lstar < 1 || Lstar > n) return OCM_ERR_INTERNAL;
+    launches += launch_extract(n, Lstar, ws, cycle_out, grid, st);
+    if (opt && (opt->eta_num || opt->eta_den || opt->potential || opt->policy)) {
+        launch_outputs(n, ws, opt->eta_num, opt->eta_den, opt->potential, opt->policy, st);
+        launches += 1;
+    }
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    Ctrl fin;
+    rc = read_ctrl(ws.ctrl, &fin, st);
+    if (rc) return rc;
+    if (fin.cnt[0] != Lstar) return OCM_ERR_INTERNAL;
+
+    *num = (int64_t)sign * (int64_t)h.res_num;
+    *den = h.res_den;
+    *cycle_len = Lstar;
+    if (stats) {
+        stats->iterations = (int32_t)it;
+        stats->cycles = h.res_cycles;
+        stats->detect_rounds = fin.rounds_detect;
+        stats->value_rounds = fin.rounds_value;
+        stats->switched = switched;
+        stats->launches = launches;
+        stats->detect_items = fin.items_detect;
+        stats->value_items = fin.items_value;
+    }
+    return OCM_OK;
+}
+
+int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *grad_lambda,
+                 int32_t m, float *grad_w, void *stream) {
+    if (!cycle_edges || !grad_lambda || !grad_w) return OCM_ERR_INVALID_ARG;
+    if (m < 1 || cycle_len < 1 || cycle_len > m) return OCM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    launch_backward(cycle_edges, cycle_len, grad_lambda, m, grad_w, st);
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    return OCM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// common.cuh -- device-side layout shared by the solver's kernels.
+//
+// Notation follows the paper (Sec. 2.4, Alg. 1): pi is the policy (one
+// out-edge per vertex), G_pi the policy graph, and every cycle of G_pi has a
+// root, its smallest vertex (Alg. 1 MinVertex).  Internally the solver always
+// maximises s*w (s = +1 for the maximum cycle mean, -1 for the minimum).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ocm.h"
+
+namespace ocm {
+
+constexpr int kThreads = 256;          // block size of every kernel
+constexpr int kSweepTileV = 256;       // vertices per improvement-sweep tile
+constexpr int kSweepChunkE = 2048;     // edges staged in shared memory per chunk
+
+// Per-vertex record the improvement sweep gathers for every edge target t:
+// the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
+// t's cycle mean among the current cycles, and q.  16 bytes, one vector load.
+struct __align__(16) Rec {
+    long long V;
+    int rank;
+    int q;
+};
+
+// Cycle-detection jump state: J = succ^(2^k)(v), M = smallest vertex among the
+// 2^k vertices starting at v.
+struct __align__(8) JM {
+    int J;
+    int M;
+};
+
+// Value-propagation jump state: J = a vertex on v's policy path (the root once
+// done), len and S = length and s*w-weight of the path from v to J.
+struct __align__(16) JLS {
+    int J;
+    int len;
+    long long S;
+};
+
+// Control block in device memory (one per solve).
+struct Ctrl {
+    int err;              // OR of kErr* bits
+    int bad_index;        // first offending index seen (for diagnostics)
+    int changed;          // the sweep switched at least one vertex
+    int switched;         // number of switched vertices in the last sweep
+    int cnt[3];           // rotating worklist counters
+    int nrep;             // number of policy cycles (roots)
+    int maxabsw;          // max |w| over all edges
+    int ncand;            // cycle-extraction candidates
+    int rounds_detect;    // jump rounds that had work (cycle detection)
+    int rounds_value;     // jump rounds that had work (value propagation)
+    long long items_detect;   // worklist items processed, all detect rounds
+    long long items_value;    // worklist items processed, all value rounds
+    unsigned long long best;  // packed (rank, INT_MAX - root) of the best cycle
+    // result of a solve, copied to the host in one transfer
+    long long res_num;
+    int res_den;
+    int res_len;
+    int res_root;
+    int res_cycles;
+    int pad[2];
+};
+
+enum : int {
+    kErrRowPtr = 1,
+    kErrNoOutEdge = 2,
+    kErrCol = 4,
+    kErrWeightMin = 8,
+    kErrDetect = 16,      // cycle detection did not finish in the round budget
+    kErrValue = 32,       // value propagation did not finish in the round budget
+    kErrExtract = 64,     // critical-cycle extraction inconsistent
+};
+
+// Workspace carved from one caller-provided buffer.
+struct Workspace {
+    int *pi, *succ, *wpi;
+    Rec *rec;
+    JM *jm[2];
+    int *aprev;
+    int *rep;
+    JLS *jls[2];
+    int *list[3];
+    int *cyc_root;
+    long long *cyc_p;
+    int *cyc_q;
+    int *cyc_L;
+    long long *cyc_key;
+    int *cyc_rank;
+    int *cid_of_root;
+    Ctrl *ctrl;
+};
+
+// Layout of the workspace for n vertices; returns total bytes and fills ws
+// when base != nullptr.
+size_t carve_workspace(void *base, int n, Workspace *ws);
+
+__device__ __forceinline__ int warp_append(int *counter, bool pred, int lane) {
+    unsigned mask = __ballot_sync(0xffffffffu, pred);
+    int base = 0;
+    if (mask) {
+        int leader = __ffs(mask) - 1;
+        if (lane == leader) base = atomicAdd(counter, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ long long gcd_ll(long long a, long long b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b != 0) {
+        long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// floor(p * N2 / q) for q > 0: an order-preserving integer image of p/q that
+// separates any two distinct fractions with denominators <= sqrt(N2).
+__device__ __forceinline__ long long mean_key(long long p, long long q, long long N2) {
+    __int128 a = (__int128)p * (__int128)N2;
+    __int128 d = a / q;
+    if ((a % q) != 0 && a < 0) d -= 1;
+    return (long long)d;
+}
+
+// profiling hooks (api.cu): bracket a kernel launch of class cls with events
+enum ProfClass : int {
+    kProfInit = 0, kProfSweep = 1, kProfDetect = 2, kProfValue = 3, kProfCycles = 4,
+    kProfMaterialise = 5, kProfExtract = 6, kProfCount = 7
+};
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+
+// kernel launchers (defined in the .cu files)
+void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
+void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
+                        Workspace ws, cudaStream_t st);
+void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                  Workspace ws, cudaStream_t st);
+int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st);
+int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
+void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t *potential,
+                    int32_t *policy, cudaStream_t st);
+void launch_backward(const int *cycle_edges, int cycle_len, const float *grad_lambda, int m,
+                     float *grad_w, cudaStream_t st);
+
+}  // namespace ocm

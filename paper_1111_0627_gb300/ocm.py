@@ -1,0 +1,169 @@
+"""Python binding of the optimal-cycle-mean solver (argument marshalling only).
+
+Every step of the computation runs in the CUDA kernels of ``libocm.so``;
+this module checks tensor types, allocates the caller-owned workspace and
+output tensors with PyTorch, and calls the C ABI of ``include/ocm.h`` with
+raw device pointers and the current CUDA stream.  There is no CPU fallback.
+
+    >>> num, den, cycle = solve(row_ptr, col_idx, w, mode="max")[:3]
+
+``OCMFunction`` exposes lambda* to autograd: the forward is ``ocm_solve`` on
+the int32 weights, the backward is ``ocm_backward`` (d lambda*/d w(e) =
+1/|C*| on the critical cycle C*, 0 elsewhere).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import torch
+
+from . import _native
+
+OCM_MAX, OCM_MIN = 0, 1
+
+
+class OCMError(RuntimeError):
+    """A negative status returned by the C ABI."""
+
+    def __init__(self, status: int, where: str):
+        lib = _native.load()
+        msg = lib.ocm_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _mode(mode) -> int:
+    if mode in (OCM_MAX, "max"):
+        return OCM_MAX
+    if mode in (OCM_MIN, "min"):
+        return OCM_MIN
+    raise ValueError(f"mode must be 'max' or 'min', got {mode!r}")
+
+
+def _dev_i32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.int32:
+        raise TypeError(f"{name} must be int32, got {t.dtype}")
+    return t.contiguous()
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def workspace_bytes(n: int, m: int) -> int:
+    return int(_native.load().ocm_workspace_size(n, m))
+
+
+def make_workspace(n: int, m: int, device=None) -> torch.Tensor:
+    nbytes = workspace_bytes(n, m)
+    if nbytes == 0:
+        raise ValueError("graph size out of range")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class Solution:
+    num: int
+    den: int
+    cycle: torch.Tensor               # int32 device tensor of CSR edge indices
+    stats: dict = field(default_factory=dict)
+    eta_num: torch.Tensor | None = None
+    eta_den: torch.Tensor | None = None
+    potential: torch.Tensor | None = None
+    policy: torch.Tensor | None = None
+
+    @property
+    def value(self) -> Fraction:
+        return Fraction(self.num, self.den)
+
+    def __iter__(self):
+        return iter((self.num, self.den, self.cycle))
+
+
+def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="max", *,
+          workspace: torch.Tensor | None = None, stream=None, max_iters: int = 0,
+          certificate: bool = False, cycle_out: torch.Tensor | None = None) -> Solution:
+    """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
+
+    Returns the exact reduced mean num/den (max or min sense) and a critical
+    cycle as CSR edge indices.  With ``certificate=True`` also returns the
+    per-vertex cycle means (eta_num/eta_den) and potentials of the final
+    policy, in the maximising sense of s*w (s = -1 in min mode)."""
+    lib = _native.load()
+    rp = _dev_i32(row_ptr, "row_ptr")
+    col = _dev_i32(col_idx, "col_idx")
+    ww = _dev_i32(w, "w")
+    n, m = rp.numel() - 1, col.numel()
+    if ww.numel() != m:
+        raise ValueError("w and col_idx must have the same length")
+    dev = rp.device
+    if workspace is None:
+        workspace = make_workspace(n, m, dev)
+    if cycle_out is None:
+        cycle_out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    opt = _native.OcmOptions()
+    opt.max_iters = int(max_iters)
+    opt.flags = 0
+    extra = {}
+    if certificate:
+        extra = dict(eta_num=torch.empty(n, dtype=torch.int64, device=dev),
+                     eta_den=torch.empty(n, dtype=torch.int32, device=dev),
+                     potential=torch.empty(n, dtype=torch.int64, device=dev),
+                     policy=torch.empty(n, dtype=torch.int32, device=dev))
+        for k, t in extra.items():
+            setattr(opt, k, t.data_ptr())
+    num = ctypes.c_int64(0)
+    den = ctypes.c_int32(0)
+    clen = ctypes.c_int32(0)
+    st = _native.OcmStats()
+    rc = lib.ocm_solve(rp.data_ptr(), col.data_ptr(), ww.data_ptr(), n, m, _mode(mode),
+                       ctypes.byref(num), ctypes.byref(den), cycle_out.data_ptr(),
+                       ctypes.byref(clen), workspace.data_ptr(), workspace.numel(),
+                       _stream_ptr(stream), ctypes.byref(opt), ctypes.byref(st))
+    if rc != 0:
+        raise OCMError(rc, "ocm_solve")
+    return Solution(int(num.value), int(den.value), cycle_out[:int(clen.value)], st.as_dict(),
+                    **extra)
+
+
+def backward(cycle: torch.Tensor, grad_lambda: torch.Tensor, m: int, *, stream=None,
+             out: torch.Tensor | None = None) -> torch.Tensor:
+    """d lambda*/d w scaled by grad_lambda (``ocm_backward``); float32 [m]."""
+    lib = _native.load()
+    cyc = _dev_i32(cycle, "cycle")
+    gl = grad_lambda.reshape(1).to(dtype=torch.float32).contiguous()
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=cyc.device)
+    rc = lib.ocm_backward(cyc.data_ptr(), cyc.numel(), gl.data_ptr(), m, out.data_ptr(),
+                          _stream_ptr(stream))
+    if rc != 0:
+        raise OCMError(rc, "ocm_backward")
+    return out
+
+
+class OCMFunction(torch.autograd.Function):
+    """lambda*(w) as a differentiable function of the edge weights.
+
+    forward(w_float, row_ptr, col_idx, w_int, mode) -> lambda* (float32 scalar)
+    ``w_float`` is the float view of the weights that receives the gradient;
+    the solve itself uses the exact int32 weights ``w_int``.  The gradient is
+    1/|C*| on the edges of the critical cycle C* and 0 elsewhere, which is the
+    derivative wherever C* is the unique optimal cycle."""
+
+    @staticmethod
+    def forward(ctx, w_float, row_ptr, col_idx, w_int, mode="max"):
+        sol = solve(row_ptr, col_idx, w_int, mode)
+        ctx.save_for_backward(sol.cycle)
+        ctx.m = col_idx.numel()
+        return torch.tensor(sol.num / sol.den, dtype=torch.float32, device=w_float.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (cycle,) = ctx.saved_tensors
+        g = backward(cycle, grad_out, ctx.m)
+        return g, None, None, None, None

@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports every function include/ocm.h
+declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1111_0627_gb300 as ocm
+from paper_1111_0627_gb300 import _native
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "ocm.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ocm_[a-z0-9_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("ocm_solve", "ocm_backward", "ocm_workspace_size", "ocm_status_string",
+                     "ocm_version"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_native.build())
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _native.SIGNATURES, f"binding lacks {name}"
+
+
+def test_host_only_entry_points():
+    lib = ocm.load()
+    assert lib.ocm_version() == 100
+    assert lib.ocm_workspace_size(0, 5) == 0
+    assert lib.ocm_workspace_size(5, 0) == 0
+    small = lib.ocm_workspace_size(1000, 4000)
+    big = lib.ocm_workspace_size(2000, 4000)
+    assert small > 0 and big > small and small % 256 == 0
+    assert lib.ocm_status_string(0) == b"ok"
+    for code in range(-9, 0):
+        assert lib.ocm_status_string(code) != b"unknown status"
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    lib = ocm.load()
+    num, den, clen = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    # null CSR pointers
+    rc = lib.ocm_solve(None, None, None, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), None,
+                       ctypes.byref(clen), None, 0, None, None, None)
+    assert rc == -1
+    fake = ctypes.c_void_p(256)   # never dereferenced: the size checks fail first
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 7, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, 10**9, None, None, None)
+    assert rc == -1                                      # bad mode
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, 16, None, None, None)
+    assert rc == -7                                      # workspace too small
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), ctypes.c_void_p(256 + 8), 10**9, None, None, None)
+    assert rc == -7                                      # workspace misaligned
+    rc = lib.ocm_backward(fake, 0, fake, 4, fake, None)
+    assert rc == -1
+
+
+def test_no_cpu_fallback_in_the_package():
+    """The product package never imports the oracle or a CPU solver."""
+    pkg = os.path.dirname(ocm.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                text = open(os.path.join(root, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
