@@ -148,6 +148,36 @@ int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *gra
 int ocm_profile_enable(int on);
 int ocm_profile_collect(double *ms_out, int64_t *launches_out);
 
+/*
+ * ocm_solve_static -- ocm_solve without a caller-provided workspace, for
+ * callers that cannot allocate device memory (a process whose device memory
+ * is capped or already handed out, a plugin or real-time loop that must not
+ * allocate after start-up).  The paper has no counterpart: this is a
+ * deployment convenience of this library.
+ *
+ * The scratch space is a fixed array of OCM_STATIC_WORKSPACE_BYTES inside
+ * the library's GPU image: every device that loads the library holds it
+ * until the process exits.  Graphs with ocm_workspace_size(n, m) larger than
+ * that (about 250,000 vertices) are rejected with OCM_ERR_WORKSPACE before
+ * any device work.  The call allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library routine (benchmark instrumentation is paused while it
+ * runs).  Arguments, outputs, synchronisation and errors are those of
+ * ocm_solve.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one array: calls whose GPU work
+ * overlaps (several host threads or streams at once) race and corrupt each
+ * other, so serialise them.  The array keeps the last call's contents, which
+ * the next call does not need: everything the solver reads is initialised by
+ * the solver first.
+ */
+#define OCM_STATIC_WORKSPACE_BYTES (32u << 20)
+int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w,
+                     int32_t n, int32_t m, int mode, int64_t *num, int32_t *den,
+                     int32_t *cycle_out, int32_t *cycle_len, void *stream,
+                     const ocm_options *opt, ocm_stats *stats);
+
 /* Text for a status code (static storage). */
 const char *ocm_status_string(int status);
 

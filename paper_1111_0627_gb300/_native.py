@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
-SOURCES = ["sweep.cu", "evaluate.cu", "api.cu"]
+SOURCES = ["sweep.cu", "evaluate.cu", "api.cu", "static_ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -103,6 +103,12 @@ SIGNATURES = {
                                  ctypes.POINTER(OcmStats)]),
     "ocm_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "ocm_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                                        ctypes.POINTER(OcmOptions), ctypes.POINTER(OcmStats)]),
     "ocm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ocm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ocm_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
