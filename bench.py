@@ -164,24 +164,24 @@ def run_reference(args, g, desc):
 def algorithmic_bytes(cls: str, n: int, m: int, st_total: dict, launches: int) -> float:
     """Bytes a kernel class must move at least, summed over its launches.
 
-    sweep:  row_ptr 4(n+1) + col_idx/w 8m + target records 16n (each once) +
-            own policy 4n per sweep, + 12 B per switched vertex (pi, succ, w_pi)
-    detect: per worklist item 40 B (list 4, own state 8, target state 8,
-            previous window min 4+4, new state 8, list out 4)
-    value:  per worklist item 56 B (list 4, own 16, target 16, new 16, list 4)
+    sweep:    row_ptr 4(n+1) + col_idx/w 8m + target records 16n (each once) +
+              own policy 4n per sweep, + 12 B per switched vertex (pi, succ, w_pi)
+    evaluate: per vertex-round of cycle detection 40 B (own state 8, target
+              state 8, previous window minimum 4+4, new state 8, done bitmap and
+              succ 8), per vertex-round of value propagation 48 B (own 16,
+              target 16, new 16), per evaluation 68n (value initialisation:
+              rep, succ, rep of succ, w_pi, state 16 + 16; materialisation:
+              state 16, cycle id 4, record 16)
     """
     if cls == "sweep":
         return launches * (4.0 * (n + 1) + 8.0 * m + 20.0 * n) + 12.0 * st_total["switched"]
-    if cls == "detect":
-        return 40.0 * st_total["detect_items"]
-    if cls == "value":
-        return 56.0 * st_total["value_items"]
-    if cls == "materialise":
-        return launches * 36.0 * n
+    if cls == "evaluate":
+        return (40.0 * st_total["detect_items"] + 48.0 * st_total["value_items"]
+                + 68.0 * n * launches)
     return 0.0
 
 
-CLASSES = ["init", "sweep", "detect", "value", "cycles", "materialise", "extract"]
+CLASSES = ["init", "sweep", "evaluate", "extract"]
 
 
 def run_ours(args, g, desc):
@@ -254,8 +254,8 @@ def run_ours(args, g, desc):
         s = solve()
         for key in st_total:
             st_total[key] += s.stats[key]
-    ms_arr = (ctypes.c_double * 7)()
-    n_arr = (ctypes.c_int64 * 7)()
+    ms_arr = (ctypes.c_double * len(CLASSES))()
+    n_arr = (ctypes.c_int64 * len(CLASSES))()
     lib.ocm_profile_collect(ms_arr, n_arr)
     lib.ocm_profile_enable(0)
     classes = {c: {"ms_total": ms_arr[i], "launches": int(n_arr[i])} for i, c in enumerate(CLASSES)}

@@ -83,12 +83,12 @@ typedef struct ocm_options {
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
     int32_t cycles;         /* cycles in the final policy graph                     */
-    int32_t detect_rounds;  /* pointer-jumping rounds of cycle detection, all iters */
-    int32_t value_rounds;   /* pointer-jumping rounds of value propagation, all iters */
+    int32_t detect_rounds;  /* cycle-detection jump rounds, summed over iterations  */
+    int32_t value_rounds;   /* value-propagation jump rounds, summed over iterations */
     int64_t switched;       /* vertex policy switches summed over iterations        */
     int64_t launches;       /* kernels launched by this call                        */
-    int64_t detect_items;   /* worklist items processed by cycle-detection rounds   */
-    int64_t value_items;    /* worklist items processed by value-propagation rounds */
+    int64_t detect_items;   /* vertex-rounds of work in cycle detection             */
+    int64_t value_items;    /* vertex-rounds of work in value propagation           */
 } ocm_stats;
 
 /* Bytes of device workspace ocm_solve needs for a graph with n vertices and m
@@ -136,15 +136,15 @@ int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *gra
 /* Instrumentation for benchmarks (not needed to solve).  While enabled,
  * every kernel launch of ocm_solve is bracketed by CUDA events recorded on
  * the solve's stream, grouped by class:
- *   0 initial policy + CSR checks, 1 improvement sweep, 2 cycle detection
- *   rounds, 3 value propagation rounds, 4 per-cycle means and ranks,
- *   5 value materialisation, 6 critical-cycle extraction and outputs.
+ *   0 CSR checks + initial policy, 1 improvement sweep, 2 policy evaluation
+ *   (cycle detection, value propagation, cycle means and ranks, values),
+ *   3 critical-cycle extraction and optional outputs.
  * ocm_profile_enable returns the previous setting.  ocm_profile_collect waits
  * for the recorded events, adds their durations (ms) and launch counts per
- * class into ms_out[0..6] and launches_out[0..6] (host arrays, either may be
- * NULL), forgets them, and returns the number of classes (7).  Not
+ * class into ms_out[0..3] and launches_out[0..3] (host arrays, either may be
+ * NULL), forgets them, and returns the number of classes (4).  Not
  * thread-safe: use from one host thread.                                    */
-#define OCM_PROFILE_CLASSES 7
+#define OCM_PROFILE_CLASSES 4
 int ocm_profile_enable(int on);
 int ocm_profile_collect(double *ms_out, int64_t *launches_out);
 

@@ -42,6 +42,7 @@ size_t carve_workspace(void *base, int n, Workspace *ws) {
     w.cyc_key = static_cast<long long *>(take(8 * N));
     w.cyc_rank = static_cast<int *>(take(4 * N));
     w.cid_of_root = static_cast<int *>(take(4 * N));
+    w.done = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align_up(off, 256);
@@ -131,6 +132,7 @@ static int persistent_grid() {
 }
 
 static int map_err_bits(int err) {
+    if (err & kErrTimeout) return OCM_ERR_TIMEOUT;
     if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
     if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
     if (err & kErrWeightMin) return OCM_ERR_OVERFLOW;
@@ -248,7 +250,9 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable
     long long it = 0, switched = 0;
     for (;;) {
-        launches += launch_evaluate(n, N2, ws, grid, st);
+        const int le = launch_evaluate(n, N2, ws, grid, st);
+        if (le < 0) return OCM_ERR_CUDA;
+        launches += le;
         launch_sweep(row_ptr, col_idx, w, sign, n, ws, st);
         launches += 1;
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;

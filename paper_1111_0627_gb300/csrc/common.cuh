@@ -17,6 +17,7 @@ namespace ocm {
 constexpr int kThreads = 256;          // block size of every kernel
 constexpr int kSweepTileV = 256;       // vertices per improvement-sweep tile
 constexpr int kSweepChunkE = 2048;     // edges staged in shared memory per chunk
+constexpr int kEvalThreads = 512;      // block size of the persistent evaluation kernel
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
 // the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
@@ -57,6 +58,10 @@ struct Ctrl {
     long long items_detect;   // worklist items processed, all detect rounds
     long long items_value;    // worklist items processed, all value rounds
     unsigned long long best;  // packed (rank, INT_MAX - root) of the best cycle
+    unsigned int bar_count;   // grid barrier: blocks arrived
+    unsigned int bar_gen;     // grid barrier: generation
+    int pending[3];           // detect: rotating per-round counts of unfinished vertices
+    int pendv[3];             // values: the same
     // result of a solve, copied to the host in one transfer
     long long res_num;
     int res_den;
@@ -74,6 +79,7 @@ enum : int {
     kErrDetect = 16,      // cycle detection did not finish in the round budget
     kErrValue = 32,       // value propagation did not finish in the round budget
     kErrExtract = 64,     // critical-cycle extraction inconsistent
+    kErrTimeout = 128,    // a grid barrier wait exceeded its spin limit
 };
 
 // Workspace carved from one caller-provided buffer.
@@ -92,6 +98,7 @@ struct Workspace {
     long long *cyc_key;
     int *cyc_rank;
     int *cid_of_root;
+    unsigned *done;       // bitmap: vertex resolved and its state in both buffers
     Ctrl *ctrl;
 };
 
@@ -131,10 +138,7 @@ __device__ __forceinline__ long long mean_key(long long p, long long q, long lon
 }
 
 // profiling hooks (api.cu): bracket a kernel launch of class cls with events
-enum ProfClass : int {
-    kProfInit = 0, kProfSweep = 1, kProfDetect = 2, kProfValue = 3, kProfCycles = 4,
-    kProfMaterialise = 5, kProfExtract = 6, kProfCount = 7
-};
+enum ProfClass : int { kProfInit = 0, kProfSweep = 1, kProfEvaluate = 2, kProfExtract = 3, kProfCount = 4 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 

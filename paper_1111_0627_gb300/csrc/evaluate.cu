@@ -1,7 +1,7 @@
 // evaluate.cu -- evaluation of a policy (Alg. 1: MinMeanWeightCycle(G_pi) and
 // the value propagation that follows it; Alg. 2: elimination*,
 // cycleIdentification, reduce_min, setMinCycle, GpiPreprocess and
-// valuePropagate*), re-designed as pointer-jumping kernels.
+// valuePropagate*), re-designed as pointer jumping in one persistent kernel.
 //
 // G_pi is a functional graph: every vertex has one successor succ(v), every
 // weakly connected component holds exactly one cycle (Sec. 2.4).  Per policy:
@@ -16,7 +16,7 @@
 //           depth of v and the cycle length the test holds, so the round count
 //           adapts to the policy graph instead of log2(n).  A vertex whose
 //           jump target is already resolved takes that root (the target lies
-//           on its path).  Resolved vertices leave the worklist.
+//           on its path).
 //   values  (replaces valuePropagate*, Alg. 3): cut each cycle at its root
 //           (Alg. 1: the root is not re-entered, val(root) = 0) and jump with
 //           accumulated (length, weight) pairs until every vertex reaches its
@@ -30,172 +30,232 @@
 //           made deterministic by a total order).
 //   materialise: V(v) = q*S(v) - p*len(v), the record {V, rank, q} the next
 //           improvement sweep gathers per edge target.
+//
+// Execution: one cooperative launch (all CTAs co-resident) runs every phase;
+// rounds are separated by a grid barrier whose waits are bounded (on expiry
+// the kernel records kErrTimeout and returns).  Rounds are dense over the
+// vertices (coalesced own-state access, no worklist atomics); a bitmap marks
+// vertices that are finished and whose final state sits in both jump buffers,
+// so they cost nothing in later rounds.  A round writes only the buffer it
+// does not read; a vertex resolved in round k copies its final state into the
+// other buffer in round k+1.
 #include <climits>
 
 #include "common.cuh"
 
 namespace ocm {
 
-static __device__ __forceinline__ int load_count(const int *p) {
+constexpr long long kBarrierSpinLimit = 1LL << 24;   // x 64 ns sleeps: about a second
+
+static __device__ __forceinline__ int load_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-// ---------------------------------------------------------------- detect --
-// State encoding: JM.J >= 0 -> unresolved jump state; JM.J < 0 -> resolved,
-// root = ~J.  A list entry v >= 0 is a vertex to advance, ~v marks a resolved
-// vertex whose state is copied into the other buffer once, so that both
-// buffers hold it for later readers (no buffer is written while being read).
-__global__ void __launch_bounds__(kThreads)
-detect_round_kernel(int r, int n, Workspace ws) {
-    Ctrl *c = ws.ctrl;
-    const bool first = (r == 0);
-    const int in_slot = r % 3, out_slot = (r + 1) % 3, zero_slot = (r + 2) % 3;
-    const int count = first ? n : load_count(&c->cnt[in_slot]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->cnt[zero_slot] = 0;
-        if (count > 0) c->rounds_detect += 1;
-        c->items_detect += count;
+// Grid-wide barrier for a cooperative launch.  Returns false (for the whole
+// block) once any block's wait has exceeded its limit.
+static __device__ bool grid_barrier(Ctrl *c, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &c->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&c->bar_count, 1u) == nblocks - 1) {
+            c->bar_count = 0;
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpinLimit || (load_volatile(&c->err) & kErrTimeout)) {
+                    atomicOr(&c->err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
     }
-    if (count == 0) return;
-    const JM *in = ws.jm[r & 1];
-    JM *out = ws.jm[(r + 1) & 1];
-    const int *lin = ws.list[in_slot];
-    int *lout = ws.list[out_slot];
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Adds the block's sum of x to *dst with one atomic.
+static __device__ __forceinline__ void block_count(int x, int *dst) {
+    __shared__ int s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(dst, s_sum);
+}
+
+constexpr int kRankTile = 2048;
+
+__global__ void __launch_bounds__(kEvalThreads)
+evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws) {
+    __shared__ long long s_key[kRankTile];
+    Ctrl *c = ws.ctrl;
+    const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
-        const int idx = base + threadIdx.x;
-        bool keep = false, resolved = false, is_root = false;
-        int v = 0;
-        if (idx < count) {
-            int item = first ? idx : lin[idx];
-            if (item < 0) {
-                v = ~item;
-                out[v] = in[v];          // copy-forward of a resolved state
+    const int first = blockIdx.x * blockDim.x;
+
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->pending[0] = c->pending[1] = c->pending[2] = 0;
+        c->pendv[0] = c->pendv[1] = c->pendv[2] = 0;
+        c->nrep = 0;
+        c->best = 0;
+    }
+    if (!grid_barrier(c, nblocks)) return;
+
+    // ------------------------------------------------------------ detect
+    int r = 0;
+    for (;; ++r) {
+        const JM *in = ws.jm[r & 1];
+        JM *out = ws.jm[(r + 1) & 1];
+        int pend = 0;
+        for (int base = first; base < n; base += stride) {
+            const int v = base + threadIdx.x;
+            const bool has = v < n;
+            bool done = true, is_root = false;
+            if (r == 0) {
+                // J_0 = succ, M_0(v) = v, A_0(v) = succ(v): nothing to test yet
+                if (has) {
+                    int J = ws.succ[v];
+                    out[v] = JM{ws.succ[J], min(v, J)};
+                    ws.aprev[v] = J;
+                    done = false;
+                    ++pend;
+                }
             } else {
-                v = item;
-                JM s = first ? JM{ws.succ[v], v} : in[v];
-                int J = s.J;
-                JM t = first ? JM{ws.succ[J], J} : in[J];
-                int root = -1;
-                if (t.J < 0) {
-                    root = ~t.J;         // J already resolved: it lies on v's path
-                } else if (!first && t.M == ws.aprev[v]) {
-                    root = t.M;          // smallest vertex of the cycle
+                const bool warp_live = base + (int)(threadIdx.x & ~31u) < n;
+                const unsigned word = warp_live ? ws.done[v >> 5] : ~0u;
+                done = !has || ((word >> lane) & 1u);
+                if (!done) {
+                    JM s = in[v];
+                    if (s.J < 0) {
+                        out[v] = s;          // resolved last round: copy forward
+                        done = true;
+                    } else {
+                        JM t = in[s.J];
+                        int root = -1;
+                        if (t.J < 0) {
+                            root = ~t.J;     // target resolved: it lies on v's path
+                        } else if (t.M == ws.aprev[v]) {
+                            root = t.M;      // smallest vertex of the cycle
+                        } else {
+                            out[v] = JM{t.J, min(s.M, t.M)};
+                            ws.aprev[v] = t.M;
+                        }
+                        if (root >= 0) {
+                            out[v] = JM{~root, 0};
+                            ws.rep[v] = root;
+                            is_root = (root == v);
+                        }
+                        ++pend;
+                    }
+                }
+            }
+            unsigned bits = __ballot_sync(0xffffffffu, done);
+            if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
+            int pos = warp_append(&c->nrep, is_root, lane);
+            if (is_root) ws.cyc_root[pos] = v;
+        }
+        block_count(pend, &c->pending[r % 3]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->pending[(r + 1) % 3] = 0;
+        if (!grid_barrier(c, nblocks)) return;
+        const int left = load_volatile(&c->pending[r % 3]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->rounds_detect += 1;
+            c->items_detect += left;
+        }
+        if (left == 0) break;
+        if (r + 1 >= max_detect) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
+            return;
+        }
+    }
+
+    // ------------------------------------------------------------ values
+    // init: roots are final; a vertex whose successor is a root is final too
+    {
+        int pend = 0;
+        for (int base = first; base < n; base += stride) {
+            const int v = base + threadIdx.x;
+            bool fin = true;
+            if (v < n) {
+                int rv = ws.rep[v];
+                JLS st;
+                if (rv == v) {
+                    st = JLS{~v, 0, 0};
                 } else {
-                    out[v] = JM{t.J, min(s.M, t.M)};
-                    ws.aprev[v] = t.M;
-                    keep = true;
+                    int s = ws.succ[v];
+                    fin = (ws.rep[s] == s);
+                    st = JLS{fin ? ~s : s, 1, (long long)ws.wpi[v]};
                 }
-                if (root >= 0) {
-                    out[v] = JM{~root, 0};
-                    ws.rep[v] = root;
-                    resolved = true;
-                    is_root = (root == v);
+                ws.jls[0][v] = st;
+                if (fin) ws.jls[1][v] = st;
+                pend += !fin;
+            }
+            unsigned bits = __ballot_sync(0xffffffffu, fin);
+            if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
+        }
+        block_count(pend, &c->pendv[0]);
+    }
+    if (!grid_barrier(c, nblocks)) return;
+    if (load_volatile(&c->pendv[0]) != 0) {
+        for (int j = 1;; ++j) {
+            const JLS *in = ws.jls[(j + 1) & 1];
+            JLS *out = ws.jls[j & 1];
+            int pend = 0;
+            for (int base = first; base < n; base += stride) {
+                const int v = base + threadIdx.x;
+                const bool warp_live = base + (int)(threadIdx.x & ~31u) < n;
+                const unsigned word = warp_live ? ws.done[v >> 5] : ~0u;
+                bool done = v >= n || ((word >> lane) & 1u);
+                if (!done) {
+                    JLS s = in[v];
+                    if (s.J < 0) {
+                        out[v] = s;
+                        done = true;
+                    } else {
+                        JLS t = in[s.J];
+                        out[v] = JLS{t.J, s.len + t.len, s.S + t.S};
+                        ++pend;
+                    }
                 }
+                unsigned bits = __ballot_sync(0xffffffffu, done);
+                if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
+            }
+            block_count(pend, &c->pendv[j % 3]);
+            if (blockIdx.x == 0 && threadIdx.x == 0) c->pendv[(j + 1) % 3] = 0;
+            if (!grid_barrier(c, nblocks)) return;
+            const int left = load_volatile(&c->pendv[j % 3]);
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                c->rounds_value += 1;
+                c->items_value += left;
+            }
+            if (left == 0) break;
+            if (j + 1 > max_value) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+                return;
             }
         }
-        int pos = warp_append(&c->cnt[out_slot], keep || resolved, lane);
-        if (keep) lout[pos] = v;
-        if (resolved) lout[pos] = ~v;
-        int rpos = warp_append(&c->nrep, is_root, lane);
-        if (is_root) ws.cyc_root[rpos] = v;
     }
-}
 
-// ---------------------------------------------------------------- values --
-// State encoding: JLS.J >= 0 -> unresolved; JLS.J < 0 -> final, root = ~J,
-// (len, S) = length and weight of the whole path to the root.
-__global__ void __launch_bounds__(kThreads)
-value_init_kernel(int slot_base, int n, Workspace ws) {
-    Ctrl *c = ws.ctrl;
-    const int out_slot = (slot_base + 1) % 3, zero_slot = (slot_base + 2) % 3;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (load_count(&c->cnt[slot_base % 3]) != 0) atomicOr(&c->err, kErrDetect);
-        c->cnt[zero_slot] = 0;
-    }
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int v = base + threadIdx.x;
-        bool keep = false;
-        if (v < n) {
-            int rv = ws.rep[v];
-            JLS st;
-            bool fin;
-            if (rv == v) {
-                st = JLS{~v, 0, 0};
-                fin = true;
-            } else {
-                int s = ws.succ[v];
-                fin = (ws.rep[s] == s);
-                st = JLS{fin ? ~s : s, 1, (long long)ws.wpi[v]};
-            }
-            ws.jls[0][v] = st;
-            if (fin) ws.jls[1][v] = st;
-            keep = !fin;
-        }
-        int pos = warp_append(&c->cnt[out_slot], keep, lane);
-        if (keep) ws.list[out_slot][pos] = v;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads)
-value_round_kernel(int slot, int j, Workspace ws) {
-    Ctrl *c = ws.ctrl;
-    const int in_slot = slot % 3, out_slot = (slot + 1) % 3, zero_slot = (slot + 2) % 3;
-    const int count = load_count(&c->cnt[in_slot]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->cnt[zero_slot] = 0;
-        if (count > 0) c->rounds_value += 1;
-        c->items_value += count;
-    }
-    if (count == 0) return;
-    const JLS *in = ws.jls[(j + 1) & 1];
-    JLS *out = ws.jls[j & 1];
-    const int *lin = ws.list[in_slot];
-    int *lout = ws.list[out_slot];
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
-        const int idx = base + threadIdx.x;
-        bool keep = false, fin = false;
-        int v = 0;
-        if (idx < count) {
-            int item = lin[idx];
-            if (item < 0) {
-                v = ~item;
-                out[v] = in[v];
-            } else {
-                v = item;
-                JLS s = in[v];
-                JLS t = in[s.J];
-                JLS u{t.J, s.len + t.len, s.S + t.S};
-                out[v] = u;
-                fin = u.J < 0;
-                keep = !fin;
-            }
-        }
-        int pos = warp_append(&c->cnt[out_slot], keep || fin, lane);
-        if (keep) lout[pos] = v;
-        if (fin) lout[pos] = ~v;
-    }
-}
-
-// ---------------------------------------------------------------- cycles --
-__global__ void __launch_bounds__(kThreads)
-cycle_stats_kernel(int final_slot, long long N2, Workspace ws) {
-    Ctrl *c = ws.ctrl;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (load_count(&c->cnt[final_slot % 3]) != 0) atomicOr(&c->err, kErrValue);
-    }
-    const int K = load_count(&c->nrep);
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
-        int r = ws.cyc_root[i];
-        int x = ws.succ[r];
+    // ------------------------------------------------------------ cycles
+    const int K = load_volatile(&c->nrep);
+    for (int i = first + threadIdx.x; i < K; i += stride) {
+        int root = ws.cyc_root[i];
+        int x = ws.succ[root];
         JLS st = ws.jls[0][x];
-        long long W = (long long)ws.wpi[r] + st.S;
+        long long W = (long long)ws.wpi[root] + st.S;
         long long L = 1 + (long long)st.len;
         long long g = gcd_ll(W, L);
         long long p = W / g, q = L / g;
@@ -203,28 +263,19 @@ cycle_stats_kernel(int final_slot, long long N2, Workspace ws) {
         ws.cyc_q[i] = (int)q;
         ws.cyc_L[i] = (int)L;
         ws.cyc_key[i] = mean_key(p, q, N2);
-        ws.cid_of_root[r] = i;
+        ws.cid_of_root[root] = i;
     }
-}
-
-constexpr int kRankTile = 2048;
-
-__global__ void __launch_bounds__(kThreads)
-cycle_rank_kernel(Workspace ws) {
-    __shared__ long long s_key[kRankTile];
-    Ctrl *c = ws.ctrl;
-    const int K = load_count(&c->nrep);
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < K; base += stride) {
+    if (!grid_barrier(c, nblocks)) return;
+    for (int base = first; base < K; base += stride) {
         const int i = base + threadIdx.x;
         const long long key = i < K ? ws.cyc_key[i] : 0;
         int rank = 0;
         for (int t0 = 0; t0 < K; t0 += kRankTile) {
             int tn = min(kRankTile, K - t0);
             __syncthreads();
-            for (int j = threadIdx.x; j < tn; j += blockDim.x) s_key[j] = ws.cyc_key[t0 + j];
+            for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
             __syncthreads();
-            for (int j = 0; j < tn; ++j) rank += (s_key[j] < key);
+            for (int q = 0; q < tn; ++q) rank += (s_key[q] < key);
         }
         if (i < K) {
             ws.cyc_rank[i] = rank;
@@ -233,16 +284,14 @@ cycle_rank_kernel(Workspace ws) {
             atomicMax(&c->best, packed);
         }
     }
-}
+    if (!grid_barrier(c, nblocks)) return;
 
-__global__ void __launch_bounds__(kThreads)
-materialise_kernel(int n, Workspace ws) {
+    // ------------------------------------------------------- materialise
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ws.ctrl->changed = 0;
-        ws.ctrl->switched = 0;
+        c->changed = 0;
+        c->switched = 0;
     }
-    const int stride = gridDim.x * blockDim.x;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    for (int v = first + threadIdx.x; v < n; v += stride) {
         JLS st = ws.jls[0][v];
         int i = ws.cid_of_root[~st.J];
         long long p = ws.cyc_p[i];
@@ -261,40 +310,39 @@ static int ceil_log2(long long x) {
     return k;
 }
 
-// Launches one policy evaluation; returns the number of kernel launches.
+// Co-resident CTAs of the evaluation kernel on the current device.
+static int evaluate_grid() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev == cached_dev && cached > 0) return cached;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel, kEvalThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        return 0;
+    cached_dev = dev;
+    cached = sms * per_sm;
+    return cached;
+}
+
+// One policy evaluation = one cooperative launch; returns 1, or -1 on a
+// launch failure.
 int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st) {
-    int launches = 0;
+    (void)grid;
+    int blocks = evaluate_grid();
+    if (blocks <= 0) return -1;
+    int need = (n + kEvalThreads - 1) / kEvalThreads;
+    if (need < blocks) blocks = need;
     const int lg = ceil_log2(n);
-    const int R2 = lg + 4;       // detect rounds incl. one copy-forward round
-    for (int r = 0; r < R2; ++r, ++launches) {
-        prof_begin(kProfDetect, st);
-        detect_round_kernel<<<grid, kThreads, 0, st>>>(r, n, ws);
-        prof_end(kProfDetect, st);
-    }
-    int slot = R2;               // value init appends to slot R2+1
-    prof_begin(kProfValue, st);
-    value_init_kernel<<<grid, kThreads, 0, st>>>(slot, n, ws);
-    prof_end(kProfValue, st);
-    ++launches;
-    const int R5 = lg + 2;       // value rounds incl. one copy-forward round
-    for (int j = 1; j <= R5; ++j, ++launches) {
-        prof_begin(kProfValue, st);
-        value_round_kernel<<<grid, kThreads, 0, st>>>(slot + j, j, ws);
-        prof_end(kProfValue, st);
-    }
-    // Every final state is written in the buffer of its round and copied once
-    // into the other, so after the last round both buffers hold all of them.
-    prof_begin(kProfCycles, st);
-    cycle_stats_kernel<<<grid, kThreads, 0, st>>>(slot + R5 + 1, N2, ws);
-    prof_end(kProfCycles, st);
-    prof_begin(kProfCycles, st);
-    cycle_rank_kernel<<<grid, kThreads, 0, st>>>(ws);
-    prof_end(kProfCycles, st);
-    prof_begin(kProfMaterialise, st);
-    materialise_kernel<<<grid, kThreads, 0, st>>>(n, ws);
-    prof_end(kProfMaterialise, st);
-    launches += 3;
-    return launches;
+    int max_detect = lg + 4;
+    int max_value = lg + 3;
+    void *args[] = {&n, &N2, &max_detect, &max_value, &ws};
+    prof_begin(kProfEvaluate, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)evaluate_kernel, dim3(blocks),
+                                                dim3(kEvalThreads), args, 0, st);
+    prof_end(kProfEvaluate, st);
+    return e == cudaSuccess ? 1 : -1;
 }
 
 // --------------------------------------------------------------- extract --
@@ -326,7 +374,7 @@ extract_candidates_kernel(int n, Workspace ws) {
 __global__ void __launch_bounds__(kThreads)
 extract_round_kernel(int b, Workspace ws) {
     Ctrl *c = ws.ctrl;
-    const int K = load_count(&c->ncand);
+    const int K = load_volatile(&c->ncand);
     const int L = c->res_len;
     const int *Jin = (b == 0) ? ws.succ : reinterpret_cast<const int *>(ws.jm[b & 1]);
     int *Jout = reinterpret_cast<int *>(ws.jm[(b + 1) & 1]);
@@ -343,7 +391,7 @@ extract_round_kernel(int b, Workspace ws) {
 __global__ void __launch_bounds__(kThreads)
 extract_scatter_kernel(Workspace ws, int *cycle_out) {
     Ctrl *c = ws.ctrl;
-    const int K = load_count(&c->ncand);
+    const int K = load_volatile(&c->ncand);
     const int L = c->res_len;
     const int stride = gridDim.x * blockDim.x;
     int found = 0;
