@@ -43,6 +43,8 @@ size_t carve_workspace(void *base, int n, Workspace *ws) {
     w.cyc_rank = static_cast<int *>(take(4 * N));
     w.cid_of_root = static_cast<int *>(take(4 * N));
     w.done = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
+    w.cls_list = static_cast<int *>(take(4 * N));
+    w.cls_hist = static_cast<int *>(take(4 * (size_t)kClasses * ((N + kClassifyBlock - 1) / kClassifyBlock)));
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align_up(off, 256);
@@ -231,9 +233,11 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (h.err) return map_err_bits(h.err);
 
     // 2. initial policy (the paper's first pass from val = 0, lambda = 0),
-    //    which also validates col_idx and w and measures max|w|
+    //    which also validates col_idx and w and measures max|w|; degree
+    //    classes of the improvement sweep
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, st);
     launches += 1;
+    launches += launch_classify(row_ptr, n, ws, st);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -253,7 +257,7 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
         const int le = launch_evaluate(n, N2, ws, grid, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
-        launch_sweep(row_ptr, col_idx, w, sign, n, ws, st);
+        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, st);
         launches += 1;
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
         rc = read_ctrl(ws.ctrl, &h, st);

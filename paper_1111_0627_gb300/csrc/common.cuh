@@ -16,8 +16,13 @@ namespace ocm {
 
 constexpr int kThreads = 256;          // block size of every kernel
 constexpr int kSweepTileV = 256;       // vertices per improvement-sweep tile
-constexpr int kSweepChunkE = 2048;     // edges staged in shared memory per chunk
-constexpr int kEvalThreads = 512;      // block size of the persistent evaluation kernel
+constexpr int kEvalThreads = 1024;     // block size of the persistent evaluation kernel
+// Degree classes of the improvement sweep: class c serves a vertex with a
+// group of 2^c lanes; a vertex of out-degree d belongs to the smallest class
+// with d <= kEdgesPerLane * 2^c (the last class takes everything larger).
+constexpr int kClasses = 6;
+constexpr int kEdgesPerLane = 4;
+constexpr int kClassifyBlock = 1024;   // vertices per classification block
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
 // the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
@@ -62,6 +67,8 @@ struct Ctrl {
     unsigned int bar_gen;     // grid barrier: generation
     int pending[3];           // detect: rotating per-round counts of unfinished vertices
     int pendv[3];             // values: the same
+    int cls_cnt[8];           // improvement sweep: vertices per degree class
+    int cls_off[8];           // start of each class in the class list
     // result of a solve, copied to the host in one transfer
     long long res_num;
     int res_den;
@@ -99,6 +106,8 @@ struct Workspace {
     int *cyc_rank;
     int *cid_of_root;
     unsigned *done;       // bitmap: vertex resolved and its state in both buffers
+    int *cls_list;        // vertices grouped by degree class (stable within a class)
+    int *cls_hist;        // per-block class counts, then their exclusive scan
     Ctrl *ctrl;
 };
 
@@ -147,7 +156,8 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, cudaStream_t st);
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, cudaStream_t st);
+                  Workspace ws, const int *cls_cnt, cudaStream_t st);
+int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st);
 int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
 void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t *potential,

@@ -96,8 +96,9 @@ static __device__ __forceinline__ void block_count(int x, int *dst) {
 }
 
 constexpr int kRankTile = 2048;
+constexpr int kU = 4;   // vertices per thread per pass of a jump round
 
-__global__ void __launch_bounds__(kEvalThreads)
+__global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws) {
     __shared__ long long s_key[kRankTile];
     Ctrl *c = ws.ctrl;
@@ -115,43 +116,58 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws
     if (!grid_barrier(c, nblocks)) return;
 
     // ------------------------------------------------------------ detect
+    // Each thread advances kU vertices per pass (v = base + u*stride + tid) so
+    // that their dependent loads (done word -> own state -> target state)
+    // overlap instead of running one chain at a time.
     int r = 0;
     for (;; ++r) {
         const JM *in = ws.jm[r & 1];
         JM *out = ws.jm[(r + 1) & 1];
         int pend = 0;
-        for (int base = first; base < n; base += stride) {
-            const int v = base + threadIdx.x;
-            const bool has = v < n;
-            bool done = true, is_root = false;
-            if (r == 0) {
-                // J_0 = succ, M_0(v) = v, A_0(v) = succ(v): nothing to test yet
-                if (has) {
-                    int J = ws.succ[v];
-                    out[v] = JM{ws.succ[J], min(v, J)};
-                    ws.aprev[v] = J;
-                    done = false;
-                    ++pend;
+        for (int base = first; base < n; base += kU * stride) {
+            unsigned word[kU];
+            bool act[kU];
+            JM s[kU], t[kU];
+            int ap[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int v = base + u * stride + threadIdx.x;
+                const bool warp_live = v - lane < n;
+                word[u] = (r > 0 && warp_live) ? ws.done[v >> 5] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int v = base + u * stride + threadIdx.x;
+                act[u] = v < n && !((word[u] >> lane) & 1u);
+                if (act[u]) s[u] = (r == 0) ? JM{ws.succ[v], v} : in[v];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int v = base + u * stride + threadIdx.x;
+                if (act[u] && s[u].J >= 0) {
+                    const int J = s[u].J;
+                    t[u] = (r == 0) ? JM{ws.succ[J], J} : in[J];
+                    ap[u] = (r == 0) ? -1 : ws.aprev[v];
                 }
-            } else {
-                const bool warp_live = base + (int)(threadIdx.x & ~31u) < n;
-                const unsigned word = warp_live ? ws.done[v >> 5] : ~0u;
-                done = !has || ((word >> lane) & 1u);
-                if (!done) {
-                    JM s = in[v];
-                    if (s.J < 0) {
-                        out[v] = s;          // resolved last round: copy forward
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int v = base + u * stride + threadIdx.x;
+                bool done = !act[u], is_root = false;
+                if (act[u]) {
+                    if (s[u].J < 0) {
+                        out[v] = s[u];       // resolved last round: copy forward
                         done = true;
                     } else {
-                        JM t = in[s.J];
                         int root = -1;
-                        if (t.J < 0) {
-                            root = ~t.J;     // target resolved: it lies on v's path
-                        } else if (t.M == ws.aprev[v]) {
-                            root = t.M;      // smallest vertex of the cycle
+                        if (t[u].J < 0) {
+                            root = ~t[u].J;  // target resolved: it lies on v's path
+                        } else if (r > 0 && t[u].M == ap[u]) {
+                            root = t[u].M;   // smallest vertex of the cycle
                         } else {
-                            out[v] = JM{t.J, min(s.M, t.M)};
-                            ws.aprev[v] = t.M;
+                            // (round 0: J_0 = succ, M_0(v) = v, no test yet)
+                            out[v] = JM{t[u].J, min(s[u].M, t[u].M)};
+                            ws.aprev[v] = t[u].M;
                         }
                         if (root >= 0) {
                             out[v] = JM{~root, 0};
@@ -161,11 +177,11 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws
                         ++pend;
                     }
                 }
+                const unsigned bits = __ballot_sync(0xffffffffu, done);
+                if (lane == 0 && v < n) ws.done[v >> 5] = bits;
+                const int pos = warp_append(&c->nrep, is_root, lane);
+                if (is_root) ws.cyc_root[pos] = v;
             }
-            unsigned bits = __ballot_sync(0xffffffffu, done);
-            if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
-            int pos = warp_append(&c->nrep, is_root, lane);
-            if (is_root) ws.cyc_root[pos] = v;
         }
         block_count(pend, &c->pending[r % 3]);
         if (blockIdx.x == 0 && threadIdx.x == 0) c->pending[(r + 1) % 3] = 0;
@@ -214,24 +230,40 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws
             const JLS *in = ws.jls[(j + 1) & 1];
             JLS *out = ws.jls[j & 1];
             int pend = 0;
-            for (int base = first; base < n; base += stride) {
-                const int v = base + threadIdx.x;
-                const bool warp_live = base + (int)(threadIdx.x & ~31u) < n;
-                const unsigned word = warp_live ? ws.done[v >> 5] : ~0u;
-                bool done = v >= n || ((word >> lane) & 1u);
-                if (!done) {
-                    JLS s = in[v];
-                    if (s.J < 0) {
-                        out[v] = s;
-                        done = true;
-                    } else {
-                        JLS t = in[s.J];
-                        out[v] = JLS{t.J, s.len + t.len, s.S + t.S};
-                        ++pend;
-                    }
+            for (int base = first; base < n; base += kU * stride) {
+                unsigned word[kU];
+                bool act[kU];
+                JLS s[kU], t[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int v = base + u * stride + threadIdx.x;
+                    word[u] = (v - lane < n) ? ws.done[v >> 5] : ~0u;
                 }
-                unsigned bits = __ballot_sync(0xffffffffu, done);
-                if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int v = base + u * stride + threadIdx.x;
+                    act[u] = v < n && !((word[u] >> lane) & 1u);
+                    if (act[u]) s[u] = in[v];
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (act[u] && s[u].J >= 0) t[u] = in[s[u].J];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int v = base + u * stride + threadIdx.x;
+                    bool done = !act[u];
+                    if (act[u]) {
+                        if (s[u].J < 0) {
+                            out[v] = s[u];
+                            done = true;
+                        } else {
+                            out[v] = JLS{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                            ++pend;
+                        }
+                    }
+                    const unsigned bits = __ballot_sync(0xffffffffu, done);
+                    if (lane == 0 && v < n) ws.done[v >> 5] = bits;
+                }
             }
             block_count(pend, &c->pendv[j % 3]);
             if (blockIdx.x == 0 && threadIdx.x == 0) c->pendv[(j + 1) % 3] = 0;

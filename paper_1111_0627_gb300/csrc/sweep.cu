@@ -11,11 +11,13 @@
 // strict improvement over its current policy edge (Alg. 1: strict ">"), so
 // ties keep the incumbent and the iteration terminates.
 //
-// Layout: one CTA per tile of 256 consecutive vertices.  The tile's edges are
-// streamed in chunks of 2048 with coalesced loads; each edge's target record
-// (16 B: V, rank, q) is gathered and its key written to shared memory; then
-// each thread reduces the segment of its own vertex.  A vertex with more
-// edges than a chunk is reduced across chunks in registers.
+// Layout: vertices are grouped once per solve by degree class; a vertex of
+// class c is served by a group of 2^c lanes that stride over its edges with
+// coalesced loads, gather each target's 16-byte record (V, rank, q), and
+// reduce by warp shuffles -- no shared memory and no block barriers, so the
+// warps of an SM keep many independent loads in flight.  The initial policy
+// (no records yet) is a plain thread-per-vertex pass that also validates the
+// input.
 #include "common.cuh"
 
 namespace ocm {
@@ -55,167 +57,274 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
     prof_end(kProfInit, st);
 }
 
-// Phase 2 of a tile: thread-owned segmented reduction over the staged keys.
-struct Best {
-    int rank;
-    long long key;
-    int e;
-};
-
-template <bool kInit>
+// Initial policy (Alg. 1's first pass from val = 0, lambda = 0): the heaviest
+// out-edge in the s*w sense, ties to the smallest edge index.  The same pass
+// validates col_idx and w and measures max|w| for the exactness bound.
 __global__ void __launch_bounds__(kThreads)
-sweep_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-             const int *__restrict__ w, int sign, int n, Workspace ws) {
-    __shared__ long long s_key[kSweepChunkE];
-    __shared__ int s_rank[kSweepChunkE];
+init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                   const int *__restrict__ w, int sign, int n, Workspace ws) {
     __shared__ int s_maxw[kThreads / 32];
-
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int v0 = blockIdx.x * kSweepTileV;
-    const int v = v0 + tid;
-    const bool has_v = v < n;
-    const int vend = min(v0 + kSweepTileV, n);
-    const int e_begin = __ldg(&row_ptr[v0]);
-    const int e_end = __ldg(&row_ptr[vend]);
-    const int my_b = has_v ? __ldg(&row_ptr[v]) : 0;
-    const int my_e = has_v ? __ldg(&row_ptr[v + 1]) : 0;
-    const int my_pi = (!kInit && has_v) ? ws.pi[v] : -1;
+    const int stride = gridDim.x * blockDim.x;
+    int maxabs = 0;
+    for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
+        const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
+        int best_e = a;
+        long long best_key = LLONG_MIN;
+        for (int e = a; e < b; ++e) {
+            const int t = __ldg(&col[e]);
+            int x = __ldg(&w[e]);
+            if ((unsigned)t >= (unsigned)n) {
+                atomicOr(&ws.ctrl->err, kErrCol);
+                atomicMin(&ws.ctrl->bad_index, e);
+            }
+            if (x == INT_MIN) {
+                atomicOr(&ws.ctrl->err, kErrWeightMin);
+                atomicMin(&ws.ctrl->bad_index, e);
+                x = 0;
+            }
+            maxabs = max(maxabs, x < 0 ? -x : x);
+            const long long k = (long long)sign * x;
+            if (k > best_key) {
+                best_key = k;
+                best_e = e;
+            }
+        }
+        const int t = __ldg(&col[best_e]);
+        const int x = __ldg(&w[best_e]);
+        ws.pi[v] = best_e;
+        ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
+        ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
+    if (lane == 0) s_maxw[tid >> 5] = maxabs;
+    __syncthreads();
+    if (tid < 32) {
+        int x = tid < kThreads / 32 ? s_maxw[tid] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (tid == 0) atomicMax(&ws.ctrl->maxabsw, x);
+    }
+}
 
+// ---------------------------------------------------------------------------
+// Degree classes.  A vertex of out-degree d is served by a group of 2^c lanes,
+// c the smallest class with d <= kEdgesPerLane * 2^c (capped at 32 lanes), so
+// every lane handles a few edges and the lanes of a warp finish together even
+// when degrees are skewed.  The partition is computed once per solve (the
+// graph does not change), stable within each class, in three passes:
+// per-block counts, one exclusive scan, and a scatter.
+static __device__ __forceinline__ int degree_class(int d) {
+    int c = 0;
+    while (c < kClasses - 1 && d > (kEdgesPerLane << c)) ++c;
+    return c;
+}
+
+__global__ void __launch_bounds__(kClassifyBlock)
+classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, Workspace ws) {
+    __shared__ int s_cnt[kClasses];
+    if (threadIdx.x < kClasses) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
+    if (v < n) atomicAdd(&s_cnt[degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]))], 1);
+    __syncthreads();
+    if (threadIdx.x < kClasses) ws.cls_hist[threadIdx.x * nb + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// One block: exclusive scan of the class-major histogram (class c, block b at
+// c * nb + b), so every (class, block) pair gets its first list position.
+__global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace ws) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int total = kClasses * nb;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < total; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int x = i < total ? ws.cls_hist[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((threadIdx.x & 31) >= o) incl += y;
+        }
+        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int wv = s_warp[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, wv, o);
+                if (threadIdx.x >= o) wv += y;
+            }
+            s_warp[threadIdx.x] = wv;
+        }
+        __syncthreads();
+        const int warp_prefix = (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+        const int excl = s_carry + warp_prefix + incl - x;
+        if (i < total) {
+            ws.cls_hist[i] = excl;
+            if (i % nb == 0) ws.ctrl->cls_off[i / nb] = excl;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry += warp_prefix + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x < kClasses) {
+        const int c = threadIdx.x;
+        const int next = (c + 1 < kClasses) ? ws.ctrl->cls_off[c + 1] : s_carry;
+        ws.ctrl->cls_cnt[c] = next - ws.ctrl->cls_off[c];
+    }
+}
+
+__global__ void __launch_bounds__(kClassifyBlock)
+classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, Workspace ws) {
+    __shared__ int s_wcnt[kClassifyBlock / 32][kClasses];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
+    const int c = (v < n) ? degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v])) : -1;
+    int my_rank = 0;
+#pragma unroll
+    for (int k = 0; k < kClasses; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, c == k);
+        if (c == k) my_rank = __popc(m & ((1u << lane) - 1u));
+        if (lane == 0) s_wcnt[warp][k] = __popc(m);
+    }
+    __syncthreads();
+    if (c >= 0) {
+        int before = 0;
+        for (int q = 0; q < warp; ++q) before += s_wcnt[q][c];
+        ws.cls_list[ws.cls_hist[c * nb + blockIdx.x] + before + my_rank] = v;
+    }
+}
+
+int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st) {
+    const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
+    prof_begin(kProfInit, st);
+    classify_count_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, ws);
+    classify_scan_kernel<<<1, 1024, 0, st>>>(nb, ws);
+    classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, ws);
+    prof_end(kProfInit, st);
+    return 3;
+}
+
+// ---------------------------------------------------------------------------
+// Improvement sweep.  Work is cut into warp tasks: a task of class c covers
+// 32 / 2^c consecutive entries of the class list, one lane group per vertex.
+// The lanes of a group stride over the vertex's edges (coalesced), gather the
+// 16-byte record of every target, keep the lexicographic best (rank, key,
+// -edge), and combine by shuffles inside the group.  The group leader compares
+// with the current policy edge, whose key it computes from the record of
+// succ(v), and switches only on strict improvement.  A persistent grid walks
+// the tasks; switches are counted in registers and published with one atomic
+// per block (same-address atomics per warp would serialise the whole sweep).
+struct ClassGrid {
+    int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
+};
+
+struct Cand {
+    int rank;
+    int e;
+    long long key;
+};
+
+static __device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
+    if (a.rank != b.rank) return a.rank > b.rank;
+    if (a.key != b.key) return a.key > b.key;
+    return a.e < b.e;
+}
+
+static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
+                                                 const int *__restrict__ w, const int4 *rec,
+                                                 int sign, int e) {
+    const int t = __ldg(&col[e]);
+    const int x = __ldg(&w[e]);
+    const int4 r = __ldg(&rec[t]);
+    const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
+    return Cand{r.z, e, (long long)r.w * (long long)(sign * x) + V};
+}
+
+__global__ void __launch_bounds__(kThreads)
+improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+               const int *__restrict__ w, int sign, ClassGrid cg, Workspace ws) {
+    __shared__ int s_sw;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    if (tid == 0) s_sw = 0;
     if (blockIdx.x == 0 && tid == 0) {
         // Publish the best cycle of the evaluation this sweep reads (it is
-        // the answer if nothing switches), then reset the counters of the
-        // next evaluation.  No other thread of this kernel touches them.
-        Ctrl *c = ws.ctrl;
-        if (!kInit) {
-            unsigned long long b = c->best;
-            int root = INT_MAX - (int)(unsigned)(b & 0xffffffffu);
-            int i = ws.cid_of_root[root];
-            c->res_root = root;
-            c->res_len = ws.cyc_L[i];
-            c->res_num = ws.cyc_p[i];
-            c->res_den = ws.cyc_q[i];
-            c->res_cycles = c->nrep;
-        }
-        c->cnt[0] = c->cnt[1] = c->cnt[2] = 0;
-        c->nrep = 0;
-        c->best = 0;
+        // the answer if nothing switches).  No other thread touches these.
+        Ctrl *cc = ws.ctrl;
+        unsigned long long bb = cc->best;
+        int root = INT_MAX - (int)(unsigned)(bb & 0xffffffffu);
+        int i = ws.cid_of_root[root];
+        cc->res_root = root;
+        cc->res_len = ws.cyc_L[i];
+        cc->res_num = ws.cyc_p[i];
+        cc->res_den = ws.cyc_q[i];
+        cc->res_cycles = cc->nrep;
     }
-    Best best{INT_MIN, LLONG_MIN, -1};
-    int cur_rank = INT_MIN;
-    long long cur_key = LLONG_MIN;
-    int maxabs = 0;
-
-    for (int cs = e_begin; cs < e_end; cs += kSweepChunkE) {
-        const int ce = min(cs + kSweepChunkE, e_end);
-        // phase 1: stream the chunk's edges, gather target records
-        constexpr int U = kSweepChunkE / kThreads;
-        int tgt[U], wt[U];
+    __syncthreads();
+    const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int total = cg.task_off[kClasses];
+    int switched = 0;
+    for (int task = (blockIdx.x * blockDim.x + tid) >> 5; task < total; task += warps) {
+        int c = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            int e = cs + u * kThreads + tid;
-            tgt[u] = 0;
-            wt[u] = 0;
-            if (e < ce) {
-                tgt[u] = __ldg(&col[e]);
-                wt[u] = __ldg(&w[e]);
+        for (int k = 1; k < kClasses; ++k)
+            if (task >= cg.task_off[k]) c = k;
+        const int g = 1 << c;
+        const int sub = lane & (g - 1);
+        const int idx = (task - cg.task_off[c]) * (32 >> c) + (lane >> c);
+        const bool valid = idx < ws.ctrl->cls_cnt[c];
+        const int v = valid ? ws.cls_list[ws.ctrl->cls_off[c] + idx] : 0;
+        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        if (valid) {
+            const int a = __ldg(&row_ptr[v]), e_end = __ldg(&row_ptr[v + 1]);
+            int e = a + sub;
+            for (; e + g < e_end; e += 2 * g) {   // two independent gathers in flight
+                Cand x0 = edge_cand(col, w, rec, sign, e);
+                Cand x1 = edge_cand(col, w, rec, sign, e + g);
+                if (better(x0, best)) best = x0;
+                if (better(x1, best)) best = x1;
+            }
+            if (e < e_end) {
+                Cand x0 = edge_cand(col, w, rec, sign, e);
+                if (better(x0, best)) best = x0;
             }
         }
-        if (kInit) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int e = cs + u * kThreads + tid;
-                if (e < ce) {
-                    int t = tgt[u];
-                    int x = wt[u];
-                    if ((unsigned)t >= (unsigned)n) {
-                        atomicOr(&ws.ctrl->err, kErrCol);
-                        atomicMin(&ws.ctrl->bad_index, e);
-                    }
-                    if (x == INT_MIN) {
-                        atomicOr(&ws.ctrl->err, kErrWeightMin);
-                        atomicMin(&ws.ctrl->bad_index, e);
-                        x = 0;
-                    }
-                    int ax = x < 0 ? -x : x;
-                    maxabs = max(maxabs, ax);
-                    s_key[e - cs] = (long long)(sign * x);
-                    s_rank[e - cs] = 0;
-                }
-            }
-        } else {
-            Rec r[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int e = cs + u * kThreads + tid;
-                if (e < ce) {
-                    int4 raw = __ldg(reinterpret_cast<const int4 *>(ws.rec) + tgt[u]);
-                    r[u].V = ((long long)(unsigned)raw.x) | ((long long)raw.y << 32);
-                    r[u].rank = raw.z;
-                    r[u].q = raw.w;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int e = cs + u * kThreads + tid;
-                if (e < ce) {
-                    s_key[e - cs] = (long long)r[u].q * (long long)(sign * wt[u]) + r[u].V;
-                    s_rank[e - cs] = r[u].rank;
-                }
+        for (int o = 16; o >= 1; o >>= 1) {
+            if (o < g) {
+                Cand other;
+                other.rank = __shfl_xor_sync(0xffffffffu, best.rank, o);
+                other.e = __shfl_xor_sync(0xffffffffu, best.e, o);
+                other.key = __shfl_xor_sync(0xffffffffu, best.key, o);
+                if (better(other, best)) best = other;
             }
         }
-        __syncthreads();
-        // phase 2: each thread reduces its own vertex's edges in this chunk
-        if (has_v) {
-            int a = max(my_b, cs), b = min(my_e, ce);
-            for (int e = a; e < b; ++e) {
-                int rk = s_rank[e - cs];
-                long long k = s_key[e - cs];
-                if (rk > best.rank || (rk == best.rank && k > best.key)) {
-                    best.rank = rk;
-                    best.key = k;
-                    best.e = e;
-                }
-                if (e == my_pi) {
-                    cur_rank = rk;
-                    cur_key = k;
-                }
+        if (valid && sub == 0) {
+            const int t = ws.succ[v];
+            const int4 r = __ldg(&rec[t]);
+            const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
+            const long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
+            if (best.rank > r.z || (best.rank == r.z && best.key > cur_key)) {
+                ws.pi[v] = best.e;
+                ws.succ[v] = __ldg(&col[best.e]);
+                ws.wpi[v] = sign * __ldg(&w[best.e]);
+                ++switched;
             }
         }
-        __syncthreads();
     }
-
-    if (kInit) {
-        // block max of |w|
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
-        if (lane == 0) s_maxw[tid >> 5] = maxabs;
-        __syncthreads();
-        if (tid < 32) {
-            int x = tid < kThreads / 32 ? s_maxw[tid] : 0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
-            if (tid == 0) atomicMax(&ws.ctrl->maxabsw, x);
-        }
-        if (has_v && best.e >= 0) {
-            int t = __ldg(&col[best.e]);
-            ws.pi[v] = best.e;
-            ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
-            int x = __ldg(&w[best.e]);
-            ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
-        }
-        return;
-    }
-
-    bool sw = has_v && (best.rank > cur_rank || (best.rank == cur_rank && best.key > cur_key));
-    if (sw) {
-        ws.pi[v] = best.e;
-        ws.succ[v] = __ldg(&col[best.e]);
-        ws.wpi[v] = sign * __ldg(&w[best.e]);
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, sw);
-    if (mask && lane == 0) {
-        atomicAdd(&ws.ctrl->switched, __popc(mask));
+    for (int o = 16; o > 0; o >>= 1) switched += __shfl_xor_sync(0xffffffffu, switched, o);
+    if (lane == 0 && switched) atomicAdd(&s_sw, switched);
+    __syncthreads();
+    if (tid == 0 && s_sw) {
+        atomicAdd(&ws.ctrl->switched, s_sw);
         ws.ctrl->changed = 1;
     }
 }
@@ -223,17 +332,39 @@ sweep_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, cudaStream_t st) {
     (void)m;
-    int tiles = (n + kSweepTileV - 1) / kSweepTileV;
+    int blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 2048) blocks = 2048;
     prof_begin(kProfInit, st);
-    sweep_kernel<true><<<tiles, kThreads, 0, st>>>(row_ptr, col, w, sign, n, ws);
+    init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n, ws);
     prof_end(kProfInit, st);
 }
 
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, cudaStream_t st) {
-    int tiles = (n + kSweepTileV - 1) / kSweepTileV;
+                  Workspace ws, const int *cls_cnt, cudaStream_t st) {
+    (void)n;
+    ClassGrid cg;
+    int tasks = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        cg.task_off[c] = tasks;
+        const long long lanes = (long long)cls_cnt[c] << c;
+        tasks += (int)((lanes + 31) / 32);
+    }
+    cg.task_off[kClasses] = tasks;
+    if (tasks == 0) return;
+    static int grid_dev = -1, grid_blocks = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != grid_dev) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, kThreads, 0);
+        grid_blocks = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
+        grid_dev = dev;
+    }
+    int blocks = (tasks + (kThreads / 32) - 1) / (kThreads / 32);
+    if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    sweep_kernel<false><<<tiles, kThreads, 0, st>>>(row_ptr, col, w, sign, n, ws);
+    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, ws);
     prof_end(kProfSweep, st);
 }
 

@@ -167,6 +167,21 @@ def test_extreme_weights_within_bound():
     assert_certificate(g, sol)
 
 
+def test_unaligned_input_slices():
+    """col_idx / w / row_ptr starting at odd int32 offsets (tensor slices)."""
+    g = synth.ring10k()
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    d = torch.device("cuda")
+    for off in (1, 2, 3):
+        def sl(a):
+            buf = torch.zeros(a.shape[0] + off, dtype=torch.int32, device=d)
+            buf[off:] = torch.from_numpy(a).to(d)
+            return buf[off:]
+        sol = ocm.solve(sl(g.row_ptr), sl(g.col_idx), sl(g.w), g.mode)
+        assert (sol.num, sol.den) == (h.num, h.den)
+        assert sol.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle]
+
+
 def test_determinism_bitwise():
     g = synth.ring10k()
     a = gpu_solve(g, certificate=True)
