@@ -43,6 +43,7 @@ size_t carve_workspace(void *base, int n, Workspace *ws) {
     w.cyc_rank = static_cast<int *>(take(4 * N));
     w.cid_of_root = static_cast<int *>(take(4 * N));
     w.done = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
+    w.sw_iter = static_cast<int *>(take(4 * N));
     w.cls_list = static_cast<int *>(take(4 * N));
     w.cls_hist = static_cast<int *>(take(4 * (size_t)kClasses * ((N + kClassifyBlock - 1) / kClassifyBlock)));
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
@@ -254,10 +255,10 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable
     long long it = 0, switched = 0;
     for (;;) {
-        const int le = launch_evaluate(n, N2, ws, grid, st);
+        const int le = launch_evaluate(n, N2, ws, (int)it, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
-        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, st);
+        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, st);
         launches += 1;
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
         rc = read_ctrl(ws.ctrl, &h, st);

@@ -65,6 +65,8 @@ struct Ctrl {
     unsigned long long best;  // packed (rank, INT_MAX - root) of the best cycle
     unsigned int bar_count;   // grid barrier: blocks arrived
     unsigned int bar_gen;     // grid barrier: generation
+    unsigned long long bar_word;  // counting barrier: arrivals << 32 | summed counts
+    int bar_total;            // counting barrier: the sum published by the last arrival
     int pending[3];           // detect: rotating per-round counts of unfinished vertices
     int pendv[3];             // values: the same
     int cls_cnt[8];           // improvement sweep: vertices per degree class
@@ -106,6 +108,7 @@ struct Workspace {
     int *cyc_rank;
     int *cid_of_root;
     unsigned *done;       // bitmap: vertex resolved and its state in both buffers
+    int *sw_iter;         // evaluation index after the sweep that last switched v
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan
     Ctrl *ctrl;
@@ -156,9 +159,9 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, cudaStream_t st);
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, cudaStream_t st);
+                  Workspace ws, const int *cls_cnt, int next_eval, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
-int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st);
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, cudaStream_t st);
 int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
 void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t *potential,
                     int32_t *policy, cudaStream_t st);

@@ -45,148 +45,197 @@
 
 namespace ocm {
 
-constexpr long long kBarrierSpinLimit = 1LL << 24;   // x 64 ns sleeps: about a second
+constexpr long long kBarrierClockLimit = 4000000000LL;   // SM cycles: about two seconds
 
 static __device__ __forceinline__ int load_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-// Grid-wide barrier for a cooperative launch.  Returns false (for the whole
-// block) once any block's wait has exceeded its limit.
-static __device__ bool grid_barrier(Ctrl *c, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = &c->bar_gen;
-        const unsigned g = *gen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(&c->bar_count, 1u) == nblocks - 1) {
-            c->bar_count = 0;
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > kBarrierSpinLimit || (load_volatile(&c->err) & kErrTimeout)) {
-                    atomicOr(&c->err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Adds the block's sum of x to *dst with one atomic.
-static __device__ __forceinline__ void block_count(int x, int *dst) {
+// Grid-wide barrier of a cooperative launch that also sums one count per
+// thread over the whole grid: the block total rides on the arrival atomic
+// (arrivals in the high 32 bits, counts in the low 32), and the last block
+// to arrive publishes the grand total before releasing the others.  Waits
+// are bounded by an SM-clock limit; on expiry every block records
+// kErrTimeout and *ok becomes false.
+static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok) {
     __shared__ int s_sum;
+    __shared__ int s_total;
+    __shared__ int s_ok;
     if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum, x);
     __syncthreads();
-    if (threadIdx.x == 0 && s_sum) atomicAdd(dst, s_sum);
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &c->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned long long old =
+            atomicAdd(&c->bar_word, (1ULL << 32) | (unsigned long long)(unsigned)s_sum);
+        int okv = 1;
+        if ((unsigned)(old >> 32) == nblocks - 1) {
+            c->bar_total = (int)(unsigned)(old & 0xffffffffULL) + s_sum;
+            c->bar_word = 0;
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kBarrierClockLimit ||
+                    (load_volatile(&c->err) & kErrTimeout)) {
+                    atomicOr(&c->err, kErrTimeout);
+                    okv = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_total = load_volatile(&c->bar_total);
+        s_ok = okv;
+    }
+    __syncthreads();
+    *ok = s_ok != 0;
+    return s_total;
+}
+
+static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks) {
+    bool ok;
+    grid_sum_barrier(c, nblocks, 0, &ok);
+    return ok;
 }
 
 constexpr int kRankTile = 2048;
 constexpr int kU = 4;   // vertices per thread per pass of a jump round
 
+// Appends item to a block-local list (warp-aggregated shared-memory atomic).
+static __device__ __forceinline__ void block_append(int *list, int *s_cnt, bool pred, int item,
+                                                    int lane) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    int base = 0;
+    if (mask) {
+        const int leader = __ffs(mask) - 1;
+        if (lane == leader) base = atomicAdd(s_cnt, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
+constexpr int kMinMask = 0x7fffffff;
+
 __global__ void __launch_bounds__(kEvalThreads, 1)
-evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws) {
+evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_index,
+                Workspace ws) {
     __shared__ long long s_key[kRankTile];
+    __shared__ int s_cnt;
     Ctrl *c = ws.ctrl;
     const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     const int first = blockIdx.x * blockDim.x;
+    // every block owns a contiguous vertex range and keeps its worklist of
+    // unfinished vertices inside the same range of the two list buffers
+    const int R = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = min((int)blockIdx.x * R, n), hi = min(lo + R, n);
+    int *LA = ws.list[0] + lo, *LB = ws.list[1] + lo;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->pending[0] = c->pending[1] = c->pending[2] = 0;
-        c->pendv[0] = c->pendv[1] = c->pendv[2] = 0;
         c->nrep = 0;
         c->best = 0;
     }
+    if (threadIdx.x == 0) s_cnt = 0;
     if (!grid_barrier(c, nblocks)) return;
 
     // ------------------------------------------------------------ detect
-    // Each thread advances kU vertices per pass (v = base + u*stride + tid) so
-    // that their dependent loads (done word -> own state -> target state)
-    // overlap instead of running one chain at a time.
+    // State: unresolved {J >= 0, M | dirty << 31}; resolved {~root, dirty}.
+    // "dirty" ORs, over the same windows as M, whether a vertex switched in
+    // the sweep before this evaluation; at resolution it covers v's whole
+    // path and cycle, so a clean vertex keeps last evaluation's path sums.
+    int cnt = hi - lo;
     int r = 0;
     for (;; ++r) {
         const JM *in = ws.jm[r & 1];
         JM *out = ws.jm[(r + 1) & 1];
+        int *lin = (r & 1) ? LB : LA;
+        int *lout = (r & 1) ? LA : LB;
         int pend = 0;
-        for (int base = first; base < n; base += kU * stride) {
-            unsigned word[kU];
-            bool act[kU];
+        for (int i0 = 0; i0 < cnt; i0 += kU * blockDim.x) {
+            int item[kU];
             JM s[kU], t[kU];
             int ap[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int v = base + u * stride + threadIdx.x;
-                const bool warp_live = v - lane < n;
-                word[u] = (r > 0 && warp_live) ? ws.done[v >> 5] : 0u;
+                const int i = i0 + u * blockDim.x + threadIdx.x;
+                item[u] = INT_MIN;
+                if (i < cnt) item[u] = (r == 0) ? lo + i : lin[i];
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int v = base + u * stride + threadIdx.x;
-                act[u] = v < n && !((word[u] >> lane) & 1u);
-                if (act[u]) s[u] = (r == 0) ? JM{ws.succ[v], v} : in[v];
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int v = base + u * stride + threadIdx.x;
-                if (act[u] && s[u].J >= 0) {
-                    const int J = s[u].J;
-                    t[u] = (r == 0) ? JM{ws.succ[J], J} : in[J];
-                    ap[u] = (r == 0) ? -1 : ws.aprev[v];
+                const int it = item[u];
+                if (it == INT_MIN) continue;
+                const int v = it < 0 ? ~it : it;
+                if (r == 0) {
+                    s[u] = JM{ws.succ[v], v | ((ws.sw_iter[v] == eval_index) ? INT_MIN : 0)};
+                    ap[u] = -1;
+                } else {
+                    s[u] = in[v];
+                    ap[u] = it >= 0 ? ws.aprev[v] : 0;
                 }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int v = base + u * stride + threadIdx.x;
-                bool done = !act[u], is_root = false;
-                if (act[u]) {
-                    if (s[u].J < 0) {
-                        out[v] = s[u];       // resolved last round: copy forward
-                        done = true;
+                const int it = item[u];
+                if (it == INT_MIN || it < 0) continue;
+                const int J = s[u].J;
+                t[u] = (r == 0) ? JM{ws.succ[J], J | ((ws.sw_iter[J] == eval_index) ? INT_MIN : 0)}
+                                : in[J];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int it = item[u];
+                bool keep = false, resolved = false, is_root = false;
+                int v = 0;
+                if (it != INT_MIN) {
+                    v = it < 0 ? ~it : it;
+                    if (it < 0) {
+                        out[v] = s[u];        // resolved last round: copy forward
                     } else {
-                        int root = -1;
+                        const int sdirty = (int)((unsigned)s[u].M >> 31);
+                        int root = -1, dirty = 0;
                         if (t[u].J < 0) {
-                            root = ~t[u].J;  // target resolved: it lies on v's path
-                        } else if (r > 0 && t[u].M == ap[u]) {
-                            root = t[u].M;   // smallest vertex of the cycle
+                            root = ~t[u].J;   // target resolved: it lies on v's path
+                            dirty = sdirty | t[u].M;
+                        } else if (r > 0 && (t[u].M & kMinMask) == ap[u]) {
+                            root = ap[u];     // smallest vertex of the cycle
+                            dirty = sdirty | (int)((unsigned)t[u].M >> 31);
                         } else {
                             // (round 0: J_0 = succ, M_0(v) = v, no test yet)
-                            out[v] = JM{t[u].J, min(s[u].M, t[u].M)};
-                            ws.aprev[v] = t[u].M;
+                            const int m = min(s[u].M & kMinMask, t[u].M & kMinMask);
+                            out[v] = JM{t[u].J, m | ((s[u].M | t[u].M) & INT_MIN)};
+                            ws.aprev[v] = t[u].M & kMinMask;
+                            keep = true;
                         }
                         if (root >= 0) {
-                            out[v] = JM{~root, 0};
+                            out[v] = JM{~root, dirty};
                             ws.rep[v] = root;
+                            resolved = true;
                             is_root = (root == v);
                         }
                         ++pend;
                     }
                 }
-                const unsigned bits = __ballot_sync(0xffffffffu, done);
-                if (lane == 0 && v < n) ws.done[v >> 5] = bits;
+                block_append(lout, &s_cnt, keep || resolved, keep ? v : ~v, lane);
                 const int pos = warp_append(&c->nrep, is_root, lane);
                 if (is_root) ws.cyc_root[pos] = v;
             }
         }
-        block_count(pend, &c->pending[r % 3]);
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->pending[(r + 1) % 3] = 0;
-        if (!grid_barrier(c, nblocks)) return;
-        const int left = load_volatile(&c->pending[r % 3]);
+        __syncthreads();
+        cnt = s_cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt = 0;
+        bool ok;
+        const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+        if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds_detect += 1;
             c->items_detect += left;
@@ -199,76 +248,97 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, Workspace ws
     }
 
     // ------------------------------------------------------------ values
-    // init: roots are final; a vertex whose successor is a root is final too
+    // Only dirty vertices are recomputed: a clean vertex's path and cycle are
+    // those of the last evaluation, whose final (root, len, S) is still in
+    // both buffers.  Dirty roots are final at once, as is a dirty vertex whose
+    // successor is a root; the rest jump until they meet a final state.
+    cnt = 0;
+    int left0 = 0;
     {
         int pend = 0;
-        for (int base = first; base < n; base += stride) {
-            const int v = base + threadIdx.x;
-            bool fin = true;
-            if (v < n) {
-                int rv = ws.rep[v];
-                JLS st;
-                if (rv == v) {
-                    st = JLS{~v, 0, 0};
-                } else {
-                    int s = ws.succ[v];
-                    fin = (ws.rep[s] == s);
-                    st = JLS{fin ? ~s : s, 1, (long long)ws.wpi[v]};
+        for (int i0 = 0; i0 < hi - lo; i0 += blockDim.x) {
+            const int i = i0 + threadIdx.x;
+            bool keep = false;
+            int v = lo + i;
+            if (i < hi - lo) {
+                const JM d = ws.jm[0][v];
+                if (d.M) {
+                    const int root = ~d.J;
+                    JLS st;
+                    bool fin = true;
+                    if (root == v) {
+                        st = JLS{~v, 0, 0};
+                    } else {
+                        const int sv = ws.succ[v];
+                        fin = (ws.rep[sv] == sv);
+                        st = JLS{fin ? ~sv : sv, 1, (long long)ws.wpi[v]};
+                    }
+                    ws.jls[0][v] = st;
+                    if (fin) ws.jls[1][v] = st;
+                    keep = !fin;
                 }
-                ws.jls[0][v] = st;
-                if (fin) ws.jls[1][v] = st;
-                pend += !fin;
             }
-            unsigned bits = __ballot_sync(0xffffffffu, fin);
-            if (lane == 0 && base + (int)(threadIdx.x & ~31u) < n) ws.done[v >> 5] = bits;
+            block_append(LA, &s_cnt, keep, v, lane);
+            pend += keep;
         }
-        block_count(pend, &c->pendv[0]);
+        __syncthreads();
+        cnt = s_cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt = 0;
+        bool ok;
+        left0 = grid_sum_barrier(c, nblocks, pend, &ok);
+        if (!ok) return;
     }
-    if (!grid_barrier(c, nblocks)) return;
-    if (load_volatile(&c->pendv[0]) != 0) {
+    if (left0 != 0) {
         for (int j = 1;; ++j) {
             const JLS *in = ws.jls[(j + 1) & 1];
             JLS *out = ws.jls[j & 1];
+            int *lin = (j & 1) ? LA : LB;
+            int *lout = (j & 1) ? LB : LA;
             int pend = 0;
-            for (int base = first; base < n; base += kU * stride) {
-                unsigned word[kU];
-                bool act[kU];
+            for (int i0 = 0; i0 < cnt; i0 += kU * blockDim.x) {
+                int item[kU];
                 JLS s[kU], t[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
-                    const int v = base + u * stride + threadIdx.x;
-                    word[u] = (v - lane < n) ? ws.done[v >> 5] : ~0u;
+                    const int i = i0 + u * blockDim.x + threadIdx.x;
+                    item[u] = i < cnt ? lin[i] : INT_MIN;
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
-                    const int v = base + u * stride + threadIdx.x;
-                    act[u] = v < n && !((word[u] >> lane) & 1u);
-                    if (act[u]) s[u] = in[v];
+                    const int it = item[u];
+                    if (it != INT_MIN) s[u] = in[it < 0 ? ~it : it];
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (act[u] && s[u].J >= 0) t[u] = in[s[u].J];
+                    if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
-                    const int v = base + u * stride + threadIdx.x;
-                    bool done = !act[u];
-                    if (act[u]) {
-                        if (s[u].J < 0) {
-                            out[v] = s[u];
-                            done = true;
+                    const int it = item[u];
+                    bool keep = false, fin = false;
+                    int v = 0;
+                    if (it != INT_MIN) {
+                        v = it < 0 ? ~it : it;
+                        if (it < 0) {
+                            out[v] = s[u];    // final last round: copy forward
                         } else {
-                            out[v] = JLS{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                            const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                            out[v] = nu;
+                            fin = nu.J < 0;
+                            keep = !fin;
                             ++pend;
                         }
                     }
-                    const unsigned bits = __ballot_sync(0xffffffffu, done);
-                    if (lane == 0 && v < n) ws.done[v >> 5] = bits;
+                    block_append(lout, &s_cnt, keep || fin, keep ? v : ~v, lane);
                 }
             }
-            block_count(pend, &c->pendv[j % 3]);
-            if (blockIdx.x == 0 && threadIdx.x == 0) c->pendv[(j + 1) % 3] = 0;
-            if (!grid_barrier(c, nblocks)) return;
-            const int left = load_volatile(&c->pendv[j % 3]);
+            __syncthreads();
+            cnt = s_cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) s_cnt = 0;
+            bool ok;
+            const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+            if (!ok) return;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 c->rounds_value += 1;
                 c->items_value += left;
@@ -360,8 +430,7 @@ static int evaluate_grid() {
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
-int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st) {
-    (void)grid;
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, cudaStream_t st) {
     int blocks = evaluate_grid();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
@@ -369,7 +438,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int grid, cudaStream_t st
     const int lg = ceil_log2(n);
     int max_detect = lg + 4;
     int max_value = lg + 3;
-    void *args[] = {&n, &N2, &max_detect, &max_value, &ws};
+    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &ws};
     prof_begin(kProfEvaluate, st);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)evaluate_kernel, dim3(blocks),
                                                 dim3(kEvalThreads), args, 0, st);

@@ -96,6 +96,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         ws.pi[v] = best_e;
         ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
         ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
+        ws.sw_iter[v] = 0;   // the first evaluation treats every vertex as changed
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
@@ -248,7 +249,7 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 
 __global__ void __launch_bounds__(kThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, ClassGrid cg, Workspace ws) {
+               const int *__restrict__ w, int sign, ClassGrid cg, int next_eval, Workspace ws) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -315,6 +316,7 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 ws.pi[v] = best.e;
                 ws.succ[v] = __ldg(&col[best.e]);
                 ws.wpi[v] = sign * __ldg(&w[best.e]);
+                ws.sw_iter[v] = next_eval;
                 ++switched;
             }
         }
@@ -340,7 +342,7 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
 }
 
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, cudaStream_t st) {
+                  Workspace ws, const int *cls_cnt, int next_eval, cudaStream_t st) {
     (void)n;
     ClassGrid cg;
     int tasks = 0;
@@ -364,7 +366,7 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
     int blocks = (tasks + (kThreads / 32) - 1) / (kThreads / 32);
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, ws);
+    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, next_eval, ws);
     prof_end(kProfSweep, st);
 }
 
