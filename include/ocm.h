@@ -121,6 +121,32 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
               const ocm_options *opt, ocm_stats *stats);
 
 /*
+ * ocm_solve_batch -- optimal cycle means of G independent graphs in one call
+ * (the paper runs its regions concurrently, Sec. 3.3; here the regions are
+ * separate graphs).  The graphs form one disjoint-union CSR:
+ *   graph_vptr[G+1] : device; graph g owns vertices [graph_vptr[g], graph_vptr[g+1]),
+ *                     graph_vptr[0] = 0, graph_vptr[G] = N, every graph non-empty
+ *   row_ptr[N+1], col_idx[M], w[M] : device CSR with global vertex ids; every
+ *                     edge must stay inside its own graph (OCM_ERR_BAD_CSR otherwise)
+ *   num[G], den[G], cycle_len[G] : device outputs, one reduced mean and cycle
+ *                     length per graph (in the given sense)
+ *   cycle_out[N]    : device; graph g's critical cycle (CSR edge indices,
+ *                     starting with the policy edge of its smallest vertex) is
+ *                     written at offset graph_vptr[g] (a simple cycle of g has
+ *                     at most n_g edges)
+ *   workspace       : at least ocm_workspace_size_batch(G, N, M) bytes
+ * Every graph's result is bit-identical to solving it alone with ocm_solve.
+ * Exactness bound: 2 * n_max^2 * max|w| < 2^62 with n_max the largest graph.
+ * Synchronises the stream before returning; on error the device outputs may
+ * be partly written.
+ */
+size_t ocm_workspace_size_batch(int32_t G, int32_t N, int32_t M);
+int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int32_t *col_idx,
+                    const int32_t *w, int32_t G, int32_t N, int32_t M, int mode, int64_t *num,
+                    int32_t *den, int32_t *cycle_len, int32_t *cycle_out, void *workspace,
+                    size_t ws_bytes, void *stream, const ocm_options *opt, ocm_stats *stats);
+
+/*
  * ocm_backward -- gradient of lambda* with respect to the edge weights.
  * While the critical cycle C* stays optimal, lambda* = w(C*)/|C*| is linear in
  * the weights of C*, so the derivative of lambda* by w(e) = 1/|C*| for e in C* and 0 otherwise

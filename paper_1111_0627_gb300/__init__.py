@@ -4,8 +4,9 @@ The compute path is the hand-written sm_103a CUDA library ``libocm.so``
 (C ABI in ``include/ocm.h``); this package builds it in-tree and binds it.
 """
 from ._native import build, load
-from .ocm import (OCM_MAX, OCM_MIN, OCMError, OCMFunction, Solution, backward, make_workspace,
-                  solve, workspace_bytes)
+from .ocm import (OCM_MAX, OCM_MIN, BatchSolution, OCMError, OCMFunction, Solution, backward,
+                  make_workspace, solve, solve_batch, workspace_bytes, workspace_bytes_batch)
 
-__all__ = ["build", "load", "solve", "backward", "OCMFunction", "OCMError", "Solution",
-           "make_workspace", "workspace_bytes", "OCM_MAX", "OCM_MIN"]
+__all__ = ["build", "load", "solve", "solve_batch", "backward", "OCMFunction", "OCMError",
+           "Solution", "BatchSolution", "make_workspace", "workspace_bytes", "workspace_bytes_batch",
+           "OCM_MAX", "OCM_MIN"]

@@ -205,17 +205,24 @@ int ocm_profile_collect(double *ms_out, int64_t *launches_out) {
     return kProfCount;
 }
 
-int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
-              int32_t m, int mode, int64_t *num, int32_t *den, int32_t *cycle_out,
-              int32_t *cycle_len, void *workspace, size_t ws_bytes, void *stream,
-              const ocm_options *opt, ocm_stats *stats) {
-    if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
-    if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
-    if (!workspace) return OCM_ERR_WORKSPACE;
-    const size_t need = ocm_workspace_size(n, m);
-    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return OCM_ERR_WORKSPACE;
+}  // extern "C"
 
+namespace ocm {
+
+// Outputs of one solve: a single graph (host scalars) or a batch (device arrays).
+struct SolveOut {
+    int64_t *num;
+    int32_t *den;
+    int32_t *cycle_len;
+    int32_t *cycle_out;
+};
+
+// The whole solve; bs == nullptr for a single graph.
+static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
+                      int32_t m, int mode, SolveOut out, void *workspace, size_t ws_bytes,
+                      size_t need, void *stream, const ocm_options *opt, ocm_stats *stats,
+                      BatchState *bs) {
+    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return OCM_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Workspace ws;
     carve_workspace(workspace, n, &ws);
@@ -223,11 +230,14 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     const int grid = persistent_grid();
     long long launches = 0;
     Ctrl h;
+    BatchState none{};
+    BatchState b = bs ? *bs : none;
 
-    // 1. row_ptr must be sane before any kernel trusts it
+    // 1. row_ptr (and the graph offsets) must be sane before any kernel trusts them
     ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl);
     launch_check_row_ptr(row_ptr, n, m, ws.ctrl, st);
     launches += 2;
+    if (bs) launches += launch_batch_prepare(n, m, b, ws, st);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     int rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -236,26 +246,29 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     // 2. initial policy (the paper's first pass from val = 0, lambda = 0),
     //    which also validates col_idx and w and measures max|w|; degree
     //    classes of the improvement sweep
-    launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, st);
+    launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, bs ? &b : nullptr, st);
     launches += 1;
     launches += launch_classify(row_ptr, n, ws, st);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
     if (h.err) return map_err_bits(h.err);
+    // Cycles never span graphs, so the largest cycle length (and denominator)
+    // is bounded by the largest graph.  Exactness bound: 2 n_max^2 max|w| <
+    // 2^62 keeps every value, key and cross product inside int64.
+    const long long nmax = bs ? h.max_ng : n;
     {
-        // exactness bound: 2 n^2 max|w| < 2^62 keeps every value, key and
-        // cross product of the iteration inside int64
-        unsigned __int128 bound = (unsigned __int128)2 * (unsigned)n * (unsigned)n * (unsigned)h.maxabsw;
+        unsigned __int128 bound = (unsigned __int128)2 * (unsigned long long)nmax *
+                                  (unsigned long long)nmax * (unsigned)h.maxabsw;
         if (bound >= ((unsigned __int128)1 << 62)) return OCM_ERR_OVERFLOW;
     }
-    const long long N2 = (long long)n * (long long)n;
+    const long long N2 = nmax * nmax;
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
 
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable
     long long it = 0, switched = 0;
     for (;;) {
-        const int le = launch_evaluate(n, N2, ws, (int)it, st);
+        const int le = launch_evaluate(n, N2, ws, (int)it, b, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
         launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, st);
@@ -269,10 +282,18 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
         if (++it >= max_iters) return OCM_ERR_NOT_CONVERGED;
     }
 
-    // 4. critical cycle of the final policy
-    const int Lstar = h.res_len;
-    if (Lstar < 1 || Lstar > n) return OCM_ERR_INTERNAL;
-    launches += launch_extract(n, Lstar, ws, cycle_out, grid, st);
+    // 4. critical cycle(s) of the final policy
+    int Lstar = 0;
+    if (bs) {
+        int bits = 0;
+        while ((1LL << bits) <= nmax) ++bits;
+        launches += launch_batch_finish(n, sign, bits, b, ws, out.num, out.den, out.cycle_len,
+                                        out.cycle_out, grid, st);
+    } else {
+        Lstar = h.res_len;
+        if (Lstar < 1 || Lstar > n) return OCM_ERR_INTERNAL;
+        launches += launch_extract(n, Lstar, ws, out.cycle_out, grid, st);
+    }
     if (opt && (opt->eta_num || opt->eta_den || opt->potential || opt->policy)) {
         launch_outputs(n, ws, opt->eta_num, opt->eta_den, opt->potential, opt->policy, st);
         launches += 1;
@@ -281,11 +302,13 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     Ctrl fin;
     rc = read_ctrl(ws.ctrl, &fin, st);
     if (rc) return rc;
-    if (fin.cnt[0] != Lstar) return OCM_ERR_INTERNAL;
-
-    *num = (int64_t)sign * (int64_t)h.res_num;
-    *den = h.res_den;
-    *cycle_len = Lstar;
+    if (fin.err) return map_err_bits(fin.err);
+    if (!bs) {
+        if (fin.cnt[0] != Lstar) return OCM_ERR_INTERNAL;
+        *out.num = (int64_t)sign * (int64_t)h.res_num;
+        *out.den = h.res_den;
+        *out.cycle_len = Lstar;
+    }
     if (stats) {
         stats->iterations = (int32_t)it;
         stats->cycles = h.res_cycles;
@@ -297,6 +320,69 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
         stats->value_items = fin.items_value;
     }
     return OCM_OK;
+}
+
+// Batch workspace: the single-graph layout for all N vertices, then the
+// per-vertex graph ids and the per-graph records.
+static size_t batch_extra(int G, int N, BatchState *bs, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off, 256);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    BatchState b{};
+    b.gid = static_cast<int *>(take(4 * (size_t)N));
+    b.gbest = static_cast<unsigned long long *>(take(8 * (size_t)G));
+    b.groot = static_cast<int *>(take(4 * (size_t)G));
+    b.glen = static_cast<int *>(take(4 * (size_t)G));
+    b.gfound = static_cast<int *>(take(4 * (size_t)G));
+    b.G = G;
+    if (bs) *bs = b;
+    return align_up(off, 256);
+}
+
+}  // namespace ocm
+
+extern "C" {
+
+int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
+              int32_t m, int mode, int64_t *num, int32_t *den, int32_t *cycle_out,
+              int32_t *cycle_len, void *workspace, size_t ws_bytes, void *stream,
+              const ocm_options *opt, ocm_stats *stats) {
+    if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
+    if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
+    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
+    if (!workspace) return OCM_ERR_WORKSPACE;
+    SolveOut out{num, den, cycle_len, cycle_out};
+    return solve_impl(row_ptr, col_idx, w, n, m, mode, out, workspace, ws_bytes,
+                      ocm_workspace_size(n, m), stream, opt, stats, nullptr);
+}
+
+size_t ocm_workspace_size_batch(int32_t G, int32_t N, int32_t M) {
+    if (G < 1 || N < G || M < 1) return 0;
+    return ocm_workspace_size(N, M) + batch_extra(G, N, nullptr, nullptr);
+}
+
+int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int32_t *col_idx,
+                    const int32_t *w, int32_t G, int32_t N, int32_t M, int mode, int64_t *num,
+                    int32_t *den, int32_t *cycle_len, int32_t *cycle_out, void *workspace,
+                    size_t ws_bytes, void *stream, const ocm_options *opt, ocm_stats *stats) {
+    if (!graph_vptr || !row_ptr || !col_idx || !w || !num || !den || !cycle_len || !cycle_out)
+        return OCM_ERR_INVALID_ARG;
+    if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
+    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
+    if (!workspace) return OCM_ERR_WORKSPACE;
+    const size_t base = ocm_workspace_size(N, M);
+    const size_t need = ocm_workspace_size_batch(G, N, M);
+    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return OCM_ERR_WORKSPACE;
+    BatchState bs;
+    batch_extra(G, N, &bs, static_cast<char *>(workspace) + base);
+    bs.vptr = graph_vptr;
+    SolveOut out{num, den, cycle_len, cycle_out};
+    return solve_impl(row_ptr, col_idx, w, N, M, mode, out, workspace, ws_bytes, base, stream, opt,
+                      stats, &bs);
 }
 
 int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *grad_lambda,

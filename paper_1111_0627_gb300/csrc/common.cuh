@@ -77,7 +77,8 @@ struct Ctrl {
     int res_len;
     int res_root;
     int res_cycles;
-    int pad[2];
+    int max_ng;               // batch: largest graph
+    int pad[1];
 };
 
 enum : int {
@@ -112,6 +113,18 @@ struct Workspace {
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan
     Ctrl *ctrl;
+};
+
+// Extra state of a batched solve (G graphs as one disjoint-union CSR);
+// all pointers are null for a single-graph solve.
+struct BatchState {
+    const int *vptr;              // [G+1] vertex offsets of the graphs
+    int *gid;                     // [N] graph of each vertex
+    unsigned long long *gbest;    // [G] packed (rank, INT_MAX - root) of each graph's best cycle
+    int *groot;                   // [G] root of each graph's critical cycle
+    int *glen;                    // [G] its length
+    int *gfound;                  // [G] cycle vertices found by the extraction
+    int G;
 };
 
 // Layout of the workspace for n vertices; returns total bytes and fills ws
@@ -157,11 +170,16 @@ void prof_end(int cls, cudaStream_t st);
 // kernel launchers (defined in the .cu files)
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        Workspace ws, cudaStream_t st);
+                        Workspace ws, const BatchState *bs, cudaStream_t st);
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                   Workspace ws, const int *cls_cnt, int next_eval, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, cudaStream_t st);
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchState bs,
+                    cudaStream_t st);
+int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
+int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws, int64_t *num,
+                        int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,
+                        cudaStream_t st);
 int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
 void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t *potential,
                     int32_t *policy, cudaStream_t st);

@@ -125,7 +125,7 @@ constexpr int kMinMask = 0x7fffffff;
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_index,
-                Workspace ws) {
+                Workspace ws, BatchState bs) {
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     Ctrl *c = ws.ctrl;
@@ -143,6 +143,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
         c->nrep = 0;
         c->best = 0;
     }
+    for (int g = first + threadIdx.x; g < bs.G; g += stride) bs.gbest[g] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
     if (!grid_barrier(c, nblocks)) return;
 
@@ -381,9 +382,13 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
         }
         if (i < K) {
             ws.cyc_rank[i] = rank;
+            const int root = ws.cyc_root[i];
             unsigned long long packed = ((unsigned long long)(unsigned)rank << 32) |
-                                        (unsigned)(INT_MAX - ws.cyc_root[i]);
+                                        (unsigned)(INT_MAX - root);
             atomicMax(&c->best, packed);
+            // batched: Alg. 4's region-specific vote, one region per graph,
+            // deterministic because the packed key is a total order
+            if (bs.G) atomicMax(&bs.gbest[bs.gid[root]], packed);
         }
     }
     if (!grid_barrier(c, nblocks)) return;
@@ -430,7 +435,8 @@ static int evaluate_grid() {
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, cudaStream_t st) {
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchState bs,
+                    cudaStream_t st) {
     int blocks = evaluate_grid();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
@@ -438,7 +444,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, cudaStrea
     const int lg = ceil_log2(n);
     int max_detect = lg + 4;
     int max_value = lg + 3;
-    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &ws};
+    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &ws, &bs};
     prof_begin(kProfEvaluate, st);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)evaluate_kernel, dim3(blocks),
                                                 dim3(kEvalThreads), args, 0, st);

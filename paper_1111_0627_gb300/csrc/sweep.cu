@@ -62,7 +62,8 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 // validates col_idx and w and measures max|w| for the exactness bound.
 __global__ void __launch_bounds__(kThreads)
 init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-                   const int *__restrict__ w, int sign, int n, Workspace ws) {
+                   const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
+                   Workspace ws) {
     __shared__ int s_maxw[kThreads / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -70,12 +71,14 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     int maxabs = 0;
     for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
         const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
+        const int my_g = gid ? gid[v] : 0;
         int best_e = a;
         long long best_key = LLONG_MIN;
         for (int e = a; e < b; ++e) {
             const int t = __ldg(&col[e]);
             int x = __ldg(&w[e]);
-            if ((unsigned)t >= (unsigned)n) {
+            if ((unsigned)t >= (unsigned)n || (gid && gid[t] != my_g)) {
+                // out of range, or (batched) an edge between different graphs
                 atomicOr(&ws.ctrl->err, kErrCol);
                 atomicMin(&ws.ctrl->bad_index, e);
             }
@@ -332,12 +335,13 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 }
 
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        Workspace ws, cudaStream_t st) {
+                        Workspace ws, const BatchState *bs, cudaStream_t st) {
     (void)m;
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 2048) blocks = 2048;
     prof_begin(kProfInit, st);
-    init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n, ws);
+    init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n,
+                                                    bs ? bs->gid : nullptr, ws);
     prof_end(kProfInit, st);
 }
 

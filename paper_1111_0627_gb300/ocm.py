@@ -131,6 +131,57 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
                     **extra)
 
 
+@dataclass
+class BatchSolution:
+    num: torch.Tensor          # int64 [G]
+    den: torch.Tensor          # int32 [G]
+    cycle_len: torch.Tensor    # int32 [G]
+    cycle_out: torch.Tensor    # int32 [N]; graph g's cycle at graph_vptr[g]
+    graph_vptr: torch.Tensor   # int32 [G+1]
+    stats: dict = field(default_factory=dict)
+
+    def cycle(self, g: int) -> torch.Tensor:
+        start = int(self.graph_vptr[g])
+        return self.cycle_out[start:start + int(self.cycle_len[g])]
+
+
+def workspace_bytes_batch(G: int, N: int, M: int) -> int:
+    return int(_native.load().ocm_workspace_size_batch(G, N, M))
+
+
+def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor,
+                w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
+                stream=None, max_iters: int = 0) -> BatchSolution:
+    """Optimal cycle means of G graphs given as one disjoint-union CSR
+    (``ocm_solve_batch``); each result equals solving that graph alone."""
+    lib = _native.load()
+    vp = _dev_i32(graph_vptr, "graph_vptr")
+    rp = _dev_i32(row_ptr, "row_ptr")
+    col = _dev_i32(col_idx, "col_idx")
+    ww = _dev_i32(w, "w")
+    G, N, M = vp.numel() - 1, rp.numel() - 1, col.numel()
+    dev = rp.device
+    if workspace is None:
+        nbytes = workspace_bytes_batch(G, N, M)
+        if nbytes == 0:
+            raise ValueError("batch size out of range")
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    num = torch.empty(G, dtype=torch.int64, device=dev)
+    den = torch.empty(G, dtype=torch.int32, device=dev)
+    clen = torch.empty(G, dtype=torch.int32, device=dev)
+    cyc = torch.empty(N, dtype=torch.int32, device=dev)
+    opt = _native.OcmOptions()
+    opt.max_iters = int(max_iters)
+    st = _native.OcmStats()
+    rc = lib.ocm_solve_batch(vp.data_ptr(), rp.data_ptr(), col.data_ptr(), ww.data_ptr(), G, N, M,
+                             _mode(mode), num.data_ptr(), den.data_ptr(), clen.data_ptr(),
+                             cyc.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                             _stream_ptr(stream), ctypes.byref(opt), ctypes.byref(st))
+    if rc != 0:
+        raise OCMError(rc, "ocm_solve_batch")
+    return BatchSolution(num, den, clen, cyc, vp, st.as_dict())
+
+
 def backward(cycle: torch.Tensor, grad_lambda: torch.Tensor, m: int, *, stream=None,
              out: torch.Tensor | None = None) -> torch.Tensor:
     """d lambda*/d w scaled by grad_lambda (``ocm_backward``); float32 [m]."""

@@ -1,0 +1,89 @@
+"""Batched form (needs a GB300): every graph of a disjoint-union batch gets
+exactly the value and critical cycle that the oracle gives for that graph
+alone, independent of the order of the graphs in the batch."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_1111_0627_gb300 as ocm
+
+
+def _solve_batch(b):
+    d = torch.device("cuda")
+    return ocm.solve_batch(torch.from_numpy(b.graph_vptr).to(d), torch.from_numpy(b.row_ptr).to(d),
+                           torch.from_numpy(b.col_idx).to(d), torch.from_numpy(b.w).to(d), b.mode)
+
+
+def _check_against_oracle(b, sol, graphs):
+    num, den = sol.num.cpu().numpy(), sol.den.cpu().numpy()
+    for g, gr in enumerate(graphs):
+        h = oracle.howard(gr.row_ptr, gr.col_idx, gr.w, gr.mode)
+        assert (int(num[g]), int(den[g])) == (h.num, h.den), g
+        e0 = int(b.row_ptr[int(b.graph_vptr[g])])
+        cyc = (sol.cycle(g).cpu().numpy() - e0).tolist()
+        assert cyc == [int(x) for x in h.cycle], g
+
+
+def test_batch_of_random_graphs_matches_per_graph_oracle():
+    graphs = synth.batch_graphs(G=64, nmin=20, nmax=3000)
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    _check_against_oracle(b, sol, graphs)
+
+
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_batch_mixed_tiny_graphs_and_modes(mode):
+    rng = np.random.default_rng(77 + (mode == "min"))
+    graphs = [synth.tiny_random(rng, int(rng.integers(1, 30)), max_extra=3, wlo=-50, whi=50,
+                                mode=mode) for _ in range(200)]
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    _check_against_oracle(b, sol, graphs)
+
+
+def test_batch_order_independence():
+    graphs = synth.batch_graphs(G=24, nmin=50, nmax=2000)
+    perm = np.random.default_rng(3).permutation(len(graphs))
+    b1 = synth.concat(graphs)
+    b2 = synth.concat([graphs[i] for i in perm])
+    s1, s2 = _solve_batch(b1), _solve_batch(b2)
+    for k, i in enumerate(perm):
+        assert int(s1.num[i]) == int(s2.num[k]) and int(s1.den[i]) == int(s2.den[k])
+        c1 = s1.cycle(int(i)).cpu().numpy() - int(b1.row_ptr[int(b1.graph_vptr[i])])
+        c2 = s2.cycle(k).cpu().numpy() - int(b2.row_ptr[int(b2.graph_vptr[k])])
+        assert c1.tolist() == c2.tolist()
+
+
+def test_batch_equals_single_solves_on_gpu():
+    graphs = synth.batch_graphs(G=16, nmin=1000, nmax=60000)
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    d = torch.device("cuda")
+    for g, gr in enumerate(graphs):
+        s = ocm.solve(torch.from_numpy(gr.row_ptr).to(d), torch.from_numpy(gr.col_idx).to(d),
+                      torch.from_numpy(gr.w).to(d), gr.mode)
+        assert (int(sol.num[g]), int(sol.den[g])) == (s.num, s.den)
+        e0 = int(b.row_ptr[int(b.graph_vptr[g])])
+        assert (sol.cycle(g).cpu() - e0).tolist() == s.cycle.cpu().tolist()
+
+
+def test_batch_rejects_edges_between_graphs_and_bad_offsets():
+    graphs = synth.batch_graphs(G=3, nmin=10, nmax=20)
+    b = synth.concat(graphs)
+    col = b.col_idx.copy()
+    col[0] = int(b.graph_vptr[2])          # an edge of graph 0 into graph 2
+    bad = synth.Batch(b.graph_vptr, b.row_ptr, col, b.w, b.mode)
+    with pytest.raises(ocm.OCMError) as ei:
+        _solve_batch(bad)
+    assert ei.value.status == -2
+    vp = b.graph_vptr.copy()
+    vp[1] = vp[0]                           # empty graph
+    with pytest.raises(ocm.OCMError) as ei:
+        _solve_batch(synth.Batch(vp, b.row_ptr, b.col_idx, b.w, b.mode))
+    assert ei.value.status == -2
