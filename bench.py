@@ -36,6 +36,16 @@ METRIC = "edge-iters/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
+BATCH_WORKLOADS = {
+    "batch4096": (4096, 200000,
+                  "4096 graphs, n_g log-uniform in [100, 200000], ring + U{0..7} extra edges, "
+                  "w U[1,10000], max"),
+    "batch4096-20k": (4096, 20000,
+                      "4096 graphs, n_g log-uniform in [100, 20000], ring + U{0..7} extra edges, "
+                      "w U[1,10000], max"),
+}
+
+
 def _workloads():
     return {
         "product4": (synth.product4,
@@ -351,18 +361,201 @@ def run_ours(args, g, desc):
     return 0
 
 
+def _gpu_setup():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    return torch, dist, world, rank, local, torch.device("cuda", local)
+
+
+def run_batch(args):
+    """Batched form: graphs/s of one ocm_solve_batch call over G graphs, against
+    a loop of ocm_solve over the same graphs (same stream, warm workspace)."""
+    import paper_1111_0627_gb300 as ocm
+    torch, dist, world, rank, local, dev = _gpu_setup()
+    G, nmax, desc = BATCH_WORKLOADS[args.workload]
+    graphs = synth.batch_graphs(G=G, nmin=100, nmax=nmax)
+    b = synth.concat(graphs, name=args.workload)
+    vp, rp, col, w = [torch.from_numpy(x).to(dev) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    ws = torch.empty(ocm.workspace_bytes_batch(G, b.N, b.M), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        sol = ocm.solve_batch(vp, rp, col, w, b.mode, workspace=ws, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clocks:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            sol = ocm.solve_batch(vp, rp, col, w, b.mode, workspace=ws, stream=stream)
+            ev[k][1].record(stream)
+            launches += sol.stats["launches"]
+        barrier()
+    total_ms = sum(a.elapsed_time(bb) for a, bb in ev)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * G / (total_ms / 1e3)
+
+    # the same graphs through the plain solver, one call each
+    num_b, den_b = sol.num.cpu().numpy(), sol.den.cpu().numpy()
+    wsl = torch.empty(max(ocm.workspace_bytes(g.n, g.m) for g in graphs), dtype=torch.uint8,
+                      device=dev)
+    cyc = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
+    devg = [tuple(torch.from_numpy(x).to(dev) for x in (g.row_ptr, g.col_idx, g.w)) for g in graphs]
+    for r_, c_, w_ in devg[:3]:
+        ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
+    identical = True
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i, (r_, c_, w_) in enumerate(devg):
+        x = ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
+        identical &= (x.num, x.den) == (int(num_b[i]), int(den_b[i]))
+        if i < 64:   # cycles of a sample of graphs compared edge by edge
+            off = int(b.row_ptr[int(b.graph_vptr[i])])
+            identical &= (sol.cycle(i).cpu() - off).tolist() == x.cycle.cpu().tolist()
+    e1.record(stream)
+    barrier()
+    loop_ms = e0.elapsed_time(e1)
+
+    # end to end: host CSR -> device, batched solve, results back
+    h = [torch.from_numpy(x).pin_memory() for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    d = [torch.empty_like(x) for x in (vp, rp, col, w)]
+    barrier()
+    e0.record(stream)
+    for src, dst in zip(h, d):
+        dst.copy_(src, non_blocking=True)
+    s2 = ocm.solve_batch(*d, b.mode, workspace=ws, stream=stream)
+    out = [s2.num.cpu(), s2.den.cpu(), s2.cycle_len.cpu(), s2.cycle_out.cpu()]
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "graphs/s", "value": value, "unit": "graphs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "G": G, "N": b.N, "M": b.M,
+                       "mode": b.mode, "iterations": sol.stats["iterations"],
+                       "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
+            "loop_of_plain_solver": {"graphs_per_s": G / (loop_ms / 1e3), "ms": loop_ms,
+                                     "identical_results": bool(identical)},
+            "speedup_vs_loop": (loop_ms / 1e3) / (total_ms / args.steps / 1e3),
+            "e2e": {"value": G / (e2e_ms / 1e3), "unit": "graphs/s",
+                    "h2d_bytes_per_step": sum(x.numel() * 4 for x in h),
+                    "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in out)},
+            "gpu_launches": launches, "clocks": clocks.summary(), "stats": sol.stats}), flush=True)
+    return 0
+
+
+def run_grad(args):
+    """Differentiation form on diff1m: forward + backward kernel against finite
+    differences by looping the plain solver over 64 random edges plus the
+    critical cycle (integer +1 perturbations, exact)."""
+    import paper_1111_0627_gb300 as ocm
+    torch, dist, world, rank, local, dev = _gpu_setup()
+    base = synth.diff1m_base()
+    # the unique-optimum construction needs the base graph's critical cycle; the
+    # solver's own answer is used here (the tests check it against the oracle)
+    rp, col = torch.from_numpy(base.row_ptr).to(dev), torch.from_numpy(base.col_idx).to(dev)
+    w0 = torch.from_numpy(base.w).to(dev)
+    ws = ocm.make_workspace(base.n, base.m, dev)
+    c0 = ocm.solve(rp, col, w0, "max", workspace=ws).cycle.long()
+    w = w0.clone()
+    w[c0] += 1
+    stream = torch.cuda.current_stream(dev)
+    gl = torch.ones(1, device=dev)
+    for _ in range(args.warmup):
+        sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
+        g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
+        g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fb_ms = e0.elapsed_time(e1) / args.steps
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    eb[0].record(stream)
+    for _ in range(args.steps):
+        g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
+    eb[1].record(stream)
+    torch.cuda.synchronize(dev)
+    bw_ms = eb[0].elapsed_time(eb[1]) / args.steps
+    rng = np.random.default_rng(1111062704)
+    edges = np.unique(np.concatenate([rng.integers(0, base.m, 64), sol.cycle.cpu().numpy()]))
+    lam0 = sol.value
+    gh = g.cpu().numpy()
+    e0.record(stream)
+    max_rel = 0.0
+    for e in edges:
+        wp = w.clone()
+        wp[int(e)] += 1
+        fd = float(ocm.solve(rp, col, wp, "max", workspace=ws, stream=stream).value - lam0)
+        if fd != 0.0:
+            max_rel = max(max_rel, abs(gh[int(e)] - fd) / abs(fd))
+        elif gh[int(e)] != 0.0:
+            max_rel = float("inf")
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fd_ms = e0.elapsed_time(e1)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "gradient evaluations/s", "value": 1e3 / fb_ms, "unit": "1/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fb_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32",
+            "data": "synthetic",
+            "config": {"workload": "diff1m: n=2^20, ring + U{0..7} extras, w 1024*U[0,1000] with +1 "
+                                   "on the critical cycle (unique optimum), max",
+                       "n": base.n, "m": base.m, "critical_cycle_len": int(sol.cycle.numel()),
+                       "fd_edges": int(len(edges))},
+            "backward_kernel_ms": bw_ms,
+            "finite_difference_loop": {"ms": fd_ms, "solves": int(len(edges)),
+                                       "max_rel_err_vs_gradient": max_rel},
+            "speedup_vs_fd_loop": fd_ms / fb_ms}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="product4", choices=sorted(_workloads()))
+    ap.add_argument("--workload", default="product4",
+                    choices=sorted(_workloads()) + sorted(BATCH_WORKLOADS) + ["diff1m-grad"])
     ap.add_argument("--ref-iters", type=int, default=2,
                     help="Howard iterations per reference (oracle) step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    if args.workload in BATCH_WORKLOADS and args.impl == "ours":
+        return run_batch(args)
+    if args.workload == "diff1m-grad" and args.impl == "ours":
+        return run_grad(args)
+    if args.workload in BATCH_WORKLOADS or args.workload == "diff1m-grad":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm is run on the single-graph workloads only"}))
+        return 0
     make, desc = _workloads()[args.workload]
     g = make()
     if args.impl == "reference":
