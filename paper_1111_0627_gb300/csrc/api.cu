@@ -271,8 +271,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         const int le = launch_evaluate(n, N2, ws, (int)it, b, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
-        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, st);
+        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, b, st);
         launches += 1;
+        if (bs) launches += launch_batch_converge((int)it + 1, b, ws, st);
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
         rc = read_ctrl(ws.ctrl, &h, st);
         if (rc) return rc;
@@ -338,6 +339,10 @@ static size_t batch_extra(int G, int N, BatchState *bs, char *base) {
     b.groot = static_cast<int *>(take(4 * (size_t)G));
     b.glen = static_cast<int *>(take(4 * (size_t)G));
     b.gfound = static_cast<int *>(take(4 * (size_t)G));
+    b.gp = static_cast<long long *>(take(8 * (size_t)G));
+    b.gq = static_cast<int *>(take(4 * (size_t)G));
+    b.gconv = static_cast<int *>(take(4 * (size_t)G));
+    b.gsw = static_cast<int *>(take(4 * (size_t)G));
     b.G = G;
     if (bs) *bs = b;
     return align_up(off, 256);

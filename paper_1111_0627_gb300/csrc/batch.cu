@@ -18,11 +18,14 @@ namespace ocm {
 
 // Graph offsets: vptr[0] = 0, vptr[G] = N, every graph non-empty.
 __global__ void __launch_bounds__(kThreads)
-batch_check_kernel(const int *__restrict__ vptr, int G, int N, Ctrl *ctrl) {
+batch_check_kernel(const int *__restrict__ vptr, int G, int N, int *bs_gconv, int *bs_gsw,
+                   Ctrl *ctrl) {
     const int stride = gridDim.x * blockDim.x;
     int local_max = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride) {
         const int a = vptr[g], b = vptr[g + 1];
+        bs_gconv[g] = 0;
+        bs_gsw[g] = 0;
         if ((g == 0 && a != 0) || (g == G - 1 && b != N) || b <= a || a < 0 || b > N) {
             atomicOr(&ctrl->err, kErrRowPtr);
             atomicMin(&ctrl->bad_index, g);
@@ -57,18 +60,27 @@ int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t
     int vb = (N + kThreads - 1) / kThreads;
     if (vb > 4096) vb = 4096;
     prof_begin(kProfInit, st);
-    batch_check_kernel<<<gb, kThreads, 0, st>>>(bs.vptr, bs.G, N, ws.ctrl);
+    batch_check_kernel<<<gb, kThreads, 0, st>>>(bs.vptr, bs.G, N, bs.gconv, bs.gsw, ws.ctrl);
     batch_gid_kernel<<<vb, kThreads, 0, st>>>(bs.vptr, bs.G, N, bs.gid);
     prof_end(kProfInit, st);
     return 2;
 }
 
-// Per-graph answer from the per-graph vote of the final evaluation.
+// After each sweep: a graph none of whose vertices switched is final (the
+// paper's per-region "work" flag, Sec. 3.3).  Its answer is taken from the
+// evaluation that preceded this sweep -- the per-graph vote and the cycle
+// tables are still those of that evaluation -- and it drops out of later
+// evaluations and sweeps.
 __global__ void __launch_bounds__(kThreads)
-batch_results_kernel(int sign, BatchState bs, Workspace ws, int64_t *num, int32_t *den,
-                     int32_t *cycle_len) {
+batch_converge_kernel(int next_eval, BatchState bs, Workspace ws) {
     const int stride = gridDim.x * blockDim.x;
+    int active = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < bs.G; g += stride) {
+        if (bs.gconv[g]) continue;
+        if (bs.gsw[g] == next_eval) {
+            ++active;
+            continue;
+        }
         const unsigned long long packed = bs.gbest[g];
         const int root = INT_MAX - (int)(unsigned)(packed & 0xffffffffu);
         if (packed == 0 || root < bs.vptr[g] || root >= bs.vptr[g + 1]) {
@@ -76,11 +88,40 @@ batch_results_kernel(int sign, BatchState bs, Workspace ws, int64_t *num, int32_
             continue;
         }
         const int i = ws.cid_of_root[root];
-        num[g] = (int64_t)sign * ws.cyc_p[i];
-        den[g] = ws.cyc_q[i];
-        cycle_len[g] = ws.cyc_L[i];
         bs.groot[g] = root;
         bs.glen[g] = ws.cyc_L[i];
+        bs.gp[g] = ws.cyc_p[i];
+        bs.gq[g] = ws.cyc_q[i];
+        bs.gconv[g] = 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) active += __shfl_xor_sync(0xffffffffu, active, o);
+    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&ws.ctrl->active_graphs, active);
+}
+
+__global__ void batch_active_reset_kernel(Ctrl *c) { c->active_graphs = 0; }
+
+int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st) {
+    int gb = (bs.G + kThreads - 1) / kThreads;
+    if (gb > 1024) gb = 1024;
+    batch_active_reset_kernel<<<1, 1, 0, st>>>(ws.ctrl);
+    batch_converge_kernel<<<gb, kThreads, 0, st>>>(next_eval, bs, ws);
+    return 2;
+}
+
+// Per-graph answers recorded when each graph converged.
+__global__ void __launch_bounds__(kThreads)
+batch_results_kernel(int sign, BatchState bs, Workspace ws, int64_t *num, int32_t *den,
+                     int32_t *cycle_len) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < bs.G; g += stride) {
+        if (!bs.gconv[g]) {
+            atomicOr(&ws.ctrl->err, kErrExtract);
+            continue;
+        }
+        num[g] = (int64_t)sign * bs.gp[g];
+        den[g] = bs.gq[g];
+        cycle_len[g] = bs.glen[g];
         bs.gfound[g] = 0;
     }
 }

@@ -78,7 +78,7 @@ struct Ctrl {
     int res_root;
     int res_cycles;
     int max_ng;               // batch: largest graph
-    int pad[1];
+    int active_graphs;        // batch: graphs whose policy may still change
 };
 
 enum : int {
@@ -124,6 +124,10 @@ struct BatchState {
     int *groot;                   // [G] root of each graph's critical cycle
     int *glen;                    // [G] its length
     int *gfound;                  // [G] cycle vertices found by the extraction
+    long long *gp;                // [G] reduced mean of the critical cycle: numerator
+    int *gq;                      //     and denominator
+    int *gconv;                   // [G] 1 once the graph's policy is final
+    int *gsw;                     // [G] evaluation index after the last sweep that switched in g
     int G;
 };
 
@@ -172,7 +176,8 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, const BatchState *bs, cudaStream_t st);
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, cudaStream_t st);
+                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st);
+int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchState bs,
                     cudaStream_t st);

@@ -168,7 +168,11 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
             for (int u = 0; u < kU; ++u) {
                 const int i = i0 + u * blockDim.x + threadIdx.x;
                 item[u] = INT_MIN;
-                if (i < cnt) item[u] = (r == 0) ? lo + i : lin[i];
+                if (i < cnt) {
+                    item[u] = (r == 0) ? lo + i : lin[i];
+                    // batched: vertices of converged graphs keep everything
+                    if (r == 0 && bs.G && bs.gconv[bs.gid[lo + i]]) item[u] = INT_MIN;
+                }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -261,7 +265,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
             const int i = i0 + threadIdx.x;
             bool keep = false;
             int v = lo + i;
-            if (i < hi - lo) {
+            if (i < hi - lo && !(bs.G && bs.gconv[bs.gid[v]])) {
                 const JM d = ws.jm[0][v];
                 if (d.M) {
                     const int root = ~d.J;
@@ -399,6 +403,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
         c->switched = 0;
     }
     for (int v = first + threadIdx.x; v < n; v += stride) {
+        if (bs.G && bs.gconv[bs.gid[v]]) continue;
         JLS st = ws.jls[0][v];
         int i = ws.cid_of_root[~st.J];
         long long p = ws.cyc_p[i];

@@ -252,7 +252,8 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 
 __global__ void __launch_bounds__(kThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, ClassGrid cg, int next_eval, Workspace ws) {
+               const int *__restrict__ w, int sign, ClassGrid cg, int next_eval, Workspace ws,
+               BatchState bs) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -283,8 +284,11 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         const int g = 1 << c;
         const int sub = lane & (g - 1);
         const int idx = (task - cg.task_off[c]) * (32 >> c) + (lane >> c);
-        const bool valid = idx < ws.ctrl->cls_cnt[c];
+        bool valid = idx < ws.ctrl->cls_cnt[c];
         const int v = valid ? ws.cls_list[ws.ctrl->cls_off[c] + idx] : 0;
+        // batched: a graph whose last sweep switched nothing never switches
+        // again (its records do not change), so its vertices are skipped
+        if (valid && bs.G && bs.gconv[bs.gid[v]]) valid = false;
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
         if (valid) {
             const int a = __ldg(&row_ptr[v]), e_end = __ldg(&row_ptr[v + 1]);
@@ -320,6 +324,10 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 ws.succ[v] = __ldg(&col[best.e]);
                 ws.wpi[v] = sign * __ldg(&w[best.e]);
                 ws.sw_iter[v] = next_eval;
+                if (bs.G) {
+                    const int g = bs.gid[v];
+                    if (bs.gsw[g] != next_eval) bs.gsw[g] = next_eval;
+                }
                 ++switched;
             }
         }
@@ -346,7 +354,7 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
 }
 
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, cudaStream_t st) {
+                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st) {
     (void)n;
     ClassGrid cg;
     int tasks = 0;
@@ -370,7 +378,7 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
     int blocks = (tasks + (kThreads / 32) - 1) / (kThreads / 32);
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, next_eval, ws);
+    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, next_eval, ws, bs);
     prof_end(kProfSweep, st);
 }
 
