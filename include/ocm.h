@@ -72,12 +72,18 @@ extern "C" {
  * eta(t) <= eta(v), and when equal, q*s*w(e) - p + V(t) - V(v) <= 0.       */
 typedef struct ocm_options {
     int32_t max_iters;   /* improvement steps before OCM_ERR_NOT_CONVERGED; <= 0: 4n + 64 */
-    int32_t flags;       /* reserved, must be 0                                     */
+    int32_t flags;       /* OCM_FLAG_* bits; 0 for normal use                       */
     int64_t *eta_num;    /* optional device [n]                                     */
     int32_t *eta_den;    /* optional device [n]                                     */
     int64_t *potential;  /* optional device [n]                                     */
     int32_t *policy;     /* optional device [n]: final policy edge of each vertex   */
 } ocm_options;
+
+/* Test-only: the first grid barrier of the evaluation waits for an arrival
+ * that never comes, with its wait limit cut to about 10 ms, so the solve
+ * exercises the bounded-wait path and returns OCM_ERR_TIMEOUT.  The device
+ * context stays usable. */
+#define OCM_FLAG_TEST_STALL 1
 
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
@@ -158,6 +164,20 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
  */
 int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *grad_lambda,
                  int32_t m, float *grad_w, void *stream);
+
+/*
+ * ocm_backward_batch -- the gradient of every graph's lambda* for a batched
+ * solve: grad_w[e] = grad_lambda[g] / cycle_len[g] for each edge e of graph
+ * g's critical cycle, 0 for every other edge (as ocm_backward, per graph).
+ *   graph_vptr[G+1], cycle_out[N], cycle_len[G] : device, as produced by
+ *                    ocm_solve_batch (graph g's cycle at offset graph_vptr[g])
+ *   grad_lambda[G] : device float, upstream gradient per graph
+ *   grad_w[M]      : device float, fully overwritten
+ * Asynchronous on `stream`; edge indices outside [0, M) are ignored.
+ */
+int ocm_backward_batch(const int32_t *graph_vptr, const int32_t *cycle_out,
+                       const int32_t *cycle_len, const float *grad_lambda, int32_t G, int32_t M,
+                       float *grad_w, void *stream);
 
 /* Instrumentation for benchmarks (not needed to solve).  While enabled,
  * every kernel launch of ocm_solve is bracketed by CUDA events recorded on

@@ -74,6 +74,25 @@ cycle_grad_kernel(const int *cyc, int L, const float *gl, float *g, int m) {
     }
 }
 
+// One warp per graph: every edge of graph g's critical cycle gets g's
+// upstream gradient divided by the cycle length.
+__global__ void __launch_bounds__(kThreads)
+batch_cycle_grad_kernel(const int *vptr, const int *cyc, const int *clen, const float *gl, int G,
+                        float *g, int m) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < G; k += warps) {
+        const int L = clen[k];
+        if (L < 1) continue;
+        const float val = __fdiv_rn(gl[k], (float)L);
+        const int base = vptr[k];
+        for (int i = lane; i < L; i += 32) {
+            const int e = cyc[base + i];
+            if ((unsigned)e < (unsigned)m) g[e] = val;
+        }
+    }
+}
+
 void launch_backward(const int *cycle_edges, int cycle_len, const float *grad_lambda, int m,
                      float *grad_w, cudaStream_t st) {
     int blocks = (m + kThreads - 1) / kThreads;
@@ -268,7 +287,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable
     long long it = 0, switched = 0;
     for (;;) {
-        const int le = launch_evaluate(n, N2, ws, (int)it, b, st);
+        const int stall = (opt && (opt->flags & OCM_FLAG_TEST_STALL)) ? 1 : 0;
+        const int le = launch_evaluate(n, N2, ws, (int)it, stall, b, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
         launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, b, st);
@@ -358,7 +378,7 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
               const ocm_options *opt, ocm_stats *stats) {
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~OCM_FLAG_TEST_STALL)) return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     SolveOut out{num, den, cycle_len, cycle_out};
     return solve_impl(row_ptr, col_idx, w, n, m, mode, out, workspace, ws_bytes,
@@ -377,7 +397,7 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
     if (!graph_vptr || !row_ptr || !col_idx || !w || !num || !den || !cycle_len || !cycle_out)
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && opt->flags != 0) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~OCM_FLAG_TEST_STALL)) return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     const size_t base = ocm_workspace_size(N, M);
     const size_t need = ocm_workspace_size_batch(G, N, M);
@@ -388,6 +408,23 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
     SolveOut out{num, den, cycle_len, cycle_out};
     return solve_impl(row_ptr, col_idx, w, N, M, mode, out, workspace, ws_bytes, base, stream, opt,
                       stats, &bs);
+}
+
+int ocm_backward_batch(const int32_t *graph_vptr, const int32_t *cycle_out,
+                       const int32_t *cycle_len, const float *grad_lambda, int32_t G, int32_t M,
+                       float *grad_w, void *stream) {
+    if (!graph_vptr || !cycle_out || !cycle_len || !grad_lambda || !grad_w) return OCM_ERR_INVALID_ARG;
+    if (G < 1 || M < 1) return OCM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int blocks = (M + kThreads - 1) / kThreads;
+    if (blocks > 8192) blocks = 8192;
+    zero_float_kernel<<<blocks, kThreads, 0, st>>>(grad_w, M);
+    int gb = (G * 32 + kThreads - 1) / kThreads;
+    if (gb > 4096) gb = 4096;
+    batch_cycle_grad_kernel<<<gb, kThreads, 0, st>>>(graph_vptr, cycle_out, cycle_len, grad_lambda,
+                                                     G, grad_w, M);
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    return OCM_OK;
 }
 
 int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *grad_lambda,

@@ -179,8 +179,8 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
                   Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st);
 int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchState bs,
-                    cudaStream_t st);
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall_test,
+                    BatchState bs, cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws, int64_t *num,
                         int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,

@@ -46,6 +46,7 @@
 namespace ocm {
 
 constexpr long long kBarrierClockLimit = 4000000000LL;   // SM cycles: about two seconds
+constexpr long long kStallTestClockLimit = 20000000LL;   // about 10 ms (OCM_FLAG_TEST_STALL)
 
 static __device__ __forceinline__ int load_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
@@ -57,7 +58,8 @@ static __device__ __forceinline__ int load_volatile(const int *p) {
 // to arrive publishes the grand total before releasing the others.  Waits
 // are bounded by an SM-clock limit; on expiry every block records
 // kErrTimeout and *ok becomes false.
-static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok) {
+static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok,
+                                       long long limit = kBarrierClockLimit) {
     __shared__ int s_sum;
     __shared__ int s_total;
     __shared__ int s_ok;
@@ -82,7 +84,7 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
         } else {
             const long long t0 = clock64();
             while (*gen == g) {
-                if (clock64() - t0 > kBarrierClockLimit ||
+                if (clock64() - t0 > limit ||
                     (load_volatile(&c->err) & kErrTimeout)) {
                     atomicOr(&c->err, kErrTimeout);
                     okv = 0;
@@ -99,9 +101,10 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
     return s_total;
 }
 
-static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks) {
+static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks,
+                                                    long long limit = kBarrierClockLimit) {
     bool ok;
-    grid_sum_barrier(c, nblocks, 0, &ok);
+    grid_sum_barrier(c, nblocks, 0, &ok, limit);
     return ok;
 }
 
@@ -125,7 +128,7 @@ constexpr int kMinMask = 0x7fffffff;
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_index,
-                Workspace ws, BatchState bs) {
+                int stall_test, Workspace ws, BatchState bs) {
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     Ctrl *c = ws.ctrl;
@@ -145,7 +148,10 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_ind
     }
     for (int g = first + threadIdx.x; g < bs.G; g += stride) bs.gbest[g] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
-    if (!grid_barrier(c, nblocks)) return;
+    // (test only: wait for one block more than exists, so the wait expires)
+    if (!grid_barrier(c, nblocks + (stall_test ? 1u : 0u),
+                      stall_test ? kStallTestClockLimit : kBarrierClockLimit))
+        return;
 
     // ------------------------------------------------------------ detect
     // State: unresolved {J >= 0, M | dirty << 31}; resolved {~root, dirty}.
@@ -440,8 +446,8 @@ static int evaluate_grid() {
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchState bs,
-                    cudaStream_t st) {
+int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall_test,
+                    BatchState bs, cudaStream_t st) {
     int blocks = evaluate_grid();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
@@ -449,7 +455,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, BatchStat
     const int lg = ceil_log2(n);
     int max_detect = lg + 4;
     int max_value = lg + 3;
-    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &ws, &bs};
+    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &stall_test, &ws, &bs};
     prof_begin(kProfEvaluate, st);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)evaluate_kernel, dim3(blocks),
                                                 dim3(kEvalThreads), args, 0, st);

@@ -252,8 +252,8 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 
 __global__ void __launch_bounds__(kThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, ClassGrid cg, int next_eval, Workspace ws,
-               BatchState bs) {
+               const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, int next_eval,
+               Workspace ws, BatchState bs) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -261,15 +261,19 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     if (blockIdx.x == 0 && tid == 0) {
         // Publish the best cycle of the evaluation this sweep reads (it is
         // the answer if nothing switches).  No other thread touches these.
+        // (best is 0 only when the evaluation stopped early on an error,
+        // which the host reports after this sweep)
         Ctrl *cc = ws.ctrl;
-        unsigned long long bb = cc->best;
-        int root = INT_MAX - (int)(unsigned)(bb & 0xffffffffu);
-        int i = ws.cid_of_root[root];
-        cc->res_root = root;
-        cc->res_len = ws.cyc_L[i];
-        cc->res_num = ws.cyc_p[i];
-        cc->res_den = ws.cyc_q[i];
-        cc->res_cycles = cc->nrep;
+        const unsigned long long bb = cc->best;
+        const int root = INT_MAX - (int)(unsigned)(bb & 0xffffffffu);
+        if (bb != 0 && root >= 0 && root < n_vertices) {
+            const int i = ws.cid_of_root[root];
+            cc->res_root = root;
+            cc->res_len = ws.cyc_L[i];
+            cc->res_num = ws.cyc_p[i];
+            cc->res_den = ws.cyc_q[i];
+            cc->res_cycles = cc->nrep;
+        }
     }
     __syncthreads();
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
@@ -355,7 +359,6 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
 
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                   Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st) {
-    (void)n;
     ClassGrid cg;
     int tasks = 0;
     for (int c = 0; c < kClasses; ++c) {
@@ -378,7 +381,7 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
     int blocks = (tasks + (kThreads / 32) - 1) / (kThreads / 32);
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, cg, next_eval, ws, bs);
+    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n, cg, next_eval, ws, bs);
     prof_end(kProfSweep, st);
 }
 

@@ -22,6 +22,7 @@ import torch
 from . import _native
 
 OCM_MAX, OCM_MIN = 0, 1
+OCM_FLAG_TEST_STALL = 1
 
 
 class OCMError(RuntimeError):
@@ -87,7 +88,8 @@ class Solution:
 
 def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="max", *,
           workspace: torch.Tensor | None = None, stream=None, max_iters: int = 0,
-          certificate: bool = False, cycle_out: torch.Tensor | None = None) -> Solution:
+          certificate: bool = False, cycle_out: torch.Tensor | None = None,
+          flags: int = 0) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
@@ -108,7 +110,7 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
         cycle_out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
-    opt.flags = 0
+    opt.flags = int(flags)
     extra = {}
     if certificate:
         extra = dict(eta_num=torch.empty(n, dtype=torch.int64, device=dev),
@@ -194,6 +196,24 @@ def backward(cycle: torch.Tensor, grad_lambda: torch.Tensor, m: int, *, stream=N
                           _stream_ptr(stream))
     if rc != 0:
         raise OCMError(rc, "ocm_backward")
+    return out
+
+
+def backward_batch(sol: "BatchSolution", grad_lambda: torch.Tensor, M: int, *, stream=None,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    """Per-graph d lambda*_g/d w scaled by grad_lambda[g] (``ocm_backward_batch``)."""
+    lib = _native.load()
+    gl = grad_lambda.reshape(-1).to(dtype=torch.float32).contiguous()
+    G = sol.graph_vptr.numel() - 1
+    if gl.numel() != G:
+        raise ValueError("grad_lambda needs one entry per graph")
+    if out is None:
+        out = torch.empty(M, dtype=torch.float32, device=sol.cycle_out.device)
+    rc = lib.ocm_backward_batch(sol.graph_vptr.data_ptr(), sol.cycle_out.data_ptr(),
+                                sol.cycle_len.data_ptr(), gl.data_ptr(), G, M, out.data_ptr(),
+                                _stream_ptr(stream))
+    if rc != 0:
+        raise OCMError(rc, "ocm_backward_batch")
     return out
 
 

@@ -87,3 +87,17 @@ def test_batch_rejects_edges_between_graphs_and_bad_offsets():
     with pytest.raises(ocm.OCMError) as ei:
         _solve_batch(synth.Batch(vp, b.row_ptr, b.col_idx, b.w, b.mode))
     assert ei.value.status == -2
+
+
+def test_batch_backward_matches_per_graph_gradients():
+    graphs = synth.batch_graphs(G=20, nmin=50, nmax=3000)
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    gl = torch.arange(1, b.G + 1, dtype=torch.float32, device="cuda")
+    grad = ocm.backward_batch(sol, gl, b.M).cpu().numpy()
+    ref = np.zeros(b.M)
+    for g, gr in enumerate(graphs):
+        h = oracle.howard(gr.row_ptr, gr.col_idx, gr.w, gr.mode)
+        e0 = int(b.row_ptr[int(b.graph_vptr[g])])
+        ref[e0:e0 + gr.m] = (g + 1) * oracle.gradient(gr.m, h.cycle)
+    assert np.allclose(grad, ref, rtol=2**-22, atol=0)

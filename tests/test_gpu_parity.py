@@ -221,6 +221,22 @@ def test_error_codes():
     assert _status(lambda: gpu_solve(synth.ring10k(), max_iters=1)) == -5
 
 
+def test_bounded_wait_expires_cleanly():
+    """A grid barrier waits for an arrival that never comes (test flag): the
+    bounded wait must expire, the solve must report OCM_ERR_TIMEOUT, and the
+    device must stay usable for the next solve."""
+    g = synth.ring10k()
+    rp, col, w = _dev(g)
+    out = torch.full((g.n,), 77, dtype=torch.int32, device="cuda")
+    with pytest.raises(ocm.OCMError) as ei:
+        ocm.solve(rp, col, w, g.mode, flags=ocm.ocm.OCM_FLAG_TEST_STALL, cycle_out=out)
+    assert ei.value.status == -6
+    assert int(out[0]) == 77
+    sol = ocm.solve(rp, col, w, g.mode)
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert (sol.num, sol.den) == (h.num, h.den)
+
+
 def test_errors_leave_outputs_untouched():
     d = torch.device("cuda")
     rp = torch.tensor([0, 1, 1, 2], dtype=torch.int32, device=d)
