@@ -33,6 +33,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "edge-iters/s"
+LOCALITY_LOG2 = [25]     # --locality-log2 (smaller sizes for profiling captures)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -52,7 +53,7 @@ def _workloads():
                      "state-space product of 4 processes x 38-state rings + 2 chords/state, "
                      "BFS-numbered, 2,085,136 states, w U[0,1000], max"),
         "ring10k": (synth.ring10k, "ring + U{0..4} uniform extra edges, n=10,000, w U[1,100], max"),
-        "locality32m": (synth.locality32m,
+        "locality32m": (lambda: synth.locality32m(1 << LOCALITY_LOG2[0]),
                         "locality graph n=2^25, deg 4/16/64, targets i+1+|N(0,4096)|, "
                         "w U[-1000,1000], min"),
         "diff1m": (synth.diff1m_base, "ring + U{0..7} extra edges, n=2^20, w 1024*U[0,1000], max"),
@@ -546,8 +547,11 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2,
                     help="Howard iterations per reference (oracle) step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--locality-log2", type=int, default=25,
+                    help="log2 of the vertex count of the locality workload (default 25)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    LOCALITY_LOG2[0] = args.locality_log2
     if args.workload in BATCH_WORKLOADS and args.impl == "ours":
         return run_batch(args)
     if args.workload == "diff1m-grad" and args.impl == "ours":

@@ -77,6 +77,13 @@ typedef struct ocm_options {
     int32_t *eta_den;    /* optional device [n]                                     */
     int64_t *potential;  /* optional device [n]                                     */
     int32_t *policy;     /* optional device [n]: final policy edge of each vertex   */
+    /* Launch tuning of the improvement sweep (0 = library default: 8 edges
+     * per lane, 512 threads; see the autotuner in the Python package).  A vertex of out-degree d is served
+     * by the smallest power-of-two lane group g <= 32 with d <= edges_per_lane
+     * * g; sweep_threads is the sweep's block size (128, 256 or 512).  Results
+     * do not depend on these.                                                */
+    int32_t edges_per_lane;
+    int32_t sweep_threads;
 } ocm_options;
 
 /* Test-only: the first grid barrier of the evaluation waits for an arrival

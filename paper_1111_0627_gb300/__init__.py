@@ -3,6 +3,7 @@
 The compute path is the hand-written sm_103a CUDA library ``libocm.so``
 (C ABI in ``include/ocm.h``); this package builds it in-tree and binds it.
 """
+from . import autotune
 from ._native import build, load
 from .ocm import (OCM_MAX, OCM_MIN, BatchSolution, OCMError, OCMFunction, Solution, backward,
                   backward_batch,

@@ -79,7 +79,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 class OcmOptions(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("eta_num", ctypes.c_void_p), ("eta_den", ctypes.c_void_p),
-                ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p)]
+                ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
+                ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32)]
 
 
 class OcmStats(ctypes.Structure):

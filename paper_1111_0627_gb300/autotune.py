@@ -1,0 +1,111 @@
+"""Autotuner for the improvement sweep's launch parameters.
+
+The sweep serves a vertex of out-degree d with a group of g lanes (the
+smallest power of two with d <= edges_per_lane * g, at most 32) and runs in
+blocks of ``sweep_threads``.  Which combination is fastest depends on the
+degree distribution, so :func:`tune` runs one full solve per candidate on the
+caller's graph, reads the sweep kernels' time from the library's own CUDA-event
+instrumentation (``ocm_profile_*``), and keeps the fastest.  Results are
+cached per graph signature (size and degree buckets) in a JSON table
+(``OCM_TUNE_FILE``, default ``~/.cache/ocm_gb300/tune.json``); ``solve(...,
+tune=True)`` looks the signature up.  The solver's results never depend on
+these parameters -- only its speed does.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+import threading
+
+import torch
+
+from . import _native
+
+CANDIDATES = [(epl, thr) for epl in (2, 4, 8, 16) for thr in (128, 256, 512)]
+SWEEP_CLASS = 1       # profiling class of the improvement sweep (include/ocm.h)
+_lock = threading.Lock()
+
+
+def table_path() -> str:
+    return os.environ.get("OCM_TUNE_FILE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "ocm_gb300", "tune.json"))
+
+
+def signature(row_ptr: torch.Tensor) -> str:
+    """Size and degree-shape buckets: log2 of n, of the mean degree (half
+    steps) and of the largest degree."""
+    deg = (row_ptr[1:] - row_ptr[:-1]).to(torch.float64)
+    n = int(deg.numel())
+    mean = float(deg.mean()) if n else 1.0
+    mx = float(deg.max()) if n else 1.0
+    return (f"n{math.ceil(math.log2(max(n, 2)))}_d{round(2 * math.log2(max(mean, 1.0)))}"
+            f"_x{math.ceil(math.log2(max(mx, 1.0)))}")
+
+
+def _load_table() -> dict:
+    try:
+        with open(table_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_table(tab: dict) -> None:
+    path = table_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(tab, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(row_ptr: torch.Tensor) -> tuple[int, int] | None:
+    with _lock:
+        entry = _load_table().get(signature(row_ptr))
+    return (int(entry["edges_per_lane"]), int(entry["sweep_threads"])) if entry else None
+
+
+def tune(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="max", *,
+         candidates=CANDIDATES, save: bool = True) -> dict:
+    """Time the sweep for every (edges_per_lane, sweep_threads) candidate and
+    record the fastest for this graph's signature."""
+    from .ocm import solve
+    lib = _native.load()
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    timings = {}
+    ref = None
+    ws = None
+    prev = lib.ocm_profile_enable(0)
+    try:
+        for epl, thr in candidates:
+            sol = solve(row_ptr, col_idx, w, mode, workspace=ws, edges_per_lane=epl,
+                        sweep_threads=thr)            # warm-up, and the result to compare
+            if ws is None:
+                from .ocm import make_workspace
+                ws = make_workspace(row_ptr.numel() - 1, col_idx.numel(), row_ptr.device)
+            if ref is None:
+                ref = (sol.num, sol.den)
+            elif (sol.num, sol.den) != ref:
+                raise RuntimeError("launch parameters changed the result")
+            lib.ocm_profile_enable(1)
+            lib.ocm_profile_collect(None, None)
+            solve(row_ptr, col_idx, w, mode, workspace=ws, edges_per_lane=epl, sweep_threads=thr)
+            lib.ocm_profile_collect(ms, cnt)
+            lib.ocm_profile_enable(0)
+            timings[f"{epl}x{thr}"] = ms[SWEEP_CLASS] / max(cnt[SWEEP_CLASS], 1)
+    finally:
+        lib.ocm_profile_enable(prev)
+    best = min(timings, key=timings.get)
+    epl, thr = (int(x) for x in best.split("x"))
+    result = {"edges_per_lane": epl, "sweep_threads": thr, "sweep_ms": timings[best],
+              "timings_ms": timings, "signature": signature(row_ptr)}
+    if save:
+        with _lock:
+            tab = _load_table()
+            tab[result["signature"]] = {k: result[k] for k in ("edges_per_lane", "sweep_threads",
+                                                               "sweep_ms")}
+            _save_table(tab)
+    return result

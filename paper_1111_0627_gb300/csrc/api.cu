@@ -267,7 +267,10 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     //    classes of the improvement sweep
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, bs ? &b : nullptr, st);
     launches += 1;
-    launches += launch_classify(row_ptr, n, ws, st);
+    int epl = (opt && opt->edges_per_lane > 0) ? opt->edges_per_lane : kEdgesPerLane;
+    if (epl > 64) epl = 64;
+    const int sweep_threads = (opt && opt->sweep_threads > 0) ? opt->sweep_threads : kSweepThreads;
+    launches += launch_classify(row_ptr, n, epl, ws, st);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -291,7 +294,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         const int le = launch_evaluate(n, N2, ws, (int)it, stall, b, st);
         if (le < 0) return OCM_ERR_CUDA;
         launches += le;
-        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, b, st);
+        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, b, sweep_threads, st);
         launches += 1;
         if (bs) launches += launch_batch_converge((int)it + 1, b, ws, st);
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;

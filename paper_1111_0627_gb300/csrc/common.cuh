@@ -21,7 +21,9 @@ constexpr int kEvalThreads = 1024;     // block size of the persistent evaluatio
 // group of 2^c lanes; a vertex of out-degree d belongs to the smallest class
 // with d <= kEdgesPerLane * 2^c (the last class takes everything larger).
 constexpr int kClasses = 6;
-constexpr int kEdgesPerLane = 4;
+constexpr int kEdgesPerLane = 8;       // default; ocm_options.edges_per_lane overrides
+constexpr int kSweepMaxThreads = 512;  // largest sweep block (ocm_options.sweep_threads)
+constexpr int kSweepThreads = 512;     // default sweep block
 constexpr int kClassifyBlock = 1024;   // vertices per classification block
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
@@ -176,9 +178,10 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, const BatchState *bs, cudaStream_t st);
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st);
+                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, int threads,
+                  cudaStream_t st);
 int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st);
-int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st);
+int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall_test,
                     BatchState bs, cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);

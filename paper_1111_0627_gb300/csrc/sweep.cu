@@ -120,19 +120,19 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 // when degrees are skewed.  The partition is computed once per solve (the
 // graph does not change), stable within each class, in three passes:
 // per-block counts, one exclusive scan, and a scatter.
-static __device__ __forceinline__ int degree_class(int d) {
+static __device__ __forceinline__ int degree_class(int d, int epl) {
     int c = 0;
-    while (c < kClasses - 1 && d > (kEdgesPerLane << c)) ++c;
+    while (c < kClasses - 1 && d > (epl << c)) ++c;
     return c;
 }
 
 __global__ void __launch_bounds__(kClassifyBlock)
-classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, Workspace ws) {
+classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, Workspace ws) {
     __shared__ int s_cnt[kClasses];
     if (threadIdx.x < kClasses) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
-    if (v < n) atomicAdd(&s_cnt[degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]))], 1);
+    if (v < n) atomicAdd(&s_cnt[degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]), epl)], 1);
     __syncthreads();
     if (threadIdx.x < kClasses) ws.cls_hist[threadIdx.x * nb + blockIdx.x] = s_cnt[threadIdx.x];
 }
@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace w
 }
 
 __global__ void __launch_bounds__(kClassifyBlock)
-classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, Workspace ws) {
+classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, Workspace ws) {
     __shared__ int s_wcnt[kClassifyBlock / 32][kClasses];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
-    const int c = (v < n) ? degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v])) : -1;
+    const int c = (v < n) ? degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]), epl) : -1;
     int my_rank = 0;
 #pragma unroll
     for (int k = 0; k < kClasses; ++k) {
@@ -204,12 +204,12 @@ classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, Workspac
     }
 }
 
-int launch_classify(const int *row_ptr, int n, Workspace ws, cudaStream_t st) {
+int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st) {
     const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
     prof_begin(kProfInit, st);
-    classify_count_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, ws);
+    classify_count_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     classify_scan_kernel<<<1, 1024, 0, st>>>(nb, ws);
-    classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, ws);
+    classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     prof_end(kProfInit, st);
     return 3;
 }
@@ -250,7 +250,7 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
     return Cand{r.z, e, (long long)r.w * (long long)(sign * x) + V};
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kSweepMaxThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, int next_eval,
                Workspace ws, BatchState bs) {
@@ -358,7 +358,8 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
 }
 
 void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, cudaStream_t st) {
+                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, int threads,
+                  cudaStream_t st) {
     ClassGrid cg;
     int tasks = 0;
     for (int c = 0; c < kClasses; ++c) {
@@ -368,20 +369,23 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
     }
     cg.task_off[kClasses] = tasks;
     if (tasks == 0) return;
-    static int grid_dev = -1, grid_blocks = 0;
+    if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
+    static int grid_dev = -1, grid_threads = 0, grid_blocks = 0;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev != grid_dev) {
+    if (dev != grid_dev || threads != grid_threads) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, threads, 0);
         grid_blocks = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
         grid_dev = dev;
+        grid_threads = threads;
     }
-    int blocks = (tasks + (kThreads / 32) - 1) / (kThreads / 32);
+    const int wpb = threads / 32;
+    int blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n, cg, next_eval, ws, bs);
+    improve_kernel<<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, next_eval, ws, bs);
     prof_end(kProfSweep, st);
 }
 

@@ -182,6 +182,25 @@ def test_unaligned_input_slices():
         assert sol.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle]
 
 
+def test_launch_parameters_do_not_change_results(tmp_path, monkeypatch):
+    """Every sweep launch configuration gives the same bits; the autotuner
+    picks one of them and records it for the graph's signature."""
+    monkeypatch.setenv("OCM_TUNE_FILE", str(tmp_path / "tune.json"))
+    g = synth.locality32m(1 << 16)
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    rp, col, w = _dev(g)
+    for epl in (1, 2, 4, 8, 16, 64):
+        for thr in (128, 256, 512):
+            sol = ocm.solve(rp, col, w, g.mode, edges_per_lane=epl, sweep_threads=thr)
+            assert (sol.num, sol.den) == (h.num, h.den)
+            assert sol.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle]
+    res = ocm.autotune.tune(rp, col, w, g.mode, candidates=[(2, 256), (8, 128)])
+    assert (res["edges_per_lane"], res["sweep_threads"]) in [(2, 256), (8, 128)]
+    assert ocm.autotune.lookup(rp) == (res["edges_per_lane"], res["sweep_threads"])
+    sol = ocm.solve(rp, col, w, g.mode, tune=True)
+    assert (sol.num, sol.den) == (h.num, h.den)
+
+
 def test_determinism_bitwise():
     g = synth.ring10k()
     a = gpu_solve(g, certificate=True)
