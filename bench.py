@@ -194,6 +194,34 @@ def algorithmic_bytes(cls: str, n: int, m: int, st_total: dict, launches: int) -
 
 CLASSES = ["init", "sweep", "evaluate", "extract"]
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of each kernel, with the sha256 prefix of the kernel's sources at the time
+# (see profiles/).  Reported only while the sources are unchanged.
+KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "common.cuh"), "sweep": ("sweep.cu", "common.cuh")}
+TRAFFIC = {
+    ("product4", "evaluate"): (55.685632e6 + 191.421952e6, "7891324909054910"),
+    ("product4", "sweep"): (280.18304e6 + 26.435072e6, "cee65ad30d99d374"),
+}
+
+
+def _source_hash(kernel: str) -> str | None:
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1111_0627_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str):
+    entry = TRAFFIC.get((workload, kernel))
+    if entry is None or _source_hash(kernel) != entry[1]:
+        return None
+    return entry[0]
+
 
 def run_ours(args, g, desc):
     import ctypes
@@ -281,7 +309,8 @@ def run_ours(args, g, desc):
     achieved = d["gbs"]
     roofline = {"bound": "hbm", "kernel": dom,
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": measured_traffic(args.workload, dom),
                 "peak_kind": peak_kind,
                 "avg_launch_us": d["ms_total"] * 1e3 / max(d["launches"], 1),
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(d["launches"], 1)}
