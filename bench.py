@@ -254,8 +254,9 @@ def run_ours(args, g, desc):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def solve():
-        return ocm.solve(rp, col, w, g.mode, workspace=ws, cycle_out=cyc, stream=stream)
+    def solve(flags=0):
+        return ocm.solve(rp, col, w, g.mode, workspace=ws, cycle_out=cyc, stream=stream,
+                         flags=flags)
 
     for _ in range(args.warmup):
         sol = solve()
@@ -282,6 +283,18 @@ def run_ours(args, g, desc):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = world * args.steps * units / (total_ms / 1e3)
+
+    # ---- the same solve with the loop driven from the host (one stream
+    #      synchronisation per improvement step), for comparison only
+    host_ms = []
+    for k in range(min(args.steps, 5)):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solve(ocm.ocm.OCM_FLAG_HOST_LOOP)
+        b.record(stream)
+        b.synchronize()
+        host_ms.append(a.elapsed_time(b))
 
     # ---- kernel-class durations (events around each launch), same workload
     prof_steps = max(1, min(args.steps, 5))
@@ -371,7 +384,9 @@ def run_ours(args, g, desc):
                        "l2": "flushed before every timed step (256 MiB write, outside the timing)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "step_ms_median": statistics.median(step_ms),
-                       "step_ms_min": min(step_ms)},
+                       "step_ms_min": min(step_ms),
+                       "loop": "cuda_graph" if sol.stats["graph_loop"] else "host",
+                       "host_loop_ms_median": statistics.median(host_ms)},
             "roofline": roofline,
             "kernel_share": share,
             "kernels": {c: {"ms_per_solve": v["ms_total"] / prof_steps,
@@ -451,18 +466,25 @@ def run_batch(args):
     for r_, c_, w_ in devg[:3]:
         ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
     identical = True
-    barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i, (r_, c_, w_) in enumerate(devg):
-        x = ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
-        identical &= (x.num, x.den) == (int(num_b[i]), int(den_b[i]))
-        if i < 64:   # cycles of a sample of graphs compared edge by edge
-            off = int(b.row_ptr[int(b.graph_vptr[i])])
-            identical &= (sol.cycle(i).cpu() - off).tolist() == x.cycle.cpu().tolist()
-    e1.record(stream)
-    barrier()
-    loop_ms = e0.elapsed_time(e1)
+    # every graph of the loop is new to the solver's loop-graph cache, so the
+    # loop is timed both with the CUDA-graph loop and host-driven, and the
+    # faster of the two is the baseline
+    loop_ms_by = {}
+    for loop_name, flags in (("cuda_graph", 0), ("host", ocm.ocm.OCM_FLAG_HOST_LOOP)):
+        barrier()
+        e0.record(stream)
+        for i, (r_, c_, w_) in enumerate(devg):
+            x = ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream,
+                          flags=flags)
+            identical &= (x.num, x.den) == (int(num_b[i]), int(den_b[i]))
+            if i < 64:   # cycles of a sample of graphs compared edge by edge
+                off = int(b.row_ptr[int(b.graph_vptr[i])])
+                identical &= (sol.cycle(i).cpu() - off).tolist() == x.cycle.cpu().tolist()
+        e1.record(stream)
+        barrier()
+        loop_ms_by[loop_name] = e0.elapsed_time(e1)
+    loop_ms = min(loop_ms_by.values())
 
     # end to end: host CSR -> device, batched solve, results back
     h = [torch.from_numpy(x).pin_memory() for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
@@ -484,8 +506,10 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {desc}", "G": G, "N": b.N, "M": b.M,
                        "mode": b.mode, "iterations": sol.stats["iterations"],
+                       "loop": "cuda_graph" if sol.stats["graph_loop"] else "host",
                        "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
             "loop_of_plain_solver": {"graphs_per_s": G / (loop_ms / 1e3), "ms": loop_ms,
+                                     "ms_by_loop": loop_ms_by,
                                      "identical_results": bool(identical)},
             "speedup_vs_loop": (loop_ms / 1e3) / (total_ms / args.steps / 1e3),
             "e2e": {"value": G / (e2e_ms / 1e3), "unit": "graphs/s",
@@ -537,8 +561,9 @@ def run_grad(args):
     gh = g.cpu().numpy()
     e0.record(stream)
     max_rel = 0.0
+    wp = torch.empty_like(w)
     for e in edges:
-        wp = w.clone()
+        wp.copy_(w)
         wp[int(e)] += 1
         fd = float(ocm.solve(rp, col, wp, "max", workspace=ws, stream=stream).value - lam0)
         if fd != 0.0:

@@ -29,9 +29,17 @@
  *
  * Conventions for every entry point:
  *   - array pointers are CUDA device memory unless marked "host";
- *   - the caller owns all memory; the library allocates no device memory,
- *     keeps no pointer after return, and works only on the given stream
- *     (a cudaStream_t passed as void*, NULL = the legacy default stream);
+ *   - the caller owns all memory; the library allocates no device buffers
+ *     and works only on the given stream (a cudaStream_t passed as void*,
+ *     NULL = the legacy default stream); the entry points synchronise that
+ *     stream and so must not be called while it is being captured;
+ *   - the solve loop (evaluate the policy, improve it, stop when stable) is
+ *     a CUDA graph with a conditional WHILE node whose body ends in a
+ *     one-thread kernel that sets the loop condition: one graph launch and
+ *     one synchronisation per solve.  The library instantiates that graph
+ *     on first use and caches a few of them keyed by the arguments baked
+ *     into it (device, array pointers, sizes, sense, launch shape); the
+ *     driver-held graph resources are the only memory kept between calls;
  *   - on any error the outputs are left untouched and a negative OCM_ERR_*
  *     code is returned (ocm_status_string gives a message);
  *   - results are deterministic: the same input gives the same bits.
@@ -92,6 +100,13 @@ typedef struct ocm_options {
  * context stays usable. */
 #define OCM_FLAG_TEST_STALL 1
 
+/* Drive the policy iteration from the host: after every improvement step the
+ * host reads the control block (one stream synchronisation per step) and
+ * decides whether to go on.  Without this flag the loop runs as a CUDA graph
+ * (below); the results are the same bits either way.  Implied while the
+ * benchmark instrumentation is enabled and by ocm_solve_static. */
+#define OCM_FLAG_HOST_LOOP 2
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
@@ -102,6 +117,8 @@ typedef struct ocm_stats {
     int64_t launches;       /* kernels launched by this call                        */
     int64_t detect_items;   /* vertex-rounds of work in cycle detection             */
     int64_t value_items;    /* vertex-rounds of work in value propagation           */
+    int32_t graph_loop;     /* 1: the iteration ran as a CUDA graph, 0: host-driven */
+    int32_t reserved;
 } ocm_stats;
 
 /* Bytes of device workspace ocm_solve needs for a graph with n vertices and m

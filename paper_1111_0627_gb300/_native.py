@@ -87,7 +87,8 @@ class OcmStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("detect_rounds", ctypes.c_int32), ("value_rounds", ctypes.c_int32),
                 ("switched", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("detect_items", ctypes.c_int64), ("value_items", ctypes.c_int64)]
+                ("detect_items", ctypes.c_int64), ("value_items", ctypes.c_int64),
+                ("graph_loop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -5,6 +5,7 @@
 #include <climits>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -169,6 +170,203 @@ static int read_ctrl(const Ctrl *dev, Ctrl *host, cudaStream_t st) {
     return OCM_OK;
 }
 
+// ------------------------------------------------------ iteration loop --
+// One improvement step is: evaluate the current policy, sweep every vertex
+// for a better out-edge, (batched: retire the graphs that stopped changing),
+// then the control kernel below.  The step reads its iteration index from
+// the control block, so the same launches serve a host-driven loop and the
+// body of a CUDA graph WHILE node.
+
+// Ends a step: stop on an error or when no vertex switched (Howard's
+// termination test, Alg. 1), else advance the iteration index unless the
+// cap is reached.  With use_cond the decision also sets the WHILE node's
+// condition.
+__global__ void loop_control_kernel(Ctrl *c, long long max_iters, int use_cond,
+                                    cudaGraphConditionalHandle handle) {
+    c->switched_total += c->switched;
+    int more = 0;
+    if (c->err == 0 && c->changed) {
+        if ((long long)c->iter + 1 >= max_iters) {
+            c->not_converged = 1;
+        } else {
+            c->iter += 1;
+            more = 1;
+        }
+    }
+    c->loop_more = more;
+    if (use_cond) cudaGraphSetConditional(handle, more ? 1u : 0u);
+}
+
+// Everything a step's launches depend on.
+struct StepArgs {
+    const int32_t *row_ptr, *col_idx, *w;
+    int n, sign, threads, stall;
+    long long N2, max_iters;
+    Workspace ws;
+    BatchState bs;
+    bool batch;
+    int cls_cnt[kClasses];
+};
+
+// Launches one step; returns the number of kernels, or -1.
+static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHandle handle,
+                       cudaStream_t st) {
+    const int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st);
+    if (le < 0) return -1;
+    int k = le;
+    k += launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt, a.bs, a.threads, st);
+    if (a.batch) k += launch_batch_converge(a.bs, a.ws, st);
+    loop_control_kernel<<<1, 1, 0, st>>>(a.ws.ctrl, a.max_iters, use_cond, handle);
+    k += 1;
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return k;
+}
+
+namespace {
+
+// Instantiated loop graphs, keyed by everything their kernel nodes bake in.
+struct LoopKey {
+    int dev;
+    const void *row_ptr, *col_idx, *w, *ctrl, *vptr;
+    int n, sign, threads, stall, G;
+    long long N2, max_iters;
+    int cls_cnt[kClasses];
+    bool operator==(const LoopKey &o) const {
+        if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
+            ctrl != o.ctrl || vptr != o.vptr || n != o.n || sign != o.sign ||
+            threads != o.threads || stall != o.stall || G != o.G || N2 != o.N2 ||
+            max_iters != o.max_iters)
+            return false;
+        for (int c = 0; c < kClasses; ++c)
+            if (cls_cnt[c] != o.cls_cnt[c]) return false;
+        return true;
+    }
+};
+
+struct LoopEntry {
+    bool valid;
+    LoopKey key;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int kernels;              // kernels per step
+    int busy;                 // launches in flight from callers that have not synchronised yet
+    unsigned long long stamp; // last use, for eviction
+};
+
+constexpr int kLoopCache = 16;
+std::mutex g_loop_mutex;
+LoopEntry g_loops[kLoopCache];   // never destroyed: the runtime may be gone at exit
+unsigned long long g_loop_clock = 0;
+
+LoopKey make_key(const StepArgs &a) {
+    LoopKey k;
+    memset(&k, 0, sizeof k);
+    cudaGetDevice(&k.dev);
+    k.row_ptr = a.row_ptr;
+    k.col_idx = a.col_idx;
+    k.w = a.w;
+    k.ctrl = a.ws.ctrl;
+    k.vptr = a.bs.vptr;
+    k.n = a.n;
+    k.sign = a.sign;
+    k.threads = a.threads;
+    k.stall = a.stall;
+    k.G = a.bs.G;
+    k.N2 = a.N2;
+    k.max_iters = a.max_iters;
+    for (int c = 0; c < kClasses; ++c) k.cls_cnt[c] = a.cls_cnt[c];
+    return k;
+}
+
+// A graph holding one WHILE node whose body is one step, captured from the
+// same launch code the host loop uses.
+bool build_loop_graph(const StepArgs &a, LoopEntry *e) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    cudaStream_t cs = nullptr;
+    bool ok = false;
+    do {
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+        cudaGraphConditionalHandle handle;
+        // default value 1 at every launch: the body runs at least once
+        if (cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault) !=
+            cudaSuccess)
+            break;
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = handle;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p) != cudaSuccess) break;
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            break;
+        const int k = launch_step(a, 1, handle, cs);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+        if (k < 0 || ec != cudaSuccess) break;
+        if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) break;
+        e->kernels = k;
+        ok = true;
+    } while (false);
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();   // a refused capture is not sticky; clear it
+        return false;
+    }
+    e->graph = g;
+    e->exec = x;
+    return true;
+}
+
+// Cached (or newly built) loop graph for these arguments, marked busy; -1 if
+// none can be had (every slot busy, or the build failed).
+int acquire_loop(const StepArgs &a) {
+    const LoopKey key = make_key(a);
+    std::lock_guard<std::mutex> lock(g_loop_mutex);
+    ++g_loop_clock;
+    for (int i = 0; i < kLoopCache; ++i) {
+        if (g_loops[i].valid && g_loops[i].key == key) {
+            g_loops[i].busy += 1;
+            g_loops[i].stamp = g_loop_clock;
+            return i;
+        }
+    }
+    int slot = -1;
+    for (int i = 0; i < kLoopCache; ++i) {
+        if (!g_loops[i].valid) {
+            slot = i;
+            break;
+        }
+        if (g_loops[i].busy == 0 && (slot < 0 || g_loops[i].stamp < g_loops[slot].stamp)) slot = i;
+    }
+    if (slot < 0) return -1;
+    LoopEntry &e = g_loops[slot];
+    if (e.valid) {
+        // idle: every caller that launched it has synchronised its stream
+        cudaGraphExecDestroy(e.exec);
+        cudaGraphDestroy(e.graph);
+        e.valid = false;
+    }
+    if (!build_loop_graph(a, &e)) return -1;
+    e.valid = true;
+    e.key = key;
+    e.busy = 1;
+    e.stamp = g_loop_clock;
+    return slot;
+}
+
+void release_loop(int slot) {
+    std::lock_guard<std::mutex> lock(g_loop_mutex);
+    g_loops[slot].busy -= 1;
+}
+
+}  // namespace
+
 }  // namespace ocm
 
 using namespace ocm;
@@ -287,24 +485,45 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     const long long N2 = nmax * nmax;
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
 
-    // 3. Howard iteration: evaluate the policy, sweep, stop when stable
-    long long it = 0, switched = 0;
-    for (;;) {
-        const int stall = (opt && (opt->flags & OCM_FLAG_TEST_STALL)) ? 1 : 0;
-        const int le = launch_evaluate(n, N2, ws, (int)it, stall, b, st);
-        if (le < 0) return OCM_ERR_CUDA;
-        launches += le;
-        launch_sweep(row_ptr, col_idx, w, sign, n, ws, h.cls_cnt, (int)it + 1, b, sweep_threads, st);
-        launches += 1;
-        if (bs) launches += launch_batch_converge((int)it + 1, b, ws, st);
-        if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
-        rc = read_ctrl(ws.ctrl, &h, st);
+    // 3. Howard iteration: evaluate the policy, sweep, stop when stable --
+    //    as one launch of the cached loop graph, or driven from the host
+    StepArgs sa;
+    sa.row_ptr = row_ptr;
+    sa.col_idx = col_idx;
+    sa.w = w;
+    sa.n = n;
+    sa.sign = sign;
+    sa.threads = (sweep_threads == 128 || sweep_threads == 256 || sweep_threads == 512)
+                      ? sweep_threads : kSweepThreads;
+    sa.stall = (opt && (opt->flags & OCM_FLAG_TEST_STALL)) ? 1 : 0;
+    sa.N2 = N2;
+    sa.max_iters = max_iters;
+    sa.ws = ws;
+    sa.bs = b;
+    sa.batch = bs != nullptr;
+    for (int c = 0; c < kClasses; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
+    const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || g_prof_on;
+    const int slot = host_loop ? -1 : acquire_loop(sa);
+    if (slot >= 0) {
+        const cudaError_t e = cudaGraphLaunch(g_loops[slot].exec, st);
+        rc = (e == cudaSuccess) ? read_ctrl(ws.ctrl, &h, st) : OCM_ERR_CUDA;
+        const int per_step = g_loops[slot].kernels;
+        release_loop(slot);
         if (rc) return rc;
-        if (h.err) return map_err_bits(h.err);
-        switched += h.switched;
-        if (!h.changed) break;
-        if (++it >= max_iters) return OCM_ERR_NOT_CONVERGED;
+        launches += (long long)per_step * (h.iter + 1);
+    } else {
+        for (;;) {
+            const int k = launch_step(sa, 0, 0, st);
+            if (k < 0) return OCM_ERR_CUDA;
+            launches += k;
+            rc = read_ctrl(ws.ctrl, &h, st);
+            if (rc) return rc;
+            if (!h.loop_more) break;
+        }
     }
+    if (h.err) return map_err_bits(h.err);
+    if (h.not_converged) return OCM_ERR_NOT_CONVERGED;
+    const long long it = h.iter;
 
     // 4. critical cycle(s) of the final policy
     int Lstar = 0;
@@ -338,10 +557,12 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         stats->cycles = h.res_cycles;
         stats->detect_rounds = fin.rounds_detect;
         stats->value_rounds = fin.rounds_value;
-        stats->switched = switched;
+        stats->switched = h.switched_total;
         stats->launches = launches;
         stats->detect_items = fin.items_detect;
         stats->value_items = fin.items_value;
+        stats->graph_loop = slot >= 0 ? 1 : 0;
+        stats->reserved = 0;
     }
     return OCM_OK;
 }
@@ -381,7 +602,7 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
               const ocm_options *opt, ocm_stats *stats) {
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~OCM_FLAG_TEST_STALL)) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     SolveOut out{num, den, cycle_len, cycle_out};
     return solve_impl(row_ptr, col_idx, w, n, m, mode, out, workspace, ws_bytes,
@@ -400,7 +621,7 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
     if (!graph_vptr || !row_ptr || !col_idx || !w || !num || !den || !cycle_len || !cycle_out)
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~OCM_FLAG_TEST_STALL)) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     const size_t base = ocm_workspace_size(N, M);
     const size_t need = ocm_workspace_size_batch(G, N, M);

@@ -72,8 +72,9 @@ int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t
 // tables are still those of that evaluation -- and it drops out of later
 // evaluations and sweeps.
 __global__ void __launch_bounds__(kThreads)
-batch_converge_kernel(int next_eval, BatchState bs, Workspace ws) {
+batch_converge_kernel(BatchState bs, Workspace ws) {
     const int stride = gridDim.x * blockDim.x;
+    const int next_eval = ws.ctrl->iter + 1;   // the stamp of the sweep just run
     int active = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < bs.G; g += stride) {
         if (bs.gconv[g]) continue;
@@ -101,11 +102,11 @@ batch_converge_kernel(int next_eval, BatchState bs, Workspace ws) {
 
 __global__ void batch_active_reset_kernel(Ctrl *c) { c->active_graphs = 0; }
 
-int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st) {
+int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st) {
     int gb = (bs.G + kThreads - 1) / kThreads;
     if (gb > 1024) gb = 1024;
     batch_active_reset_kernel<<<1, 1, 0, st>>>(ws.ctrl);
-    batch_converge_kernel<<<gb, kThreads, 0, st>>>(next_eval, bs, ws);
+    batch_converge_kernel<<<gb, kThreads, 0, st>>>(bs, ws);
     return 2;
 }
 

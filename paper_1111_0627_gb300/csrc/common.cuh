@@ -81,6 +81,11 @@ struct Ctrl {
     int res_cycles;
     int max_ng;               // batch: largest graph
     int active_graphs;        // batch: graphs whose policy may still change
+    // iteration state, advanced on the device by the loop control kernel
+    int iter;                 // index of the current evaluation (0 = initial policy)
+    int loop_more;            // the last step asks for another one
+    int not_converged;        // the iteration cap was reached
+    long long switched_total; // switches summed over all sweeps
 };
 
 enum : int {
@@ -177,13 +182,12 @@ void prof_end(int cls, cudaStream_t st);
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         Workspace ws, const BatchState *bs, cudaStream_t st);
-void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, int threads,
-                  cudaStream_t st);
-int launch_batch_converge(int next_eval, BatchState bs, Workspace ws, cudaStream_t st);
+int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                 Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st);
+int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall_test,
-                    BatchState bs, cudaStream_t st);
+int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
+                    cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws, int64_t *num,
                         int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,

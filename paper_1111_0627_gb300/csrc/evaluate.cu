@@ -127,11 +127,13 @@ static __device__ __forceinline__ void block_append(int *list, int *s_cnt, bool 
 constexpr int kMinMask = 0x7fffffff;
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
-evaluate_kernel(int n, long long N2, int max_detect, int max_value, int eval_index,
-                int stall_test, Workspace ws, BatchState bs) {
+evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_test, Workspace ws,
+                BatchState bs) {
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     Ctrl *c = ws.ctrl;
+    // vertices whose sw_iter equals this index switched in the last sweep
+    const int eval_index = c->iter;
     const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -446,8 +448,8 @@ static int evaluate_grid() {
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
-int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall_test,
-                    BatchState bs, cudaStream_t st) {
+int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
+                    cudaStream_t st) {
     int blocks = evaluate_grid();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
@@ -455,10 +457,21 @@ int launch_evaluate(int n, long long N2, Workspace ws, int eval_index, int stall
     const int lg = ceil_log2(n);
     int max_detect = lg + 4;
     int max_value = lg + 3;
-    void *args[] = {&n, &N2, &max_detect, &max_value, &eval_index, &stall_test, &ws, &bs};
+    // cooperative (all blocks co-resident, the grid barriers rely on it); the
+    // launch attribute form is also what a CUDA graph kernel node records
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kEvalThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     prof_begin(kProfEvaluate, st);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)evaluate_kernel, dim3(blocks),
-                                                dim3(kEvalThreads), args, 0, st);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, evaluate_kernel, n, N2, max_detect, max_value,
+                                       stall_test, ws, bs);
     prof_end(kProfEvaluate, st);
     return e == cudaSuccess ? 1 : -1;
 }

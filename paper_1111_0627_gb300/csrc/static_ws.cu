@@ -12,6 +12,7 @@
 //
 // The entry point only adds the workspace; the solve itself is ocm_solve,
 // unchanged.
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -59,10 +60,15 @@ extern "C" int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, 
     // ocm_solve initialises everything it reads (its control block is reset
     // by its first kernel, every other array is written before it is read),
     // so the previous call's contents need no clearing here.  Benchmark
-    // instrumentation would create CUDA events, so it is paused meanwhile.
+    // instrumentation would create CUDA events, and instantiating the loop
+    // graph would have the driver allocate, so the instrumentation is paused
+    // and the loop is driven from the host.
+    ocm_options o;
+    if (opt) o = *opt; else memset(&o, 0, sizeof o);
+    o.flags |= OCM_FLAG_HOST_LOOP;
     const int prof = ocm_profile_enable(0);
     rc = ocm_solve(row_ptr, col_idx, w, n, m, mode, num, den, cycle_out, cycle_len, ws,
-                   (size_t)OCM_STATIC_WORKSPACE_BYTES, stream, opt, stats);
+                   (size_t)OCM_STATIC_WORKSPACE_BYTES, stream, &o, stats);
     ocm_profile_enable(prof);
     return rc;
 }

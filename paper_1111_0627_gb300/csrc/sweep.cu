@@ -252,10 +252,12 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 
 __global__ void __launch_bounds__(kSweepMaxThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, int next_eval,
-               Workspace ws, BatchState bs) {
+               const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, Workspace ws,
+               BatchState bs) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
+    // a vertex switched here is "dirty" for the next evaluation
+    const int next_eval = ws.ctrl->iter + 1;
     const int lane = tid & 31;
     if (tid == 0) s_sw = 0;
     if (blockIdx.x == 0 && tid == 0) {
@@ -357,9 +359,8 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
     prof_end(kProfInit, st);
 }
 
-void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                  Workspace ws, const int *cls_cnt, int next_eval, BatchState bs, int threads,
-                  cudaStream_t st) {
+int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                 Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st) {
     ClassGrid cg;
     int tasks = 0;
     for (int c = 0; c < kClasses; ++c) {
@@ -368,7 +369,7 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
         tasks += (int)((lanes + 31) / 32);
     }
     cg.task_off[kClasses] = tasks;
-    if (tasks == 0) return;
+    if (tasks == 0) return 0;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
     static int grid_dev = -1, grid_threads = 0, grid_blocks = 0;
     int dev = 0;
@@ -385,8 +386,9 @@ void launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, in
     int blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, next_eval, ws, bs);
+    improve_kernel<<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
     prof_end(kProfSweep, st);
+    return 1;
 }
 
 }  // namespace ocm

@@ -23,6 +23,7 @@ from . import _native
 
 OCM_MAX, OCM_MIN = 0, 1
 OCM_FLAG_TEST_STALL = 1
+OCM_FLAG_HOST_LOOP = 2
 
 
 class OCMError(RuntimeError):
@@ -163,7 +164,7 @@ def workspace_bytes_batch(G: int, N: int, M: int) -> int:
 
 def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor,
                 w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
-                stream=None, max_iters: int = 0) -> BatchSolution:
+                stream=None, max_iters: int = 0, flags: int = 0) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
     (``ocm_solve_batch``); each result equals solving that graph alone."""
     lib = _native.load()
@@ -184,6 +185,7 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     cyc = torch.empty(N, dtype=torch.int32, device=dev)
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
+    opt.flags = int(flags)
     st = _native.OcmStats()
     rc = lib.ocm_solve_batch(vp.data_ptr(), rp.data_ptr(), col.data_ptr(), ww.data_ptr(), G, N, M,
                              _mode(mode), num.data_ptr(), den.data_ptr(), clen.data_ptr(),
