@@ -86,13 +86,27 @@ typedef struct ocm_options {
     int64_t *potential;  /* optional device [n]                                     */
     int32_t *policy;     /* optional device [n]: final policy edge of each vertex   */
     /* Launch tuning of the improvement sweep (0 = library default: 8 edges
-     * per lane, 512 threads; see the autotuner in the Python package).  A vertex of out-degree d is served
-     * by the smallest power-of-two lane group g <= 32 with d <= edges_per_lane
-     * * g; sweep_threads is the sweep's block size (128, 256 or 512).  Results
-     * do not depend on these.                                                */
+     * per lane, 512 threads; the Python package has an autotuner):
+     * edges_per_lane as described under OCM_SWEEP_* below, sweep_threads the
+     * sweep's block size (64 to 512, see there).  Results do not depend on
+     * these.                                                                 */
     int32_t edges_per_lane;
     int32_t sweep_threads;
+    int32_t sweep_kind;  /* OCM_SWEEP_*; 0 = library default (degree classes)      */
 } ocm_options;
+
+/* Layouts of the improvement sweep (results do not depend on the choice).
+ * OCM_SWEEP_TILES: the CSR edge array is cut into aligned tiles of 32 *
+ *   edges_per_lane edges (edges_per_lane 4 or 8; default 8), one warp per
+ *   tile, each lane scanning consecutive edges; vertices crossing lanes or
+ *   tiles are joined by a segmented scan and a fix-up pass.  Blocks of 64,
+ *   128 or 256 threads (512 runs as 256).
+ * OCM_SWEEP_CLASSES: vertices grouped by degree class; a vertex of out-degree
+ *   d is served by the smallest power-of-two lane group g <= 32 with
+ *   d <= edges_per_lane * g (edges_per_lane 1..64; default 8).             */
+#define OCM_SWEEP_DEFAULT 0
+#define OCM_SWEEP_CLASSES 1
+#define OCM_SWEEP_TILES 2
 
 /* Test-only: the first grid barrier of the evaluation waits for an arrival
  * that never comes, with its wait limit cut to about 10 ms, so the solve

@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
-SOURCES = ["sweep.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu"]
+SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -80,7 +80,8 @@ class OcmOptions(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("eta_num", ctypes.c_void_p), ("eta_den", ctypes.c_void_p),
                 ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
-                ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32)]
+                ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
+                ("sweep_kind", ctypes.c_int32)]
 
 
 class OcmStats(ctypes.Structure):

@@ -1,15 +1,18 @@
-"""Autotuner for the improvement sweep's launch parameters.
+"""Autotuner for the improvement sweep's layout and launch parameters.
 
-The sweep serves a vertex of out-degree d with a group of g lanes (the
-smallest power of two with d <= edges_per_lane * g, at most 32) and runs in
+The sweep has two layouts.  Edge tiles: the CSR edge array is cut into tiles
+of 32 * edges_per_lane edges, one warp each (edges_per_lane 4 or 8).
+Degree classes: a vertex of out-degree d is served by a group of g lanes (the
+smallest power of two with d <= edges_per_lane * g, at most 32).  Both run in
 blocks of ``sweep_threads``.  Which combination is fastest depends on the
-degree distribution, so :func:`tune` runs one full solve per candidate on the
-caller's graph, reads the sweep kernels' time from the library's own CUDA-event
-instrumentation (``ocm_profile_*``), and keeps the fastest.  Results are
-cached per graph signature (size and degree buckets) in a JSON table
-(``OCM_TUNE_FILE``, default ``~/.cache/ocm_gb300/tune.json``); ``solve(...,
-tune=True)`` looks the signature up.  The solver's results never depend on
-these parameters -- only its speed does.
+degree distribution and on how local the targets are, so :func:`tune` runs
+one full solve per candidate on the caller's graph, reads the sweep kernels'
+time from the library's own CUDA-event instrumentation (``ocm_profile_*``),
+and keeps the fastest.  Results are cached per graph signature (size and
+degree buckets) in a JSON table (``OCM_TUNE_FILE``, default
+``~/.cache/ocm_gb300/tune.json``); ``solve(..., tune=True)`` looks the
+signature up.  The solver's results never depend on these parameters -- only
+its speed does.
 """
 from __future__ import annotations
 
@@ -23,7 +26,9 @@ import torch
 
 from . import _native
 
-CANDIDATES = [(epl, thr) for epl in (2, 4, 8, 16) for thr in (128, 256, 512)]
+TILES, CLASSES = 2, 1   # OCM_SWEEP_TILES, OCM_SWEEP_CLASSES (include/ocm.h)
+CANDIDATES = ([(TILES, epl, thr) for epl in (4, 8) for thr in (64, 128, 256)] +
+              [(CLASSES, epl, thr) for epl in (2, 4, 8, 16) for thr in (128, 256, 512)])
 SWEEP_CLASS = 1       # profiling class of the improvement sweep (include/ocm.h)
 _lock = threading.Lock()
 
@@ -61,16 +66,18 @@ def _save_table(tab: dict) -> None:
     os.replace(tmp, path)
 
 
-def lookup(row_ptr: torch.Tensor) -> tuple[int, int] | None:
+def lookup(row_ptr: torch.Tensor) -> tuple[int, int, int] | None:
     with _lock:
         entry = _load_table().get(signature(row_ptr))
-    return (int(entry["edges_per_lane"]), int(entry["sweep_threads"])) if entry else None
+    if not entry or "sweep_kind" not in entry:
+        return None
+    return int(entry["sweep_kind"]), int(entry["edges_per_lane"]), int(entry["sweep_threads"])
 
 
 def tune(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="max", *,
          candidates=CANDIDATES, save: bool = True) -> dict:
-    """Time the sweep for every (edges_per_lane, sweep_threads) candidate and
-    record the fastest for this graph's signature."""
+    """Time the sweep for every (sweep_kind, edges_per_lane, sweep_threads)
+    candidate and record the fastest for this graph's signature."""
     from .ocm import solve
     lib = _native.load()
     ms = (ctypes.c_double * 4)()
@@ -80,9 +87,9 @@ def tune(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="ma
     ws = None
     prev = lib.ocm_profile_enable(0)
     try:
-        for epl, thr in candidates:
+        for kind, epl, thr in candidates:
             sol = solve(row_ptr, col_idx, w, mode, workspace=ws, edges_per_lane=epl,
-                        sweep_threads=thr)            # warm-up, and the result to compare
+                        sweep_threads=thr, sweep_kind=kind)   # warm-up, and the result to compare
             if ws is None:
                 from .ocm import make_workspace
                 ws = make_workspace(row_ptr.numel() - 1, col_idx.numel(), row_ptr.device)
@@ -92,20 +99,21 @@ def tune(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="ma
                 raise RuntimeError("launch parameters changed the result")
             lib.ocm_profile_enable(1)
             lib.ocm_profile_collect(None, None)
-            solve(row_ptr, col_idx, w, mode, workspace=ws, edges_per_lane=epl, sweep_threads=thr)
+            solve(row_ptr, col_idx, w, mode, workspace=ws, edges_per_lane=epl, sweep_threads=thr,
+                  sweep_kind=kind)
             lib.ocm_profile_collect(ms, cnt)
             lib.ocm_profile_enable(0)
-            timings[f"{epl}x{thr}"] = ms[SWEEP_CLASS] / max(cnt[SWEEP_CLASS], 1)
+            timings[f"{kind}x{epl}x{thr}"] = ms[SWEEP_CLASS] / max(cnt[SWEEP_CLASS], 1)
     finally:
         lib.ocm_profile_enable(prev)
     best = min(timings, key=timings.get)
-    epl, thr = (int(x) for x in best.split("x"))
-    result = {"edges_per_lane": epl, "sweep_threads": thr, "sweep_ms": timings[best],
-              "timings_ms": timings, "signature": signature(row_ptr)}
+    kind, epl, thr = (int(x) for x in best.split("x"))
+    result = {"sweep_kind": kind, "edges_per_lane": epl, "sweep_threads": thr,
+              "sweep_ms": timings[best], "timings_ms": timings, "signature": signature(row_ptr)}
     if save:
         with _lock:
             tab = _load_table()
-            tab[result["signature"]] = {k: result[k] for k in ("edges_per_lane", "sweep_threads",
-                                                               "sweep_ms")}
+            tab[result["signature"]] = {k: result[k] for k in ("sweep_kind", "edges_per_lane",
+                                                               "sweep_threads", "sweep_ms")}
             _save_table(tab)
     return result

@@ -14,10 +14,11 @@ namespace ocm {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-size_t carve_workspace(void *base, int n, Workspace *ws) {
+size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     char *b = static_cast<char *>(base);
     size_t off = 0;
     const size_t N = static_cast<size_t>(n);
+    const size_t T = (static_cast<size_t>(m) + kMinTileEdges - 1) / kMinTileEdges;
     auto take = [&](size_t bytes) -> void * {
         off = align_up(off, 256);
         void *p = b ? b + off : nullptr;
@@ -47,6 +48,11 @@ size_t carve_workspace(void *base, int n, Workspace *ws) {
     w.sw_iter = static_cast<int *>(take(4 * N));
     w.cls_list = static_cast<int *>(take(4 * N));
     w.cls_hist = static_cast<int *>(take(4 * (size_t)kClasses * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.tile_v = static_cast<int *>(take(4 * (T + 1)));
+    w.tile_pend = static_cast<int *>(take(4 * T));
+    w.tile_fopen = static_cast<int *>(take(4 * T));
+    w.tile_first = static_cast<TilePart *>(take(sizeof(TilePart) * T));
+    w.tile_last = static_cast<TilePart *>(take(sizeof(TilePart) * T));
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align_up(off, 256);
@@ -159,6 +165,7 @@ static int map_err_bits(int err) {
     if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
     if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
     if (err & kErrWeightMin) return OCM_ERR_OVERFLOW;
+    if (err & kErrSweep) return OCM_ERR_INTERNAL;
     if (err) return OCM_ERR_INTERNAL;
     return OCM_OK;
 }
@@ -200,7 +207,8 @@ __global__ void loop_control_kernel(Ctrl *c, long long max_iters, int use_cond,
 // Everything a step's launches depend on.
 struct StepArgs {
     const int32_t *row_ptr, *col_idx, *w;
-    int n, sign, threads, stall;
+    int n, m, sign, threads, stall;
+    int kind, epl;            // sweep layout (OCM_SWEEP_TILES or _CLASSES) and its lane load
     long long N2, max_iters;
     Workspace ws;
     BatchState bs;
@@ -213,8 +221,13 @@ static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHand
                        cudaStream_t st) {
     const int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st);
     if (le < 0) return -1;
-    int k = le;
-    k += launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt, a.bs, a.threads, st);
+    const int ks = (a.kind == OCM_SWEEP_TILES)
+                       ? launch_sweep_tiles(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.m, a.epl,
+                                            a.ws, a.bs, a.threads, st)
+                       : launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt,
+                                      a.bs, a.threads, st);
+    if (ks < 0) return -1;
+    int k = le + ks;
     if (a.batch) k += launch_batch_converge(a.bs, a.ws, st);
     loop_control_kernel<<<1, 1, 0, st>>>(a.ws.ctrl, a.max_iters, use_cond, handle);
     k += 1;
@@ -228,14 +241,14 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr;
-    int n, sign, threads, stall, G;
+    int n, m, sign, threads, stall, G, kind, epl;
     long long N2, max_iters;
     int cls_cnt[kClasses];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
-            ctrl != o.ctrl || vptr != o.vptr || n != o.n || sign != o.sign ||
-            threads != o.threads || stall != o.stall || G != o.G || N2 != o.N2 ||
-            max_iters != o.max_iters)
+            ctrl != o.ctrl || vptr != o.vptr || n != o.n || m != o.m || sign != o.sign ||
+            threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
+            epl != o.epl || N2 != o.N2 || max_iters != o.max_iters)
             return false;
         for (int c = 0; c < kClasses; ++c)
             if (cls_cnt[c] != o.cls_cnt[c]) return false;
@@ -268,6 +281,9 @@ LoopKey make_key(const StepArgs &a) {
     k.ctrl = a.ws.ctrl;
     k.vptr = a.bs.vptr;
     k.n = a.n;
+    k.m = a.m;
+    k.kind = a.kind;
+    k.epl = a.epl;
     k.sign = a.sign;
     k.threads = a.threads;
     k.stall = a.stall;
@@ -375,7 +391,7 @@ extern "C" {
 
 size_t ocm_workspace_size(int32_t n, int32_t m) {
     if (n < 1 || m < 1) return 0;
-    return carve_workspace(nullptr, n, nullptr);
+    return carve_workspace(nullptr, n, m, nullptr);
 }
 
 const char *ocm_status_string(int status) {
@@ -442,7 +458,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return OCM_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Workspace ws;
-    carve_workspace(workspace, n, &ws);
+    carve_workspace(workspace, n, m, &ws);
     const int sign = (mode == OCM_MAX) ? 1 : -1;
     const int grid = persistent_grid();
     long long launches = 0;
@@ -465,10 +481,16 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     //    classes of the improvement sweep
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, bs ? &b : nullptr, st);
     launches += 1;
+    const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES) ? OCM_SWEEP_TILES
+                                                                : OCM_SWEEP_CLASSES;
     int epl = (opt && opt->edges_per_lane > 0) ? opt->edges_per_lane : kEdgesPerLane;
     if (epl > 64) epl = 64;
+    if (kind == OCM_SWEEP_TILES) epl = epl <= 4 ? 4 : 8;
     const int sweep_threads = (opt && opt->sweep_threads > 0) ? opt->sweep_threads : kSweepThreads;
-    launches += launch_classify(row_ptr, n, epl, ws, st);
+    if (kind == OCM_SWEEP_TILES)
+        launches += launch_tile_index(row_ptr, n, m, 32 * epl, ws, st);
+    else
+        launches += launch_classify(row_ptr, n, epl, ws, st);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -492,9 +514,12 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.col_idx = col_idx;
     sa.w = w;
     sa.n = n;
+    sa.m = m;
+    sa.kind = kind;
+    sa.epl = epl;
     sa.sign = sign;
-    sa.threads = (sweep_threads == 128 || sweep_threads == 256 || sweep_threads == 512)
-                      ? sweep_threads : kSweepThreads;
+    sa.threads = (sweep_threads == 64 || sweep_threads == 128 || sweep_threads == 256 ||
+                  sweep_threads == 512) ? sweep_threads : kSweepThreads;
     sa.stall = (opt && (opt->flags & OCM_FLAG_TEST_STALL)) ? 1 : 0;
     sa.N2 = N2;
     sa.max_iters = max_iters;
@@ -502,6 +527,10 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.bs = b;
     sa.batch = bs != nullptr;
     for (int c = 0; c < kClasses; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
+    if (prepare_evaluate() != 0 ||
+        (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
+                                 : prepare_sweep_classes(sa.threads)) != 0)
+        return OCM_ERR_CUDA;
     const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || g_prof_on;
     const int slot = host_loop ? -1 : acquire_loop(sa);
     if (slot >= 0) {
@@ -603,6 +632,8 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))
+        return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     SolveOut out{num, den, cycle_len, cycle_out};
     return solve_impl(row_ptr, col_idx, w, n, m, mode, out, workspace, ws_bytes,
@@ -622,6 +653,8 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))
+        return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     const size_t base = ocm_workspace_size(N, M);
     const size_t need = ocm_workspace_size_batch(G, N, M);

@@ -97,6 +97,7 @@ enum : int {
     kErrValue = 32,       // value propagation did not finish in the round budget
     kErrExtract = 64,     // critical-cycle extraction inconsistent
     kErrTimeout = 128,    // a grid barrier wait exceeded its spin limit
+    kErrSweep = 256,      // a vertex's current policy edge was not among its edges
 };
 
 // Workspace carved from one caller-provided buffer.
@@ -119,7 +120,42 @@ struct Workspace {
     int *sw_iter;         // evaluation index after the sweep that last switched v
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan
+    // edge-tiled sweep: tile t covers edges [t*ET, (t+1)*ET)
+    int *tile_v;          // [T+1] source vertex of each tile's first edge
+    int *tile_pend;       // [T] vertex whose edges run past the tile's end and whose
+                          //     first edge lies in it (-1: none)
+    int *tile_fopen;      // [T] the tile's first vertex (begun in an earlier tile)
+                          //     still has edges after this tile
+    struct TilePart *tile_first;  // [T] best and current-edge key of that vertex in this tile
+    struct TilePart *tile_last;   // [T] the same for tile_pend's vertex, up to the tile's end
     Ctrl *ctrl;
+};
+
+// Candidate edge of the improvement sweep and its total order: larger
+// rank(t) first, then larger key q_t * s*w(e) + V(t), then smaller edge index
+// (the deterministic tie-break that makes the choice unique).
+struct Cand {
+    int rank;
+    int e;
+    long long key;
+};
+
+__device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
+    if (a.rank != b.rank) return a.rank > b.rank;
+    if (a.key != b.key) return a.key > b.key;
+    return a.e < b.e;
+}
+
+// The part of a vertex's sweep that one tile saw: the best candidate among
+// its edges there, and the key of its current policy edge if that edge lies
+// in the tile (crank = INT_MIN otherwise).
+struct __align__(16) TilePart {
+    int rank;
+    int e;
+    long long key;
+    int crank;
+    int pad;
+    long long ckey;
 };
 
 // Extra state of a batched solve (G graphs as one disjoint-union CSR);
@@ -140,7 +176,28 @@ struct BatchState {
 
 // Layout of the workspace for n vertices; returns total bytes and fills ws
 // when base != nullptr.
-size_t carve_workspace(void *base, int n, Workspace *ws);
+size_t carve_workspace(void *base, int n, int m, Workspace *ws);
+
+// Smallest tile of the edge-tiled sweep (32 lanes x 4 edges); the workspace
+// holds the per-tile arrays for this size, enough for every larger one.
+constexpr int kMinTileEdges = 128;
+
+// Block 0, thread 0 of every sweep: publish the best cycle of the evaluation
+// the sweep reads (the answer if nothing switches).  best is 0 only when that
+// evaluation stopped early on an error, which the host reports.
+__device__ __forceinline__ void publish_result(const Workspace &ws, int n) {
+    Ctrl *cc = ws.ctrl;
+    const unsigned long long bb = cc->best;
+    const int root = 0x7fffffff - (int)(unsigned)(bb & 0xffffffffu);
+    if (bb != 0 && root >= 0 && root < n) {
+        const int i = ws.cid_of_root[root];
+        cc->res_root = root;
+        cc->res_len = ws.cyc_L[i];
+        cc->res_num = ws.cyc_p[i];
+        cc->res_den = ws.cyc_q[i];
+        cc->res_cycles = cc->nrep;
+    }
+}
 
 __device__ __forceinline__ int warp_append(int *counter, bool pred, int lane) {
     unsigned mask = __ballot_sync(0xffffffffu, pred);
@@ -184,6 +241,17 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
                         Workspace ws, const BatchState *bs, cudaStream_t st);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st);
+int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspace ws,
+                      cudaStream_t st);
+// Host-side kernel configuration (shared-memory opt-in, occupancy), done
+// before the loop so that a captured loop graph holds launches only;
+// 0 on success.
+int prepare_evaluate();
+int prepare_sweep_classes(int threads);
+int prepare_sweep_tiles(int edges_per_lane, int threads);
+int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
+                       int edges_per_lane, Workspace ws, BatchState bs, int threads,
+                       cudaStream_t st);
 int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,

@@ -446,6 +446,8 @@ static int evaluate_grid() {
     return cached;
 }
 
+int prepare_evaluate() { return evaluate_grid() > 0 ? 0 : -1; }
+
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,

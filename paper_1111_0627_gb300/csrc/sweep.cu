@@ -228,18 +228,6 @@ struct ClassGrid {
     int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
 };
 
-struct Cand {
-    int rank;
-    int e;
-    long long key;
-};
-
-static __device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
-    if (a.rank != b.rank) return a.rank > b.rank;
-    if (a.key != b.key) return a.key > b.key;
-    return a.e < b.e;
-}
-
 static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
                                                  const int *__restrict__ w, const int4 *rec,
                                                  int sign, int e) {
@@ -260,23 +248,7 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const int next_eval = ws.ctrl->iter + 1;
     const int lane = tid & 31;
     if (tid == 0) s_sw = 0;
-    if (blockIdx.x == 0 && tid == 0) {
-        // Publish the best cycle of the evaluation this sweep reads (it is
-        // the answer if nothing switches).  No other thread touches these.
-        // (best is 0 only when the evaluation stopped early on an error,
-        // which the host reports after this sweep)
-        Ctrl *cc = ws.ctrl;
-        const unsigned long long bb = cc->best;
-        const int root = INT_MAX - (int)(unsigned)(bb & 0xffffffffu);
-        if (bb != 0 && root >= 0 && root < n_vertices) {
-            const int i = ws.cid_of_root[root];
-            cc->res_root = root;
-            cc->res_len = ws.cyc_L[i];
-            cc->res_num = ws.cyc_p[i];
-            cc->res_den = ws.cyc_q[i];
-            cc->res_cycles = cc->nrep;
-        }
-    }
+    if (blockIdx.x == 0 && tid == 0) publish_result(ws, n_vertices);
     __syncthreads();
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -359,6 +331,31 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
     prof_end(kProfInit, st);
 }
 
+// Co-resident blocks of the degree-class sweep per block size on the current
+// device (host-side configuration, done before any launch is captured).
+static int classes_grid(int threads) {
+    static int cached_dev[3] = {-1, -1, -1}, cached_blocks[3] = {0, 0, 0};
+    const int slot = threads == 128 ? 0 : threads == 256 ? 1 : 2;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cached_dev[slot] != dev) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, threads, 0) !=
+                cudaSuccess ||
+            sms <= 0 || per_sm <= 0)
+            return 0;
+        cached_blocks[slot] = sms * per_sm;
+        cached_dev[slot] = dev;
+    }
+    return cached_blocks[slot];
+}
+
+int prepare_sweep_classes(int threads) {
+    if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
+    return classes_grid(threads) > 0 ? 0 : -1;
+}
+
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st) {
     ClassGrid cg;
@@ -371,17 +368,8 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     cg.task_off[kClasses] = tasks;
     if (tasks == 0) return 0;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
-    static int grid_dev = -1, grid_threads = 0, grid_blocks = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev != grid_dev || threads != grid_threads) {
-        int sms = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, threads, 0);
-        grid_blocks = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
-        grid_dev = dev;
-        grid_threads = threads;
-    }
+    const int grid_blocks = classes_grid(threads);
+    if (grid_blocks <= 0) return -1;
     const int wpb = threads / 32;
     int blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;

@@ -24,6 +24,7 @@ from . import _native
 OCM_MAX, OCM_MIN = 0, 1
 OCM_FLAG_TEST_STALL = 1
 OCM_FLAG_HOST_LOOP = 2
+OCM_SWEEP_DEFAULT, OCM_SWEEP_CLASSES, OCM_SWEEP_TILES = 0, 1, 2
 
 
 class OCMError(RuntimeError):
@@ -91,15 +92,15 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
           workspace: torch.Tensor | None = None, stream=None, max_iters: int = 0,
           certificate: bool = False, cycle_out: torch.Tensor | None = None,
           flags: int = 0, edges_per_lane: int = 0, sweep_threads: int = 0,
-          tune: bool = False) -> Solution:
+          sweep_kind: int = 0, tune: bool = False) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
     cycle as CSR edge indices.  With ``certificate=True`` also returns the
     per-vertex cycle means (eta_num/eta_den) and potentials of the final
     policy, in the maximising sense of s*w (s = -1 in min mode).  ``tune=True``
-    uses the sweep launch parameters the autotuner recorded for graphs of this
-    shape (results never depend on them)."""
+    uses the sweep layout and launch parameters the autotuner recorded for
+    graphs of this shape (results never depend on them)."""
     lib = _native.load()
     rp = _dev_i32(row_ptr, "row_ptr")
     col = _dev_i32(col_idx, "col_idx")
@@ -115,13 +116,14 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
-    if tune and not (edges_per_lane or sweep_threads):
+    if tune and not (edges_per_lane or sweep_threads or sweep_kind):
         from .autotune import lookup
         found = lookup(rp)
         if found:
-            edges_per_lane, sweep_threads = found
+            sweep_kind, edges_per_lane, sweep_threads = found
     opt.edges_per_lane = int(edges_per_lane)
     opt.sweep_threads = int(sweep_threads)
+    opt.sweep_kind = int(sweep_kind)
     extra = {}
     if certificate:
         extra = dict(eta_num=torch.empty(n, dtype=torch.int64, device=dev),

@@ -70,6 +70,11 @@ def test_argument_errors_are_reported_before_any_device_work():
     rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
                        ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
     assert rc == -1
+    opt.flags = 0
+    opt.sweep_kind = 7                                   # no such sweep layout
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
+    assert rc == -1
     rc = lib.ocm_backward(fake, 0, fake, 4, fake, None)
     assert rc == -1
 

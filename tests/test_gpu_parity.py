@@ -189,16 +189,53 @@ def test_launch_parameters_do_not_change_results(tmp_path, monkeypatch):
     g = synth.locality32m(1 << 16)
     h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
     rp, col, w = _dev(g)
-    for epl in (1, 2, 4, 8, 16, 64):
-        for thr in (128, 256, 512):
-            sol = ocm.solve(rp, col, w, g.mode, edges_per_lane=epl, sweep_threads=thr)
-            assert (sol.num, sol.den) == (h.num, h.den)
-            assert sol.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle]
-    res = ocm.autotune.tune(rp, col, w, g.mode, candidates=[(2, 256), (8, 128)])
-    assert (res["edges_per_lane"], res["sweep_threads"]) in [(2, 256), (8, 128)]
-    assert ocm.autotune.lookup(rp) == (res["edges_per_lane"], res["sweep_threads"])
+    for kind, epls in ((ocm.ocm.OCM_SWEEP_CLASSES, (1, 2, 4, 8, 16, 64)),
+                       (ocm.ocm.OCM_SWEEP_TILES, (4, 8, 16))):
+        for epl in epls:
+            for thr in (64, 128, 256, 512):
+                sol = ocm.solve(rp, col, w, g.mode, edges_per_lane=epl, sweep_threads=thr,
+                                sweep_kind=kind)
+                assert (sol.num, sol.den) == (h.num, h.den)
+                assert sol.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle]
+                assert sol.stats["iterations"] == h.iterations
+    cands = [(1, 2, 256), (2, 8, 128), (2, 4, 256)]
+    res = ocm.autotune.tune(rp, col, w, g.mode, candidates=cands)
+    picked = (res["sweep_kind"], res["edges_per_lane"], res["sweep_threads"])
+    assert picked in cands
+    assert ocm.autotune.lookup(rp) == picked
     sol = ocm.solve(rp, col, w, g.mode, tune=True)
     assert (sol.num, sol.den) == (h.num, h.den)
+
+
+@pytest.mark.parametrize("epl", [4, 8])
+def test_edge_tiles_against_degree_classes(epl):
+    """The two sweep layouts make the same choices at every step: random
+    graphs whose degrees straddle the tile and lane sizes (vertices inside a
+    lane, across lanes, across tiles, and exactly filling them), compared
+    with the oracle and with each other, including the iteration count and
+    the number of switches."""
+    rng = np.random.default_rng(4400 + epl)
+    et = 32 * epl
+    for trial in range(12):
+        n = int(rng.integers(50, 1500))
+        choices = np.array([1, 2, epl - 1, epl, epl + 1, et - 1, et, et + 1, 3 * et + 5])
+        choices = choices[choices >= 1]
+        deg = rng.choice(choices, size=n, p=None)
+        edges = []
+        for v in range(n):
+            edges.append((v, (v + 1) % n, int(rng.integers(-50, 50))))
+            for _ in range(int(deg[v]) - 1):
+                edges.append((v, int(rng.integers(0, n)), int(rng.integers(-50, 50))))
+        g = synth.from_edges(n, edges, mode="max" if trial % 2 else "min")
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        rp, col, w = _dev(g)
+        a = ocm.solve(rp, col, w, g.mode, sweep_kind=ocm.ocm.OCM_SWEEP_TILES, edges_per_lane=epl)
+        b = ocm.solve(rp, col, w, g.mode, sweep_kind=ocm.ocm.OCM_SWEEP_CLASSES)
+        for s in (a, b):
+            assert (s.num, s.den) == (h.num, h.den), trial
+            assert s.cycle.cpu().numpy().tolist() == [int(x) for x in h.cycle], trial
+            assert s.stats["iterations"] == h.iterations, trial
+        assert a.stats["switched"] == b.stats["switched"], trial
 
 
 def test_determinism_bitwise():
