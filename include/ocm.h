@@ -93,6 +93,18 @@ typedef struct ocm_options {
     int32_t edges_per_lane;
     int32_t sweep_threads;
     int32_t sweep_kind;  /* OCM_SWEEP_*; 0 = library default (degree classes)      */
+    int32_t reserved0;
+    /* Warm start (optional, device [n]; [N] with global edge ids for
+     * ocm_solve_batch): the policy the iteration starts from, one out-edge
+     * per vertex, row_ptr[v] <= init_policy[v] < row_ptr[v+1]
+     * (OCM_ERR_INVALID_ARG otherwise).  NULL = the first pass of Alg. 1
+     * from val = 0, lambda = 0 (heaviest out-edge).  Policy iteration reaches
+     * an optimal policy from any start (Sec. 2.4), so lambda* does not
+     * depend on it; the number of iterations does, and where several cycles
+     * are optimal, so may the returned one.  Passing the final policy of an
+     * earlier solve (the `policy` output) resumes from it: re-solving after
+     * a small weight change typically takes a few iterations.             */
+    const int32_t *init_policy;
 } ocm_options;
 
 /* Layouts of the improvement sweep (results do not depend on the choice).
@@ -265,7 +277,7 @@ int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, const int32
 /* Text for a status code (static storage). */
 const char *ocm_status_string(int status);
 
-/* ABI version: 100 * major + minor. */
+/* ABI version: 100 * major + minor (101: ocm_options.init_policy). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -63,7 +63,8 @@ def _load():
             i64p = ctypes.POINTER(ctypes.c_int64)
             i32, i64, c_int = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
             lib.oracle_howard.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64, i64p, i64p,
-                                          i32p, i32p, i64p, i64p, i64p, i32p, i64p, i64p, i64]
+                                          i32p, i32p, i64p, i64p, i64p, i32p, i64p, i64p, i64,
+                                          i32p]
             lib.oracle_karp.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64p, i64p]
             lib.oracle_brute.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64p, i64p, i64p,
                                          i32p, i64, i64p, i64, i64p]
@@ -115,7 +116,10 @@ class HowardResult:
         return Fraction(self.num, self.den)
 
 
-def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 4096) -> HowardResult:
+def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 4096,
+           init_policy=None) -> HowardResult:
+    """Howard policy iteration; ``init_policy`` (an out-edge index per vertex)
+    replaces the initial policy of Alg. 1's first pass (warm start)."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
     col, colp = _i32(col_idx)
@@ -131,12 +135,15 @@ def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 
     pol = np.zeros(n, np.int32)
     its = np.zeros(1, np.int64)
     tr = np.zeros(3 * trace_cap, np.int64)
+    init, initp = _i32(init_policy) if init_policy is not None else (None, None)
+    if init is not None and init.shape[0] != n:
+        raise ValueError("init_policy must have one entry per vertex")
     rc = lib.oracle_howard(n, m, rpp, colp, wp, _mode(mode), max_iter, _i64p(num), _i64p(den),
                            cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                            clen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                            _i64p(ep), _i64p(eq), _i64p(V),
                            pol.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _i64p(its),
-                           _i64p(tr), trace_cap)
+                           _i64p(tr), trace_cap, initp)
     if rc != 0:
         raise OracleError(rc, "howard")
     it = int(its[0])

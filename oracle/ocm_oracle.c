@@ -222,14 +222,23 @@ static inline int howard_better(const howard_ws *h, int32_t a, int32_t b) {
  *   policy [n]         : optional, final policy edge per vertex
  *   iters              : optional, number of improvement steps taken
  *   trace [3*tcap]     : optional, per iteration (cycles, switched, eval id)
+ *   init [n]           : optional initial policy (an out-edge index of each
+ *                        vertex); NULL = the first pass of Alg. 1 from val = 0,
+ *                        lambda = 0.  Policy iteration reaches an optimal
+ *                        policy from any start (Sec. 2.4), so a caller may
+ *                        resume from an earlier policy (warm start).
  * Returns 0 or a negative OR_ERR_* code.
  */
 int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, const int32_t *w,
                   int mode, int64_t max_iter, int64_t *num, int64_t *den, int32_t *cycle,
                   int32_t *clen, int64_t *eta_p, int64_t *eta_q, int64_t *V_out,
-                  int32_t *policy, int64_t *iters, int64_t *trace, int64_t tcap) {
+                  int32_t *policy, int64_t *iters, int64_t *trace, int64_t tcap,
+                  const int32_t *init) {
     int rc = check_csr(n, m, rp, col);
     if (rc) return rc;
+    if (init)
+        for (int32_t v = 0; v < n; ++v)
+            if (init[v] < rp[v] || init[v] >= rp[v + 1]) return OR_ERR_ARG;
     if (!w || (mode != 0 && mode != 1)) return OR_ERR_ARG;
     for (int32_t e = 0; e < m; ++e)
         if (w[e] == INT32_MIN) return OR_ERR_RANGE;
@@ -258,12 +267,13 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
         goto done;
     }
 
-    /* first pass from val = 0, lambda = 0: heaviest out-edge, smallest index */
+    /* first pass from val = 0, lambda = 0: heaviest out-edge, smallest index
+     * (or the caller's initial policy) */
     for (int32_t v = 0; v < n; ++v) {
         int32_t best = rp[v];
         for (int32_t e = rp[v] + 1; e < rp[v + 1]; ++e)
             if (wmax(w, e, mode) > wmax(w, best, mode)) best = e;
-        h.pi[v] = best;
+        h.pi[v] = init ? init[v] : best;
     }
 
     int64_t it = 0;

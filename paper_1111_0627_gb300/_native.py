@@ -81,7 +81,8 @@ class OcmOptions(ctypes.Structure):
                 ("eta_num", ctypes.c_void_p), ("eta_den", ctypes.c_void_p),
                 ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
                 ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
-                ("sweep_kind", ctypes.c_int32)]
+                ("sweep_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("init_policy", ctypes.c_void_p)]
 
 
 class OcmStats(ctypes.Structure):

@@ -162,6 +162,7 @@ static int persistent_grid() {
 
 static int map_err_bits(int err) {
     if (err & kErrTimeout) return OCM_ERR_TIMEOUT;
+    if (err & kErrInitPolicy) return OCM_ERR_INVALID_ARG;
     if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
     if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
     if (err & kErrWeightMin) return OCM_ERR_OVERFLOW;
@@ -410,7 +411,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 100; }
+int ocm_version(void) { return 101; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -479,7 +480,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     // 2. initial policy (the paper's first pass from val = 0, lambda = 0),
     //    which also validates col_idx and w and measures max|w|; degree
     //    classes of the improvement sweep
-    launch_init_policy(row_ptr, col_idx, w, sign, n, m, ws, bs ? &b : nullptr, st);
+    launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
+                       bs ? &b : nullptr, st);
     launches += 1;
     const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES) ? OCM_SWEEP_TILES
                                                                 : OCM_SWEEP_CLASSES;

@@ -98,6 +98,7 @@ enum : int {
     kErrExtract = 64,     // critical-cycle extraction inconsistent
     kErrTimeout = 128,    // a grid barrier wait exceeded its spin limit
     kErrSweep = 256,      // a vertex's current policy edge was not among its edges
+    kErrInitPolicy = 512, // a caller-given initial policy edge is not an out-edge of its vertex
 };
 
 // Workspace carved from one caller-provided buffer.
@@ -238,7 +239,7 @@ void prof_end(int cls, cudaStream_t st);
 // kernel launchers (defined in the .cu files)
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        Workspace ws, const BatchState *bs, cudaStream_t st);
+                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st);
 int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspace ws,

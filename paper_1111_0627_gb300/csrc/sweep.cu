@@ -58,12 +58,14 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 }
 
 // Initial policy (Alg. 1's first pass from val = 0, lambda = 0): the heaviest
-// out-edge in the s*w sense, ties to the smallest edge index.  The same pass
-// validates col_idx and w and measures max|w| for the exactness bound.
+// out-edge in the s*w sense, ties to the smallest edge index -- or, for a warm
+// start, the caller's policy (init != nullptr), which must name an out-edge
+// of each vertex.  The same pass validates col_idx and w and measures max|w|
+// for the exactness bound.
 __global__ void __launch_bounds__(kThreads)
 init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
-                   Workspace ws) {
+                   const int *__restrict__ init, Workspace ws) {
     __shared__ int s_maxw[kThreads / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -92,6 +94,15 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             if (k > best_key) {
                 best_key = k;
                 best_e = e;
+            }
+        }
+        if (init) {
+            const int e = __ldg(&init[v]);
+            if (e >= a && e < b) {
+                best_e = e;
+            } else {
+                atomicOr(&ws.ctrl->err, kErrInitPolicy);
+                atomicMin(&ws.ctrl->bad_index, v);
             }
         }
         const int t = __ldg(&col[best_e]);
@@ -321,13 +332,13 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 }
 
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        Workspace ws, const BatchState *bs, cudaStream_t st) {
+                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st) {
     (void)m;
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 2048) blocks = 2048;
     prof_begin(kProfInit, st);
     init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n,
-                                                    bs ? bs->gid : nullptr, ws);
+                                                    bs ? bs->gid : nullptr, init, ws);
     prof_end(kProfInit, st);
 }
 

@@ -58,6 +58,15 @@ def _stream_ptr(stream) -> int:
     return int(s.cuda_stream)
 
 
+def _init_policy(init_policy, n: int):
+    if init_policy is None:
+        return None
+    t = _dev_i32(init_policy, "init_policy")
+    if t.numel() != n:
+        raise ValueError("init_policy needs one entry per vertex")
+    return t
+
+
 def workspace_bytes(n: int, m: int) -> int:
     return int(_native.load().ocm_workspace_size(n, m))
 
@@ -92,7 +101,8 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
           workspace: torch.Tensor | None = None, stream=None, max_iters: int = 0,
           certificate: bool = False, cycle_out: torch.Tensor | None = None,
           flags: int = 0, edges_per_lane: int = 0, sweep_threads: int = 0,
-          sweep_kind: int = 0, tune: bool = False) -> Solution:
+          sweep_kind: int = 0, tune: bool = False,
+          init_policy: torch.Tensor | None = None) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
@@ -124,6 +134,9 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     opt.edges_per_lane = int(edges_per_lane)
     opt.sweep_threads = int(sweep_threads)
     opt.sweep_kind = int(sweep_kind)
+    init = _init_policy(init_policy, n)
+    if init is not None:
+        opt.init_policy = init.data_ptr()
     extra = {}
     if certificate:
         extra = dict(eta_num=torch.empty(n, dtype=torch.int64, device=dev),
@@ -166,9 +179,11 @@ def workspace_bytes_batch(G: int, N: int, M: int) -> int:
 
 def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor,
                 w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
-                stream=None, max_iters: int = 0, flags: int = 0) -> BatchSolution:
+                stream=None, max_iters: int = 0, flags: int = 0,
+                init_policy: torch.Tensor | None = None) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
-    (``ocm_solve_batch``); each result equals solving that graph alone."""
+    (``ocm_solve_batch``); each result equals solving that graph alone.
+    ``init_policy`` (int32 [N], global edge ids) warm-starts every graph."""
     lib = _native.load()
     vp = _dev_i32(graph_vptr, "graph_vptr")
     rp = _dev_i32(row_ptr, "row_ptr")
@@ -188,6 +203,9 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
+    init = _init_policy(init_policy, N)
+    if init is not None:
+        opt.init_policy = init.data_ptr()
     st = _native.OcmStats()
     rc = lib.ocm_solve_batch(vp.data_ptr(), rp.data_ptr(), col.data_ptr(), ww.data_ptr(), G, N, M,
                              _mode(mode), num.data_ptr(), den.data_ptr(), clen.data_ptr(),

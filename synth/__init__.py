@@ -295,3 +295,11 @@ def from_edges(n: int, edges: list[tuple[int, int, int]], mode: str = "max", nam
     col = np.array([t for r in rows for (t, _) in r], dtype=np.int32)
     w = np.array([wt for r in rows for (_, wt) in r], dtype=np.int32)
     return Graph(rp, col, w, mode, name)
+
+
+def random_policy(rng: np.random.Generator, row_ptr: np.ndarray) -> np.ndarray:
+    """One uniformly drawn out-edge index per vertex (a start policy for warm
+    starts): row_ptr[v] + U{0 .. deg(v)-1}."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    deg = rp[1:] - rp[:-1]
+    return (rp[:-1] + rng.integers(0, 1 << 62, size=deg.shape[0]) % deg).astype(np.int32)

@@ -274,3 +274,63 @@ def test_gradient_is_one_over_cycle_length():
         w2 = g.w.copy()
         w2[e] += 1
         assert oracle.howard(g.row_ptr, g.col_idx, w2).value - h.value == Fraction(1, 5)
+
+
+# ----------------------------------------------------------------- warm start
+# Policy iteration reaches an optimal policy from any start (Sec. 2.4): the
+# value from a random start policy must still be the brute-force optimum and
+# carry a valid certificate, and a start from the final policy must stop at
+# once with the same answer.
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_warm_start_from_random_policies_reaches_the_optimum(mode):
+    rng = np.random.default_rng(1111062750 + (mode == "min"))
+    for trial in range(600):
+        n = int(rng.integers(1, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=bool(trial % 2), mode=mode)
+        init = synth.random_policy(rng, g.row_ptr)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, mode, init_policy=init)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode)
+        assert h.value == b.value, (trial, n)
+        assert tuple(int(e) for e in h.cycle) in b.optimal, trial
+        rc, bad = oracle.certificate(g.row_ptr, g.col_idx, g.w, mode, h.eta_p, h.eta_q, h.V,
+                                     h.num, h.den, h.cycle)
+        assert rc == 0, (trial, rc, bad)
+
+
+def test_warm_start_from_the_final_policy_stops_at_once():
+    rng = np.random.default_rng(1111062752)
+    graphs = [synth.tiny_random(rng, int(rng.integers(1, 9)), max_extra=3) for _ in range(200)]
+    graphs.append(synth.ring10k())
+    for g in graphs:
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        h2 = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode, init_policy=h.policy)
+        assert h2.iterations == 0
+        assert (h2.num, h2.den) == (h.num, h.den)
+        assert h2.cycle.tolist() == h.cycle.tolist()
+        assert h2.policy.tolist() == h.policy.tolist()
+
+
+def test_warm_start_after_a_weight_change_matches_a_cold_solve_in_value():
+    # the use the option exists for: re-solve after perturbing some weights,
+    # starting from the previous optimal policy
+    g = synth.ring10k()
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    rng = np.random.default_rng(1111062753)
+    w2 = g.w.copy()
+    idx = rng.integers(0, g.m, size=50)
+    w2[idx] += rng.integers(-20, 21, size=50).astype(np.int32)
+    cold = oracle.howard(g.row_ptr, g.col_idx, w2, g.mode)
+    warm = oracle.howard(g.row_ptr, g.col_idx, w2, g.mode, init_policy=h.policy)
+    assert warm.value == cold.value == oracle.karp(g.row_ptr, g.col_idx, w2, g.mode)
+    rc, _ = oracle.certificate(g.row_ptr, g.col_idx, w2, g.mode, warm.eta_p, warm.eta_q, warm.V,
+                               warm.num, warm.den, warm.cycle)
+    assert rc == 0
+
+
+def test_warm_start_rejects_an_edge_of_another_vertex():
+    g = synth.from_edges(3, [(0, 1, 1), (1, 2, 1), (2, 0, 1), (2, 2, 5)])
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.howard(g.row_ptr, g.col_idx, g.w, init_policy=np.array([0, 0, 2], np.int32))
+    assert e.value.code == -1
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, init_policy=np.array([0, 1, 2], np.int32))
+    assert h.value == 5
