@@ -17,6 +17,10 @@ routine follows:
 * :func:`certificate` -- LP-dual optimality check of an answer (Eq. 1,
                           Prop. 2.1);
 * :func:`gradient`    -- d lambda*/dw = 1/|C*| on the critical cycle, else 0.
+
+:func:`howard`, :func:`brute` and :func:`certificate` take an optional
+``transit`` array (int32 transit times t(e) >= 1, Sec. 2.2): they then work on
+the optimal cycle ratio w(C)/t(C); ``transit`` of all ones gives the mean.
 """
 from __future__ import annotations
 
@@ -72,6 +76,13 @@ def _load():
             lib.oracle_tarjan_scc.restype = i32
             lib.oracle_certificate.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64p, i64p,
                                                i64p, i64, i64, i32p, i32, i64p]
+            lib.oracle_howard_ratio.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64,
+                                                i64p, i64p, i32p, i32p, i64p, i64p, i64p, i32p,
+                                                i64p, i32p]
+            lib.oracle_brute_ratio.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64p,
+                                               i64p, i64p, i32p, i64, i64p, i64, i64p]
+            lib.oracle_certificate_ratio.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int,
+                                                     i64p, i64p, i64p, i64, i64, i32p, i32, i64p]
             _lib = lib
     return _lib
 
@@ -117,9 +128,10 @@ class HowardResult:
 
 
 def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 4096,
-           init_policy=None) -> HowardResult:
+           init_policy=None, transit=None) -> HowardResult:
     """Howard policy iteration; ``init_policy`` (an out-edge index per vertex)
-    replaces the initial policy of Alg. 1's first pass (warm start)."""
+    replaces the initial policy of Alg. 1's first pass (warm start);
+    ``transit`` switches to the optimal cycle ratio (no trace is kept then)."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
     col, colp = _i32(col_idx)
@@ -138,12 +150,24 @@ def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 
     init, initp = _i32(init_policy) if init_policy is not None else (None, None)
     if init is not None and init.shape[0] != n:
         raise ValueError("init_policy must have one entry per vertex")
-    rc = lib.oracle_howard(n, m, rpp, colp, wp, _mode(mode), max_iter, _i64p(num), _i64p(den),
-                           cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                           clen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                           _i64p(ep), _i64p(eq), _i64p(V),
-                           pol.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _i64p(its),
-                           _i64p(tr), trace_cap, initp)
+    if transit is not None:
+        tt, ttp = _i32(transit)
+        if tt.shape[0] != m:
+            raise ValueError("transit needs one entry per edge")
+        rc = lib.oracle_howard_ratio(n, m, rpp, colp, wp, ttp, _mode(mode), max_iter,
+                                     _i64p(num), _i64p(den),
+                                     cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     clen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     _i64p(ep), _i64p(eq), _i64p(V),
+                                     pol.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     _i64p(its), initp)
+    else:
+        rc = lib.oracle_howard(n, m, rpp, colp, wp, _mode(mode), max_iter, _i64p(num), _i64p(den),
+                               cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               clen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               _i64p(ep), _i64p(eq), _i64p(V),
+                               pol.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _i64p(its),
+                               _i64p(tr), trace_cap, initp)
     if rc != 0:
         raise OracleError(rc, "howard")
     it = int(its[0])
@@ -173,7 +197,7 @@ class BruteResult:
     optimal: list            # each optimal cycle as a tuple of edge indices, from its min vertex
 
 
-def brute(row_ptr, col_idx, w, mode="max", cap: int = 100000) -> BruteResult:
+def brute(row_ptr, col_idx, w, mode="max", cap: int = 100000, transit=None) -> BruteResult:
     lib = _load()
     rp, rpp = _i32(row_ptr)
     col, colp = _i32(col_idx)
@@ -185,9 +209,17 @@ def brute(row_ptr, col_idx, w, mode="max", cap: int = 100000) -> BruteResult:
     nopt = np.zeros(1, np.int64)
     edges = np.zeros(cap * min(n, 16), np.int32)
     ptr = np.zeros(cap + 1, np.int64)
-    rc = lib.oracle_brute(n, col.shape[0], rpp, colp, wp, _mode(mode), _i64p(num), _i64p(den),
-                          _i64p(nc), edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                          edges.shape[0], _i64p(ptr), cap, _i64p(nopt))
+    if transit is not None:
+        tt, ttp = _i32(transit)
+        rc = lib.oracle_brute_ratio(n, col.shape[0], rpp, colp, wp, ttp, _mode(mode), _i64p(num),
+                                    _i64p(den), _i64p(nc),
+                                    edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    edges.shape[0], _i64p(ptr), cap, _i64p(nopt))
+    else:
+        rc = lib.oracle_brute(n, col.shape[0], rpp, colp, wp, _mode(mode), _i64p(num),
+                              _i64p(den), _i64p(nc),
+                              edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              edges.shape[0], _i64p(ptr), cap, _i64p(nopt))
     if rc != 0:
         raise OracleError(rc, "brute")
     k = int(nopt[0])
@@ -207,7 +239,8 @@ def tarjan_scc(row_ptr, col_idx) -> tuple[int, np.ndarray]:
     return int(k), comp
 
 
-def certificate(row_ptr, col_idx, w, mode, eta_p, eta_q, V, num: int, den: int, cycle) -> tuple[int, int]:
+def certificate(row_ptr, col_idx, w, mode, eta_p, eta_q, V, num: int, den: int, cycle,
+                transit=None) -> tuple[int, int]:
     """0 if (eta, V, num/den, cycle) proves optimality, else a failure code (1-6) and index."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
@@ -218,10 +251,26 @@ def certificate(row_ptr, col_idx, w, mode, eta_p, eta_q, V, num: int, den: int, 
     vv = np.ascontiguousarray(V, dtype=np.int64)
     cy, cyp = _i32(cycle if len(cycle) else np.zeros(1, np.int32))
     bad = np.zeros(1, np.int64)
-    rc = lib.oracle_certificate(rp.shape[0] - 1, col.shape[0], rpp, colp, wp, _mode(mode),
-                                _i64p(ep), _i64p(eq), _i64p(vv), int(num), int(den), cyp,
-                                len(cycle), _i64p(bad))
+    if transit is not None:
+        tt, ttp = _i32(transit)
+        rc = lib.oracle_certificate_ratio(rp.shape[0] - 1, col.shape[0], rpp, colp, wp, ttp,
+                                          _mode(mode), _i64p(ep), _i64p(eq), _i64p(vv), int(num),
+                                          int(den), cyp, len(cycle), _i64p(bad))
+    else:
+        rc = lib.oracle_certificate(rp.shape[0] - 1, col.shape[0], rpp, colp, wp, _mode(mode),
+                                    _i64p(ep), _i64p(eq), _i64p(vv), int(num), int(den), cyp,
+                                    len(cycle), _i64p(bad))
     return int(rc), int(bad[0])
+
+
+def gradient_ratio(m: int, cycle, transit) -> np.ndarray:
+    """d lambda*/dw for the optimal cycle ratio: lambda* = w(C*)/t(C*) is linear
+    in the weights of C* with slope 1/t(C*), so each critical-cycle edge gets
+    1/t(C*) and every other edge 0."""
+    g = np.zeros(m, np.float64)
+    cyc = np.asarray(cycle, dtype=np.int64)
+    g[cyc] += 1.0 / float(np.asarray(transit, dtype=np.int64)[cyc].sum())
+    return g
 
 
 def gradient(m: int, cycle) -> np.ndarray:

@@ -10,7 +10,10 @@
  *
  * Problem (paper Sec. 2.1, definition of cycle mean and the OCM problem): for
  * a digraph G = (V, E) with integer edge weights w, the cycle mean of a cycle
- * C is w(C)/|C|.  The paper states the minimal cycle mean; this oracle works
+ * C is w(C)/|C|.  The *_ratio entry points take a second integer label, a
+ * transit time t(e) >= 1 per edge (the "time" of a transition, Sec. 2.2), and
+ * compute the optimal cycle ratio w(C)/t(C) instead; with t = 1 everywhere
+ * the ratio is the mean, and every routine below reduces to its mean form.  The paper states the minimal cycle mean; this oracle works
  * in the maximising sense, lambda* = max over cycles C of w(C)/|C|, and the
  * minimising sense is obtained as  min(w) = -max(-w)  with the same critical
  * cycle.  Results are reduced rationals num/den with den > 0.
@@ -29,6 +32,8 @@
  *                      per-vertex means that never increase along an edge and
  *                      potentials under which no edge has positive reduced
  *                      weight (Prop. 2.1), plus a cycle attaining the value.
+ *   oracle_howard_ratio, oracle_brute_ratio, oracle_certificate_ratio
+ *                      the same three for the optimal cycle ratio.
  *
  * Readings of the paper taken here (where it is silent or garbled):
  *   - max sense (the paper defines min); min via negated weights;
@@ -88,6 +93,9 @@ static inline int64_t wmax(const int32_t *w, int32_t e, int mode) {
     return mode == 0 ? (int64_t)w[e] : -(int64_t)w[e];
 }
 
+/* transit time of edge e (1 when no times are given) */
+static inline int64_t tval(const int32_t *tt, int32_t e) { return tt ? (int64_t)tt[e] : 1; }
+
 /* compare fractions a/b and c/d (b, d > 0): -1, 0, 1 */
 static inline int frac_cmp(int64_t a, int64_t b, int64_t c, int64_t d) {
     i128 l = (i128)a * d, r = (i128)c * b;
@@ -108,8 +116,9 @@ typedef struct {
     int32_t *state;     /* walk colouring                                  */
     int32_t *path;      /* walk stack                                      */
     int64_t *S;         /* weight of the policy path to the cycle's root   */
-    int64_t *len;       /* length of that path                             */
-    i128 *V;            /* q*S - p*len : value scaled by the mean's denominator */
+    const int32_t *tt;  /* transit times (NULL: 1 on every edge)          */
+    int64_t *T;         /* transit time of the path to the root            */
+    i128 *V;            /* q*S - p*T : value scaled by the mean's denominator */
     int32_t ncyc;
     int32_t *cyc_root;  /* per cycle: smallest vertex on it                */
     int64_t *cyc_p, *cyc_q;  /* per cycle: reduced mean p/q                */
@@ -118,9 +127,12 @@ typedef struct {
 /* Evaluate the policy pi: find every cycle of the functional graph G_pi by
  * following successors and colouring visited vertices (Sec. 2.4: each weakly
  * connected component of G_pi holds exactly one cycle), take its root = the
- * smallest vertex, its mean W/L reduced to p/q, and propagate values from the
- * root along policy predecessors (Alg. 1 value propagation):
- * V(root) = 0, V(v) = q*w(v, succ v) - p + V(succ v), i.e. V = q*S - p*len. */
+ * smallest vertex, its mean W/L (ratio: W/T, T = transit time of the cycle)
+ * reduced to p/q, and propagate values from the root along policy
+ * predecessors (Alg. 1 value propagation):
+ * V(root) = 0, V(v) = q*w(v, succ v) - p*t(v, succ v) + V(succ v),
+ * i.e. V = q*S - p*T with S, T the weight and time of v's path to the root
+ * (T = len for the mean). */
 static void howard_evaluate(howard_ws *h) {
     int32_t n = h->n;
     for (int32_t v = 0; v < n; ++v) {
@@ -143,20 +155,20 @@ static void howard_evaluate(howard_ws *h) {
             while (h->path[k] != u) --k;
             int32_t c = h->ncyc++;
             int32_t root = u;
-            int64_t W = 0, L = 0;
+            int64_t W = 0, Tc = 0;
             for (int32_t j = k; j < top; ++j) {
                 int32_t x = h->path[j];
                 if (x < root) root = x;
                 W += wmax(h->w, h->pi[x], h->mode);
-                L += 1;
+                Tc += tval(h->tt, h->pi[x]);
             }
-            int64_t g = gcd64(W, L);
+            int64_t g = gcd64(W, Tc);
             h->cyc_root[c] = root;
             h->cyc_p[c] = W / g;
-            h->cyc_q[c] = L / g;
+            h->cyc_q[c] = Tc / g;
             /* walk the cycle backwards from the root: the root is terminal */
             h->S[root] = 0;
-            h->len[root] = 0;
+            h->T[root] = 0;
             h->cyc[root] = c;
             h->state[root] = 2;
             /* vertices of the cycle in order starting at root */
@@ -167,7 +179,7 @@ static void howard_evaluate(howard_ws *h) {
                 int32_t x = h->path[k + (start - k + t) % cl];
                 int32_t y = h->succ[x];
                 h->S[x] = wmax(h->w, h->pi[x], h->mode) + h->S[y];
-                h->len[x] = 1 + h->len[y];
+                h->T[x] = tval(h->tt, h->pi[x]) + h->T[y];
                 h->cyc[x] = c;
                 h->state[x] = 2;
             }
@@ -178,22 +190,23 @@ static void howard_evaluate(howard_ws *h) {
             int32_t x = h->path[j];
             int32_t y = h->succ[x];
             h->S[x] = wmax(h->w, h->pi[x], h->mode) + h->S[y];
-            h->len[x] = 1 + h->len[y];
+            h->T[x] = tval(h->tt, h->pi[x]) + h->T[y];
             h->cyc[x] = h->cyc[y];
             h->state[x] = 2;
         }
     }
     for (int32_t v = 0; v < n; ++v) {
         int32_t c = h->cyc[v];
-        h->V[v] = (i128)h->cyc_q[c] * h->S[v] - (i128)h->cyc_p[c] * h->len[v];
+        h->V[v] = (i128)h->cyc_q[c] * h->S[v] - (i128)h->cyc_p[c] * h->T[v];
     }
 }
 
-/* improvement key of edge e: (eta(t), q_t*w(e) - p_t + V(t)), t = col[e] */
+/* improvement key of edge e: (eta(t), q_t*w(e) - p_t*t(e) + V(t)), t = col[e] */
 static inline i128 howard_key2(const howard_ws *h, int32_t e) {
     int32_t t = h->col[e];
     int32_t c = h->cyc[t];
-    return (i128)h->cyc_q[c] * wmax(h->w, e, h->mode) - h->cyc_p[c] + h->V[t];
+    return (i128)h->cyc_q[c] * wmax(h->w, e, h->mode) - (i128)h->cyc_p[c] * tval(h->tt, e) +
+           h->V[t];
 }
 
 /* Is edge a better than edge b for the improvement step?  Lexicographic
@@ -229,13 +242,16 @@ static inline int howard_better(const howard_ws *h, int32_t a, int32_t b) {
  *                        resume from an earlier policy (warm start).
  * Returns 0 or a negative OR_ERR_* code.
  */
-int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  int mode, int64_t max_iter, int64_t *num, int64_t *den, int32_t *cycle,
-                  int32_t *clen, int64_t *eta_p, int64_t *eta_q, int64_t *V_out,
-                  int32_t *policy, int64_t *iters, int64_t *trace, int64_t tcap,
-                  const int32_t *init) {
+static int howard_impl(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                       const int32_t *w, const int32_t *tt, int mode, int64_t max_iter,
+                       int64_t *num, int64_t *den, int32_t *cycle, int32_t *clen,
+                       int64_t *eta_p, int64_t *eta_q, int64_t *V_out, int32_t *policy,
+                       int64_t *iters, int64_t *trace, int64_t tcap, const int32_t *init) {
     int rc = check_csr(n, m, rp, col);
     if (rc) return rc;
+    if (tt)
+        for (int32_t e = 0; e < m; ++e)
+            if (tt[e] < 1) return OR_ERR_ARG;
     if (init)
         for (int32_t v = 0; v < n; ++v)
             if (init[v] < rp[v] || init[v] >= rp[v + 1]) return OR_ERR_ARG;
@@ -246,7 +262,7 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
 
     howard_ws h;
     memset(&h, 0, sizeof h);
-    h.n = n; h.rp = rp; h.col = col; h.w = w; h.mode = mode;
+    h.n = n; h.rp = rp; h.col = col; h.w = w; h.mode = mode; h.tt = tt;
     size_t N = (size_t)n;
     h.pi = malloc(N * sizeof(int32_t));
     h.succ = malloc(N * sizeof(int32_t));
@@ -254,14 +270,14 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
     h.state = malloc(N * sizeof(int32_t));
     h.path = malloc(N * sizeof(int32_t));
     h.S = malloc(N * sizeof(int64_t));
-    h.len = malloc(N * sizeof(int64_t));
+    h.T = malloc(N * sizeof(int64_t));
     h.V = malloc(N * sizeof(i128));
     h.cyc_root = malloc(N * sizeof(int32_t));
     h.cyc_p = malloc(N * sizeof(int64_t));
     h.cyc_q = malloc(N * sizeof(int64_t));
     int32_t *newpi = malloc(N * sizeof(int32_t));
     rc = OR_OK;
-    if (!h.pi || !h.succ || !h.cyc || !h.state || !h.path || !h.S || !h.len || !h.V ||
+    if (!h.pi || !h.succ || !h.cyc || !h.state || !h.path || !h.S || !h.T || !h.V ||
         !h.cyc_root || !h.cyc_p || !h.cyc_q || !newpi) {
         rc = OR_ERR_NOMEM;
         goto done;
@@ -340,9 +356,30 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
 
 done:
     free(h.pi); free(h.succ); free(h.cyc); free(h.state); free(h.path);
-    free(h.S); free(h.len); free(h.V); free(h.cyc_root); free(h.cyc_p); free(h.cyc_q);
+    free(h.S); free(h.T); free(h.V); free(h.cyc_root); free(h.cyc_p);
+    free(h.cyc_q);
     free(newpi);
     return rc;
+}
+
+int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, const int32_t *w,
+                  int mode, int64_t max_iter, int64_t *num, int64_t *den, int32_t *cycle,
+                  int32_t *clen, int64_t *eta_p, int64_t *eta_q, int64_t *V_out,
+                  int32_t *policy, int64_t *iters, int64_t *trace, int64_t tcap,
+                  const int32_t *init) {
+    return howard_impl(n, m, rp, col, w, NULL, mode, max_iter, num, den, cycle, clen, eta_p,
+                       eta_q, V_out, policy, iters, trace, tcap, init);
+}
+
+/* Optimal cycle ratio w(C)/t(C) by the same iteration, transit times tt[m] >= 1. */
+int oracle_howard_ratio(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                        const int32_t *w, const int32_t *tt, int mode, int64_t max_iter,
+                        int64_t *num, int64_t *den, int32_t *cycle, int32_t *clen,
+                        int64_t *eta_p, int64_t *eta_q, int64_t *V_out, int32_t *policy,
+                        int64_t *iters, const int32_t *init) {
+    if (!tt) return OR_ERR_ARG;
+    return howard_impl(n, m, rp, col, w, tt, mode, max_iter, num, den, cycle, clen, eta_p,
+                       eta_q, V_out, policy, iters, NULL, 0, init);
 }
 
 /* ======================================================================== */
@@ -443,13 +480,14 @@ int oracle_karp(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, con
  */
 typedef struct {
     const int32_t *rp, *col, *w;
+    const int32_t *tt;    /* transit times, NULL = 1 per edge */
     int mode;
     int32_t s;
     int32_t *stk_e;
     char *onpath;
     int32_t depth;
     int have;
-    int64_t bp, bq;       /* best mean (max sense) */
+    int64_t bp, bq;       /* best mean or ratio (max sense) */
     int64_t ncycles;
     int32_t *opt_edges;
     int64_t opt_cap_edges, opt_used_edges;
@@ -458,14 +496,14 @@ typedef struct {
     int overflow;
 } brute_ctx;
 
-static void brute_record(brute_ctx *b, int64_t W, int64_t L) {
+static void brute_record(brute_ctx *b, int64_t W, int64_t T, int64_t L) {
     b->ncycles++;
-    int c = b->have ? frac_cmp(W, L, b->bp, b->bq) : 1;
+    int c = b->have ? frac_cmp(W, T, b->bp, b->bq) : 1;
     if (c < 0) return;
     if (c > 0) {
         b->have = 1;
         b->bp = W;
-        b->bq = L;
+        b->bq = T;
         b->nopt = 0;
         b->opt_used_edges = 0;
         b->overflow = 0;
@@ -480,27 +518,32 @@ static void brute_record(brute_ctx *b, int64_t W, int64_t L) {
     b->opt_ptr[b->nopt] = b->opt_used_edges;
 }
 
-static void brute_dfs(brute_ctx *b, int32_t u, int64_t W) {
+static void brute_dfs(brute_ctx *b, int32_t u, int64_t W, int64_t T) {
     for (int32_t e = b->rp[u]; e < b->rp[u + 1]; ++e) {
         int32_t t = b->col[e];
         int64_t W2 = W + wmax(b->w, e, b->mode);
+        int64_t T2 = T + tval(b->tt, e);
         b->stk_e[b->depth] = e;
         if (t == b->s) {
-            brute_record(b, W2, b->depth + 1);
+            brute_record(b, W2, T2, b->depth + 1);
         } else if (t > b->s && !b->onpath[t]) {
             b->onpath[t] = 1;
             b->depth++;
-            brute_dfs(b, t, W2);
+            brute_dfs(b, t, W2, T2);
             b->depth--;
             b->onpath[t] = 0;
         }
     }
 }
 
-int oracle_brute(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, const int32_t *w,
-                 int mode, int64_t *num, int64_t *den, int64_t *ncycles, int32_t *opt_edges,
-                 int64_t opt_cap_edges, int64_t *opt_ptr, int64_t opt_cap, int64_t *nopt) {
+static int brute_impl(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                      const int32_t *w, const int32_t *tt, int mode, int64_t *num, int64_t *den,
+                      int64_t *ncycles, int32_t *opt_edges, int64_t opt_cap_edges,
+                      int64_t *opt_ptr, int64_t opt_cap, int64_t *nopt) {
     if (n <= 0 || n > 16 || !rp || !col || !w || (mode != 0 && mode != 1)) return OR_ERR_ARG;
+    if (tt)
+        for (int32_t e = 0; e < m; ++e)
+            if (tt[e] < 1) return OR_ERR_ARG;
     if (rp[0] != 0 || rp[n] != m) return OR_ERR_CSR;
     for (int32_t v = 0; v < n; ++v)
         if (rp[v + 1] < rp[v]) return OR_ERR_CSR;
@@ -508,7 +551,7 @@ int oracle_brute(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, co
         if (col[e] < 0 || col[e] >= n || w[e] == INT32_MIN) return OR_ERR_CSR;
     brute_ctx b;
     memset(&b, 0, sizeof b);
-    b.rp = rp; b.col = col; b.w = w; b.mode = mode;
+    b.rp = rp; b.col = col; b.w = w; b.tt = tt; b.mode = mode;
     int32_t stk[17];
     char onp[16];
     memset(onp, 0, sizeof onp);
@@ -523,7 +566,7 @@ int oracle_brute(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, co
         b.s = s;
         b.depth = 0;
         onp[s] = 1;
-        brute_dfs(&b, s, 0);
+        brute_dfs(&b, s, 0, 0);
         onp[s] = 0;
     }
     if (ncycles) *ncycles = b.ncycles;
@@ -533,6 +576,23 @@ int oracle_brute(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, co
     if (den) *den = b.bq / g;
     if (nopt) *nopt = b.nopt;
     return b.overflow ? OR_ERR_TOO_MANY : OR_OK;
+}
+
+int oracle_brute(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, const int32_t *w,
+                 int mode, int64_t *num, int64_t *den, int64_t *ncycles, int32_t *opt_edges,
+                 int64_t opt_cap_edges, int64_t *opt_ptr, int64_t opt_cap, int64_t *nopt) {
+    return brute_impl(n, m, rp, col, w, NULL, mode, num, den, ncycles, opt_edges, opt_cap_edges,
+                      opt_ptr, opt_cap, nopt);
+}
+
+/* Every simple cycle, best ratio w(C)/t(C) (transit times tt[m] >= 1). */
+int oracle_brute_ratio(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                       const int32_t *w, const int32_t *tt, int mode, int64_t *num, int64_t *den,
+                       int64_t *ncycles, int32_t *opt_edges, int64_t opt_cap_edges,
+                       int64_t *opt_ptr, int64_t opt_cap, int64_t *nopt) {
+    if (!tt) return OR_ERR_ARG;
+    return brute_impl(n, m, rp, col, w, tt, mode, num, den, ncycles, opt_edges, opt_cap_edges,
+                      opt_ptr, opt_cap, nopt);
 }
 
 /* ======================================================================== */
@@ -599,9 +659,10 @@ int32_t oracle_tarjan_scc(int32_t n, const int32_t *rp, const int32_t *col, int3
 /*
  * Checks, in the maximising sense (w negated in min mode, num negated too):
  *   (a) every edge e = (v, t): eta(t) <= eta(v)                 [code 1]
- *   (b) if eta(t) = eta(v) = p/q:  q*w(e) - p + V(t) - V(v) <= 0  [code 2]
+ *   (b) if eta(t) = eta(v) = p/q:  q*w(e) - p*t(e) + V(t) - V(v) <= 0
+ *       (t(e) = 1 for the mean)                                  [code 2]
  *   (c) the cycle is a closed walk of CSR edges, simple,
- *       and w(C) * den = num * |C|                                [codes 3,4,5]
+ *       and w(C) * den = num * t(C)  (t(C) = |C| for the mean)    [codes 3,4,5]
  *   (d) num/den = max_v eta(v), den > 0                          [code 6]
  * (a)+(b): summing (b) around any cycle (on which eta is constant by (a))
  * shows every cycle mean is <= the eta of its vertices <= max eta; (c)+(d)
@@ -609,10 +670,10 @@ int32_t oracle_tarjan_scc(int32_t n, const int32_t *rp, const int32_t *col, int3
  * Returns 0 if all hold, else the code of the first failure; *bad receives
  * the offending edge or vertex index.
  */
-int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
-                       const int32_t *w, int mode, const int64_t *eta_p, const int64_t *eta_q,
-                       const int64_t *V, int64_t num, int64_t den, const int32_t *cycle,
-                       int32_t clen, int64_t *bad) {
+static int certificate_impl(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                            const int32_t *w, const int32_t *tt, int mode, const int64_t *eta_p,
+                            const int64_t *eta_q, const int64_t *V, int64_t num, int64_t den,
+                            const int32_t *cycle, int32_t clen, int64_t *bad) {
     if (check_csr(n, m, rp, col)) return -1;
     if (mode != 0 && mode != 1) return -1;
     int64_t P = mode == 0 ? num : -num;
@@ -624,7 +685,8 @@ int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *c
             int c = frac_cmp(eta_p[t], eta_q[t], eta_p[v], eta_q[v]);
             if (c > 0) { if (bad) *bad = e; return 1; }
             if (c == 0) {
-                i128 red = (i128)eta_q[v] * wmax(w, e, mode) - eta_p[v] + V[t] - V[v];
+                i128 red = (i128)eta_q[v] * wmax(w, e, mode) - (i128)eta_p[v] * tval(tt, e) +
+                           V[t] - V[v];
                 if (red > 0) { if (bad) *bad = e; return 2; }
             }
         }
@@ -634,7 +696,7 @@ int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *c
     if (!seen) return -1;
     /* source of each cycle edge: binary search in rp */
     int32_t first_src = -1, prev_t = -1;
-    i128 W = 0;
+    i128 W = 0, Tc = 0;
     int code = 0;
     int32_t i = 0;
     for (i = 0; i < clen && !code; ++i) {
@@ -652,11 +714,12 @@ int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *c
         seen[src] = 1;
         prev_t = col[e];
         W += wmax(w, e, mode);
+        Tc += tval(tt, e);
     }
     free(seen);
     if (code) { if (bad) *bad = i; return code; }
     if (prev_t != first_src) return 3;
-    if (W * den != (i128)P * clen) return 5;
+    if (W * den != (i128)P * Tc) return 5;
     /* (d) */
     int32_t arg = 0;
     for (int32_t v = 1; v < n; ++v)
@@ -664,3 +727,23 @@ int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *c
     if (frac_cmp(eta_p[arg], eta_q[arg], P, den) != 0) { if (bad) *bad = arg; return 6; }
     return 0;
 }
+
+int oracle_certificate(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                       const int32_t *w, int mode, const int64_t *eta_p, const int64_t *eta_q,
+                       const int64_t *V, int64_t num, int64_t den, const int32_t *cycle,
+                       int32_t clen, int64_t *bad) {
+    return certificate_impl(n, m, rp, col, w, NULL, mode, eta_p, eta_q, V, num, den, cycle,
+                            clen, bad);
+}
+
+/* The same check for an optimal cycle ratio (transit times tt[m] >= 1). */
+int oracle_certificate_ratio(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                             const int32_t *w, const int32_t *tt, int mode,
+                             const int64_t *eta_p, const int64_t *eta_q, const int64_t *V,
+                             int64_t num, int64_t den, const int32_t *cycle, int32_t clen,
+                             int64_t *bad) {
+    if (!tt) return -1;
+    return certificate_impl(n, m, rp, col, w, tt, mode, eta_p, eta_q, V, num, den, cycle, clen,
+                            bad);
+}
+

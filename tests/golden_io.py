@@ -48,6 +48,48 @@ def closed_forms() -> list[ClosedForm]:
 
 
 @dataclass
+class RatioForm:
+    name: str
+    graph: synth.Graph
+    transit: np.ndarray
+    num: int
+    den: int
+    cycle: tuple
+
+
+def ratio_closed_forms() -> list[RatioForm]:
+    out: list[RatioForm] = []
+    cur = None
+    edges: list[tuple[int, int, int]] = []
+    times: list[int] = []
+
+    def flush():
+        if cur is not None:
+            name, n, mode, num, den, cyc = cur
+            g = synth.from_edges(n, edges, mode, name)
+            # from_edges keeps the order of appearance per source, and the
+            # fixture lists edges in CSR order, so times line up with edges
+            out.append(RatioForm(name, g, np.array(times, np.int32), num, den, cyc))
+
+    with open(os.path.join(GOLDEN, "ratio_closed_forms.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "graph":
+                flush()
+                cur = (tok[1], int(tok[2]), tok[3], int(tok[4]), int(tok[5]),
+                       tuple(int(x) for x in tok[6:]))
+                edges, times = [], []
+            else:
+                edges.append((int(tok[0]), int(tok[1]), int(tok[2])))
+                times.append(int(tok[3]))
+    flush()
+    return out
+
+
+@dataclass
 class Fig1:
     graph_max: synth.Graph
     graph_min: synth.Graph

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from golden_io import closed_forms, fig1, relabel
+from golden_io import closed_forms, fig1, ratio_closed_forms, relabel
 
 
 def _frac(num, den):
@@ -334,3 +334,66 @@ def test_warm_start_rejects_an_edge_of_another_vertex():
     assert e.value.code == -1
     h = oracle.howard(g.row_ptr, g.col_idx, g.w, init_policy=np.array([0, 1, 2], np.int32))
     assert h.value == 5
+
+
+# ---------------------------------------------------------- optimal cycle ratio
+# The cost/time labels of Sec. 2.2 give the optimal cycle ratio w(C)/t(C).
+# Pins: unit times reproduce the mean oracle bit for bit; brute-force
+# enumeration of every simple cycle on thousands of tiny graphs; hand-derived
+# closed forms (tests/golden/ratio_closed_forms.txt); scaling of w and t.
+def test_ratio_with_unit_times_is_the_mean():
+    rng = np.random.default_rng(1111062770)
+    graphs = [synth.tiny_random(rng, int(rng.integers(1, 12)), max_extra=3, wlo=-20, whi=20)
+              for _ in range(300)] + [synth.ring10k()]
+    for g in graphs:
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        r = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode, transit=np.ones(g.m, np.int32))
+        assert (r.num, r.den, r.iterations) == (h.num, h.den, h.iterations)
+        assert r.cycle.tolist() == h.cycle.tolist()
+        assert (r.V == h.V).all() and (r.eta_p == h.eta_p).all() and (r.eta_q == h.eta_q).all()
+
+
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_ratio_matches_brute_force_on_tiny_graphs(mode):
+    rng = np.random.default_rng(1111062771 + (mode == "min"))
+    for trial in range(1200):
+        n = int(rng.integers(1, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=bool(trial % 3 == 0),
+                              mode=mode)
+        t = rng.integers(1, 6, size=g.m).astype(np.int32)
+        h = oracle.howard(g.row_ptr, g.col_idx, g.w, mode, transit=t)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode, transit=t)
+        assert h.value == b.value, (trial, n)
+        assert tuple(int(e) for e in h.cycle) in b.optimal, trial
+        rc, bad = oracle.certificate(g.row_ptr, g.col_idx, g.w, mode, h.eta_p, h.eta_q, h.V,
+                                     h.num, h.den, h.cycle, transit=t)
+        assert rc == 0, (trial, rc, bad)
+
+
+@pytest.mark.parametrize("rf", ratio_closed_forms(), ids=lambda r: r.name)
+def test_ratio_closed_forms(rf):
+    g = rf.graph
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode, transit=rf.transit)
+    assert (h.num, h.den) == (rf.num, rf.den)
+    assert tuple(int(e) for e in h.cycle) == rf.cycle
+    b = oracle.brute(g.row_ptr, g.col_idx, g.w, g.mode, transit=rf.transit)
+    assert b.value == Fraction(rf.num, rf.den)
+
+
+def test_ratio_scaling_and_duality():
+    rng = np.random.default_rng(1111062773)
+    for trial in range(200):
+        g = synth.tiny_random(rng, int(rng.integers(2, 10)), max_extra=3, wlo=-30, whi=30)
+        t = rng.integers(1, 8, size=g.m).astype(np.int32)
+        base = oracle.howard(g.row_ptr, g.col_idx, g.w, "max", transit=t).value
+        k = int(rng.integers(2, 5))
+        assert oracle.howard(g.row_ptr, g.col_idx, g.w * k, "max", transit=t).value == k * base
+        assert oracle.howard(g.row_ptr, g.col_idx, g.w, "max", transit=t * k).value == base / k
+        lo = oracle.howard(g.row_ptr, g.col_idx, -g.w, "min", transit=t).value
+        assert lo == -base
+
+
+def test_ratio_rejects_nonpositive_times():
+    g = synth.from_edges(2, [(0, 1, 1), (1, 0, 1)])
+    with pytest.raises(oracle.OracleError):
+        oracle.howard(g.row_ptr, g.col_idx, g.w, transit=np.array([1, 0], np.int32))
