@@ -124,6 +124,156 @@ static __device__ __forceinline__ void block_append(int *list, int *s_cnt, bool 
     if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
 }
 
+
+constexpr int kRankDirectMax = 65536;   // all-pairs rank count up to this many cycles
+
+// Inclusive sum of x over the block (all threads call it; 1024 threads).
+static __device__ __forceinline__ int block_inclusive_scan(int x, int *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int wv = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wv, o);
+            if (lane >= o) wv += y;
+        }
+        s_warp[lane] = wv;
+    }
+    __syncthreads();
+    return x + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+// Dense ranks of the K cycle keys (rank = number of distinct keys below) for
+// policies with many cycles, where counting over all pairs would cost K^2: a
+// stable least-significant-digit radix sort of (key, cycle) pairs with 8-bit
+// digits across the cooperative grid, then a scan of the run starts of the
+// sorted keys.  Block b owns a contiguous chunk of positions in every pass;
+// per pass: per-block digit histograms, one exclusive scan in (digit, block)
+// order by block 0, and a stable scatter (warps of a block in turn, lanes
+// with equal digits ranked by a match mask).  A pass whose digit is the same
+// for all keys leaves the order unchanged and is skipped.  Scratch: the
+// detection jump states and worklists, which are dead at this point.
+// Returns false if a grid barrier gave up.
+static __device__ bool radix_ranks(int K, const Workspace &ws, Ctrl *c, unsigned nblocks) {
+    __shared__ int s_off[256];
+    __shared__ int s_warp[32];
+    __shared__ int s_skip;
+    unsigned long long *keyA = reinterpret_cast<unsigned long long *>(ws.cyc_key);
+    unsigned long long *keyB = reinterpret_cast<unsigned long long *>(ws.jm[0]);
+    int *idA = ws.list[1], *idB = ws.list[0];
+    const int G = (int)gridDim.x;
+    const int chunk = (K + G - 1) / G;
+    const int c0 = min(K, (int)blockIdx.x * chunk), c1 = min(K, c0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    // order-preserving unsigned image of the signed keys; identity ids
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+        keyA[i] ^= 0x8000000000000000ULL;
+        idA[i] = i;
+    }
+    for (int pass = 0; pass < 8; ++pass) {
+        const int sh = 8 * pass;
+        // two histogram buffers by pass parity: the skip test of one pass may
+        // still read its buffer while the next pass fills the other
+        int *hist = ws.list[2] + (pass & 1) * 256 * G;
+        if (threadIdx.x < 256) s_off[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x)
+            atomicAdd(&s_off[(int)((keyA[i] >> sh) & 255u)], 1);
+        __syncthreads();
+        if (threadIdx.x < 256) hist[threadIdx.x * G + blockIdx.x] = s_off[threadIdx.x];
+        if (!grid_barrier(c, nblocks)) return false;
+        if (blockIdx.x == 0) {
+            // exclusive scan of hist[0 .. 256 G) in place, per = entries per thread
+            const int total = 256 * G;
+            const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int b0 = min(total, (int)threadIdx.x * per), b1 = min(total, b0 + per);
+            int sum = 0;
+            for (int i = b0; i < b1; ++i) sum += hist[i];
+            const int incl = block_inclusive_scan(sum, s_warp);
+            int run = incl - sum;
+            for (int i = b0; i < b1; ++i) {
+                const int x = hist[i];
+                hist[i] = run;
+                run += x;
+            }
+        }
+        if (!grid_barrier(c, nblocks)) return false;
+        if (threadIdx.x == 0) s_skip = 0;
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int lo = hist[threadIdx.x * G];
+            const int hi = threadIdx.x < 255 ? hist[(threadIdx.x + 1) * G] : K;
+            if (hi - lo == K) s_skip = 1;
+            s_off[threadIdx.x] = hist[threadIdx.x * G + blockIdx.x];
+        }
+        __syncthreads();
+        if (s_skip) continue;   // the same decision in every block
+        for (int t0 = c0; t0 < c1; t0 += blockDim.x) {
+            const int i = t0 + (int)threadIdx.x;
+            const bool valid = i < c1;
+            const unsigned long long k = valid ? keyA[i] : 0ULL;
+            const int id = valid ? idA[i] : 0;
+            // lanes past the chunk get distinct dummy digits so they match nobody
+            const int dg = valid ? (int)((k >> sh) & 255u) : 256 + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, dg);
+            const int r = __popc(peers & ((1u << lane) - 1u));
+            const bool leader = r == 0;
+            for (int wv = 0; wv < nwarps; ++wv) {
+                int base = 0;
+                if (warp == wv && valid) base = s_off[dg];
+                __syncwarp();
+                if (warp == wv && valid) {
+                    keyB[base + r] = k;
+                    idB[base + r] = id;
+                    if (leader) s_off[dg] = base + __popc(peers);
+                }
+                __syncthreads();
+            }
+        }
+        unsigned long long *tk = keyA;
+        keyA = keyB;
+        keyB = tk;
+        int *ti = idA;
+        idA = idB;
+        idB = ti;
+        if (!grid_barrier(c, nblocks)) return false;
+    }
+    if (!grid_barrier(c, nblocks)) return false;
+    // dense ranks: rank at sorted position i = (run starts in [0, i]) - 1
+    int *bsum = ws.list[2];
+    int cnt = 0;
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x)
+        cnt += (i == 0 || keyA[i] != keyA[i - 1]) ? 1 : 0;
+    const int tot = block_inclusive_scan(cnt, s_warp);
+    if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = tot;
+    if (!grid_barrier(c, nblocks)) return false;
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int k = 0; k < (int)blockIdx.x; ++k) b += bsum[k];
+        s_off[0] = b;
+    }
+    __syncthreads();
+    int carry = s_off[0];
+    for (int t0 = c0; t0 < c1; t0 += blockDim.x) {
+        const int i = t0 + (int)threadIdx.x;
+        const int f = (i < c1 && (i == 0 || keyA[i] != keyA[i - 1])) ? 1 : 0;
+        const int incl = block_inclusive_scan(f, s_warp);
+        if (i < c1) ws.cyc_rank[idA[i]] = carry + incl - 1;
+        carry += s_warp[nwarps - 1];
+        __syncthreads();
+    }
+    return grid_barrier(c, nblocks);
+}
+
 constexpr int kMinMask = 0x7fffffff;
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
@@ -381,27 +531,33 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         ws.cid_of_root[root] = i;
     }
     if (!grid_barrier(c, nblocks)) return;
-    for (int base = first; base < K; base += stride) {
-        const int i = base + threadIdx.x;
-        const long long key = i < K ? ws.cyc_key[i] : 0;
-        int rank = 0;
-        for (int t0 = 0; t0 < K; t0 += kRankTile) {
-            int tn = min(kRankTile, K - t0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
-            __syncthreads();
-            for (int q = 0; q < tn; ++q) rank += (s_key[q] < key);
+    if (K > kRankDirectMax && n >= 2 * 256 * (int)gridDim.x) {
+        if (!radix_ranks(K, ws, c, nblocks)) return;
+    } else {
+        // all pairs: rank(i) = number of cycle keys below key(i)
+        for (int base = first; base < K; base += stride) {
+            const int i = base + threadIdx.x;
+            const long long key = i < K ? ws.cyc_key[i] : 0;
+            int rank = 0;
+            for (int t0 = 0; t0 < K; t0 += kRankTile) {
+                int tn = min(kRankTile, K - t0);
+                __syncthreads();
+                for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
+                __syncthreads();
+                for (int q = 0; q < tn; ++q) rank += (s_key[q] < key);
+            }
+            if (i < K) ws.cyc_rank[i] = rank;
         }
-        if (i < K) {
-            ws.cyc_rank[i] = rank;
-            const int root = ws.cyc_root[i];
-            unsigned long long packed = ((unsigned long long)(unsigned)rank << 32) |
-                                        (unsigned)(INT_MAX - root);
-            atomicMax(&c->best, packed);
-            // batched: Alg. 4's region-specific vote, one region per graph,
-            // deterministic because the packed key is a total order
-            if (bs.G) atomicMax(&bs.gbest[bs.gid[root]], packed);
-        }
+    }
+    for (int i = first + threadIdx.x; i < K; i += stride) {
+        const int rank = ws.cyc_rank[i];
+        const int root = ws.cyc_root[i];
+        unsigned long long packed = ((unsigned long long)(unsigned)rank << 32) |
+                                    (unsigned)(INT_MAX - root);
+        atomicMax(&c->best, packed);
+        // batched: Alg. 4's region-specific vote, one region per graph,
+        // deterministic because the packed key is a total order
+        if (bs.G) atomicMax(&bs.gbest[bs.gid[root]], packed);
     }
     if (!grid_barrier(c, nblocks)) return;
 

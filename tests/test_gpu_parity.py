@@ -121,6 +121,25 @@ def test_all_self_loops_many_cycles():
     assert_certificate(g, sol)
 
 
+@pytest.mark.parametrize("wrange", [(-1000, 1000), (-3, 3)], ids=["distinct", "duplicates"])
+def test_rank_many_cycles_by_radix(wrange):
+    """More than 65,536 cycles in the first policy (heavy self-loops): the
+    exact ranks come from the radix-sort path; with weights in -3..3 most of
+    the 200,000 cycle means are equal (duplicate keys, negative keys)."""
+    rng = np.random.default_rng(41 + wrange[1])
+    n = 200000
+    lo, hi = wrange
+    edges = []
+    for v in range(n):
+        edges.append((v, v, int(rng.integers(lo, hi + 1)) + 2 * hi))
+        edges.append((v, (v + 1) % n, int(rng.integers(lo, hi + 1))))
+        edges.append((v, int(rng.integers(0, n)), int(rng.integers(lo, hi + 1))))
+    g = synth.from_edges(n, edges)
+    sol = gpu_solve(g, certificate=True)
+    assert_parity(g, sol)
+    assert_certificate(g, sol)
+
+
 def test_long_single_ring_extraction():
     """A critical cycle with 2^17 + 3 edges (many lifting bits in extraction)."""
     n = (1 << 17) + 3
