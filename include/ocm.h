@@ -105,6 +105,17 @@ typedef struct ocm_options {
      * earlier solve (the `policy` output) resumes from it: re-solving after
      * a small weight change typically takes a few iterations.             */
     const int32_t *init_policy;
+    /* Optimal cycle ratio (optional, device [m]; [M] for ocm_solve_batch):
+     * a transit time t(e) >= 1 per edge (OCM_ERR_INVALID_ARG otherwise), the
+     * "time" label of a transition next to its cost w (Sec. 2.2).  The solve
+     * then returns the maximum (minimum) over cycles C of w(C)/t(C) as
+     * num/den and a cycle attaining it; t = 1 everywhere gives the mean.
+     * The per-vertex outputs are the ratio of the reached cycle and the
+     * value V(v) = eta_den[v] * (s*w-weight of v's path to the cycle's
+     * smallest vertex) - eta_num[v] * (its transit time).  Exactness bound:
+     * 4 n^2 max|w| max t < 2^62 and n max t < 2^31 (OCM_ERR_OVERFLOW).  The
+     * improvement sweep always uses OCM_SWEEP_CLASSES in this mode.         */
+    const int32_t *transit;
 } ocm_options;
 
 /* Layouts of the improvement sweep (results do not depend on the choice).
@@ -216,6 +227,21 @@ int ocm_backward(const int32_t *cycle_edges, int32_t cycle_len, const float *gra
                  int32_t m, float *grad_w, void *stream);
 
 /*
+ * ocm_backward_ratio -- the gradient of an optimal cycle ratio
+ * lambda* = w(C*)/t(C*) (a solve with ocm_options.transit).  While C* stays
+ * optimal, lambda* is linear in the weights of C* with slope 1/t(C*), so
+ * grad_w[e] = grad_lambda[0] / t(C*) for e in C* and 0 otherwise; t(C*) is
+ * summed on the device from transit over cycle_edges.
+ *   cycle_edges : device [cycle_len], distinct edge indices in [0, m)
+ *   transit     : device [m] int32 transit times, as given to the solve
+ *   grad_lambda : device [1] float, upstream gradient
+ *   grad_w      : device [m] float, fully overwritten
+ * Asynchronous on `stream`.
+ */
+int ocm_backward_ratio(const int32_t *cycle_edges, int32_t cycle_len, const int32_t *transit,
+                       const float *grad_lambda, int32_t m, float *grad_w, void *stream);
+
+/*
  * ocm_backward_batch -- the gradient of every graph's lambda* for a batched
  * solve: grad_w[e] = grad_lambda[g] / cycle_len[g] for each edge e of graph
  * g's critical cycle, 0 for every other edge (as ocm_backward, per graph).
@@ -254,11 +280,11 @@ int ocm_profile_collect(double *ms_out, int64_t *launches_out);
  * The scratch space is a fixed array of OCM_STATIC_WORKSPACE_BYTES inside
  * the library's GPU image: every device that loads the library holds it
  * until the process exits.  Graphs with ocm_workspace_size(n, m) larger than
- * that (about 250,000 vertices) are rejected with OCM_ERR_WORKSPACE before
- * any device work.  The call allocates nothing: no cudaMalloc, no cudaFree,
- * no allocating library routine (benchmark instrumentation is paused while it
- * runs).  Arguments, outputs, synchronisation and errors are those of
- * ocm_solve.
+ * that (about 195,000 vertices at mean out-degree 4) are rejected with
+ * OCM_ERR_WORKSPACE before any device work.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine (benchmark
+ * instrumentation is paused while it runs).  Arguments, outputs,
+ * synchronisation and errors are those of ocm_solve.
  *
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any stream
@@ -277,7 +303,8 @@ int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, const int32
 /* Text for a status code (static storage). */
 const char *ocm_status_string(int status);
 
-/* ABI version: 100 * major + minor (101: ocm_options.init_policy). */
+/* ABI version: 100 * major + minor (101: ocm_options.init_policy; 102:
+ * ocm_options.transit and ocm_backward_ratio). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -82,7 +82,7 @@ class OcmOptions(ctypes.Structure):
                 ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
                 ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
                 ("sweep_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("init_policy", ctypes.c_void_p)]
+                ("init_policy", ctypes.c_void_p), ("transit", ctypes.c_void_p)]
 
 
 class OcmStats(ctypes.Structure):
@@ -107,6 +107,9 @@ SIGNATURES = {
                                  ctypes.POINTER(OcmStats)]),
     "ocm_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "ocm_backward_ratio": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "ocm_workspace_size_batch": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "ocm_backward_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,

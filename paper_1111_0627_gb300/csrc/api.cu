@@ -53,6 +53,11 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.tile_fopen = static_cast<int *>(take(4 * T));
     w.tile_first = static_cast<TilePart *>(take(sizeof(TilePart) * T));
     w.tile_last = static_cast<TilePart *>(take(sizeof(TilePart) * T));
+    w.tpi = static_cast<int *>(take(4 * N));
+    w.jt[0] = static_cast<long long *>(take(8 * N));
+    w.jt[1] = static_cast<long long *>(take(8 * N));
+    w.recp = static_cast<long long *>(take(8 * N));
+    w.transit = nullptr;
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align_up(off, 256);
@@ -97,6 +102,30 @@ batch_cycle_grad_kernel(const int *vptr, const int *cyc, const int *clen, const 
             const int e = cyc[base + i];
             if ((unsigned)e < (unsigned)m) g[e] = val;
         }
+    }
+}
+
+// Cycle ratio: every edge of C* gets grad_lambda / t(C*); one block sums
+// t(C*) and then scatters (the cycle is short next to the m-long zero fill).
+__global__ void __launch_bounds__(kThreads)
+cycle_grad_ratio_kernel(const int *cyc, int L, const int *transit, const float *gl, float *g,
+                        int m) {
+    __shared__ long long s_sum[kThreads / 32];
+    long long T = 0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int e = cyc[i];
+        if ((unsigned)e < (unsigned)m) T += transit[e];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xffffffffu, T, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = T;
+    __syncthreads();
+    long long tot = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_sum[k];
+    const float val = __fdiv_rn(gl[0], (float)tot);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int e = cyc[i];
+        if ((unsigned)e < (unsigned)m) g[e] = val;
     }
 }
 
@@ -162,7 +191,8 @@ static int persistent_grid() {
 
 static int map_err_bits(int err) {
     if (err & kErrTimeout) return OCM_ERR_TIMEOUT;
-    if (err & kErrInitPolicy) return OCM_ERR_INVALID_ARG;
+    if (err & (kErrInitPolicy | kErrTransit)) return OCM_ERR_INVALID_ARG;
+    if (err & kErrRatioKey) return OCM_ERR_OVERFLOW;
     if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
     if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
     if (err & kErrWeightMin) return OCM_ERR_OVERFLOW;
@@ -241,13 +271,14 @@ namespace {
 // Instantiated loop graphs, keyed by everything their kernel nodes bake in.
 struct LoopKey {
     int dev;
-    const void *row_ptr, *col_idx, *w, *ctrl, *vptr;
+    const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
     int n, m, sign, threads, stall, G, kind, epl;
     long long N2, max_iters;
     int cls_cnt[kClasses];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
-            ctrl != o.ctrl || vptr != o.vptr || n != o.n || m != o.m || sign != o.sign ||
+            ctrl != o.ctrl || vptr != o.vptr || transit != o.transit || n != o.n || m != o.m ||
+            sign != o.sign ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters)
             return false;
@@ -281,6 +312,7 @@ LoopKey make_key(const StepArgs &a) {
     k.w = a.w;
     k.ctrl = a.ws.ctrl;
     k.vptr = a.bs.vptr;
+    k.transit = a.ws.transit;
     k.n = a.n;
     k.m = a.m;
     k.kind = a.kind;
@@ -411,7 +443,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 101; }
+int ocm_version(void) { return 102; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -460,6 +492,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Workspace ws;
     carve_workspace(workspace, n, m, &ws);
+    ws.transit = opt ? opt->transit : nullptr;   // optimal cycle ratio when set
+    const bool ratio = ws.transit != nullptr;
     const int sign = (mode == OCM_MAX) ? 1 : -1;
     const int grid = persistent_grid();
     long long launches = 0;
@@ -483,8 +517,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
                        bs ? &b : nullptr, st);
     launches += 1;
-    const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES) ? OCM_SWEEP_TILES
-                                                                : OCM_SWEEP_CLASSES;
+    // (the edge-tiled sweep has no cycle-ratio form)
+    const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES && !ratio) ? OCM_SWEEP_TILES
+                                                                          : OCM_SWEEP_CLASSES;
     int epl = (opt && opt->edges_per_lane > 0) ? opt->edges_per_lane : kEdgesPerLane;
     if (epl > 64) epl = 64;
     if (kind == OCM_SWEEP_TILES) epl = epl <= 4 ? 4 : 8;
@@ -499,12 +534,17 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (h.err) return map_err_bits(h.err);
     // Cycles never span graphs, so the largest cycle length (and denominator)
     // is bounded by the largest graph.  Exactness bound: 2 n_max^2 max|w| <
-    // 2^62 keeps every value, key and cross product inside int64.
+    // 2^62 keeps every value, key and cross product inside int64.  Cycle
+    // ratio: values q*S - p*T and keys q*w - p*t + V are bounded by
+    // 4 n_max^2 max|w| max t, and a cycle's time n_max max t must fit int32.
     const long long nmax = bs ? h.max_ng : n;
     {
         unsigned __int128 bound = (unsigned __int128)2 * (unsigned long long)nmax *
                                   (unsigned long long)nmax * (unsigned)h.maxabsw;
+        if (ratio) bound *= 2 * (unsigned __int128)(unsigned)h.maxt;
         if (bound >= ((unsigned __int128)1 << 62)) return OCM_ERR_OVERFLOW;
+        if (ratio && (unsigned long long)nmax * (unsigned)h.maxt > 0x7fffffffULL)
+            return OCM_ERR_OVERFLOW;
     }
     const long long N2 = nmax * nmax;
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
@@ -529,9 +569,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.bs = b;
     sa.batch = bs != nullptr;
     for (int c = 0; c < kClasses; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
-    if (prepare_evaluate() != 0 ||
+    if (prepare_evaluate(ratio) != 0 ||
         (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
-                                 : prepare_sweep_classes(sa.threads)) != 0)
+                                 : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
     const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || g_prof_on;
     const int slot = host_loop ? -1 : acquire_loop(sa);
@@ -682,6 +722,20 @@ int ocm_backward_batch(const int32_t *graph_vptr, const int32_t *cycle_out,
     if (gb > 4096) gb = 4096;
     batch_cycle_grad_kernel<<<gb, kThreads, 0, st>>>(graph_vptr, cycle_out, cycle_len, grad_lambda,
                                                      G, grad_w, M);
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    return OCM_OK;
+}
+
+int ocm_backward_ratio(const int32_t *cycle_edges, int32_t cycle_len, const int32_t *transit,
+                       const float *grad_lambda, int32_t m, float *grad_w, void *stream) {
+    if (!cycle_edges || !transit || !grad_lambda || !grad_w) return OCM_ERR_INVALID_ARG;
+    if (m < 1 || cycle_len < 1 || cycle_len > m) return OCM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int blocks = (m + kThreads - 1) / kThreads;
+    if (blocks > 8192) blocks = 8192;
+    zero_float_kernel<<<blocks, kThreads, 0, st>>>(grad_w, m);
+    cycle_grad_ratio_kernel<<<1, kThreads, 0, st>>>(cycle_edges, cycle_len, transit, grad_lambda,
+                                                    grad_w, m);
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     return OCM_OK;
 }

@@ -86,6 +86,8 @@ struct Ctrl {
     int loop_more;            // the last step asks for another one
     int not_converged;        // the iteration cap was reached
     long long switched_total; // switches summed over all sweeps
+    int maxt;                 // cycle ratio: largest transit time
+    int qmax;                 // cycle ratio: largest ratio denominator of the current cycles
 };
 
 enum : int {
@@ -99,6 +101,8 @@ enum : int {
     kErrTimeout = 128,    // a grid barrier wait exceeded its spin limit
     kErrSweep = 256,      // a vertex's current policy edge was not among its edges
     kErrInitPolicy = 512, // a caller-given initial policy edge is not an out-edge of its vertex
+    kErrTransit = 1024,   // a transit time below 1
+    kErrRatioKey = 2048,  // cycle ratio: the exact order keys of the current cycles overflow int64
 };
 
 // Workspace carved from one caller-provided buffer.
@@ -129,6 +133,11 @@ struct Workspace {
                           //     still has edges after this tile
     struct TilePart *tile_first;  // [T] best and current-edge key of that vertex in this tile
     struct TilePart *tile_last;   // [T] the same for tile_pend's vertex, up to the tile's end
+    // optimal cycle ratio (used only when transit != nullptr)
+    const int *transit;   // caller's transit times t(e) >= 1 (input, not workspace memory)
+    int *tpi;             // [n] transit time of the policy edge
+    long long *jt[2];     // [n] value jumping: transit time of the path from v to J
+    long long *recp;      // [n] numerator p of the ratio of v's cycle (gathered by the sweep)
     Ctrl *ctrl;
 };
 
@@ -247,8 +256,8 @@ int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspac
 // Host-side kernel configuration (shared-memory opt-in, occupancy), done
 // before the loop so that a captured loop graph holds launches only;
 // 0 on success.
-int prepare_evaluate();
-int prepare_sweep_classes(int threads);
+int prepare_evaluate(bool ratio);
+int prepare_sweep_classes(int threads, bool ratio);
 int prepare_sweep_tiles(int edges_per_lane, int threads);
 int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                        int edges_per_lane, Workspace ws, BatchState bs, int threads,

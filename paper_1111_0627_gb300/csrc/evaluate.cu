@@ -276,6 +276,9 @@ static __device__ bool radix_ranks(int K, const Workspace &ws, Ctrl *c, unsigned
 
 constexpr int kMinMask = 0x7fffffff;
 
+// RATIO: optimal cycle ratio (transit times carried through values and
+// cycles); a separate instance so that the mean keeps its register budget.
+template <bool RATIO>
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_test, Workspace ws,
                 BatchState bs) {
@@ -294,9 +297,11 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     const int lo = min((int)blockIdx.x * R, n), hi = min(lo + R, n);
     int *LA = ws.list[0] + lo, *LB = ws.list[1] + lo;
 
+    constexpr bool ratio = RATIO;   // optimal cycle ratio: times ride along
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->nrep = 0;
         c->best = 0;
+        c->qmax = 0;
     }
     for (int g = first + threadIdx.x; g < bs.G; g += stride) bs.gbest[g] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
@@ -428,6 +433,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                 if (d.M) {
                     const int root = ~d.J;
                     JLS st;
+                    long long T = 0;
                     bool fin = true;
                     if (root == v) {
                         st = JLS{~v, 0, 0};
@@ -435,9 +441,14 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                         const int sv = ws.succ[v];
                         fin = (ws.rep[sv] == sv);
                         st = JLS{fin ? ~sv : sv, 1, (long long)ws.wpi[v]};
+                        if (ratio) T = ws.tpi[v];
                     }
                     ws.jls[0][v] = st;
                     if (fin) ws.jls[1][v] = st;
+                    if (ratio) {
+                        ws.jt[0][v] = T;
+                        if (fin) ws.jt[1][v] = T;
+                    }
                     keep = !fin;
                 }
             }
@@ -456,12 +467,16 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         for (int j = 1;; ++j) {
             const JLS *in = ws.jls[(j + 1) & 1];
             JLS *out = ws.jls[j & 1];
+            // cycle ratio: the transit time of the path to J, jumped alongside
+            const long long *tin = ws.jt[(j + 1) & 1];
+            long long *tout = ws.jt[j & 1];
             int *lin = (j & 1) ? LA : LB;
             int *lout = (j & 1) ? LB : LA;
             int pend = 0;
             for (int i0 = 0; i0 < cnt; i0 += kU * blockDim.x) {
                 int item[kU];
                 JLS s[kU], t[kU];
+                long long ts[kU], tt[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int i = i0 + u * blockDim.x + threadIdx.x;
@@ -470,11 +485,17 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int it = item[u];
-                    if (it != INT_MIN) s[u] = in[it < 0 ? ~it : it];
+                    if (it != INT_MIN) {
+                        s[u] = in[it < 0 ? ~it : it];
+                        if (ratio) ts[u] = tin[it < 0 ? ~it : it];
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
+                    if (item[u] != INT_MIN && item[u] >= 0) {
+                        t[u] = in[s[u].J];
+                        if (ratio) tt[u] = tin[s[u].J];
+                    }
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int it = item[u];
@@ -484,9 +505,11 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                         v = it < 0 ? ~it : it;
                         if (it < 0) {
                             out[v] = s[u];    // final last round: copy forward
+                            if (ratio) tout[v] = ts[u];
                         } else {
                             const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
                             out[v] = nu;
+                            if (ratio) tout[v] = ts[u] + tt[u];
                             fin = nu.J < 0;
                             keep = !fin;
                             ++pend;
@@ -515,22 +538,45 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     }
 
     // ------------------------------------------------------------ cycles
+    // mean W/L, or for the cycle ratio W/T with T the cycle's transit time
     const int K = load_volatile(&c->nrep);
+    int qmax = 0;
     for (int i = first + threadIdx.x; i < K; i += stride) {
         int root = ws.cyc_root[i];
         int x = ws.succ[root];
         JLS st = ws.jls[0][x];
         long long W = (long long)ws.wpi[root] + st.S;
         long long L = 1 + (long long)st.len;
-        long long g = gcd_ll(W, L);
-        long long p = W / g, q = L / g;
+        const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[0][x] : L;
+        long long g = gcd_ll(W, Tc);
+        long long p = W / g, q = Tc / g;
         ws.cyc_p[i] = p;
         ws.cyc_q[i] = (int)q;
         ws.cyc_L[i] = (int)L;
-        ws.cyc_key[i] = mean_key(p, q, N2);
+        if (!ratio) ws.cyc_key[i] = mean_key(p, q, N2);
+        qmax = max(qmax, (int)q);
         ws.cid_of_root[root] = i;
     }
+    if (ratio) {
+        // the order keys need N2 >= (largest denominator)^2 to separate
+        // distinct ratios; the current cycles' largest one keeps them small
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+        if (lane == 0 && qmax) atomicMax(&c->qmax, qmax);
+    }
     if (!grid_barrier(c, nblocks)) return;
+    if (ratio) {
+        const long long qm = load_volatile(&c->qmax);
+        const long long N2r = qm * qm;
+        // |key| <= max|w| * N2r (every ratio is at most max|w| in size, t >= 1)
+        if ((__int128)N2r * (__int128)(c->maxabsw + 1) >= ((__int128)1 << 62)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrRatioKey);
+            return;
+        }
+        for (int i = first + threadIdx.x; i < K; i += stride)
+            ws.cyc_key[i] = mean_key(ws.cyc_p[i], ws.cyc_q[i], N2r);
+        if (!grid_barrier(c, nblocks)) return;
+    }
     if (K > kRankDirectMax && n >= 2 * 256 * (int)gridDim.x) {
         if (!radix_ranks(K, ws, c, nblocks)) return;
     } else {
@@ -573,10 +619,12 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         long long p = ws.cyc_p[i];
         int q = ws.cyc_q[i];
         Rec rec;
-        rec.V = (long long)q * st.S - p * (long long)st.len;
+        const long long T = ratio ? ws.jt[0][v] : (long long)st.len;
+        rec.V = (long long)q * st.S - p * T;
         rec.rank = ws.cyc_rank[i];
         rec.q = q;
         ws.rec[v] = rec;
+        if (ratio) ws.recp[v] = p;
     }
 }
 
@@ -586,7 +634,9 @@ static int ceil_log2(long long x) {
     return k;
 }
 
-// Co-resident CTAs of the evaluation kernel on the current device.
+// Co-resident CTAs of the evaluation kernel (mean or ratio instance) on the
+// current device.
+template <bool RATIO>
 static int evaluate_grid() {
     static int cached_dev = -1, cached = 0;
     int dev = 0;
@@ -594,21 +644,25 @@ static int evaluate_grid() {
     if (dev == cached_dev && cached > 0) return cached;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel, kEvalThreads, 0) !=
-            cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel<RATIO>,
+                                                      kEvalThreads, 0) != cudaSuccess ||
+        per_sm < 1)
         return 0;
     cached_dev = dev;
     cached = sms * per_sm;
     return cached;
 }
 
-int prepare_evaluate() { return evaluate_grid() > 0 ? 0 : -1; }
+int prepare_evaluate(bool ratio) {
+    return (ratio ? evaluate_grid<true>() : evaluate_grid<false>()) > 0 ? 0 : -1;
+}
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
 // launch failure.
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
                     cudaStream_t st) {
-    int blocks = evaluate_grid();
+    const bool ratio = ws.transit != nullptr;
+    int blocks = ratio ? evaluate_grid<true>() : evaluate_grid<false>();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
     if (need < blocks) blocks = need;
@@ -628,8 +682,11 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     prof_begin(kProfEvaluate, st);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, evaluate_kernel, n, N2, max_detect, max_value,
-                                       stall_test, ws, bs);
+    cudaError_t e =
+        ratio ? cudaLaunchKernelEx(&cfg, evaluate_kernel<true>, n, N2, max_detect, max_value,
+                                   stall_test, ws, bs)
+              : cudaLaunchKernelEx(&cfg, evaluate_kernel<false>, n, N2, max_detect, max_value,
+                                   stall_test, ws, bs);
     prof_end(kProfEvaluate, st);
     return e == cudaSuccess ? 1 : -1;
 }

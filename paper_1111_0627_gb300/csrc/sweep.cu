@@ -58,19 +58,22 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 }
 
 // Initial policy (Alg. 1's first pass from val = 0, lambda = 0): the heaviest
-// out-edge in the s*w sense, ties to the smallest edge index -- or, for a warm
-// start, the caller's policy (init != nullptr), which must name an out-edge
-// of each vertex.  The same pass validates col_idx and w and measures max|w|
-// for the exactness bound.
+// out-edge in the s*w sense, ties to the smallest edge index (for the cycle
+// ratio too: with lambda = 0 the key w(e) - lambda t(e) is w(e)) -- or, for a
+// warm start, the caller's policy (init != nullptr), which must name an
+// out-edge of each vertex.  The same pass validates col_idx, w and the
+// transit times and measures max|w| and max t for the exactness bound.
 __global__ void __launch_bounds__(kThreads)
 init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
                    const int *__restrict__ init, Workspace ws) {
     __shared__ int s_maxw[kThreads / 32];
+    __shared__ int s_maxt[kThreads / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int stride = gridDim.x * blockDim.x;
-    int maxabs = 0;
+    const int *__restrict__ tt = ws.transit;
+    int maxabs = 0, maxt = 0;
     for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
         const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
         const int my_g = gid ? gid[v] : 0;
@@ -90,6 +93,14 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 x = 0;
             }
             maxabs = max(maxabs, x < 0 ? -x : x);
+            if (tt) {
+                const int te = __ldg(&tt[e]);
+                if (te < 1) {
+                    atomicOr(&ws.ctrl->err, kErrTransit);
+                    atomicMin(&ws.ctrl->bad_index, e);
+                }
+                maxt = max(maxt, te);
+            }
             const long long k = (long long)sign * x;
             if (k > best_key) {
                 best_key = k;
@@ -110,17 +121,31 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         ws.pi[v] = best_e;
         ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
         ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
+        if (tt) ws.tpi[v] = __ldg(&tt[best_e]);
         ws.sw_iter[v] = 0;   // the first evaluation treats every vertex as changed
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
-    if (lane == 0) s_maxw[tid >> 5] = maxabs;
+    for (int o = 16; o > 0; o >>= 1) {
+        maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
+        maxt = max(maxt, __shfl_xor_sync(0xffffffffu, maxt, o));
+    }
+    if (lane == 0) {
+        s_maxw[tid >> 5] = maxabs;
+        s_maxt[tid >> 5] = maxt;
+    }
     __syncthreads();
     if (tid < 32) {
         int x = tid < kThreads / 32 ? s_maxw[tid] : 0;
+        int y = tid < kThreads / 32 ? s_maxt[tid] : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if (tid == 0) atomicMax(&ws.ctrl->maxabsw, x);
+        for (int o = 16; o > 0; o >>= 1) {
+            x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+            y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
+        }
+        if (tid == 0) {
+            atomicMax(&ws.ctrl->maxabsw, x);
+            if (tt) atomicMax(&ws.ctrl->maxt, y);
+        }
     }
 }
 
@@ -239,16 +264,24 @@ struct ClassGrid {
     int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
 };
 
+// Candidate of edge e.  Cycle ratio (RATIO): the key also subtracts
+// p_t * t(e), the target's ratio numerator times the edge's transit time;
+// for the mean t(e) = 1 and p_t is the same for every target of equal rank,
+// so the term is dropped.
+template <bool RATIO>
 static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
                                                  const int *__restrict__ w, const int4 *rec,
-                                                 int sign, int e) {
+                                                 const Workspace &ws, int sign, int e) {
     const int t = __ldg(&col[e]);
     const int x = __ldg(&w[e]);
     const int4 r = __ldg(&rec[t]);
     const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
-    return Cand{r.z, e, (long long)r.w * (long long)(sign * x) + V};
+    long long key = (long long)r.w * (long long)(sign * x) + V;
+    if (RATIO) key -= __ldg(&ws.recp[t]) * (long long)__ldg(&ws.transit[e]);
+    return Cand{r.z, e, key};
 }
 
+template <bool RATIO>
 __global__ void __launch_bounds__(kSweepMaxThreads)
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, Workspace ws,
@@ -283,13 +316,13 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             const int a = __ldg(&row_ptr[v]), e_end = __ldg(&row_ptr[v + 1]);
             int e = a + sub;
             for (; e + g < e_end; e += 2 * g) {   // two independent gathers in flight
-                Cand x0 = edge_cand(col, w, rec, sign, e);
-                Cand x1 = edge_cand(col, w, rec, sign, e + g);
+                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
+                Cand x1 = edge_cand<RATIO>(col, w, rec, ws, sign, e + g);
                 if (better(x0, best)) best = x0;
                 if (better(x1, best)) best = x1;
             }
             if (e < e_end) {
-                Cand x0 = edge_cand(col, w, rec, sign, e);
+                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
                 if (better(x0, best)) best = x0;
             }
         }
@@ -307,11 +340,13 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             const int t = ws.succ[v];
             const int4 r = __ldg(&rec[t]);
             const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
-            const long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
+            long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
+            if (RATIO) cur_key -= __ldg(&ws.recp[t]) * (long long)ws.tpi[v];
             if (best.rank > r.z || (best.rank == r.z && best.key > cur_key)) {
                 ws.pi[v] = best.e;
                 ws.succ[v] = __ldg(&col[best.e]);
                 ws.wpi[v] = sign * __ldg(&w[best.e]);
+                if (RATIO) ws.tpi[v] = __ldg(&ws.transit[best.e]);
                 ws.sw_iter[v] = next_eval;
                 if (bs.G) {
                     const int g = bs.gid[v];
@@ -344,6 +379,7 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
 
 // Co-resident blocks of the degree-class sweep per block size on the current
 // device (host-side configuration, done before any launch is captured).
+template <bool RATIO>
 static int classes_grid(int threads) {
     static int cached_dev[3] = {-1, -1, -1}, cached_blocks[3] = {0, 0, 0};
     const int slot = threads == 128 ? 0 : threads == 256 ? 1 : 2;
@@ -352,8 +388,8 @@ static int classes_grid(int threads) {
     if (cached_dev[slot] != dev) {
         int sms = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel, threads, 0) !=
-                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel<RATIO>, threads,
+                                                          0) != cudaSuccess ||
             sms <= 0 || per_sm <= 0)
             return 0;
         cached_blocks[slot] = sms * per_sm;
@@ -362,9 +398,9 @@ static int classes_grid(int threads) {
     return cached_blocks[slot];
 }
 
-int prepare_sweep_classes(int threads) {
+int prepare_sweep_classes(int threads, bool ratio) {
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
-    return classes_grid(threads) > 0 ? 0 : -1;
+    return (ratio ? classes_grid<true>(threads) : classes_grid<false>(threads)) > 0 ? 0 : -1;
 }
 
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
@@ -379,13 +415,17 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     cg.task_off[kClasses] = tasks;
     if (tasks == 0) return 0;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
-    const int grid_blocks = classes_grid(threads);
+    const bool ratio = ws.transit != nullptr;
+    const int grid_blocks = ratio ? classes_grid<true>(threads) : classes_grid<false>(threads);
     if (grid_blocks <= 0) return -1;
     const int wpb = threads / 32;
     int blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;
     prof_begin(kProfSweep, st);
-    improve_kernel<<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
+    if (ratio)
+        improve_kernel<true><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
+    else
+        improve_kernel<false><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
     prof_end(kProfSweep, st);
     return 1;
 }

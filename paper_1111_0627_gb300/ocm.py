@@ -67,6 +67,15 @@ def _init_policy(init_policy, n: int):
     return t
 
 
+def _transit(transit, m: int):
+    if transit is None:
+        return None
+    t = _dev_i32(transit, "transit")
+    if t.numel() != m:
+        raise ValueError("transit needs one entry per edge")
+    return t
+
+
 def workspace_bytes(n: int, m: int) -> int:
     return int(_native.load().ocm_workspace_size(n, m))
 
@@ -102,7 +111,8 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
           certificate: bool = False, cycle_out: torch.Tensor | None = None,
           flags: int = 0, edges_per_lane: int = 0, sweep_threads: int = 0,
           sweep_kind: int = 0, tune: bool = False,
-          init_policy: torch.Tensor | None = None) -> Solution:
+          init_policy: torch.Tensor | None = None,
+          transit: torch.Tensor | None = None) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
@@ -137,6 +147,9 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     init = _init_policy(init_policy, n)
     if init is not None:
         opt.init_policy = init.data_ptr()
+    tt = _transit(transit, m)
+    if tt is not None:
+        opt.transit = tt.data_ptr()
     extra = {}
     if certificate:
         extra = dict(eta_num=torch.empty(n, dtype=torch.int64, device=dev),
@@ -180,10 +193,12 @@ def workspace_bytes_batch(G: int, N: int, M: int) -> int:
 def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor,
                 w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
                 stream=None, max_iters: int = 0, flags: int = 0,
-                init_policy: torch.Tensor | None = None) -> BatchSolution:
+                init_policy: torch.Tensor | None = None,
+                transit: torch.Tensor | None = None) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
     (``ocm_solve_batch``); each result equals solving that graph alone.
-    ``init_policy`` (int32 [N], global edge ids) warm-starts every graph."""
+    ``init_policy`` (int32 [N], global edge ids) warm-starts every graph;
+    ``transit`` (int32 [M]) gives optimal cycle ratios."""
     lib = _native.load()
     vp = _dev_i32(graph_vptr, "graph_vptr")
     rp = _dev_i32(row_ptr, "row_ptr")
@@ -206,6 +221,9 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     init = _init_policy(init_policy, N)
     if init is not None:
         opt.init_policy = init.data_ptr()
+    tt = _transit(transit, M)
+    if tt is not None:
+        opt.transit = tt.data_ptr()
     st = _native.OcmStats()
     rc = lib.ocm_solve_batch(vp.data_ptr(), rp.data_ptr(), col.data_ptr(), ww.data_ptr(), G, N, M,
                              _mode(mode), num.data_ptr(), den.data_ptr(), clen.data_ptr(),
@@ -217,15 +235,22 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
 
 
 def backward(cycle: torch.Tensor, grad_lambda: torch.Tensor, m: int, *, stream=None,
-             out: torch.Tensor | None = None) -> torch.Tensor:
-    """d lambda*/d w scaled by grad_lambda (``ocm_backward``); float32 [m]."""
+             out: torch.Tensor | None = None, transit: torch.Tensor | None = None) -> torch.Tensor:
+    """d lambda*/d w scaled by grad_lambda (``ocm_backward``, or
+    ``ocm_backward_ratio`` for an optimal cycle ratio solved with ``transit``);
+    float32 [m]."""
     lib = _native.load()
     cyc = _dev_i32(cycle, "cycle")
     gl = grad_lambda.reshape(1).to(dtype=torch.float32).contiguous()
     if out is None:
         out = torch.empty(m, dtype=torch.float32, device=cyc.device)
-    rc = lib.ocm_backward(cyc.data_ptr(), cyc.numel(), gl.data_ptr(), m, out.data_ptr(),
-                          _stream_ptr(stream))
+    tt = _transit(transit, m)
+    if tt is not None:
+        rc = lib.ocm_backward_ratio(cyc.data_ptr(), cyc.numel(), tt.data_ptr(), gl.data_ptr(), m,
+                                    out.data_ptr(), _stream_ptr(stream))
+    else:
+        rc = lib.ocm_backward(cyc.data_ptr(), cyc.numel(), gl.data_ptr(), m, out.data_ptr(),
+                              _stream_ptr(stream))
     if rc != 0:
         raise OCMError(rc, "ocm_backward")
     return out
@@ -252,21 +277,23 @@ def backward_batch(sol: "BatchSolution", grad_lambda: torch.Tensor, M: int, *, s
 class OCMFunction(torch.autograd.Function):
     """lambda*(w) as a differentiable function of the edge weights.
 
-    forward(w_float, row_ptr, col_idx, w_int, mode) -> lambda* (float32 scalar)
+    forward(w_float, row_ptr, col_idx, w_int, mode, transit) -> lambda* (float32 scalar)
     ``w_float`` is the float view of the weights that receives the gradient;
     the solve itself uses the exact int32 weights ``w_int``.  The gradient is
-    1/|C*| on the edges of the critical cycle C* and 0 elsewhere, which is the
+    1/|C*| on the edges of the critical cycle C* (1/t(C*) for an optimal cycle
+    ratio with transit times ``transit``) and 0 elsewhere, which is the
     derivative wherever C* is the unique optimal cycle."""
 
     @staticmethod
-    def forward(ctx, w_float, row_ptr, col_idx, w_int, mode="max"):
-        sol = solve(row_ptr, col_idx, w_int, mode)
+    def forward(ctx, w_float, row_ptr, col_idx, w_int, mode="max", transit=None):
+        sol = solve(row_ptr, col_idx, w_int, mode, transit=transit)
         ctx.save_for_backward(sol.cycle)
         ctx.m = col_idx.numel()
+        ctx.transit = transit
         return torch.tensor(sol.num / sol.den, dtype=torch.float32, device=w_float.device)
 
     @staticmethod
     def backward(ctx, grad_out):
         (cycle,) = ctx.saved_tensors
-        g = backward(cycle, grad_out, ctx.m)
-        return g, None, None, None, None
+        g = backward(cycle, grad_out, ctx.m, transit=ctx.transit)
+        return g, None, None, None, None, None

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_only_entry_points():
     lib = ocm.load()
-    assert lib.ocm_version() == 101
+    assert lib.ocm_version() == 102
     assert lib.ocm_workspace_size(0, 5) == 0
     assert lib.ocm_workspace_size(5, 0) == 0
     small = lib.ocm_workspace_size(1000, 4000)
@@ -76,6 +76,10 @@ def test_argument_errors_are_reported_before_any_device_work():
                        ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
     assert rc == -1
     rc = lib.ocm_backward(fake, 0, fake, 4, fake, None)
+    assert rc == -1
+    rc = lib.ocm_backward_ratio(fake, 0, fake, fake, 4, fake, None)   # empty cycle
+    assert rc == -1
+    rc = lib.ocm_backward_ratio(fake, 2, None, fake, 4, fake, None)   # no transit times
     assert rc == -1
 
 
