@@ -194,13 +194,14 @@ def algorithmic_bytes(cls: str, n: int, m: int, st_total: dict, launches: int) -
 
 CLASSES = ["init", "sweep", "evaluate", "extract"]
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of each kernel, with the sha256 prefix of the kernel's sources at the time
-# (see profiles/).  Reported only while the sources are unchanged.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged over
+# every launch of the kernel in one host-driven solve captured by ncu, with the
+# sha256 prefix of the kernel's sources at the time (see profiles/).  Reported only
+# while the sources are unchanged.
 KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "common.cuh"), "sweep": ("sweep.cu", "common.cuh")}
 TRAFFIC = {
-    ("product4", "evaluate"): (55.685632e6 + 191.421952e6, "7891324909054910"),
-    ("product4", "sweep"): (280.18304e6 + 26.435072e6, "cee65ad30d99d374"),
+    ("product4", "evaluate"): (55.246e6 + 159.276e6, "99a90da6f42ebf74"),
+    ("product4", "sweep"): (273.453e6 + 13.855e6, "e9963f7c1e540698"),
 }
 
 
