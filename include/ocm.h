@@ -300,11 +300,64 @@ int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, const int32
                      int32_t *cycle_out, int32_t *cycle_len, void *stream,
                      const ocm_options *opt, ocm_stats *stats);
 
+/*
+ * ocm_scc -- strongly connected components (the decomposition the paper runs
+ * before its solver, Sec. 3.3; Prop. 2.2 reduces the optimal cycle mean of a
+ * graph to those of its components).  Forward-backward searches with trimming
+ * over colour classes, on the GPU; any CSR digraph (vertices without
+ * out-edges allowed, m may be 0).
+ *   row_ptr[n+1], col_idx[m] : device CSR (no weights needed)
+ *   scc[n]      : device output; scc[v] = the smallest vertex of v's component
+ *   num_scc     : host output; number of components
+ *   workspace   : at least ocm_workspace_size_scc(n, m) bytes, 256-byte aligned
+ * Synchronises the stream.  Errors: OCM_ERR_INVALID_ARG (null pointers, n < 1,
+ * m < 0, n > (2^31 - 3) / 3), OCM_ERR_BAD_CSR, OCM_ERR_WORKSPACE, OCM_ERR_CUDA,
+ * OCM_ERR_TIMEOUT; outputs untouched on an argument or CSR error.
+ */
+size_t ocm_workspace_size_scc(int32_t n, int32_t m);
+int ocm_scc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t m, int32_t *scc,
+            int32_t *num_scc, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * ocm_solve_scc -- the optimal cycle mean of every strongly connected
+ * component that holds a cycle (Sec. 3.3: the components are solved
+ * concurrently as regions).  The graph may have vertices without out-edges
+ * and acyclic parts; components without a cycle (a single vertex without a
+ * self-loop) are left out.  Each component is solved as its induced subgraph
+ * with its vertices in their original order (same value, cycle and
+ * iteration as ocm_solve on that subgraph); the optimum over components is
+ * the optimal cycle mean of the whole graph.
+ *   row_ptr, col_idx, w, n, m, mode : as for ocm_solve, except that out-degree
+ *                 0 is allowed and m may be 0
+ *   scc[n]      : device; component labels as for ocm_scc
+ *   num_comp    : host; G = number of components with a cycle (0 if none)
+ *   comp_root[n], num[n], den[n], cycle_len[n] : device; entries 0..G-1, one
+ *                 per component in increasing order of its smallest vertex
+ *                 (comp_root[c]), with its reduced mean num/den (in the given
+ *                 sense) and its critical cycle's length
+ *   comp_off[n+1], cycle_out[n] : device; component c's critical cycle, as
+ *                 CSR edge indices of the input graph starting with the policy
+ *                 edge of its smallest vertex, is cycle_out[comp_off[c] ..
+ *                 comp_off[c] + cycle_len[c])
+ *   workspace   : at least ocm_workspace_size_solve_scc(n, m) bytes
+ *   opt         : max_iters, flags (OCM_FLAG_HOST_LOOP) and the sweep's launch
+ *                 fields apply; init_policy and transit must be NULL
+ *   stats       : counters of the batched solve, launches of the whole call
+ * Synchronises the stream.  Errors as for ocm_scc and ocm_solve_batch.
+ */
+size_t ocm_workspace_size_solve_scc(int32_t n, int32_t m);
+int ocm_solve_scc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
+                  int32_t m, int mode, int32_t *scc, int32_t *num_comp, int32_t *comp_root,
+                  int32_t *comp_off, int64_t *num, int32_t *den, int32_t *cycle_len,
+                  int32_t *cycle_out, void *workspace, size_t ws_bytes, void *stream,
+                  const ocm_options *opt, ocm_stats *stats);
+
 /* Text for a status code (static storage). */
 const char *ocm_status_string(int status);
 
 /* ABI version: 100 * major + minor (101: ocm_options.init_policy; 102:
- * ocm_options.transit and ocm_backward_ratio). */
+ * ocm_options.transit and ocm_backward_ratio; 103: ocm_scc and
+ * ocm_solve_scc). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -5,11 +5,10 @@ The compute path is the hand-written sm_103a CUDA library ``libocm.so``
 """
 from . import autotune
 from ._native import build, load
-from .ocm import (OCM_MAX, OCM_MIN, BatchSolution, OCMError, OCMFunction, Solution, backward,
-                  backward_batch,
-                  make_workspace, solve, solve_batch, workspace_bytes, workspace_bytes_batch)
+from .ocm import (OCM_MAX, OCM_MIN, BatchSolution, OCMError, OCMFunction, SccSolution, Solution,
+                  backward, backward_batch, make_workspace, scc, solve, solve_batch, solve_scc,
+                  workspace_bytes, workspace_bytes_batch)
 
-__all__ = ["build", "load", "solve", "solve_batch", "backward", "backward_batch", "OCMFunction",
-           "OCMError",
-           "Solution", "BatchSolution", "make_workspace", "workspace_bytes", "workspace_bytes_batch",
-           "OCM_MAX", "OCM_MIN"]
+__all__ = ["build", "load", "solve", "solve_batch", "solve_scc", "scc", "backward",
+           "backward_batch", "OCMFunction", "OCMError", "Solution", "BatchSolution", "SccSolution",
+           "make_workspace", "workspace_bytes", "workspace_bytes_batch", "OCM_MAX", "OCM_MIN"]

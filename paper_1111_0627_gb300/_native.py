@@ -19,7 +19,8 @@ CSRC = os.path.join(_PKG, "csrc")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
-SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu"]
+SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu",
+           "scc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -126,6 +127,18 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
                                         ctypes.POINTER(OcmOptions), ctypes.POINTER(OcmStats)]),
+    "ocm_workspace_size_scc": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "ocm_scc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                               ctypes.c_size_t, ctypes.c_void_p]),
+    "ocm_workspace_size_solve_scc": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "ocm_solve_scc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.POINTER(OcmOptions), ctypes.POINTER(OcmStats)]),
     "ocm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ocm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ocm_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),

@@ -443,7 +443,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 102; }
+int ocm_version(void) { return 103; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;

@@ -234,6 +234,86 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     return BatchSolution(num, den, clen, cyc, vp, st.as_dict())
 
 
+def scc(row_ptr: torch.Tensor, col_idx: torch.Tensor, *, workspace: torch.Tensor | None = None,
+        stream=None) -> tuple[torch.Tensor, int]:
+    """Strongly connected components (``ocm_scc``): int32 labels, label = the
+    smallest vertex of the component, and the number of components."""
+    lib = _native.load()
+    rp = _dev_i32(row_ptr, "row_ptr")
+    col = _dev_i32(col_idx, "col_idx")
+    n, m = rp.numel() - 1, col.numel()
+    if workspace is None:
+        nbytes = int(lib.ocm_workspace_size_scc(n, m))
+        if nbytes == 0:
+            raise ValueError("graph size out of range")
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=rp.device)
+    labels = torch.empty(n, dtype=torch.int32, device=rp.device)
+    count = ctypes.c_int32(0)
+    rc = lib.ocm_scc(rp.data_ptr(), col.data_ptr(), n, m, labels.data_ptr(), ctypes.byref(count),
+                     workspace.data_ptr(), workspace.numel(), _stream_ptr(stream))
+    if rc != 0:
+        raise OCMError(rc, "ocm_scc")
+    return labels, int(count.value)
+
+
+@dataclass
+class SccSolution:
+    labels: torch.Tensor       # int32 [n]: smallest vertex of each vertex's component
+    root: torch.Tensor         # int32 [G]: smallest vertex of each component with a cycle
+    num: torch.Tensor          # int64 [G]
+    den: torch.Tensor          # int32 [G]
+    cycle_len: torch.Tensor    # int32 [G]
+    offsets: torch.Tensor      # int32 [G+1]
+    cycle_out: torch.Tensor    # int32: component c's cycle at offsets[c]
+    stats: dict = field(default_factory=dict)
+
+    def cycle(self, c: int) -> torch.Tensor:
+        start = int(self.offsets[c])
+        return self.cycle_out[start:start + int(self.cycle_len[c])]
+
+
+def solve_scc(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="max", *,
+              workspace: torch.Tensor | None = None, stream=None, max_iters: int = 0,
+              flags: int = 0) -> SccSolution:
+    """Optimal cycle mean of every strongly connected component that holds a
+    cycle (``ocm_solve_scc``); vertices without out-edges are allowed."""
+    lib = _native.load()
+    rp = _dev_i32(row_ptr, "row_ptr")
+    col = _dev_i32(col_idx, "col_idx")
+    ww = _dev_i32(w, "w")
+    n, m = rp.numel() - 1, col.numel()
+    if ww.numel() != m:
+        raise ValueError("w and col_idx must have the same length")
+    dev = rp.device
+    if workspace is None:
+        nbytes = int(lib.ocm_workspace_size_solve_scc(n, m))
+        if nbytes == 0:
+            raise ValueError("graph size out of range")
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    root = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    num = torch.empty(n, dtype=torch.int64, device=dev)
+    den = torch.empty(n, dtype=torch.int32, device=dev)
+    clen = torch.empty(n, dtype=torch.int32, device=dev)
+    cyc = torch.empty(n, dtype=torch.int32, device=dev)
+    G = ctypes.c_int32(0)
+    opt = _native.OcmOptions()
+    opt.max_iters = int(max_iters)
+    opt.flags = int(flags)
+    st = _native.OcmStats()
+    rc = lib.ocm_solve_scc(rp.data_ptr(), col.data_ptr(), ww.data_ptr(), n, m, _mode(mode),
+                           labels.data_ptr(), ctypes.byref(G), root.data_ptr(), off.data_ptr(),
+                           num.data_ptr(), den.data_ptr(), clen.data_ptr(), cyc.data_ptr(),
+                           workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
+                           ctypes.byref(opt), ctypes.byref(st))
+    if rc != 0:
+        raise OCMError(rc, "ocm_solve_scc")
+    g = int(G.value)
+    return SccSolution(labels, root[:g], num[:g], den[:g], clen[:g], off[:g + 1], cyc,
+                       st.as_dict())
+
+
 def backward(cycle: torch.Tensor, grad_lambda: torch.Tensor, m: int, *, stream=None,
              out: torch.Tensor | None = None, transit: torch.Tensor | None = None) -> torch.Tensor:
     """d lambda*/d w scaled by grad_lambda (``ocm_backward``, or

@@ -303,3 +303,19 @@ def random_policy(rng: np.random.Generator, row_ptr: np.ndarray) -> np.ndarray:
     rp = np.asarray(row_ptr, dtype=np.int64)
     deg = rp[1:] - rp[:-1]
     return (rp[:-1] + rng.integers(0, 1 << 62, size=deg.shape[0]) % deg).astype(np.int32)
+
+
+def random_digraph(rng: np.random.Generator, n: int, avg_deg: float, wlo: int = -50,
+                   whi: int = 50, sink_frac: float = 0.1, mode: str = "max") -> Graph:
+    """Sparse random digraph with vertices that have no out-edges (a fraction
+    sink_frac of them) and, at low average degree, many strongly connected
+    components: out-degree ~ Poisson(avg_deg) elsewhere, targets uniform,
+    self-loops and parallel edges allowed."""
+    deg = rng.poisson(avg_deg, size=n).astype(np.int64)
+    deg[rng.random(n) < sink_frac] = 0
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=rp[1:])
+    m = int(rp[-1])
+    col = rng.integers(0, n, size=m).astype(np.int32)
+    w = rng.integers(wlo, whi + 1, size=m).astype(np.int32)
+    return Graph(rp.astype(np.int32), col, w, mode, f"digraph(n={n})")

@@ -397,3 +397,47 @@ def test_ratio_rejects_nonpositive_times():
     g = synth.from_edges(2, [(0, 1, 1), (1, 0, 1)])
     with pytest.raises(oracle.OracleError):
         oracle.howard(g.row_ptr, g.col_idx, g.w, transit=np.array([1, 0], np.int32))
+
+
+# ------------------------------------------- strongly connected components
+# Tarjan's decomposition (the front-end of Sec. 3.3) against its definition:
+# u and v share a component iff each reaches the other (brute-force closure);
+# the per-component optimum against brute-force cycle enumeration (Prop. 2.2:
+# the graph's optimum is the best component's).
+def _reach(g):
+    n = g.n
+    R = np.eye(n, dtype=bool)
+    for v in range(n):
+        for e in range(int(g.row_ptr[v]), int(g.row_ptr[v + 1])):
+            R[v, g.col_idx[e]] = True
+    for k in range(n):
+        R |= R[:, [k]] & R[[k], :]
+    return R
+
+
+def test_tarjan_matches_mutual_reachability():
+    from scc_helpers import canonical_labels
+    rng = np.random.default_rng(1111062790)
+    for trial in range(400):
+        n = int(rng.integers(1, 14))
+        g = synth.random_digraph(rng, n, avg_deg=float(rng.uniform(0.3, 2.5)), sink_frac=0.2)
+        R = _reach(g)
+        lab = canonical_labels(g.row_ptr, g.col_idx)
+        same = R & R.T
+        for u in range(n):
+            expect = int(np.nonzero(same[u])[0].min())
+            assert lab[u] == expect, (trial, u)
+
+
+def test_per_component_optima_match_brute_force():
+    from scc_helpers import components
+    rng = np.random.default_rng(1111062791)
+    for trial in range(300):
+        n = int(rng.integers(1, 10))
+        g = synth.random_digraph(rng, n, avg_deg=float(rng.uniform(0.5, 2.5)), sink_frac=0.15)
+        comps = components(g)
+        has_cycle = any(True for _ in comps)
+        if not has_cycle:
+            continue
+        best = max(Fraction(num, den) for _, num, den, _ in comps)
+        assert best == oracle.brute(g.row_ptr, g.col_idx, g.w, "max").value, trial
