@@ -198,7 +198,8 @@ CLASSES = ["init", "sweep", "evaluate", "extract"]
 # every launch of the kernel in one host-driven solve captured by ncu, with the
 # sha256 prefix of the kernel's sources at the time (see profiles/).  Reported only
 # while the sources are unchanged.
-KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "common.cuh"), "sweep": ("sweep.cu", "common.cuh")}
+KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
+                  "sweep": ("sweep.cu", "common.cuh")}
 TRAFFIC = {
     ("product4", "evaluate"): (55.246e6 + 159.276e6, "99a90da6f42ebf74"),
     ("product4", "sweep"): (273.453e6 + 13.855e6, "e9963f7c1e540698"),
@@ -591,6 +592,82 @@ def run_grad(args):
     return 0
 
 
+def run_scc(args):
+    """SCC front-end: decomposition plus the per-component solve of a sparse
+    random digraph with many components and vertices without out-edges,
+    vertices/s; the oracle's Tarjan decomposition timed beside it."""
+    import paper_1111_0627_gb300 as ocm
+    torch, dist, world, rank, local, dev = _gpu_setup()
+    n = 10_000_000
+    g = synth.random_digraph(np.random.default_rng(1111062799), n, 1.5, sink_frac=0.05)
+    rp, col, w = [torch.from_numpy(x).to(dev) for x in (g.row_ptr, g.col_idx, g.w)]
+    lib = ocm.load()
+    ws = torch.empty(int(lib.ocm_workspace_size_solve_scc(g.n, g.m)), dtype=torch.uint8,
+                     device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        sol = ocm.solve_scc(rp, col, w, g.mode, workspace=ws, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            sol = ocm.solve_scc(rp, col, w, g.mode, workspace=ws, stream=stream)
+            ev[k][1].record(stream)
+            launches += sol.stats["launches"]
+        torch.cuda.synchronize(dev)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    labels, count = ocm.scc(rp, col, workspace=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    scc_ms = e0.elapsed_time(e1)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        k_cpu, _ = oracle.tarjan_scc(g.row_ptr, g.col_idx)
+        dt = time.perf_counter() - t0
+        assert k_cpu == count, "oracle and GPU disagree on the number of components"
+        cpu = {"value": n / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+               "sample": f"Tarjan's decomposition of the same graph ({dt:.2f} s, single-threaded; "
+                         f"decomposition only)"}
+    h = [torch.from_numpy(x).pin_memory() for x in (g.row_ptr, g.col_idx, g.w)]
+    d = [torch.empty_like(x) for x in (rp, col, w)]
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for src, dst in zip(h, d):
+        dst.copy_(src, non_blocking=True)
+    s2 = ocm.solve_scc(*d, g.mode, workspace=ws, stream=stream)
+    out = [s2.num.cpu(), s2.den.cpu(), s2.root.cpu()]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "vertices/s", "value": world * args.steps * n / (total_ms / 1e3),
+            "unit": "vertices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "digraph-scc: random digraph, n=10^7, out-degree Poisson(1.5), "
+                                   "5% vertices without out-edges, w U[-50,50], max",
+                       "n": g.n, "m": g.m, "components": count,
+                       "components_with_cycle": int(sol.root.numel()),
+                       "decomposition_ms": scc_ms,
+                       "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": n / (e2e_ms / 1e3), "unit": "vertices/s",
+                    "h2d_bytes_per_step": sum(x.numel() * 4 for x in h),
+                    "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in out)},
+            "gpu_launches": launches, "clocks": clocks.summary()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,7 +675,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="product4",
-                    choices=sorted(_workloads()) + sorted(BATCH_WORKLOADS) + ["diff1m-grad"])
+                    choices=sorted(_workloads()) + sorted(BATCH_WORKLOADS) +
+                    ["diff1m-grad", "digraph-scc"])
     ap.add_argument("--ref-iters", type=int, default=2,
                     help="Howard iterations per reference (oracle) step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -611,7 +689,9 @@ def main():
         return run_batch(args)
     if args.workload == "diff1m-grad" and args.impl == "ours":
         return run_grad(args)
-    if args.workload in BATCH_WORKLOADS or args.workload == "diff1m-grad":
+    if args.workload == "digraph-scc" and args.impl == "ours":
+        return run_scc(args)
+    if args.workload in BATCH_WORKLOADS or args.workload in ("diff1m-grad", "digraph-scc"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the reference arm is run on the single-graph workloads only"}))
         return 0

@@ -33,7 +33,8 @@
 
 namespace ocm {
 
-constexpr int kSccThreads = 512;
+constexpr int kSccThreads = 1024;   // one block per SM: fewer arrivals at each grid barrier
+constexpr int kSortThreads = 512;
 constexpr int kScanBlock = 1024;
 constexpr int kTrimRounds = 8;
 constexpr int kActive = 1, kFw = 2, kBw = 4;
@@ -206,7 +207,51 @@ csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         }
 }
 
+// largest out- or in-degree (after the CSC is built)
+__global__ void __launch_bounds__(kThreads)
+max_degree_kernel(const int *__restrict__ row_ptr, const int *__restrict__ in_ptr, int n,
+                  Ctrl *c) {
+    const int stride = gridDim.x * blockDim.x;
+    int d = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        d = max(d, max(row_ptr[v + 1] - row_ptr[v], in_ptr[v + 1] - in_ptr[v]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0 && d) atomicMax(&c->maxt, d);
+}
+
 // -------------------------------------------------------- one iteration --
+// atomicMax / atomicMin on slot[key] by every lane with pred, combined first
+// among the lanes of the warp that share the key (one atomic per distinct key
+// per warp): all vertices of a large class meet on one pivot slot.
+static __device__ __forceinline__ void warp_atomic_max(int *slot, bool pred, int key, int val,
+                                                       int lane) {
+    const unsigned act = __ballot_sync(0xffffffffu, pred);
+    if (!act) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, pred ? key : INT_MIN);
+    const int mine = pred ? val : INT_MIN;
+    int m = mine;
+    // reduce over the peer group (every lane takes part in every shuffle)
+    for (int src = 0; src < 32; ++src) {
+        const int o = __shfl_sync(0xffffffffu, mine, src);
+        if ((peers >> src) & 1u) m = max(m, o);
+    }
+    if (pred && (__ffs(peers) - 1) == lane) atomicMax(&slot[key], m);
+}
+
+static __device__ __forceinline__ void warp_atomic_min(int *slot, bool pred, int key, int val,
+                                                       int lane) {
+    const unsigned act = __ballot_sync(0xffffffffu, pred);
+    if (!act) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, pred ? key : INT_MIN);
+    const int mine = pred ? val : INT_MAX;
+    int m = mine;
+    for (int src = 0; src < 32; ++src) {
+        const int o = __shfl_sync(0xffffffffu, mine, src);
+        if ((peers >> src) & 1u) m = min(m, o);
+    }
+    if (pred && (__ffs(peers) - 1) == lane) atomicMin(&slot[key], m);
+}
 // Appends item to a global frontier (warp-aggregated atomic on its counter).
 static __device__ __forceinline__ void frontier_append(int *q, int *cnt, bool pred, int item,
                                                        int lane) {
@@ -214,6 +259,10 @@ static __device__ __forceinline__ void frontier_append(int *q, int *cnt, bool pr
     if (pred) q[pos] = item;
 }
 
+// LG = lanes serving one frontier vertex in the searches (8, 16 or 32),
+// chosen from the largest degree so that wide vertices do not serialise a
+// small group and narrow ones do not idle a whole warp.
+template <int LG>
 __global__ void __launch_bounds__(kSccThreads, 1)
 scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n,
                      SccWs s, int *scc) {
@@ -260,8 +309,11 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
     for (int v = gtid; v < n; v += stride)
         if (s.flags[v] & kActive) s.piv[s.color[v]] = -1;
     if (!grid_barrier(c, nb)) return;
-    for (int v = gtid; v < n; v += stride)
-        if (s.flags[v] & kActive) atomicMax(&s.piv[s.color[v]], v);
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int v = base + threadIdx.x;
+        const bool act = v < n && (s.flags[v] & kActive);
+        warp_atomic_max(s.piv, act, act ? s.color[v] : 0, v, lane);
+    }
     if (!grid_barrier(c, nb)) return;
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const int v = base + threadIdx.x;
@@ -287,52 +339,40 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
         const int *qf = s.q[lvl & 1], *qb = s.q[2 + (lvl & 1)];
         int *qf2 = s.q[(lvl + 1) & 1], *qb2 = s.q[2 + ((lvl + 1) & 1)];
         int added = 0;
-        for (int base = blockIdx.x * blockDim.x; base < nf; base += stride) {
-            const int i = base + threadIdx.x;
-            int u = -1, cu = 0, e = 0, e_end = 0;
-            if (i < nf) {
-                u = qf[i];
+        // groups of LG lanes per frontier vertex (32 / LG vertices per warp
+        // task, forward tasks first, then backward ones); a group strides
+        // over its vertex's edges
+        constexpr int kPer = 32 / LG;
+        const int warp_id = gtid >> 5, nwarps = stride >> 5;
+        const int grp = lane / LG, sub = lane % LG;
+        const int ntf = (nf + kPer - 1) / kPer, ntb = (nbk + kPer - 1) / kPer;
+        for (int task = warp_id; task < ntf + ntb; task += nwarps) {
+            const bool fwd = task < ntf;
+            const int i = (fwd ? task : task - ntf) * kPer + grp;
+            const int bit = fwd ? kFw : kBw;
+            const int *adj = fwd ? col : s.in_src;
+            int *qout = fwd ? qf2 : qb2;
+            int *cout = fwd ? &c->cnt[nxt] : &c->pending[nxt];
+            int e = 0, e1 = 0, cu = 0;
+            if (i < (fwd ? nf : nbk)) {
+                const int u = fwd ? qf[i] : qb[i];
                 cu = s.color[u];
-                e = row_ptr[u];
-                e_end = row_ptr[u + 1];
+                e = (fwd ? row_ptr[u] : s.in_ptr[u]) + sub;
+                e1 = fwd ? row_ptr[u + 1] : s.in_ptr[u + 1];
             }
-            // lanes walk their own edge lists; appends are warp-aggregated
             for (;;) {
-                const bool more = e < e_end;
+                const bool more = e < e1;
                 if (!__any_sync(0xffffffffu, more)) break;
                 bool take = false;
                 int x = 0;
                 if (more) {
-                    x = col[e++];
+                    x = adj[e];
+                    e += LG;
                     const int f = s.flags[x];
-                    if ((f & kActive) && !(f & kFw) && s.color[x] == cu)
-                        take = !(atomicOr(&s.flags[x], kFw) & kFw);
+                    if ((f & kActive) && !(f & bit) && s.color[x] == cu)
+                        take = !(atomicOr(&s.flags[x], bit) & bit);
                 }
-                frontier_append(qf2, &c->cnt[nxt], take, x, lane);
-                added += take;
-            }
-        }
-        for (int base = blockIdx.x * blockDim.x; base < nbk; base += stride) {
-            const int i = base + threadIdx.x;
-            int u = -1, cu = 0, e = 0, e_end = 0;
-            if (i < nbk) {
-                u = qb[i];
-                cu = s.color[u];
-                e = s.in_ptr[u];
-                e_end = s.in_ptr[u + 1];
-            }
-            for (;;) {
-                const bool more = e < e_end;
-                if (!__any_sync(0xffffffffu, more)) break;
-                bool take = false;
-                int x = 0;
-                if (more) {
-                    x = s.in_src[e++];
-                    const int f = s.flags[x];
-                    if ((f & kActive) && !(f & kBw) && s.color[x] == cu)
-                        take = !(atomicOr(&s.flags[x], kBw) & kBw);
-                }
-                frontier_append(qb2, &c->pending[nxt], take, x, lane);
+                frontier_append(qout, cout, take, x, lane);
                 added += take;
             }
         }
@@ -347,9 +387,11 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
         }
     }
     // 4. split: reached both ways = the pivot's component
-    for (int v = gtid; v < n; v += stride) {
-        const int f = s.flags[v];
-        if ((f & kActive) && (f & kFw) && (f & kBw)) atomicMin(&s.minv[s.piv[s.color[v]]], v);
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int v = base + threadIdx.x;
+        const int f = v < n ? s.flags[v] : 0;
+        const bool in = (f & kActive) && (f & kFw) && (f & kBw);
+        warp_atomic_min(s.minv, in, in ? s.piv[s.color[v]] : 0, v, lane);
     }
     if (!grid_barrier(c, nb)) return;
     int still = 0;
@@ -389,6 +431,7 @@ __global__ void scc_ctrl_init_kernel(Ctrl *c) {
     *c = z;
 }
 
+template <int LG>
 static int scc_grid() {
     static int cached_dev = -1, cached = 0;
     int dev = 0;
@@ -396,8 +439,8 @@ static int scc_grid() {
     if (dev == cached_dev && cached > 0) return cached;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scc_iteration_kernel, kSccThreads,
-                                                      0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scc_iteration_kernel<LG>,
+                                                      kSccThreads, 0) != cudaSuccess ||
         per_sm < 1)
         return 0;
     cached_dev = dev;
@@ -444,8 +487,14 @@ int scc_decompose(const int *row_ptr, const int *col, int n, int m, int *scc, in
     if (m > 0) csc_count_kernel<<<eb, kThreads, 0, st>>>(col, m, s.in_ptr);
     inclusive_scan(s.in_ptr + 1, n, s.bsum, st);
     csc_scatter_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, s);
-    k += 6;
-    const int grid = scc_grid();
+    max_degree_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, s.in_ptr, n, s.ctrl);
+    k += 7;
+    if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    rc = read_scc_ctrl(s.ctrl, &h, st);
+    if (rc) return rc;
+    // lanes per frontier vertex: about half the largest degree, 8 to 32
+    const int lg = h.maxt > 32 ? 32 : h.maxt > 16 ? 16 : 8;
+    const int grid = lg == 32 ? scc_grid<32>() : lg == 16 ? scc_grid<16>() : scc_grid<8>();
     if (grid <= 0) return OCM_ERR_CUDA;
     int g = (n + kSccThreads - 1) / kSccThreads;
     if (g > grid) g = grid;
@@ -461,9 +510,11 @@ int scc_decompose(const int *row_ptr, const int *col, int n, int m, int *scc, in
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, scc_iteration_kernel, row_ptr, col, n, s, scc) !=
-            cudaSuccess)
-            return OCM_ERR_CUDA;
+        const cudaError_t le =
+            lg == 32 ? cudaLaunchKernelEx(&cfg, scc_iteration_kernel<32>, row_ptr, col, n, s, scc)
+            : lg == 16 ? cudaLaunchKernelEx(&cfg, scc_iteration_kernel<16>, row_ptr, col, n, s, scc)
+                       : cudaLaunchKernelEx(&cfg, scc_iteration_kernel<8>, row_ptr, col, n, s, scc);
+        if (le != cudaSuccess) return OCM_ERR_CUDA;
         ++k;
         rc = read_scc_ctrl(s.ctrl, &h, st);
         if (rc) return rc;
@@ -521,7 +572,7 @@ namespace ocm {
 // whose digit is the same for every key are skipped.  keys are non-negative.
 // On return the sorted pairs are in (k0, i0) if the number of executed
 // passes is even, else in (k1, i1); *which reports it (block 0, thread 0).
-__global__ void __launch_bounds__(kSccThreads, 1)
+__global__ void __launch_bounds__(kSortThreads, 1)
 sort_pairs_kernel(int len, int *k0, int *i0, int *k1, int *i1, int *hist, Ctrl *c) {
     __shared__ int s_off[256];
     __shared__ int s_warp[32];
@@ -780,7 +831,7 @@ static int sort_grid() {
     if (dev == cached_dev && cached > 0) return cached;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pairs_kernel, kSccThreads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pairs_kernel, kSortThreads,
                                                       0) != cudaSuccess ||
         per_sm < 1)
         return 0;
@@ -856,12 +907,12 @@ int ocm_solve_scc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t 
     // contiguous, each in increasing vertex order
     const int sg = sort_grid();
     if (sg <= 0) return OCM_ERR_CUDA;
-    int g = (len + kSccThreads - 1) / kSccThreads;
+    int g = (len + kSortThreads - 1) / kSortThreads;
     if (g > sg) g = sg;
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g);
-        cfg.blockDim = dim3(kSccThreads);
+        cfg.blockDim = dim3(kSortThreads);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;

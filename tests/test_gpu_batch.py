@@ -101,3 +101,24 @@ def test_batch_backward_matches_per_graph_gradients():
         e0 = int(b.row_ptr[int(b.graph_vptr[g])])
         ref[e0:e0 + gr.m] = (g + 1) * oracle.gradient(gr.m, h.cycle)
     assert np.allclose(grad, ref, rtol=2**-22, atol=0)
+
+
+def test_full_batch_config_sampled_against_oracle():
+    """The full batched workload (4096 graphs, sizes log-uniform in [100,
+    200000]) in one call, as the benchmark runs it; members are checked
+    against the oracle on a seeded sample that includes the largest and the
+    smallest graph."""
+    graphs = synth.batch_graphs(G=4096, nmin=100, nmax=200000)
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    num, den = sol.num.cpu().numpy(), sol.den.cpu().numpy()
+    sizes = np.array([g.n for g in graphs])
+    rng = np.random.default_rng(1111062703)
+    sample = set(rng.choice(len(graphs), 12, replace=False).tolist())
+    sample |= {int(sizes.argmax()), int(sizes.argmin())}
+    for g in sorted(sample):
+        gr = graphs[g]
+        h = oracle.howard(gr.row_ptr, gr.col_idx, gr.w, gr.mode)
+        assert (int(num[g]), int(den[g])) == (h.num, h.den), g
+        e0 = int(b.row_ptr[int(b.graph_vptr[g])])
+        assert (sol.cycle(g).cpu().numpy() - e0).tolist() == [int(x) for x in h.cycle], g
