@@ -198,13 +198,41 @@ csc_count_kernel(const int *__restrict__ col, int m, int *in_ptr) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n, SccWs s) {
+csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n,
+                   const int *__restrict__ in_ptr, int *in_src, int *cursor) {
     const int stride = gridDim.x * blockDim.x;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
         for (int e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
             const int x = col[e];
-            s.in_src[s.in_ptr[x] + atomicAdd(&s.cursor[x], 1)] = u;
+            in_src[in_ptr[x] + atomicAdd(&cursor[x], 1)] = u;
         }
+}
+
+__global__ void __launch_bounds__(kThreads)
+csc_zero_kernel(int n, int *in_ptr, int *cursor) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+        in_ptr[v] = 0;
+        if (v < n) cursor[v] = 0;
+    }
+}
+
+// Transposed CSR of a graph (in-edges by target; sources in no particular
+// order within a row) for the backward searches.  bsum needs n / 1024 + 2
+// ints, cursor n.  Returns the number of kernels launched.
+static int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, int *in_src,
+                      int *cursor, int *bsum, cudaStream_t st) {
+    int blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    int eb = (m + kThreads - 1) / kThreads;
+    if (eb > 8192) eb = 8192;
+    if (eb < 1) eb = 1;
+    csc_zero_kernel<<<blocks, kThreads, 0, st>>>(n, in_ptr, cursor);
+    if (m > 0) csc_count_kernel<<<eb, kThreads, 0, st>>>(col, m, in_ptr);
+    inclusive_scan(in_ptr + 1, n, bsum, st);
+    csc_scatter_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, in_ptr, in_src, cursor);
+    return 6;
 }
 
 // largest out- or in-degree (after the CSC is built)
@@ -480,13 +508,8 @@ int scc_decompose(const int *row_ptr, const int *col, int n, int m, int *scc, in
     int rc = read_scc_ctrl(s.ctrl, &h, st);
     if (rc) return rc;
     if (h.err) return scc_err(h.err);
-    int eb = (m + kThreads - 1) / kThreads;
-    if (eb > 8192) eb = 8192;
-    if (eb < 1) eb = 1;
     scc_init_kernel<<<blocks, kThreads, 0, st>>>(n, s, scc);
-    if (m > 0) csc_count_kernel<<<eb, kThreads, 0, st>>>(col, m, s.in_ptr);
-    inclusive_scan(s.in_ptr + 1, n, s.bsum, st);
-    csc_scatter_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, s);
+    launch_csc(row_ptr, col, n, m, s.in_ptr, s.in_src, s.cursor, s.bsum, st);
     max_degree_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, s.in_ptr, n, s.ctrl);
     k += 7;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
