@@ -41,7 +41,7 @@ _lib = None
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "bad CSR", -3: "vertex without out-edge",
           -4: "weight out of range", -5: "not converged", -6: "out of memory",
-          -7: "too many optimal cycles"}
+          -7: "too many optimal cycles", -8: "not strongly connected"}
 
 MAX, MIN = 0, 1
 
@@ -76,6 +76,8 @@ def _load():
             lib.oracle_tarjan_scc.restype = i32
             lib.oracle_certificate.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64p, i64p,
                                                i64p, i64, i64, i32p, i32, i64p]
+            lib.oracle_howard_single.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64,
+                                                 i64p, i64p, i32p, i32p, i64p, i32p, i64p]
             lib.oracle_howard_ratio.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64,
                                                 i64p, i64p, i32p, i32p, i64p, i64p, i64p, i32p,
                                                 i64p, i32p]
@@ -174,6 +176,53 @@ def howard(row_ptr, col_idx, w, mode="max", max_iter: int = 0, trace_cap: int = 
     ntr = min(it + 1, trace_cap)
     return HowardResult(int(num[0]), int(den[0]), cyc[:int(clen[0])].copy(), ep, eq, V, pol, it,
                         tr[:3 * ntr].reshape(ntr, 3))
+
+
+@dataclass
+class SingleResult:
+    num: int
+    den: int
+    cycle: np.ndarray
+    V: np.ndarray
+    policy: np.ndarray
+    iterations: int
+
+    @property
+    def value(self) -> Fraction:
+        return Fraction(self.num, self.den)
+
+
+def howard_single(row_ptr, col_idx, w, mode="max", max_iter: int = 0,
+                  transit=None) -> SingleResult:
+    """The paper's form of Howard's iteration (Alg. 1 as written): one lambda,
+    every other policy cycle broken each iteration by a backward search from
+    the chosen cycle's component; every vertex must reach that cycle."""
+    lib = _load()
+    rp, rpp = _i32(row_ptr)
+    col, colp = _i32(col_idx)
+    ww, wp = _i32(w)
+    n, m = rp.shape[0] - 1, col.shape[0]
+    num = np.zeros(1, np.int64)
+    den = np.zeros(1, np.int64)
+    cyc = np.zeros(max(n, 1), np.int32)
+    clen = np.zeros(1, np.int32)
+    V = np.zeros(n, np.int64)
+    pol = np.zeros(n, np.int32)
+    its = np.zeros(1, np.int64)
+    ttp = None
+    if transit is not None:
+        tt, ttp = _i32(transit)
+        if tt.shape[0] != m:
+            raise ValueError("transit needs one entry per edge")
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    rc = lib.oracle_howard_single(n, m, rpp, colp, wp, ttp, _mode(mode), max_iter, _i64p(num),
+                                  _i64p(den), cyc.ctypes.data_as(i32p),
+                                  clen.ctypes.data_as(i32p), _i64p(V), pol.ctypes.data_as(i32p),
+                                  _i64p(its))
+    if rc != 0:
+        raise OracleError(rc, "howard_single")
+    return SingleResult(int(num[0]), int(den[0]), cyc[:int(clen[0])].copy(), V, pol,
+                        int(its[0]))
 
 
 def karp(row_ptr, col_idx, w, mode="max") -> Fraction:

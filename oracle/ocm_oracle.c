@@ -34,6 +34,9 @@
  *                      weight (Prop. 2.1), plus a cycle attaining the value.
  *   oracle_howard_ratio, oracle_brute_ratio, oracle_certificate_ratio
  *                      the same three for the optimal cycle ratio.
+ *   oracle_howard_single  the paper's own form of the iteration (Alg. 1 as
+ *                      written): one lambda, every other policy cycle broken
+ *                      each iteration (strongly connected input only).
  *
  * Readings of the paper taken here (where it is silent or garbled):
  *   - max sense (the paper defines min); min via negated weights;
@@ -46,7 +49,11 @@
  *     (Alg. 1 "break all other cycles", Alg. 2 markMinComponent/connectGpi),
  *     every policy cycle keeps its own mean (multichain policy iteration),
  *     so input need not be strongly connected; lambda* is the largest mean of
- *     the final policy, the critical cycle that of the smallest root with it.
+ *     the final policy, the critical cycle that of the smallest root with it;
+ *   - oracle_howard_single keeps the rebuild; where several out-edges of an
+ *     unconnected vertex lead into the connected part, it takes the smallest
+ *     CSR edge index among those into vertices connected at earlier levels
+ *     of the backward search (the paper leaves the choice open).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -63,6 +70,7 @@ enum {
     OR_ERR_NOT_CONVERGED = -5,
     OR_ERR_NOMEM = -6,
     OR_ERR_TOO_MANY = -7,
+    OR_ERR_NOT_SC = -8,
 };
 
 static int64_t gcd64(int64_t a, int64_t b) {
@@ -369,6 +377,159 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
                   const int32_t *init) {
     return howard_impl(n, m, rp, col, w, NULL, mode, max_iter, num, den, cycle, clen, eta_p,
                        eta_q, V_out, policy, iters, trace, tcap, init);
+}
+
+/*
+ * oracle_howard_single -- Alg. 1 as the paper writes it: after every
+ * improvement step, take the policy cycle of best mean (ties: smallest root,
+ * "the same vertex whenever the same cycle is chosen"), keep the component of
+ * the policy graph that reaches it, and connect every other vertex to it
+ * ("break all other cycles ... so that all vertices have path to C", done in
+ * the paper by backward reachabilities): level by level, a vertex outside the
+ * connected set takes its smallest-index out-edge into the vertices
+ * connected at earlier levels.  Values are then propagated from the cycle's
+ * smallest vertex with the one lambda, and the improvement step switches a
+ * vertex on strict improvement of q*w(e) - p*t(e) + V(t).  Every vertex must
+ * reach the chosen cycle (true for strongly connected input; OR_ERR_NOT_SC
+ * otherwise).  tt = transit times for the cycle ratio, NULL for the mean.
+ * Outputs as oracle_howard (V and policy optional, the final policy has the
+ * one cycle); iters counts improvement steps that switched a vertex.
+ */
+int oracle_howard_single(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
+                         const int32_t *w, const int32_t *tt, int mode, int64_t max_iter,
+                         int64_t *num, int64_t *den, int32_t *cycle, int32_t *clen,
+                         int64_t *V_out, int32_t *policy, int64_t *iters) {
+    int rc = check_csr(n, m, rp, col);
+    if (rc) return rc;
+    if (tt)
+        for (int32_t e = 0; e < m; ++e)
+            if (tt[e] < 1) return OR_ERR_ARG;
+    if (!w || (mode != 0 && mode != 1)) return OR_ERR_ARG;
+    for (int32_t e = 0; e < m; ++e)
+        if (w[e] == INT32_MIN) return OR_ERR_RANGE;
+    if (max_iter <= 0) max_iter = 4 * (int64_t)n + 64;
+    howard_ws h;
+    memset(&h, 0, sizeof h);
+    h.n = n; h.rp = rp; h.col = col; h.w = w; h.mode = mode; h.tt = tt;
+    size_t N = (size_t)n;
+    h.pi = malloc(N * sizeof(int32_t));
+    h.succ = malloc(N * sizeof(int32_t));
+    h.cyc = malloc(N * sizeof(int32_t));
+    h.state = malloc(N * sizeof(int32_t));
+    h.path = malloc(N * sizeof(int32_t));
+    h.S = malloc(N * sizeof(int64_t));
+    h.T = malloc(N * sizeof(int64_t));
+    h.V = malloc(N * sizeof(i128));
+    h.cyc_root = malloc(N * sizeof(int32_t));
+    h.cyc_p = malloc(N * sizeof(int64_t));
+    h.cyc_q = malloc(N * sizeof(int64_t));
+    int32_t *newpi = malloc(N * sizeof(int32_t));
+    int32_t *level = malloc(N * sizeof(int32_t));
+    int32_t *pick = malloc(N * sizeof(int32_t));
+    rc = OR_OK;
+    if (!h.pi || !h.succ || !h.cyc || !h.state || !h.path || !h.S || !h.T || !h.V ||
+        !h.cyc_root || !h.cyc_p || !h.cyc_q || !newpi || !level || !pick) {
+        rc = OR_ERR_NOMEM;
+        goto done;
+    }
+    for (int32_t v = 0; v < n; ++v) {     /* first pass from val = 0, lambda = 0 */
+        int32_t best = rp[v];
+        for (int32_t e = rp[v] + 1; e < rp[v + 1]; ++e)
+            if (wmax(w, e, mode) > wmax(w, best, mode)) best = e;
+        h.pi[v] = best;
+    }
+    int64_t it = 0;
+    int32_t bc = 0;
+    for (;;) {
+        howard_evaluate(&h);
+        /* the chosen cycle: best mean, smallest root */
+        bc = 0;
+        for (int32_t c = 1; c < h.ncyc; ++c) {
+            int k = frac_cmp(h.cyc_p[c], h.cyc_q[c], h.cyc_p[bc], h.cyc_q[bc]);
+            if (k > 0 || (k == 0 && h.cyc_root[c] < h.cyc_root[bc])) bc = c;
+        }
+        /* connect every vertex to it: level 0 = its component */
+        int32_t left = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            level[v] = h.cyc[v] == bc ? 0 : -1;
+            left += level[v] < 0;
+        }
+        for (int32_t k = 1; left > 0; ++k) {
+            int32_t got = 0;
+            for (int32_t v = 0; v < n; ++v) {
+                pick[v] = -1;
+                if (level[v] >= 0) continue;
+                for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
+                    int32_t t = col[e];
+                    if (level[t] >= 0 && level[t] < k) {
+                        pick[v] = e;
+                        break;
+                    }
+                }
+            }
+            for (int32_t v = 0; v < n; ++v)
+                if (pick[v] >= 0) {
+                    level[v] = k;
+                    h.pi[v] = pick[v];
+                    ++got;
+                }
+            if (got == 0) {
+                rc = OR_ERR_NOT_SC;
+                goto done;
+            }
+            left -= got;
+        }
+        howard_evaluate(&h);   /* one cycle now: values with its lambda */
+        bc = 0;
+        /* improvement (Jacobi), strict */
+        int64_t switched = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t best = rp[v];
+            for (int32_t e = rp[v] + 1; e < rp[v + 1]; ++e)
+                if (howard_better(&h, e, best)) best = e;
+            int32_t cur = h.pi[v];
+            int sw = howard_key2(&h, best) > howard_key2(&h, cur);
+            newpi[v] = sw ? best : cur;
+            switched += sw;
+        }
+        if (switched == 0) break;
+        if (++it >= max_iter) {
+            rc = OR_ERR_NOT_CONVERGED;
+            goto done;
+        }
+        memcpy(h.pi, newpi, N * sizeof(int32_t));
+    }
+    if (h.ncyc != 1) {
+        rc = OR_ERR_ARG;
+        goto done;
+    }
+    if (num) *num = mode == 0 ? h.cyc_p[0] : -h.cyc_p[0];
+    if (den) *den = h.cyc_q[0];
+    {
+        int32_t r = h.cyc_root[0], x = r, L = 0;
+        do {
+            if (cycle) cycle[L] = h.pi[x];
+            ++L;
+            x = h.succ[x];
+        } while (x != r);
+        if (clen) *clen = L;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        if (V_out) {
+            if (h.V[v] > (i128)INT64_MAX || h.V[v] < (i128)INT64_MIN) {
+                rc = OR_ERR_RANGE;
+                goto done;
+            }
+            V_out[v] = (int64_t)h.V[v];
+        }
+        if (policy) policy[v] = h.pi[v];
+    }
+    if (iters) *iters = it;
+done:
+    free(h.pi); free(h.succ); free(h.cyc); free(h.state); free(h.path);
+    free(h.S); free(h.T); free(h.V); free(h.cyc_root); free(h.cyc_p); free(h.cyc_q);
+    free(newpi); free(level); free(pick);
+    return rc;
 }
 
 /* Optimal cycle ratio w(C)/t(C) by the same iteration, transit times tt[m] >= 1. */

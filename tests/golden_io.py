@@ -161,3 +161,48 @@ def relabel(g: synth.Graph, perm: np.ndarray) -> synth.Graph:
         for e in range(g.row_ptr[old_v], g.row_ptr[old_v + 1]):
             edges.append((new_v, int(perm[g.col_idx[e]]), int(g.w[e])))
     return synth.from_edges(n, edges, g.mode, g.name + "-relabelled")
+
+
+@dataclass
+class SingleTrace:
+    name: str
+    graph: synth.Graph
+    num: int
+    den: int
+    single_iters: int
+    multichain_iters: int
+    cycle: tuple
+    policy: np.ndarray
+    values: np.ndarray
+
+
+def single_lambda_traces() -> list[SingleTrace]:
+    out: list[SingleTrace] = []
+    cur = None
+    edges: list[tuple[int, int, int]] = []
+
+    def flush():
+        if cur is not None:
+            name, n, mode, num, den, si, mi, cyc, pol, val = cur
+            out.append(SingleTrace(name, synth.from_edges(n, edges, mode, name), num, den, si, mi,
+                                   cyc, np.array(pol, np.int32), np.array(val, np.int64)))
+
+    with open(os.path.join(GOLDEN, "single_lambda_traces.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            if tok[0] == "graph":
+                flush()
+                cur = [tok[1], int(tok[2]), tok[3], int(tok[4]), int(tok[5]), int(tok[6]),
+                       int(tok[7]), tuple(int(x) for x in tok[8:]), None, None]
+                edges = []
+            elif tok[0] == "policy":
+                cur[8] = [int(x) for x in tok[1:]]
+            elif tok[0] == "values":
+                cur[9] = [int(x) for x in tok[1:]]
+            else:
+                edges.append((int(tok[0]), int(tok[1]), int(tok[2])))
+    flush()
+    return out

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from golden_io import closed_forms, fig1, ratio_closed_forms, relabel
+from golden_io import closed_forms, fig1, ratio_closed_forms, relabel, single_lambda_traces
 
 
 def _frac(num, den):
@@ -441,3 +441,100 @@ def test_per_component_optima_match_brute_force():
             continue
         best = max(Fraction(num, den) for _, num, den, _ in comps)
         assert best == oracle.brute(g.row_ptr, g.col_idx, g.w, "max").value, trial
+
+
+# ------------------------------------------------- the paper's single-lambda form
+# Alg. 1 as written: one lambda, every other policy cycle broken each iteration
+# so that all vertices reach the chosen one.  Pins: brute-force enumeration and
+# Karp on thousands of strongly connected tiny graphs (a ring through all
+# vertices makes them so), the LP-dual certificate of the final values with
+# every vertex at lambda* (it also pins the values and the single-cycle
+# policy), the ratio form against brute force, and the error on a vertex that
+# cannot reach the chosen cycle.
+def _single_cycle_policy(g, policy):
+    succ = g.col_idx[policy]
+    roots = set()
+    for v in range(g.n):
+        seen, x = set(), v
+        while x not in seen:
+            seen.add(x)
+            x = int(succ[x])
+        # x is on v's cycle; name the cycle by its smallest vertex
+        cyc, y = [x], int(succ[x])
+        while y != x:
+            cyc.append(y)
+            y = int(succ[y])
+        roots.add(min(cyc))
+    return len(roots) == 1
+
+
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_single_lambda_matches_brute_force_on_strongly_connected_graphs(mode):
+    rng = np.random.default_rng(1111062800 + (mode == "min"))
+    for trial in range(1200):
+        n = int(rng.integers(1, 9))
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=True, mode=mode)
+        s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode)
+        assert s.value == b.value == oracle.karp(g.row_ptr, g.col_idx, g.w, mode), trial
+        assert tuple(int(e) for e in s.cycle) in b.optimal, (trial, s.cycle, b.optimal)
+        assert _single_cycle_policy(g, s.policy), trial
+        # every vertex reaches the one cycle: eta = lambda* (max sense) everywhere
+        p = s.num if mode == "max" else -s.num
+        ep = np.full(n, p, np.int64)
+        eq = np.full(n, s.den, np.int64)
+        rc, bad = oracle.certificate(g.row_ptr, g.col_idx, g.w, mode, ep, eq, s.V, s.num, s.den,
+                                     s.cycle)
+        assert rc == 0, (trial, rc, bad)
+
+
+def test_single_lambda_ratio_matches_brute_force():
+    rng = np.random.default_rng(1111062802)
+    for trial in range(800):
+        n = int(rng.integers(1, 9))
+        mode = "max" if trial % 2 == 0 else "min"
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=True, mode=mode)
+        t = rng.integers(1, 6, size=g.m).astype(np.int32)
+        s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode, transit=t)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode, transit=t)
+        assert s.value == b.value, trial
+        assert tuple(int(e) for e in s.cycle) in b.optimal, trial
+        p = s.num if mode == "max" else -s.num
+        rc, bad = oracle.certificate(g.row_ptr, g.col_idx, g.w, mode, np.full(n, p, np.int64),
+                                     np.full(n, s.den, np.int64), s.V, s.num, s.den, s.cycle,
+                                     transit=t)
+        assert rc == 0, (trial, rc, bad)
+
+
+def test_single_lambda_agrees_with_multichain_in_value_on_larger_graphs():
+    g = synth.ring10k()
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert (s.num, s.den) == (h.num, h.den)
+    assert s.value == oracle.karp(g.row_ptr, g.col_idx, g.w, g.mode)
+
+
+def test_single_lambda_needs_every_vertex_to_reach_the_chosen_cycle():
+    # two separate 2-cycles of means 5 and 1: the second cannot reach the first
+    g = synth.from_edges(4, [(0, 1, 5), (1, 0, 5), (2, 3, 1), (3, 2, 1)])
+    with pytest.raises(oracle.OracleError) as ex:
+        oracle.howard_single(g.row_ptr, g.col_idx, g.w)
+    assert ex.value.code == -8
+    # the same with a bridge 2 -> 0: not strongly connected, but every vertex
+    # reaches the best cycle, and the answer is the optimum
+    g = synth.from_edges(4, [(0, 1, 5), (1, 0, 5), (2, 3, 1), (2, 0, 0), (3, 2, 1)])
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w)
+    assert (s.num, s.den) == (5, 1)
+
+
+@pytest.mark.parametrize("tr", single_lambda_traces(), ids=lambda t: t.name)
+def test_single_lambda_hand_traces(tr):
+    g = tr.graph
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert (s.num, s.den, s.iterations) == (tr.num, tr.den, tr.single_iters)
+    assert tuple(int(e) for e in s.cycle) == tr.cycle
+    assert s.policy.tolist() == tr.policy.tolist()
+    assert s.V.tolist() == tr.values.tolist()
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    assert (h.num, h.den, h.iterations) == (tr.num, tr.den, tr.multichain_iters)
+    assert tuple(int(e) for e in h.cycle) == tr.cycle
