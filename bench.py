@@ -247,7 +247,8 @@ def run_ours(args, g, desc):
     rp = torch.from_numpy(g.row_ptr).to(dev)
     col = torch.from_numpy(g.col_idx).to(dev)
     w = torch.from_numpy(g.w).to(dev)
-    ws = ocm.make_workspace(g.n, g.m, dev)
+    single = bool(args.single_lambda)
+    ws = ocm.make_workspace(g.n, g.m, dev, single_lambda=single)
     cyc = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -258,7 +259,7 @@ def run_ours(args, g, desc):
 
     def solve(flags=0):
         return ocm.solve(rp, col, w, g.mode, workspace=ws, cycle_out=cyc, stream=stream,
-                         flags=flags)
+                         flags=flags, single_lambda=single)
 
     for _ in range(args.warmup):
         sol = solve()
@@ -325,7 +326,8 @@ def run_ours(args, g, desc):
     roofline = {"bound": "hbm", "kernel": dom,
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": measured_traffic(args.workload, dom),
+                # (the counters were taken on the default form's launches)
+                "traffic": None if single else measured_traffic(args.workload, dom),
                 "peak_kind": peak_kind,
                 "avg_launch_us": d["ms_total"] * 1e3 / max(d["launches"], 1),
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(d["launches"], 1)}
@@ -349,7 +351,8 @@ def run_ours(args, g, desc):
         d_rp.copy_(h_rp, non_blocking=True)
         d_col.copy_(h_col, non_blocking=True)
         d_w.copy_(h_w, non_blocking=True)
-        s = ocm.solve(d_rp, d_col, d_w, g.mode, workspace=ws, cycle_out=cyc, stream=stream)
+        s = ocm.solve(d_rp, d_col, d_w, g.mode, workspace=ws, cycle_out=cyc, stream=stream,
+                      single_lambda=single)
         L = s.cycle.numel()
         h_cyc[:L].copy_(s.cycle, non_blocking=True)
         e_ev[k][1].record(stream)
@@ -366,7 +369,7 @@ def run_ours(args, g, desc):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
-        h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+        h = (oracle.howard_single if single else oracle.howard)(g.row_ptr, g.col_idx, g.w, g.mode)
         dt = time.perf_counter() - t0
         cpu = {"value": g.m * (h.iterations + 1) / dt, "unit": "edge-iters/s", "cores": 1,
                "kind": "oracle",
@@ -388,7 +391,9 @@ def run_ours(args, g, desc):
                        "step_ms_median": statistics.median(step_ms),
                        "step_ms_min": min(step_ms),
                        "loop": "cuda_graph" if sol.stats["graph_loop"] else "host",
-                       "host_loop_ms_median": statistics.median(host_ms)},
+                       "host_loop_ms_median": statistics.median(host_ms),
+                       "iteration": ("single-lambda (Alg. 1 rebuild around the chosen cycle)"
+                                     if single else "multichain (one mean per policy cycle)")},
             "roofline": roofline,
             "kernel_share": share,
             "kernels": {c: {"ms_per_solve": v["ms_total"] / prof_steps,
@@ -680,6 +685,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2,
                     help="Howard iterations per reference (oracle) step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-lambda", action="store_true",
+                    help="the paper's single-lambda form of the iteration (single-graph workloads)")
     ap.add_argument("--locality-log2", type=int, default=25,
                     help="log2 of the vertex count of the locality workload (default 25)")
     args = ap.parse_args()

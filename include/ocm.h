@@ -144,6 +144,21 @@ typedef struct ocm_options {
  * benchmark instrumentation is enabled and by ocm_solve_static. */
 #define OCM_FLAG_HOST_LOOP 2
 
+/* The paper's own form of the iteration (Alg. 1 as written, Alg. 2's
+ * markMinComponent / connectGpi / valuePropagate), for comparison with the
+ * default multichain form: after every evaluation the policy cycle of largest
+ * mean (ties: smallest root) is kept with its whole policy component, and
+ * every other vertex is re-pointed, one backward breadth-first level at a
+ * time, to its smallest-index out-edge into the vertices connected at earlier
+ * levels; all values then refer to that one cycle's mean.  Needs every vertex
+ * to reach the chosen cycle, which holds for strongly connected graphs
+ * (OCM_ERR_INVALID_ARG otherwise), and the larger workspace
+ * ocm_workspace_size_single(n, m) (the transposed graph and the search
+ * frontiers).  ocm_solve only (not the batch).  lambda* is the same; the
+ * iteration count, and where several cycles are optimal the returned cycle,
+ * may differ from the default form's. */
+#define OCM_FLAG_SINGLE_LAMBDA 4
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
@@ -155,7 +170,8 @@ typedef struct ocm_stats {
     int64_t detect_items;   /* vertex-rounds of work in cycle detection             */
     int64_t value_items;    /* vertex-rounds of work in value propagation           */
     int32_t graph_loop;     /* 1: the iteration ran as a CUDA graph, 0: host-driven */
-    int32_t reserved;
+    int32_t rebuild_levels; /* OCM_FLAG_SINGLE_LAMBDA: backward-search levels of the
+                               rebuilds, summed over iterations; 0 otherwise         */
 } ocm_stats;
 
 /* Bytes of device workspace ocm_solve needs for a graph with n vertices and m
@@ -163,6 +179,10 @@ typedef struct ocm_stats {
  * range.  The workspace holds the policy, per-vertex values, pointer-jumping
  * buffers and per-cycle records; its contents are scratch between calls.    */
 size_t ocm_workspace_size(int32_t n, int32_t m);
+
+/* Bytes of device workspace for ocm_solve with OCM_FLAG_SINGLE_LAMBDA:
+ * ocm_workspace_size(n, m) plus about 4 m + 20 n bytes.  0 if out of range. */
+size_t ocm_workspace_size_single(int32_t n, int32_t m);
 
 /*
  * ocm_solve -- optimal cycle mean of one graph.
@@ -357,7 +377,8 @@ const char *ocm_status_string(int status);
 
 /* ABI version: 100 * major + minor (101: ocm_options.init_policy; 102:
  * ocm_options.transit and ocm_backward_ratio; 103: ocm_scc and
- * ocm_solve_scc). */
+ * ocm_solve_scc; 104: OCM_FLAG_SINGLE_LAMBDA, ocm_workspace_size_single,
+ * ocm_stats.rebuild_levels). */
 int ocm_version(void);
 
 #ifdef __cplusplus

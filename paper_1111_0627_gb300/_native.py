@@ -20,7 +20,7 @@ BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
 SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu",
-           "scc.cu"]
+           "scc.cu", "single.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -91,7 +91,7 @@ class OcmStats(ctypes.Structure):
                 ("detect_rounds", ctypes.c_int32), ("value_rounds", ctypes.c_int32),
                 ("switched", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("detect_items", ctypes.c_int64), ("value_items", ctypes.c_int64),
-                ("graph_loop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_loop", ctypes.c_int32), ("rebuild_levels", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -100,6 +100,7 @@ class OcmStats(ctypes.Structure):
 # exported symbols and their signatures (kept in step with include/ocm.h)
 SIGNATURES = {
     "ocm_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "ocm_workspace_size_single": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     "ocm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,

@@ -191,7 +191,7 @@ static int persistent_grid() {
 
 static int map_err_bits(int err) {
     if (err & kErrTimeout) return OCM_ERR_TIMEOUT;
-    if (err & (kErrInitPolicy | kErrTransit)) return OCM_ERR_INVALID_ARG;
+    if (err & (kErrInitPolicy | kErrTransit | kErrUnreached)) return OCM_ERR_INVALID_ARG;
     if (err & kErrRatioKey) return OCM_ERR_OVERFLOW;
     if (err & (kErrRowPtr | kErrCol)) return OCM_ERR_BAD_CSR;
     if (err & kErrNoOutEdge) return OCM_ERR_NO_OUT_EDGE;
@@ -244,14 +244,20 @@ struct StepArgs {
     Workspace ws;
     BatchState bs;
     bool batch;
+    bool single;              // the paper's single-lambda form: rebuild after each evaluation
+    SingleWs sg;
     int cls_cnt[kClasses];
 };
 
 // Launches one step; returns the number of kernels, or -1.
 static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHandle handle,
                        cudaStream_t st) {
-    const int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st);
+    int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st);
     if (le < 0) return -1;
+    if (a.single) {
+        if (launch_connect(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.sg, st) < 0) return -1;
+        le += 1;
+    }
     const int ks = (a.kind == OCM_SWEEP_TILES)
                        ? launch_sweep_tiles(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.m, a.epl,
                                             a.ws, a.bs, a.threads, st)
@@ -272,13 +278,13 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl;
+    int n, m, sign, threads, stall, G, kind, epl, single;
     long long N2, max_iters;
     int cls_cnt[kClasses];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
             ctrl != o.ctrl || vptr != o.vptr || transit != o.transit || n != o.n || m != o.m ||
-            sign != o.sign ||
+            sign != o.sign || single != o.single ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters)
             return false;
@@ -321,6 +327,7 @@ LoopKey make_key(const StepArgs &a) {
     k.threads = a.threads;
     k.stall = a.stall;
     k.G = a.bs.G;
+    k.single = a.single ? 1 : 0;
     k.N2 = a.N2;
     k.max_iters = a.max_iters;
     for (int c = 0; c < kClasses; ++c) k.cls_cnt[c] = a.cls_cnt[c];
@@ -443,7 +450,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 103; }
+int ocm_version(void) { return 104; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -494,6 +501,11 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     carve_workspace(workspace, n, m, &ws);
     ws.transit = opt ? opt->transit : nullptr;   // optimal cycle ratio when set
     const bool ratio = ws.transit != nullptr;
+    // the paper's single-lambda form (single graphs only): its extra state
+    // follows the workspace
+    const bool single = !bs && opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA);
+    SingleWs sg{};
+    if (single) carve_single(static_cast<char *>(workspace) + ocm_workspace_size(n, m), n, m, &sg);
     const int sign = (mode == OCM_MAX) ? 1 : -1;
     const int grid = persistent_grid();
     long long launches = 0;
@@ -548,6 +560,13 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     }
     const long long N2 = nmax * nmax;
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
+    if (single) {
+        // the backward search of the rebuild walks the transposed graph
+        // (col_idx was validated above)
+        launches += launch_csc(row_ptr, col_idx, n, m, sg.in_ptr, sg.in_src, sg.cursor, sg.bsum,
+                               st);
+        if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
+    }
 
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable --
     //    as one launch of the cached loop graph, or driven from the host
@@ -568,8 +587,10 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.ws = ws;
     sa.bs = b;
     sa.batch = bs != nullptr;
+    sa.single = single;
+    sa.sg = sg;
     for (int c = 0; c < kClasses; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
-    if (prepare_evaluate(ratio) != 0 ||
+    if ((single && prepare_connect() != 0) || prepare_evaluate(ratio) != 0 ||
         (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
                                  : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
@@ -633,7 +654,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         stats->detect_items = fin.items_detect;
         stats->value_items = fin.items_value;
         stats->graph_loop = slot >= 0 ? 1 : 0;
-        stats->reserved = 0;
+        stats->rebuild_levels = fin.connect_levels;
     }
     return OCM_OK;
 }
@@ -667,19 +688,27 @@ static size_t batch_extra(int G, int N, BatchState *bs, char *base) {
 
 extern "C" {
 
+size_t ocm_workspace_size_single(int32_t n, int32_t m) {
+    if (n < 1 || m < 1) return 0;
+    return carve_workspace(nullptr, n, m, nullptr) + carve_single(nullptr, n, m, nullptr);
+}
+
 int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t n,
               int32_t m, int mode, int64_t *num, int32_t *den, int32_t *cycle_out,
               int32_t *cycle_len, void *workspace, size_t ws_bytes, void *stream,
               const ocm_options *opt, ocm_stats *stats) {
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA)))
+        return OCM_ERR_INVALID_ARG;
+    const bool single = opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA);
     if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))
         return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     SolveOut out{num, den, cycle_len, cycle_out};
     return solve_impl(row_ptr, col_idx, w, n, m, mode, out, workspace, ws_bytes,
-                      ocm_workspace_size(n, m), stream, opt, stats, nullptr);
+                      single ? ocm_workspace_size_single(n, m) : ocm_workspace_size(n, m), stream,
+                      opt, stats, nullptr);
 }
 
 size_t ocm_workspace_size_batch(int32_t G, int32_t N, int32_t M) {

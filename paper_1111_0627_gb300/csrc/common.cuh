@@ -88,6 +88,8 @@ struct Ctrl {
     long long switched_total; // switches summed over all sweeps
     int maxt;                 // cycle ratio: largest transit time
     int qmax;                 // cycle ratio: largest ratio denominator of the current cycles
+    int fcnt[3];              // single-lambda rebuild: rotating frontier counters
+    int connect_levels;       // single-lambda rebuild: backward-search levels, all iterations
 };
 
 enum : int {
@@ -103,6 +105,8 @@ enum : int {
     kErrInitPolicy = 512, // a caller-given initial policy edge is not an out-edge of its vertex
     kErrTransit = 1024,   // a transit time below 1
     kErrRatioKey = 2048,  // cycle ratio: the exact order keys of the current cycles overflow int64
+    kErrUnreached = 4096, // single-lambda rebuild: a vertex cannot reach the chosen cycle
+    kErrConnect = 8192,   // single-lambda rebuild: inconsistent state (no chosen cycle, no edge)
 };
 
 // Workspace carved from one caller-provided buffer.
@@ -188,6 +192,19 @@ struct BatchState {
 // when base != nullptr.
 size_t carve_workspace(void *base, int n, int m, Workspace *ws);
 
+// Extra state of the single-lambda iteration (OCM_FLAG_SINGLE_LAMBDA), carved
+// after the workspace above: the transposed graph for the backward search
+// and its levels and frontiers.
+struct SingleWs {
+    int *in_ptr;    // [n+1] CSC offsets
+    int *in_src;    // [m] source vertex of each in-edge
+    int *cursor;    // [n] CSC scatter cursors
+    int *bsum;      // [n / 1024 + 2] block sums of the offset scan
+    int *lev;       // [n] search level: -1 unconnected, -2 reached at the current level
+    int *fr[2];     // [n] frontiers of consecutive levels
+};
+size_t carve_single(void *base, int n, int m, SingleWs *sw);
+
 // Smallest tile of the edge-tiled sweep (32 lanes x 4 edges); the workspace
 // holds the per-tile arrays for this size, enough for every larger one.
 constexpr int kMinTileEdges = 128;
@@ -271,6 +288,13 @@ int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws,
                         int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,
                         cudaStream_t st);
 int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
+// Transposed CSR (scc.cu); returns the number of kernels launched.
+int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, int *in_src,
+               int *cursor, int *bsum, cudaStream_t st);
+// Single-lambda rebuild after an evaluation (single.cu); 1, or -1 on a launch failure.
+int prepare_connect();
+int launch_connect(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                   Workspace ws, SingleWs sw, cudaStream_t st);
 void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t *potential,
                     int32_t *policy, cudaStream_t st);
 void launch_backward(const int *cycle_edges, int cycle_len, const float *grad_lambda, int m,

@@ -220,8 +220,8 @@ csc_zero_kernel(int n, int *in_ptr, int *cursor) {
 // Transposed CSR of a graph (in-edges by target; sources in no particular
 // order within a row) for the backward searches.  bsum needs n / 1024 + 2
 // ints, cursor n.  Returns the number of kernels launched.
-static int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, int *in_src,
-                      int *cursor, int *bsum, cudaStream_t st) {
+int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, int *in_src,
+               int *cursor, int *bsum, cudaStream_t st) {
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;

@@ -1,0 +1,293 @@
+// single.cu -- the paper's own form of the policy iteration (Alg. 1 as
+// written; Alg. 2's markMinComponent, connectGpi and valuePropagate): one
+// lambda per iteration, the mean of the chosen policy cycle, and every other
+// policy cycle broken so that all vertices reach the chosen one.
+//
+// The solver's default iteration keeps one mean per policy cycle (multichain)
+// and needs no rebuild; with OCM_FLAG_SINGLE_LAMBDA the step becomes
+//   evaluate -> connect (this file) -> sweep -> control,
+// where connect, one cooperative launch, does the rebuild and the value
+// propagation of Alg. 1 at once:
+//   level 0   the component of the chosen cycle (the evaluation's best: the
+//             largest mean, then the smallest root) keeps its policy and its
+//             values -- markMinComponent;
+//   level k   every vertex not yet connected with an out-edge into level
+//             k-1 takes its smallest-index out-edge into the vertices
+//             connected at levels < k -- connectGpi; the paper leaves that
+//             choice open, the smallest index makes it deterministic.  A level
+//             is found by pushing from level k-1 along its in-edges (the
+//             transposed graph), or, when fewer vertices are left than level
+//             k-1 holds (always for level 1: level 0 is the chosen cycle's
+//             whole component), by pulling: every unconnected vertex scans
+//             its own out-edges;
+//   values    a vertex connected at level k gets its path sums from its new
+//             successor, final since level k-1: (len, S) = (len(t) + 1,
+//             S(t) + s*w(e)) and V = q*S - p*len relative to the chosen
+//             cycle's smallest vertex -- valuePropagate along the new edges.
+// Both state buffers of the value jumping receive the final state, so the
+// next evaluation treats a rebuilt vertex like any vertex the sweep did not
+// touch.  The levels are separated by the bounded grid barrier.
+#include <climits>
+
+#include "common.cuh"
+#include "grid_sync.cuh"
+
+namespace ocm {
+
+constexpr int kConnectThreads = 1024;   // one block per SM: few arrivals per barrier
+constexpr int kConnectLanes = 8;        // lanes serving one frontier vertex
+
+size_t carve_single(void *base, int n, int m, SingleWs *sw) {
+    char *b = static_cast<char *>(base);
+    size_t off = 0;
+    const size_t N = (size_t)n, M = (size_t)m;
+    auto take = [&](size_t bytes) -> void * {
+        off = (off + 255) / 256 * 256;
+        void *p = b ? b + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    SingleWs w{};
+    w.in_ptr = static_cast<int *>(take(4 * (N + 1)));
+    w.in_src = static_cast<int *>(take(4 * M));
+    w.cursor = static_cast<int *>(take(4 * N));
+    w.bsum = static_cast<int *>(take(4 * (N / 1024 + 2)));
+    w.lev = static_cast<int *>(take(4 * N));
+    w.fr[0] = static_cast<int *>(take(4 * N));
+    w.fr[1] = static_cast<int *>(take(4 * N));
+    if (sw) *sw = w;
+    return (off + 255) / 256 * 256;
+}
+
+static __device__ __forceinline__ void append(int *q, int *cnt, bool pred, int item, int lane) {
+    const int pos = warp_append(cnt, pred, lane);
+    if (pred) q[pos] = item;
+}
+
+// Vertex u joins level k through edge e: its policy, its final path sums
+// (both buffers of the value jumping) and its record for the sweep, all
+// relative to the chosen cycle (root rstar, mean P/Q, rank RK).
+static __device__ __forceinline__ void take_edge(int u, int e, int k, int rstar, long long P,
+                                                 long long Q, int RK, bool ratio, int sign,
+                                                 const int *__restrict__ col,
+                                                 const int *__restrict__ w, const Workspace &ws,
+                                                 const SingleWs &sg) {
+    const int t = col[e];
+    const int wv = sign * w[e];
+    ws.pi[u] = e;
+    ws.succ[u] = t;
+    ws.wpi[u] = wv;
+    const JLS st = ws.jls[0][t];
+    const JLS su{~rstar, st.len + 1, st.S + (long long)wv};
+    ws.jls[0][u] = su;
+    ws.jls[1][u] = su;
+    long long T = su.len;
+    if (ratio) {
+        const int tr = ws.transit[e];
+        ws.tpi[u] = tr;
+        T = ws.jt[0][t] + tr;
+        ws.jt[0][u] = T;
+        ws.jt[1][u] = T;
+        ws.recp[u] = P;
+    }
+    Rec r;
+    r.V = Q * su.S - P * T;
+    r.rank = RK;
+    r.q = (int)Q;
+    ws.rec[u] = r;
+    // level k is numbered at once: the edge tests above take levels < k only
+    sg.lev[u] = k;
+}
+
+__global__ void __launch_bounds__(kConnectThreads, 1)
+connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+               const int *__restrict__ w, int sign, int n, Workspace ws, SingleWs sg) {
+    Ctrl *c = ws.ctrl;
+    const unsigned nb = gridDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const bool leader = gtid == 0;
+    // the evaluation before this launch finished (or stopped on an error)
+    // before any block started, so every block takes the same branch here
+    if (c->err) return;
+    const unsigned long long bb = c->best;
+    const int rstar = 0x7fffffff - (int)(unsigned)(bb & 0xffffffffu);
+    if (bb == 0 || rstar < 0 || rstar >= n) {
+        if (leader) atomicOr(&c->err, kErrConnect);
+        return;
+    }
+    const int istar = ws.cid_of_root[rstar];
+    const long long P = ws.cyc_p[istar];
+    const long long Q = ws.cyc_q[istar];
+    const int RK = ws.cyc_rank[istar];
+    const bool ratio = ws.transit != nullptr;
+    if (leader) {
+        c->fcnt[0] = 0;
+        c->fcnt[1] = 0;
+        c->fcnt[2] = 0;
+    }
+    if (!grid_barrier(c, nb)) return;
+
+    // level 0: the vertices whose policy path ends on the chosen cycle
+    int mine = 0;
+    for (int v = gtid; v < n; v += stride) {
+        const bool in0 = (~ws.jls[0][v].J == rstar);
+        sg.lev[v] = in0 ? 0 : -1;
+        mine += !in0;
+    }
+    bool ok;
+    int left = grid_sum_barrier(c, nb, mine, &ok);   // vertices still unconnected
+    if (!ok) return;
+
+    constexpr int kPer = 32 / kConnectLanes;
+    const int warp_id = gtid >> 5, nwarps = stride >> 5;
+    const int grp = lane / kConnectLanes, sub = lane % kConnectLanes;
+    int levels = 0, nf = 0;
+    for (int k = 1; left > 0; ++k) {
+        if (k > n) {   // a search cannot have more levels than vertices
+            if (leader) atomicOr(&c->err, kErrConnect);
+            return;
+        }
+        const int *F = sg.fr[(k - 1) & 1];
+        int *Fn = sg.fr[k & 1];
+        int *cn = &c->fcnt[k % 3];
+        // counters rotate over three slots: the one reset here was last
+        // appended to two levels ago and is next appended to at level k+1
+        if (leader) c->fcnt[(k + 1) % 3] = 0;
+        int added = 0;
+        const bool pull = (k == 1 || left <= nf);
+        if (pull) {
+            // pull: every unconnected vertex looks for an out-edge into
+            // levels < k (level 0 is too large a frontier to push from)
+            for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+                const int u = base + threadIdx.x;
+                int pick = -1;
+                if (u < n && sg.lev[u] == -1) {
+                    for (int e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                        const int l = sg.lev[col[e]];
+                        if (l >= 0 && l < k) {
+                            pick = e;
+                            break;
+                        }
+                    }
+                }
+                if (pick >= 0) take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                append(Fn, cn, pick >= 0, u, lane);
+                added += pick >= 0;
+            }
+        } else {
+            // push: (a) the unconnected in-neighbours of level k-1 are
+            // reached at level k ...
+            const int ntask = (nf + kPer - 1) / kPer;
+            for (int task = warp_id; task < ntask; task += nwarps) {
+                const int i = task * kPer + grp;
+                int e = 0, e1 = 0;
+                if (i < nf) {
+                    const int f = F[i];
+                    e = sg.in_ptr[f] + sub;
+                    e1 = sg.in_ptr[f + 1];
+                }
+                for (;;) {
+                    const bool more = e < e1;
+                    if (!__any_sync(0xffffffffu, more)) break;
+                    bool take = false;
+                    int u = 0;
+                    if (more) {
+                        u = sg.in_src[e];
+                        e += kConnectLanes;
+                        if (sg.lev[u] == -1) take = atomicCAS(&sg.lev[u], -1, -2) == -1;
+                    }
+                    append(Fn, cn, take, u, lane);
+                    added += take;
+                }
+            }
+            const int reached = grid_sum_barrier(c, nb, added, &ok);
+            if (!ok) return;
+            // ... (b) and each takes its smallest out-edge into levels < k
+            const int ntask2 = (reached + kPer - 1) / kPer;
+            for (int task = warp_id; task < ntask2; task += nwarps) {
+                const int i = task * kPer + grp;
+                int u = -1, e = 0, e1 = 0;
+                if (i < reached) {
+                    u = Fn[i];
+                    e = row_ptr[u] + sub;
+                    e1 = row_ptr[u + 1];
+                }
+                int pick = INT_MAX;
+                for (; e < e1; e += kConnectLanes) {
+                    const int l = sg.lev[col[e]];
+                    if (l >= 0 && l < k) {
+                        pick = e;
+                        break;
+                    }
+                }
+#pragma unroll
+                for (int o = kConnectLanes / 2; o > 0; o >>= 1)
+                    pick = min(pick, __shfl_xor_sync(0xffffffffu, pick, o));
+                if (u >= 0 && sub == 0) {
+                    if (pick == INT_MAX)
+                        atomicOr(&c->err, kErrConnect);
+                    else
+                        take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                }
+            }
+            if (!grid_barrier(c, nb)) return;
+            nf = reached;
+        }
+        if (pull) {
+            nf = grid_sum_barrier(c, nb, added, &ok);
+            if (!ok) return;
+        }
+        if (nf == 0) break;   // the rest cannot reach the chosen cycle
+        left -= nf;
+        ++levels;
+    }
+    if (leader) {
+        if (left > 0) atomicOr(&c->err, kErrUnreached);
+        c->connect_levels += levels;
+        c->nrep = 1;   // the chosen cycle is now the only one
+    }
+}
+
+static int connect_grid() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev == cached_dev && cached > 0) return cached;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, connect_kernel, kConnectThreads,
+                                                      0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    cached_dev = dev;
+    cached = sms * per_sm;
+    return cached;
+}
+
+int prepare_connect() { return connect_grid() > 0 ? 0 : -1; }
+
+int launch_connect(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                   Workspace ws, SingleWs sw, cudaStream_t st) {
+    int blocks = connect_grid();
+    if (blocks <= 0) return -1;
+    const int need = (n + kConnectThreads - 1) / kConnectThreads;
+    if (need < blocks) blocks = need;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kConnectThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_begin(kProfEvaluate, st);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, connect_kernel, row_ptr, col, w, sign, n, ws, sw);
+    prof_end(kProfEvaluate, st);
+    return e == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace ocm

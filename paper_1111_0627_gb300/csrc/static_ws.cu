@@ -52,7 +52,9 @@ extern "C" int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, 
                                 int32_t *cycle_out, int32_t *cycle_len, void *stream,
                                 const ocm_options *opt, ocm_stats *stats) {
     if (n < 1 || m < 1) return OCM_ERR_INVALID_ARG;
-    const size_t need = ocm_workspace_size(n, m);
+    const size_t need = (opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA))
+                            ? ocm_workspace_size_single(n, m)
+                            : ocm_workspace_size(n, m);
     if (need == 0 || need > (size_t)OCM_STATIC_WORKSPACE_BYTES) return OCM_ERR_WORKSPACE;
     void *ws = nullptr;
     int rc = static_workspace_address(&ws);

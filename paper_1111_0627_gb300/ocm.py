@@ -24,6 +24,7 @@ from . import _native
 OCM_MAX, OCM_MIN = 0, 1
 OCM_FLAG_TEST_STALL = 1
 OCM_FLAG_HOST_LOOP = 2
+OCM_FLAG_SINGLE_LAMBDA = 4
 OCM_SWEEP_DEFAULT, OCM_SWEEP_CLASSES, OCM_SWEEP_TILES = 0, 1, 2
 
 
@@ -76,12 +77,15 @@ def _transit(transit, m: int):
     return t
 
 
-def workspace_bytes(n: int, m: int) -> int:
-    return int(_native.load().ocm_workspace_size(n, m))
+def workspace_bytes(n: int, m: int, single_lambda: bool = False) -> int:
+    lib = _native.load()
+    if single_lambda:
+        return int(lib.ocm_workspace_size_single(n, m))
+    return int(lib.ocm_workspace_size(n, m))
 
 
-def make_workspace(n: int, m: int, device=None) -> torch.Tensor:
-    nbytes = workspace_bytes(n, m)
+def make_workspace(n: int, m: int, device=None, single_lambda: bool = False) -> torch.Tensor:
+    nbytes = workspace_bytes(n, m, single_lambda)
     if nbytes == 0:
         raise ValueError("graph size out of range")
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
@@ -112,7 +116,8 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
           flags: int = 0, edges_per_lane: int = 0, sweep_threads: int = 0,
           sweep_kind: int = 0, tune: bool = False,
           init_policy: torch.Tensor | None = None,
-          transit: torch.Tensor | None = None) -> Solution:
+          transit: torch.Tensor | None = None,
+          single_lambda: bool = False) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
@@ -120,7 +125,10 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     per-vertex cycle means (eta_num/eta_den) and potentials of the final
     policy, in the maximising sense of s*w (s = -1 in min mode).  ``tune=True``
     uses the sweep layout and launch parameters the autotuner recorded for
-    graphs of this shape (results never depend on them)."""
+    graphs of this shape (results never depend on them).  ``single_lambda``
+    runs the paper's own form of the iteration (one lambda, the policy graph
+    rebuilt around the chosen cycle each time); every vertex must reach that
+    cycle, as in a strongly connected graph."""
     lib = _native.load()
     rp = _dev_i32(row_ptr, "row_ptr")
     col = _dev_i32(col_idx, "col_idx")
@@ -129,8 +137,10 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     if ww.numel() != m:
         raise ValueError("w and col_idx must have the same length")
     dev = rp.device
+    if single_lambda:
+        flags = int(flags) | OCM_FLAG_SINGLE_LAMBDA
     if workspace is None:
-        workspace = make_workspace(n, m, dev)
+        workspace = make_workspace(n, m, dev, bool(int(flags) & OCM_FLAG_SINGLE_LAMBDA))
     if cycle_out is None:
         cycle_out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     opt = _native.OcmOptions()

@@ -37,12 +37,15 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_only_entry_points():
     lib = ocm.load()
-    assert lib.ocm_version() == 103
+    assert lib.ocm_version() == 104
     assert lib.ocm_workspace_size(0, 5) == 0
     assert lib.ocm_workspace_size(5, 0) == 0
     small = lib.ocm_workspace_size(1000, 4000)
     big = lib.ocm_workspace_size(2000, 4000)
     assert small > 0 and big > small and small % 256 == 0
+    single = lib.ocm_workspace_size_single(1000, 4000)
+    assert single % 256 == 0 and 4 * 4000 + 20 * 1000 <= single - small <= 4 * 4000 + 20 * 1000 + 4096
+    assert lib.ocm_workspace_size_single(0, 5) == 0
     assert lib.ocm_status_string(0) == b"ok"
     for code in range(-9, 0):
         assert lib.ocm_status_string(code) != b"unknown status"
@@ -66,10 +69,19 @@ def test_argument_errors_are_reported_before_any_device_work():
                        ctypes.byref(clen), ctypes.c_void_p(256 + 8), 10**9, None, None, None)
     assert rc == -7                                      # workspace misaligned
     opt = _native.OcmOptions()
-    opt.flags = 4                                        # no such flag
+    opt.flags = 8                                        # no such flag
     rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
                        ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
     assert rc == -1
+    opt.flags = 4                                        # single lambda: larger workspace
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, lib.ocm_workspace_size(4, 4), None,
+                       ctypes.byref(opt), None)
+    assert rc == -7
+    clen_g = ctypes.c_void_p(256)
+    rc = lib.ocm_solve_batch(fake, fake, fake, fake, 1, 4, 4, 0, fake, fake, clen_g, fake, fake,
+                             10**9, None, ctypes.byref(opt), None)
+    assert rc == -1                                      # single lambda: not for batches
     opt.flags = 0
     opt.sweep_kind = 7                                   # no such sweep layout
     rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,

@@ -66,3 +66,29 @@ def test_static_entry_rejects_graphs_beyond_its_capacity():
                               ctypes.byref(clen), None, None, None)
     assert rc == -7      # OCM_ERR_WORKSPACE, before any device work
     assert (num.value, den.value, clen.value) == (0, 0, 0)
+
+
+def test_static_entry_in_the_single_lambda_form():
+    """OCM_FLAG_SINGLE_LAMBDA needs the larger workspace; the static entry
+    sizes its check by the flag and gives ocm_solve's answer."""
+    lib = ocm.load()
+    g = synth.ring10k()
+    assert lib.ocm_workspace_size_single(g.n, g.m) <= STATIC_BYTES
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col_idx).cuda()
+    w = torch.from_numpy(g.w).cuda()
+    ref = ocm.solve(rp, col, w, g.mode, single_lambda=True)
+    opt = _native.OcmOptions()
+    opt.flags = 4
+    num, den, clen = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    out = torch.full((g.n,), -1, dtype=torch.int32, device="cuda")
+    st = _native.OcmStats()
+    rc = lib.ocm_solve_static(rp.data_ptr(), col.data_ptr(), w.data_ptr(), g.n, g.m,
+                              0 if g.mode == "max" else 1, ctypes.byref(num), ctypes.byref(den),
+                              out.data_ptr(), ctypes.byref(clen),
+                              int(torch.cuda.current_stream().cuda_stream), ctypes.byref(opt),
+                              ctypes.byref(st))
+    assert rc == 0
+    assert (int(num.value), int(den.value)) == (ref.num, ref.den)
+    assert out[:int(clen.value)].cpu().tolist() == ref.cycle.cpu().tolist()
+    assert st.iterations == ref.stats["iterations"] and st.rebuild_levels > 0
