@@ -77,7 +77,7 @@ def _load():
             lib.oracle_certificate.argtypes = [i32, i32, i32p, i32p, i32p, c_int, i64p, i64p,
                                                i64p, i64, i64, i32p, i32, i64p]
             lib.oracle_howard_single.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64,
-                                                 i64p, i64p, i32p, i32p, i64p, i32p, i64p]
+                                                 i64p, i64p, i32p, i32p, i64p, i32p, i64p, i32p]
             lib.oracle_howard_ratio.argtypes = [i32, i32, i32p, i32p, i32p, i32p, c_int, i64,
                                                 i64p, i64p, i32p, i32p, i64p, i64p, i64p, i32p,
                                                 i64p, i32p]
@@ -193,10 +193,11 @@ class SingleResult:
 
 
 def howard_single(row_ptr, col_idx, w, mode="max", max_iter: int = 0,
-                  transit=None) -> SingleResult:
+                  transit=None, init_policy=None) -> SingleResult:
     """The paper's form of Howard's iteration (Alg. 1 as written): one lambda,
     every other policy cycle broken each iteration by a backward search from
-    the chosen cycle's component; every vertex must reach that cycle."""
+    the chosen cycle's component; every vertex must reach that cycle.
+    ``init_policy`` replaces the first pass (warm start)."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
     col, colp = _i32(col_idx)
@@ -214,11 +215,14 @@ def howard_single(row_ptr, col_idx, w, mode="max", max_iter: int = 0,
         tt, ttp = _i32(transit)
         if tt.shape[0] != m:
             raise ValueError("transit needs one entry per edge")
+    init, initp = _i32(init_policy) if init_policy is not None else (None, None)
+    if init is not None and init.shape[0] != n:
+        raise ValueError("init_policy must have one entry per vertex")
     i32p = ctypes.POINTER(ctypes.c_int32)
     rc = lib.oracle_howard_single(n, m, rpp, colp, wp, ttp, _mode(mode), max_iter, _i64p(num),
                                   _i64p(den), cyc.ctypes.data_as(i32p),
                                   clen.ctypes.data_as(i32p), _i64p(V), pol.ctypes.data_as(i32p),
-                                  _i64p(its))
+                                  _i64p(its), initp)
     if rc != 0:
         raise OracleError(rc, "howard_single")
     return SingleResult(int(num[0]), int(den[0]), cyc[:int(clen[0])].copy(), V, pol,

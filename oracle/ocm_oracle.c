@@ -391,19 +391,23 @@ int oracle_howard(int32_t n, int32_t m, const int32_t *rp, const int32_t *col, c
  * smallest vertex with the one lambda, and the improvement step switches a
  * vertex on strict improvement of q*w(e) - p*t(e) + V(t).  Every vertex must
  * reach the chosen cycle (true for strongly connected input; OR_ERR_NOT_SC
- * otherwise).  tt = transit times for the cycle ratio, NULL for the mean.
+ * otherwise).  tt = transit times for the cycle ratio, NULL for the mean;
+ * init = an optional start policy as in oracle_howard.
  * Outputs as oracle_howard (V and policy optional, the final policy has the
  * one cycle); iters counts improvement steps that switched a vertex.
  */
 int oracle_howard_single(int32_t n, int32_t m, const int32_t *rp, const int32_t *col,
                          const int32_t *w, const int32_t *tt, int mode, int64_t max_iter,
                          int64_t *num, int64_t *den, int32_t *cycle, int32_t *clen,
-                         int64_t *V_out, int32_t *policy, int64_t *iters) {
+                         int64_t *V_out, int32_t *policy, int64_t *iters, const int32_t *init) {
     int rc = check_csr(n, m, rp, col);
     if (rc) return rc;
     if (tt)
         for (int32_t e = 0; e < m; ++e)
             if (tt[e] < 1) return OR_ERR_ARG;
+    if (init)
+        for (int32_t v = 0; v < n; ++v)
+            if (init[v] < rp[v] || init[v] >= rp[v + 1]) return OR_ERR_ARG;
     if (!w || (mode != 0 && mode != 1)) return OR_ERR_ARG;
     for (int32_t e = 0; e < m; ++e)
         if (w[e] == INT32_MIN) return OR_ERR_RANGE;
@@ -436,7 +440,7 @@ int oracle_howard_single(int32_t n, int32_t m, const int32_t *rp, const int32_t 
         int32_t best = rp[v];
         for (int32_t e = rp[v] + 1; e < rp[v + 1]; ++e)
             if (wmax(w, e, mode) > wmax(w, best, mode)) best = e;
-        h.pi[v] = best;
+        h.pi[v] = init ? init[v] : best;   /* or the caller's start (warm start) */
     }
     int64_t it = 0;
     int32_t bc = 0;

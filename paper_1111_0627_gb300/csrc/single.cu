@@ -14,12 +14,15 @@
 //   level k   every vertex not yet connected with an out-edge into level
 //             k-1 takes its smallest-index out-edge into the vertices
 //             connected at levels < k -- connectGpi; the paper leaves that
-//             choice open, the smallest index makes it deterministic.  A level
-//             is found by pushing from level k-1 along its in-edges (the
-//             transposed graph), or, when fewer vertices are left than level
-//             k-1 holds (always for level 1: level 0 is the chosen cycle's
-//             whole component), by pulling: every unconnected vertex scans
-//             its own out-edges;
+//             choice open, the smallest index makes it deterministic.  A
+//             level of more than n/64 vertices (there are at most 64) is
+//             found by passes over all vertices -- pulling (every unconnected
+//             vertex scans its out-edges) when fewer vertices are left than
+//             level k-1 holds, else pushing (level k-1 marks its in-neighbours
+//             over the transposed graph, plain stores, then every marked
+//             vertex picks its edge) -- and a smaller one through compact
+//             lists (atomic claims and appends), so small levels cost no pass
+//             over the graph;
 //   values    a vertex connected at level k gets its path sums from its new
 //             successor, final since level k-1: (len, S) = (len(t) + 1,
 //             S(t) + s*w(e)) and V = q*S - p*len relative to the chosen
@@ -63,6 +66,7 @@ static __device__ __forceinline__ void append(int *q, int *cnt, bool pred, int i
     const int pos = warp_append(cnt, pred, lane);
     if (pred) q[pos] = item;
 }
+
 
 // Vertex u joins level k through edge e: its policy, its final path sums
 // (both buffers of the value jumping) and its record for the sweep, all
@@ -139,46 +143,87 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     bool ok;
     int left = grid_sum_barrier(c, nb, mine, &ok);   // vertices still unconnected
     if (!ok) return;
-
     constexpr int kPer = 32 / kConnectLanes;
     const int warp_id = gtid >> 5, nwarps = stride >> 5;
     const int grp = lane / kConnectLanes, sub = lane % kConnectLanes;
-    int levels = 0, nf = 0;
+    int levels = 0;
+    int nf = n - left;        // size of level k-1 (level 0 first)
+    bool have_list = false;   // level k-1 is listed in fr[(k-1) & 1]
     for (int k = 1; left > 0; ++k) {
         if (k > n) {   // a search cannot have more levels than vertices
             if (leader) atomicOr(&c->err, kErrConnect);
             return;
         }
-        const int *F = sg.fr[(k - 1) & 1];
+        int *F = sg.fr[(k - 1) & 1];
         int *Fn = sg.fr[k & 1];
-        int *cn = &c->fcnt[k % 3];
         // counters rotate over three slots: the one reset here was last
         // appended to two levels ago and is next appended to at level k+1
         if (leader) c->fcnt[(k + 1) % 3] = 0;
-        int added = 0;
-        const bool pull = (k == 1 || left <= nf);
-        if (pull) {
-            // pull: every unconnected vertex looks for an out-edge into
-            // levels < k (level 0 is too large a frontier to push from)
-            for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-                const int u = base + threadIdx.x;
-                int pick = -1;
-                if (u < n && sg.lev[u] == -1) {
-                    for (int e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-                        const int l = sg.lev[col[e]];
-                        if (l >= 0 && l < k) {
-                            pick = e;
-                            break;
-                        }
+        // A level of more than n/64 vertices is handled by passes over all
+        // vertices (at most 64 such levels: the levels are disjoint), a
+        // smaller one through a compact list.
+        const bool big = (long long)nf * 64 > (long long)n;
+        int found = 0;
+        if (big) {
+            // passes over all vertices, one thread per vertex, edges four at
+            // a time (independent loads in flight).  pull: the unconnected
+            // vertices look for an out-edge into levels < k (when fewer are
+            // left than level k-1 holds); push: (a) level k-1 marks its
+            // unconnected in-neighbours (-2, plain stores: every writer
+            // writes the same), (b) the marked vertices pick their edge as in
+            // the pull.
+            const bool pull = left <= nf;
+            if (!pull) {
+                for (int v = gtid; v < n; v += stride) {
+                    if (sg.lev[v] != k - 1) continue;
+                    const int e1 = sg.in_ptr[v + 1];
+                    for (int e = sg.in_ptr[v]; e < e1; e += 4) {
+                        int u[4], l[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) u[j] = e + j < e1 ? sg.in_src[e + j] : -1;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) l[j] = u[j] >= 0 ? sg.lev[u[j]] : 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (l[j] == -1) sg.lev[u[j]] = -2;
                     }
                 }
-                if (pick >= 0) take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
-                append(Fn, cn, pick >= 0, u, lane);
-                added += pick >= 0;
+                if (!grid_barrier(c, nb)) return;
             }
+            const int want = pull ? -1 : -2;
+            for (int u = gtid; u < n; u += stride) {
+                if (sg.lev[u] != want) continue;
+                const int e1 = row_ptr[u + 1];
+                int pick = -1;
+                for (int e = row_ptr[u]; e < e1 && pick < 0; e += 4) {
+                    int l[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) l[j] = e + j < e1 ? sg.lev[col[e + j]] : -1;
+#pragma unroll
+                    for (int j = 3; j >= 0; --j)
+                        if (l[j] >= 0 && l[j] < k) pick = e + j;   // the smallest index wins
+                }
+                if (pick >= 0) {
+                    take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                    ++found;
+                } else if (!pull) {
+                    atomicOr(&c->err, kErrConnect);   // a marked vertex has the edge
+                }
+            }
+            nf = grid_sum_barrier(c, nb, found, &ok);
+            if (!ok) return;
+            have_list = false;
         } else {
-            // push: (a) the unconnected in-neighbours of level k-1 are
-            // reached at level k ...
+            // push through lists: list level k-1 first if a pass made it
+            if (!have_list) {
+                for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+                    const int v = base + threadIdx.x;
+                    append(F, &c->fcnt[(k - 1) % 3], v < n && sg.lev[v] == k - 1, v, lane);
+                }
+                if (!grid_barrier(c, nb)) return;
+            }
+            // (a) the unconnected in-neighbours of level k-1 are reached ...
+            int added = 0;
             const int ntask = (nf + kPer - 1) / kPer;
             for (int task = warp_id; task < ntask; task += nwarps) {
                 const int i = task * kPer + grp;
@@ -198,7 +243,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                         e += kConnectLanes;
                         if (sg.lev[u] == -1) take = atomicCAS(&sg.lev[u], -1, -2) == -1;
                     }
-                    append(Fn, cn, take, u, lane);
+                    append(Fn, &c->fcnt[k % 3], take, u, lane);
                     added += take;
                 }
             }
@@ -234,10 +279,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             }
             if (!grid_barrier(c, nb)) return;
             nf = reached;
-        }
-        if (pull) {
-            nf = grid_sum_barrier(c, nb, added, &ok);
-            if (!ok) return;
+            have_list = true;
         }
         if (nf == 0) break;   // the rest cannot reach the chosen cycle
         left -= nf;

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
     import paper_1111_0627_gb300 as ocm
-    from paper_1111_0627_gb300.ocm import OCM_FLAG_HOST_LOOP
+    from paper_1111_0627_gb300.ocm import OCM_FLAG_HOST_LOOP, OCM_FLAG_TEST_STALL, OCM_SWEEP_TILES
 
 
 def _dev(*arrays):
@@ -154,3 +154,40 @@ def test_full_size_against_stored_oracle(name):
                                  sol.eta_den.cpu().numpy(), sol.potential.cpu().numpy(), sol.num,
                                  sol.den, cyc)
     assert rc == 0, (name, rc, bad)
+
+
+def test_warm_start_follows_the_oracle():
+    rng = np.random.default_rng(1111062814)
+    for trial in range(60):
+        n = int(rng.integers(1, 300))
+        mode = "max" if trial % 2 == 0 else "min"
+        g = synth.tiny_random(rng, n, max_extra=4, wlo=-60, whi=60, ring=True, mode=mode)
+        init = synth.random_policy(rng, g.row_ptr)
+        s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode, init_policy=init)
+        _check(g, _solve(g, init_policy=_dev(init)[0], certificate=True), s=s)
+    g = synth.ring10k()
+    first = _solve(g, certificate=True)
+    again = _solve(g, init_policy=first.policy, certificate=True)
+    assert (again.num, again.den, again.stats["iterations"]) == (first.num, first.den, 0)
+    assert torch.equal(again.cycle, first.cycle) and torch.equal(again.potential, first.potential)
+
+
+def test_edge_tiled_sweep_gives_the_same_iteration():
+    for g in (synth.ring10k(), synth.locality32m(1 << 16)):
+        a = _solve(g, certificate=True)
+        b = _solve(g, certificate=True, sweep_kind=OCM_SWEEP_TILES)
+        assert (a.num, a.den, a.stats["iterations"]) == (b.num, b.den, b.stats["iterations"])
+        assert torch.equal(a.cycle, b.cycle) and torch.equal(a.policy, b.policy)
+        assert torch.equal(a.potential, b.potential)
+
+
+def test_bounded_wait_expires_cleanly_in_the_single_lambda_form():
+    """The test flag makes the evaluation's first barrier wait for an arrival
+    that never comes; the rebuild that follows must not wait either, and the
+    device stays usable."""
+    g = synth.ring10k()
+    for flags in (OCM_FLAG_TEST_STALL, OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP):
+        with pytest.raises(ocm.OCMError) as ex:
+            _solve(g, flags=flags)
+        assert ex.value.status == -6
+    _check(g, _solve(g))

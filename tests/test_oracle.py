@@ -538,3 +538,20 @@ def test_single_lambda_hand_traces(tr):
     h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
     assert (h.num, h.den, h.iterations) == (tr.num, tr.den, tr.multichain_iters)
     assert tuple(int(e) for e in h.cycle) == tr.cycle
+
+
+def test_single_lambda_warm_start_reaches_the_optimum():
+    rng = np.random.default_rng(1111062804)
+    for trial in range(400):
+        n = int(rng.integers(1, 9))
+        mode = "max" if trial % 2 == 0 else "min"
+        g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, ring=True, mode=mode)
+        init = synth.random_policy(rng, g.row_ptr)
+        s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode, init_policy=init)
+        b = oracle.brute(g.row_ptr, g.col_idx, g.w, mode)
+        assert s.value == b.value, trial
+        assert tuple(int(e) for e in s.cycle) in b.optimal, trial
+        # resuming from the final policy stops at once with the same answer
+        r = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode, init_policy=s.policy)
+        assert (r.num, r.den, r.iterations) == (s.num, s.den, 0), trial
+        assert r.cycle.tolist() == s.cycle.tolist() and r.V.tolist() == s.V.tolist()
