@@ -206,6 +206,20 @@ TRAFFIC = {
 }
 
 
+def job_rate(units_per_step: float, steps: int, local_ms: float, world: int, device):
+    """Whole-job rate of `world` replicas that each ran `steps` steps of
+    `units_per_step` units in `local_ms` (their own timed region): the job
+    took as long as its slowest rank (max over ranks), and its rate counts
+    the units of all ranks.  Returns (rate per second, job milliseconds)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    job_ms = float(t.item())
+    return world * steps * units_per_step / (job_ms / 1e3), job_ms
+
+
 def _source_hash(kernel: str) -> str | None:
     import hashlib
     files = KERNEL_SOURCES.get(kernel)
@@ -280,12 +294,7 @@ def run_ours(args, g, desc):
             launches += s.stats["launches"]
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * units / (total_ms / 1e3)
+    value, total_ms = job_rate(units, args.steps, sum(step_ms), world, dev)
 
     # ---- the same solve with the loop driven from the host (one stream
     #      synchronisation per improvement step), for comparison only
@@ -358,11 +367,7 @@ def run_ours(args, g, desc):
         e_ev[k][1].record(stream)
         d2h = 4 * L + 16
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps * units / (float(t.item()) / 1e3)
+    e2e_value, _ = job_rate(units, e2e_steps, sum(a.elapsed_time(b) for a, b in e_ev), world, dev)
 
     # ---- CPU baseline: the oracle as it stands, rank 0 at N = 1
     cpu = None
@@ -457,12 +462,7 @@ def run_batch(args):
             ev[k][1].record(stream)
             launches += sol.stats["launches"]
         barrier()
-    total_ms = sum(a.elapsed_time(bb) for a, bb in ev)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * G / (total_ms / 1e3)
+    value, total_ms = job_rate(G, args.steps, sum(a.elapsed_time(bb) for a, bb in ev), world, dev)
 
     # the same graphs through the plain solver, one call each
     num_b, den_b = sol.num.cpu().numpy(), sol.den.cpu().numpy()
@@ -546,6 +546,8 @@ def run_grad(args):
     for _ in range(args.warmup):
         sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
         g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -553,8 +555,11 @@ def run_grad(args):
         sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
         g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
     e1.record(stream)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize(dev)
-    fb_ms = e0.elapsed_time(e1) / args.steps
+    rate, job_ms = job_rate(1, args.steps, e0.elapsed_time(e1), world, dev)
+    fb_ms = job_ms / args.steps
     eb = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     eb[0].record(stream)
     for _ in range(args.steps):
@@ -582,7 +587,7 @@ def run_grad(args):
     fd_ms = e0.elapsed_time(e1)
     if rank == 0:
         print(json.dumps({
-            "metric": "gradient evaluations/s", "value": 1e3 / fb_ms, "unit": "1/s",
+            "metric": "gradient evaluations/s", "value": rate, "unit": "1/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fb_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32",
             "data": "synthetic",
@@ -617,6 +622,8 @@ def run_scc(args):
           for _ in range(args.steps)]
     launches = 0
     with ClockSampler(local) as clocks:
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
@@ -624,8 +631,10 @@ def run_scc(args):
             sol = ocm.solve_scc(rp, col, w, g.mode, workspace=ws, stream=stream)
             ev[k][1].record(stream)
             launches += sol.stats["launches"]
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    value, total_ms = job_rate(n, args.steps, sum(a.elapsed_time(b) for a, b in ev), world, dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     labels, count = ocm.scc(rp, col, workspace=ws, stream=stream)
@@ -655,7 +664,7 @@ def run_scc(args):
     e2e_ms = e0.elapsed_time(e1)
     if rank == 0:
         print(json.dumps({
-            "metric": "vertices/s", "value": world * args.steps * n / (total_ms / 1e3),
+            "metric": "vertices/s", "value": value,
             "unit": "vertices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
