@@ -65,6 +65,8 @@ static __device__ __forceinline__ void block_append(int *list, int *s_cnt, bool 
 
 
 constexpr int kRankDirectMax = 65536;   // all-pairs rank count up to this many cycles
+constexpr int kRankSplitMin = 4096;     // from this many cycles the count is spread over all blocks
+constexpr int kRankPairTile = 1024;     // keys per piece of the spread count
 
 // Inclusive sum of x over the block (all threads call it; 1024 threads).
 static __device__ __forceinline__ int block_inclusive_scan(int x, int *s_warp) {
@@ -493,6 +495,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         ws.cyc_q[i] = (int)q;
         ws.cyc_L[i] = (int)L;
         if (!ratio) ws.cyc_key[i] = mean_key(p, q, N2);
+        ws.cyc_rank[i] = 0;   // summed into by the spread all-pairs count
         qmax = max(qmax, (int)q);
         ws.cid_of_root[root] = i;
     }
@@ -518,6 +521,27 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     }
     if (K > kRankDirectMax && n >= 2 * 256 * (int)gridDim.x) {
         if (!radix_ranks(K, ws, c, nblocks)) return;
+    } else if (K >= kRankSplitMin) {
+        // all pairs, spread: (kEvalThreads cycles x kRankPairTile keys)
+        // pieces over every block, each adding its count of smaller keys to
+        // the cycle's rank (integer sums: the order of the adds is immaterial)
+        const int nI = (K + kEvalThreads - 1) / kEvalThreads;
+        const int nT = (K + kRankPairTile - 1) / kRankPairTile;
+        for (int wi = blockIdx.x; wi < nI * nT; wi += gridDim.x) {
+            const int t0 = (wi % nT) * kRankPairTile;
+            const int tn = min(kRankPairTile, K - t0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
+            __syncthreads();
+            const int i = (wi / nT) * kEvalThreads + threadIdx.x;
+            if (i < K) {
+                const long long key = ws.cyc_key[i];
+                int cnt = 0;
+                for (int q = 0; q < tn; ++q) cnt += (s_key[q] < key);
+                if (cnt) atomicAdd(&ws.cyc_rank[i], cnt);
+            }
+        }
+        if (!grid_barrier(c, nblocks)) return;
     } else {
         // all pairs: rank(i) = number of cycle keys below key(i)
         for (int base = first; base < K; base += stride) {

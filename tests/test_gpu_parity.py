@@ -122,6 +122,24 @@ def test_all_self_loops_many_cycles():
 
 
 @pytest.mark.parametrize("wrange", [(-1000, 1000), (-3, 3)], ids=["distinct", "duplicates"])
+def test_rank_many_cycles_spread_over_blocks(wrange):
+    """4,096 to 65,536 cycles in the first policy: the all-pairs rank count is
+    split into pieces over every block and summed; duplicate keys (weights in
+    -3..3) must still get equal ranks."""
+    rng = np.random.default_rng(43 + wrange[1])
+    n = 40000
+    lo, hi = wrange
+    edges = []
+    for v in range(n):
+        edges.append((v, v, int(rng.integers(lo, hi + 1)) + 2 * hi))
+        edges.append((v, (v + 1) % n, int(rng.integers(lo, hi + 1))))
+    g = synth.from_edges(n, edges)
+    sol = gpu_solve(g, certificate=True)
+    assert_parity(g, sol)
+    assert_certificate(g, sol)
+
+
+@pytest.mark.parametrize("wrange", [(-1000, 1000), (-3, 3)], ids=["distinct", "duplicates"])
 def test_rank_many_cycles_by_radix(wrange):
     """More than 65,536 cycles in the first policy (heavy self-loops): the
     exact ranks come from the radix-sort path; with weights in -3..3 most of
