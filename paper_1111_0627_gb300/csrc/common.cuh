@@ -50,6 +50,15 @@ struct __align__(16) JLS {
     long long S;
 };
 
+// State of the grid-wide barrier of one cooperative kernel (grid_sync.cuh):
+// arrivals counted since the launch, and the summed counts of the barriers
+// in four rotating slots.  Zero when the kernel is launched.
+struct GridBar {
+    unsigned long long arrive;
+    int sum[4];
+    int pad[2];
+};
+
 // Control block in device memory (one per solve).
 struct Ctrl {
     int err;              // OR of kErr* bits
@@ -65,10 +74,7 @@ struct Ctrl {
     long long items_detect;   // worklist items processed, all detect rounds
     long long items_value;    // worklist items processed, all value rounds
     unsigned long long best;  // packed (rank, INT_MAX - root) of the best cycle
-    unsigned int bar_count;   // grid barrier: blocks arrived
-    unsigned int bar_gen;     // grid barrier: generation
-    unsigned long long bar_word;  // counting barrier: arrivals << 32 | summed counts
-    int bar_total;            // counting barrier: the sum published by the last arrival
+    GridBar bar[2];           // grid barriers: [0] evaluation (and the SCC kernels), [1] rebuild
     int pending[3];           // detect: rotating per-round counts of unfinished vertices
     int pendv[3];             // values: the same
     int cls_cnt[8];           // improvement sweep: vertices per degree class

@@ -225,6 +225,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                 BatchState bs) {
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
+    grid_sync_start();
     Ctrl *c = ws.ctrl;
     // vertices whose sw_iter equals this index switched in the last sweep
     const int eval_index = c->iter;

@@ -1,8 +1,8 @@
 // grid_sync.cuh -- the bounded grid-wide barrier of the library's cooperative
-// kernels (policy evaluation, SCC decomposition).  Every block of a
-// cooperative launch is co-resident, so a counter in device memory can act as
-// a barrier; waits are bounded by an SM-clock limit, after which the kernel
-// records kErrTimeout and returns instead of hanging.
+// kernels (policy evaluation, single-lambda rebuild, SCC decomposition and its
+// sort).  Every block of a cooperative launch is co-resident, so a counter in
+// device memory can act as a barrier; waits are bounded by an SM-clock limit,
+// after which the kernel records kErrTimeout and returns instead of hanging.
 #pragma once
 
 #include "common.cuh"
@@ -16,14 +16,30 @@ static __device__ __forceinline__ int load_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }
 
+// Per block, the number of grid barriers passed in this launch (used by
+// thread 0 only).  Every cooperative kernel calls grid_sync_start() first.
+static __device__ __forceinline__ unsigned *bar_round() {
+    __shared__ unsigned r;
+    return &r;
+}
+
+static __device__ __forceinline__ void grid_sync_start() {
+    if (threadIdx.x == 0) *bar_round() = 0;
+}
+
 // Grid-wide barrier of a cooperative launch that also sums one count per
-// thread over the whole grid: the block total rides on the arrival atomic
-// (arrivals in the high 32 bits, counts in the low 32), and the last block
-// to arrive publishes the grand total before releasing the others.  Waits
-// are bounded by an SM-clock limit; on expiry every block records
-// kErrTimeout and *ok becomes false.
+// thread over the whole grid.  Thread 0 of each block adds its block's total
+// to the slot of barrier g (g = barriers this block passed before, the same
+// for every block), then counts its arrival with a release add; the barrier
+// is complete once the arrivals reach nblocks * (g + 1), which every block
+// polls with acquire loads -- no block has to publish a release, saving the
+// second round trip a last-arriver scheme needs.  Block 0 clears the slot of
+// barrier g + 2 before it arrives at g: that slot was last read before
+// barrier g - 1 completed and is next written after barrier g + 1 completes.
+// Waits are bounded by an SM-clock limit; on expiry every block records
+// kErrTimeout and *ok becomes false.  `which` selects the kernel's GridBar.
 static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok,
-                                       long long limit = kBarrierClockLimit) {
+                                       long long limit = kBarrierClockLimit, int which = 0) {
     __shared__ int s_sum;
     __shared__ int s_total;
     __shared__ int s_ok;
@@ -34,31 +50,36 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum, x);
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &c->bar_gen;
-        const unsigned g = *gen;
+        GridBar *b = &c->bar[which];
+        unsigned *rp = bar_round();
+        const unsigned g = *rp;
+        const int slot = (int)(g & 3u);
+        if (s_sum) atomicAdd(&b->sum[slot], s_sum);
+        if (blockIdx.x == 0) b->sum[(g + 2) & 3u] = 0;
         __threadfence();
-        const unsigned long long old =
-            atomicAdd(&c->bar_word, (1ULL << 32) | (unsigned long long)(unsigned)s_sum);
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;"
+                     :: "l"(&b->arrive), "l"(1ULL) : "memory");
+        const unsigned long long target = (unsigned long long)nblocks * (g + 1);
         int okv = 1;
-        if ((unsigned)(old >> 32) == nblocks - 1) {
-            c->bar_total = (int)(unsigned)(old & 0xffffffffULL) + s_sum;
-            c->bar_word = 0;
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*gen == g) {
-                if (clock64() - t0 > limit ||
-                    (load_volatile(&c->err) & kErrTimeout)) {
-                    atomicOr(&c->err, kErrTimeout);
-                    okv = 0;
-                    break;
-                }
+        const long long t0 = clock64();
+        for (unsigned it = 1;; ++it) {
+            unsigned long long a;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+                         : "=l"(a) : "l"(&b->arrive) : "memory");
+            if (a >= target) break;
+            if ((it & 63u) == 0 &&
+                (clock64() - t0 > limit || (load_volatile(&c->err) & kErrTimeout))) {
+                atomicOr(&c->err, kErrTimeout);
+                okv = 0;
+                break;
             }
         }
-        __threadfence();
-        s_total = load_volatile(&c->bar_total);
+        int t;
+        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];"
+                     : "=r"(t) : "l"(&b->sum[slot]) : "memory");
+        s_total = t;
         s_ok = okv;
+        *rp = g + 1;
     }
     __syncthreads();
     *ok = s_ok != 0;
@@ -66,9 +87,10 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
 }
 
 static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks,
-                                                    long long limit = kBarrierClockLimit) {
+                                                    long long limit = kBarrierClockLimit,
+                                                    int which = 0) {
     bool ok;
-    grid_sum_barrier(c, nblocks, 0, &ok, limit);
+    grid_sum_barrier(c, nblocks, 0, &ok, limit, which);
     return ok;
 }
 

@@ -294,6 +294,7 @@ template <int LG>
 __global__ void __launch_bounds__(kSccThreads, 1)
 scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n,
                      SccWs s, int *scc) {
+    grid_sync_start();
     Ctrl *c = s.ctrl;
     const unsigned nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -533,6 +534,9 @@ int scc_decompose(const int *row_ptr, const int *col, int n, int m, int *scc, in
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        // the grid barrier counts arrivals from zero in every launch
+        if (cudaMemsetAsync(&s.ctrl->bar[0], 0, sizeof(GridBar), st) != cudaSuccess)
+            return OCM_ERR_CUDA;
         const cudaError_t le =
             lg == 32 ? cudaLaunchKernelEx(&cfg, scc_iteration_kernel<32>, row_ptr, col, n, s, scc)
             : lg == 16 ? cudaLaunchKernelEx(&cfg, scc_iteration_kernel<16>, row_ptr, col, n, s, scc)
@@ -600,6 +604,7 @@ sort_pairs_kernel(int len, int *k0, int *i0, int *k1, int *i1, int *hist, Ctrl *
     __shared__ int s_off[256];
     __shared__ int s_warp[32];
     __shared__ int s_skip;
+    grid_sync_start();
     const unsigned nb = gridDim.x;
     const int G = (int)gridDim.x;
     const int chunk = (len + G - 1) / G;

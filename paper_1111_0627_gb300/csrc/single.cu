@@ -39,6 +39,7 @@ namespace ocm {
 
 constexpr int kConnectThreads = 1024;   // one block per SM: few arrivals per barrier
 constexpr int kConnectLanes = 8;        // lanes serving one frontier vertex
+constexpr int kBarConnect = 1;          // this kernel's GridBar in the control block
 
 size_t carve_single(void *base, int n, int m, SingleWs *sw) {
     char *b = static_cast<char *>(base);
@@ -106,6 +107,7 @@ static __device__ __forceinline__ void take_edge(int u, int e, int k, int rstar,
 __global__ void __launch_bounds__(kConnectThreads, 1)
 connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                const int *__restrict__ w, int sign, int n, Workspace ws, SingleWs sg) {
+    grid_sync_start();
     Ctrl *c = ws.ctrl;
     const unsigned nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,7 +133,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         c->fcnt[1] = 0;
         c->fcnt[2] = 0;
     }
-    if (!grid_barrier(c, nb)) return;
+    if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
 
     // level 0: the vertices whose policy path ends on the chosen cycle
     int mine = 0;
@@ -141,7 +143,8 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         mine += !in0;
     }
     bool ok;
-    int left = grid_sum_barrier(c, nb, mine, &ok);   // vertices still unconnected
+    // vertices still unconnected
+    int left = grid_sum_barrier(c, nb, mine, &ok, kBarrierClockLimit, kBarConnect);
     if (!ok) return;
     constexpr int kPer = 32 / kConnectLanes;
     const int warp_id = gtid >> 5, nwarps = stride >> 5;
@@ -188,7 +191,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                             if (l[j] == -1) sg.lev[u[j]] = -2;
                     }
                 }
-                if (!grid_barrier(c, nb)) return;
+                if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
             }
             const int want = pull ? -1 : -2;
             for (int u = gtid; u < n; u += stride) {
@@ -210,7 +213,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     atomicOr(&c->err, kErrConnect);   // a marked vertex has the edge
                 }
             }
-            nf = grid_sum_barrier(c, nb, found, &ok);
+            nf = grid_sum_barrier(c, nb, found, &ok, kBarrierClockLimit, kBarConnect);
             if (!ok) return;
             have_list = false;
         } else {
@@ -220,7 +223,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     const int v = base + threadIdx.x;
                     append(F, &c->fcnt[(k - 1) % 3], v < n && sg.lev[v] == k - 1, v, lane);
                 }
-                if (!grid_barrier(c, nb)) return;
+                if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
             }
             // (a) the unconnected in-neighbours of level k-1 are reached ...
             int added = 0;
@@ -247,7 +250,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     added += take;
                 }
             }
-            const int reached = grid_sum_barrier(c, nb, added, &ok);
+            const int reached = grid_sum_barrier(c, nb, added, &ok, kBarrierClockLimit, kBarConnect);
             if (!ok) return;
             // ... (b) and each takes its smallest out-edge into levels < k
             const int ntask2 = (reached + kPer - 1) / kPer;
@@ -277,7 +280,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                         take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
                 }
             }
-            if (!grid_barrier(c, nb)) return;
+            if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
             nf = reached;
             have_list = true;
         }
