@@ -247,10 +247,12 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     }
     for (int g = first + threadIdx.x; g < bs.G; g += stride) bs.gbest[g] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
+    // No grid barrier is needed here: the counters reset above are first
+    // used after the barrier that ends detection round 0 (round 0 resolves
+    // nothing), and gbest only at the end.
+    __syncthreads();
     // (test only: wait for one block more than exists, so the wait expires)
-    if (!grid_barrier(c, nblocks + (stall_test ? 1u : 0u),
-                      stall_test ? kStallTestClockLimit : kBarrierClockLimit))
-        return;
+    if (stall_test && !grid_barrier(c, nblocks + 1u, kStallTestClockLimit)) return;
 
     // ------------------------------------------------------------ detect
     // State: unresolved {J >= 0, M | dirty << 31}; resolved {~root, dirty}.

@@ -128,12 +128,12 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const long long Q = ws.cyc_q[istar];
     const int RK = ws.cyc_rank[istar];
     const bool ratio = ws.transit != nullptr;
+    // the frontier counters are first used after the barrier ending level 0
     if (leader) {
         c->fcnt[0] = 0;
         c->fcnt[1] = 0;
         c->fcnt[2] = 0;
     }
-    if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
 
     // level 0: the vertices whose policy path ends on the chosen cycle
     int mine = 0;
