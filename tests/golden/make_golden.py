@@ -1,7 +1,7 @@
 """Writes oracle_values.txt: the CPU oracle's answers on the full-size workloads.
 
 Calls only oracle/ (and synth/ for the inputs).  The GPU parity tests compare
-the CUDA path with these values where re-running the oracle on the GPU machine
+the CUDA path with these values where re-running the oracle inside a test
 would take minutes (the 2^25-vertex locality graph), and they rebuild the
 differentiation workload from the critical cycle recorded here.
 

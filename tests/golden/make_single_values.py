@@ -4,7 +4,7 @@ full-size workloads.
 
 Calls only oracle/ (and synth/ for the inputs).  The GPU tests compare the
 CUDA path's single-lambda solve with these values where re-running the oracle
-on the GPU machine would take minutes.
+inside a test would take minutes.
 
 Run from the repository root (a few minutes, mostly the 2^25-vertex graph):
     python tests/golden/make_single_values.py [--skip-large]
