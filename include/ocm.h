@@ -119,6 +119,11 @@ typedef struct ocm_options {
 } ocm_options;
 
 /* Layouts of the improvement sweep (results do not depend on the choice).
+ * In both, the initial pass, and in OCM_SWEEP_CLASSES the sweep itself, treat
+ * a vertex with more than 1,024 out-edges as heavy: the heavy vertices' edges
+ * are cut into chunks of 1,024, one thread block per chunk, and the chunks'
+ * best candidates are combined per vertex, so a hub of millions of edges
+ * costs no more than the same number of edges spread over many vertices.
  * OCM_SWEEP_TILES: the CSR edge array is cut into aligned tiles of 32 *
  *   edges_per_lane edges (edges_per_lane 4 or 8; default 8), one warp per
  *   tile, each lane scanning consecutive edges; vertices crossing lanes or

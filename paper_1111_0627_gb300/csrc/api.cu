@@ -47,7 +47,9 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.done = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
     w.sw_iter = static_cast<int *>(take(4 * N));
     w.cls_list = static_cast<int *>(take(4 * N));
-    w.cls_hist = static_cast<int *>(take(4 * (size_t)kClasses * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.cls_hist = static_cast<int *>(take(4 * (size_t)kClassSlots * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.heavy_off = static_cast<int *>(take(4 * (N + 1)));
+    w.heavy_part = static_cast<Cand *>(take(sizeof(Cand) * 2 * ((size_t)m / kHeavyChunk + 2)));
     w.tile_v = static_cast<int *>(take(4 * (T + 1)));
     w.tile_pend = static_cast<int *>(take(4 * T));
     w.tile_fopen = static_cast<int *>(take(4 * T));
@@ -251,7 +253,8 @@ struct StepArgs {
     bool batch;
     bool single;              // the paper's single-lambda form: rebuild after each evaluation
     SingleWs sg;
-    int cls_cnt[kClasses];
+    int cls_cnt[kClassSlots];
+    int heavy_edges;
 };
 
 // Launches one step; returns the number of kernels, or -1.
@@ -267,7 +270,7 @@ static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHand
                        ? launch_sweep_tiles(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.m, a.epl,
                                             a.ws, a.bs, a.threads, st)
                        : launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt,
-                                      a.bs, a.threads, st);
+                                      a.heavy_edges, a.bs, a.threads, st);
     if (ks < 0) return -1;
     int k = le + ks;
     if (a.batch) k += launch_batch_converge(a.bs, a.ws, st);
@@ -283,17 +286,17 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl, single;
+    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges;
     long long N2, max_iters;
-    int cls_cnt[kClasses];
+    int cls_cnt[kClassSlots];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
             ctrl != o.ctrl || vptr != o.vptr || transit != o.transit || n != o.n || m != o.m ||
             sign != o.sign || single != o.single ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
-            epl != o.epl || N2 != o.N2 || max_iters != o.max_iters)
+            epl != o.epl || N2 != o.N2 || max_iters != o.max_iters || heavy_edges != o.heavy_edges)
             return false;
-        for (int c = 0; c < kClasses; ++c)
+        for (int c = 0; c < kClassSlots; ++c)
             if (cls_cnt[c] != o.cls_cnt[c]) return false;
         return true;
     }
@@ -335,7 +338,8 @@ LoopKey make_key(const StepArgs &a) {
     k.single = a.single ? 1 : 0;
     k.N2 = a.N2;
     k.max_iters = a.max_iters;
-    for (int c = 0; c < kClasses; ++c) k.cls_cnt[c] = a.cls_cnt[c];
+    for (int c = 0; c < kClassSlots; ++c) k.cls_cnt[c] = a.cls_cnt[c];
+    k.heavy_edges = a.heavy_edges;
     return k;
 }
 
@@ -528,12 +532,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (rc) return rc;
     if (h.err) return map_err_bits(h.err);
 
-    // 2. initial policy (the paper's first pass from val = 0, lambda = 0),
-    //    which also validates col_idx and w and measures max|w|; degree
-    //    classes of the improvement sweep
-    launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
-                       bs ? &b : nullptr, st);
-    launches += 1;
+    // 2. degree classes of the improvement sweep (and the heavy vertices), then
+    //    the initial policy (the paper's first pass from val = 0, lambda = 0),
+    //    which also validates col_idx and w and measures max|w|
     // (the edge-tiled sweep has no cycle-ratio form)
     const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES && !ratio) ? OCM_SWEEP_TILES
                                                                           : OCM_SWEEP_CLASSES;
@@ -541,10 +542,11 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (epl > 64) epl = 64;
     if (kind == OCM_SWEEP_TILES) epl = epl <= 4 ? 4 : 8;
     const int sweep_threads = (opt && opt->sweep_threads > 0) ? opt->sweep_threads : kSweepThreads;
-    if (kind == OCM_SWEEP_TILES)
-        launches += launch_tile_index(row_ptr, n, m, 32 * epl, ws, st);
-    else
-        launches += launch_classify(row_ptr, n, epl, ws, st);
+    launches += launch_classify(row_ptr, n, kind == OCM_SWEEP_TILES ? kEdgesPerLane : epl, ws, st);
+    if (kind == OCM_SWEEP_TILES) launches += launch_tile_index(row_ptr, n, m, 32 * epl, ws, st);
+    launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
+                       bs ? &b : nullptr, st);
+    launches += 3;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -594,7 +596,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.batch = bs != nullptr;
     sa.single = single;
     sa.sg = sg;
-    for (int c = 0; c < kClasses; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
+    for (int c = 0; c < kClassSlots; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
+    sa.heavy_edges = (kind == OCM_SWEEP_TILES) ? 0 : h.heavy_edges;
     if ((single && prepare_connect() != 0) || prepare_evaluate(ratio) != 0 ||
         (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
                                  : prepare_sweep_classes(sa.threads, ratio)) != 0)

@@ -21,6 +21,15 @@ constexpr int kEvalThreads = 1024;     // block size of the persistent evaluatio
 // group of 2^c lanes; a vertex of out-degree d belongs to the smallest class
 // with d <= kEdgesPerLane * 2^c (the last class takes everything larger).
 constexpr int kClasses = 6;
+// A vertex with more than kHeavyEdges out-edges leaves the lane-group classes
+// for the heavy path: the heavy vertices' edges, taken as one sequence, are
+// cut into chunks of kHeavyChunk edges, one block per chunk, and the chunks'
+// partial results are combined per vertex (a chunk meets at most two heavy
+// vertices because each has more than kHeavyChunk edges).
+constexpr int kHeavyEdges = 1024;
+constexpr int kHeavyChunk = 1024;
+constexpr int kHeavyThreads = 256;
+constexpr int kClassSlots = kClasses + 1;   // the lane-group classes, then the heavy class
 constexpr int kEdgesPerLane = 8;       // default; ocm_options.edges_per_lane overrides
 constexpr int kSweepMaxThreads = 512;  // largest sweep block (ocm_options.sweep_threads)
 constexpr int kSweepThreads = 512;     // default sweep block
@@ -77,8 +86,9 @@ struct Ctrl {
     GridBar bar[2];           // grid barriers: [0] evaluation (and the SCC kernels), [1] rebuild
     int pending[3];           // detect: rotating per-round counts of unfinished vertices
     int pendv[3];             // values: the same
-    int cls_cnt[8];           // improvement sweep: vertices per degree class
+    int cls_cnt[8];           // improvement sweep: vertices per degree class (then heavy)
     int cls_off[8];           // start of each class in the class list
+    int heavy_edges;          // improvement sweep: edges of all heavy vertices
     // result of a solve, copied to the host in one transfer
     long long res_num;
     int res_den;
@@ -135,6 +145,10 @@ struct Workspace {
     int *sw_iter;         // evaluation index after the sweep that last switched v
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan
+    int *heavy_off;       // [n+1] heavy vertex i's edges are entries heavy_off[i] .. heavy_off[i+1]
+                          //       of the heavy edge sequence
+    struct Cand *heavy_part;  // [2 * (m / kHeavyChunk + 2)] per chunk: best of its first and
+                              //       of its second heavy vertex
     // edge-tiled sweep: tile t covers edges [t*ET, (t+1)*ET)
     int *tile_v;          // [T+1] source vertex of each tile's first edge
     int *tile_pend;       // [T] vertex whose edges run past the tile's end and whose
@@ -273,7 +287,8 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                 Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st);
+                 Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
+                 cudaStream_t st);
 int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspace ws,
                       cudaStream_t st);
 // Host-side kernel configuration (shared-memory opt-in, occupancy), done

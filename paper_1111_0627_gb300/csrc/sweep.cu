@@ -22,6 +22,19 @@
 
 namespace ocm {
 
+// Lexicographic best (rank, key, -edge) over the 32 lanes of a warp.
+static __device__ __forceinline__ Cand warp_best(Cand b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand other;
+        other.rank = __shfl_xor_sync(0xffffffffu, b.rank, o);
+        other.e = __shfl_xor_sync(0xffffffffu, b.e, o);
+        other.key = __shfl_xor_sync(0xffffffffu, b.key, o);
+        if (better(other, b)) b = other;
+    }
+    return b;
+}
+
 __global__ void __launch_bounds__(kThreads)
 check_row_ptr_kernel(const int *__restrict__ row_ptr, int n, int m, Ctrl *ctrl) {
     int stride = gridDim.x * blockDim.x;
@@ -76,6 +89,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     int maxabs = 0, maxt = 0;
     for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
         const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
+        if (b - a > kHeavyEdges) continue;   // the heavy path (heavy_init_*_kernel)
         const int my_g = gid ? gid[v] : 0;
         int best_e = a;
         long long best_key = LLONG_MIN;
@@ -157,6 +171,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 // graph does not change), stable within each class, in three passes:
 // per-block counts, one exclusive scan, and a scatter.
 static __device__ __forceinline__ int degree_class(int d, int epl) {
+    if (d > kHeavyEdges) return kClasses;   // the heavy path
     int c = 0;
     while (c < kClasses - 1 && d > (epl << c)) ++c;
     return c;
@@ -164,13 +179,13 @@ static __device__ __forceinline__ int degree_class(int d, int epl) {
 
 __global__ void __launch_bounds__(kClassifyBlock)
 classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, Workspace ws) {
-    __shared__ int s_cnt[kClasses];
-    if (threadIdx.x < kClasses) s_cnt[threadIdx.x] = 0;
+    __shared__ int s_cnt[kClassSlots];
+    if (threadIdx.x < kClassSlots) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
     if (v < n) atomicAdd(&s_cnt[degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]), epl)], 1);
     __syncthreads();
-    if (threadIdx.x < kClasses) ws.cls_hist[threadIdx.x * nb + blockIdx.x] = s_cnt[threadIdx.x];
+    if (threadIdx.x < kClassSlots) ws.cls_hist[threadIdx.x * nb + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
 // One block: exclusive scan of the class-major histogram (class c, block b at
@@ -178,7 +193,7 @@ classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, W
 __global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace ws) {
     __shared__ int s_warp[32];
     __shared__ int s_carry;
-    const int total = kClasses * nb;
+    const int total = kClassSlots * nb;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int base = 0; base < total; base += 1024) {
@@ -212,22 +227,22 @@ __global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace w
         if (threadIdx.x == 1023) s_carry += warp_prefix + incl;
         __syncthreads();
     }
-    if (threadIdx.x < kClasses) {
+    if (threadIdx.x < kClassSlots) {
         const int c = threadIdx.x;
-        const int next = (c + 1 < kClasses) ? ws.ctrl->cls_off[c + 1] : s_carry;
+        const int next = (c + 1 < kClassSlots) ? ws.ctrl->cls_off[c + 1] : s_carry;
         ws.ctrl->cls_cnt[c] = next - ws.ctrl->cls_off[c];
     }
 }
 
 __global__ void __launch_bounds__(kClassifyBlock)
 classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, Workspace ws) {
-    __shared__ int s_wcnt[kClassifyBlock / 32][kClasses];
+    __shared__ int s_wcnt[kClassifyBlock / 32][kClassSlots];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int v = blockIdx.x * kClassifyBlock + threadIdx.x;
     const int c = (v < n) ? degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]), epl) : -1;
     int my_rank = 0;
 #pragma unroll
-    for (int k = 0; k < kClasses; ++k) {
+    for (int k = 0; k < kClassSlots; ++k) {
         const unsigned m = __ballot_sync(0xffffffffu, c == k);
         if (c == k) my_rank = __popc(m & ((1u << lane) - 1u));
         if (lane == 0) s_wcnt[warp][k] = __popc(m);
@@ -240,14 +255,59 @@ classify_scatter_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl,
     }
 }
 
+// One block: the heavy vertices (the last class, in increasing vertex order)
+// get their offsets in the heavy edge sequence, an exclusive scan of their
+// out-degrees; the total goes to the control block.
+__global__ void __launch_bounds__(1024) heavy_prep_kernel(const int *__restrict__ row_ptr,
+                                                          Workspace ws) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int H = ws.ctrl->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < H; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int x = i < H ? __ldg(&row_ptr[hv[i] + 1]) - __ldg(&row_ptr[hv[i]]) : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((threadIdx.x & 31) >= o) incl += y;
+        }
+        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int wv = s_warp[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wv, o);
+                if (threadIdx.x >= o) wv += y;
+            }
+            s_warp[threadIdx.x] = wv;
+        }
+        __syncthreads();
+        const int warp_prefix = (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+        if (i < H) ws.heavy_off[i] = s_carry + warp_prefix + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry += warp_prefix + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ws.heavy_off[H] = s_carry;
+        ws.ctrl->heavy_edges = s_carry;
+    }
+}
+
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st) {
     const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
     prof_begin(kProfInit, st);
     classify_count_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     classify_scan_kernel<<<1, 1024, 0, st>>>(nb, ws);
     classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
+    heavy_prep_kernel<<<1, 1024, 0, st>>>(row_ptr, ws);
     prof_end(kProfInit, st);
-    return 3;
+    return 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,14 +426,162 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     }
 }
 
+// The initial pass for heavy vertices (after the classes are known): each
+// chunk of the heavy edge sequence validates its edges as init_policy_kernel
+// does and keeps the heaviest edge (ties: smallest index) of each heavy vertex
+// it meets; one warp per heavy vertex combines its chunks.  Grid-stride over
+// the chunk and vertex counts in the control block (nothing to do without
+// heavy vertices).
+__global__ void __launch_bounds__(kHeavyThreads)
+heavy_init_chunk_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                        const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
+                        Workspace ws) {
+    __shared__ Cand s_b[2][kHeavyThreads / 32];
+    __shared__ int s_max[2];
+    const int H = ws.ctrl->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
+    const int total = ws.ctrl->heavy_edges;
+    const int nchunks = (total + kHeavyChunk - 1) / kHeavyChunk;
+    const int *__restrict__ tt = ws.transit;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Cand none{INT_MIN, INT_MAX, LLONG_MIN};
+    if (threadIdx.x == 0) {
+        s_max[0] = 0;
+        s_max[1] = 0;
+    }
+    int maxabs = 0, maxt = 0;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int g0 = c * kHeavyChunk, g1 = min(g0 + kHeavyChunk, total);
+        int lo = 0, hi = H;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ws.heavy_off[mid] <= g0) lo = mid; else hi = mid;
+        }
+        const int split = min(ws.heavy_off[lo + 1], g1);
+        const int v0 = hv[lo], v1 = split < g1 ? hv[lo + 1] : v0;
+        const int base0 = __ldg(&row_ptr[v0]) - ws.heavy_off[lo];
+        const int base1 = split < g1 ? __ldg(&row_ptr[v1]) - ws.heavy_off[lo + 1] : 0;
+        Cand b0 = none, b1 = none;
+        for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) {
+            const bool first = g < split;
+            const int e = (first ? base0 : base1) + g;
+            const int t = __ldg(&col[e]);
+            int x = __ldg(&w[e]);
+            if ((unsigned)t >= (unsigned)n || (gid && gid[t] != gid[first ? v0 : v1])) {
+                atomicOr(&ws.ctrl->err, kErrCol);
+                atomicMin(&ws.ctrl->bad_index, e);
+            }
+            if (x == INT_MIN) {
+                atomicOr(&ws.ctrl->err, kErrWeightMin);
+                atomicMin(&ws.ctrl->bad_index, e);
+                x = 0;
+            }
+            maxabs = max(maxabs, x < 0 ? -x : x);
+            if (tt) {
+                const int te = __ldg(&tt[e]);
+                if (te < 1) {
+                    atomicOr(&ws.ctrl->err, kErrTransit);
+                    atomicMin(&ws.ctrl->bad_index, e);
+                }
+                maxt = max(maxt, te);
+            }
+            const Cand cand{0, e, (long long)sign * x};
+            if (first) {
+                if (better(cand, b0)) b0 = cand;
+            } else if (better(cand, b1)) {
+                b1 = cand;
+            }
+        }
+        b0 = warp_best(b0);
+        b1 = warp_best(b1);
+        if (lane == 0) {
+            s_b[0][warp] = b0;
+            s_b[1][warp] = b1;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Cand x0 = lane < kHeavyThreads / 32 ? s_b[0][lane] : none;
+            Cand x1 = lane < kHeavyThreads / 32 ? s_b[1][lane] : none;
+            x0 = warp_best(x0);
+            x1 = warp_best(x1);
+            if (lane == 0) {
+                ws.heavy_part[2 * c] = x0;
+                ws.heavy_part[2 * c + 1] = x1;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
+        maxt = max(maxt, __shfl_xor_sync(0xffffffffu, maxt, o));
+    }
+    if (lane == 0) {
+        if (maxabs) atomicMax(&s_max[0], maxabs);
+        if (maxt) atomicMax(&s_max[1], maxt);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_max[0]) atomicMax(&ws.ctrl->maxabsw, s_max[0]);
+        if (s_max[1]) atomicMax(&ws.ctrl->maxt, s_max[1]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                        const int *__restrict__ w, int sign, int n,
+                        const int *__restrict__ init, Workspace ws) {
+    const int H = ws.ctrl->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
+        const int v = hv[i];
+        const int a = ws.heavy_off[i], b = ws.heavy_off[i + 1];
+        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        for (int c = a / kHeavyChunk + lane; c <= (b - 1) / kHeavyChunk; c += 32) {
+            const Cand x = ws.heavy_part[2 * c + ((long long)c * kHeavyChunk >= a ? 0 : 1)];
+            if (better(x, best)) best = x;
+        }
+        best = warp_best(best);
+        if (lane == 0) {
+            int e = best.e;
+            if (init) {
+                const int ei = __ldg(&init[v]);
+                const int ra = __ldg(&row_ptr[v]), rb = __ldg(&row_ptr[v + 1]);
+                if (ei >= ra && ei < rb) {
+                    e = ei;
+                } else {
+                    atomicOr(&ws.ctrl->err, kErrInitPolicy);
+                    atomicMin(&ws.ctrl->bad_index, v);
+                }
+            }
+            const int t = __ldg(&col[e]);
+            const int x = __ldg(&w[e]);
+            ws.pi[v] = e;
+            ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
+            ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
+            if (ws.transit) ws.tpi[v] = __ldg(&ws.transit[e]);
+            ws.sw_iter[v] = 0;
+        }
+    }
+}
+
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st) {
-    (void)m;
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 2048) blocks = 2048;
     prof_begin(kProfInit, st);
     init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n,
                                                     bs ? bs->gid : nullptr, init, ws);
+    // heavy vertices (their count is on the device: fixed grids, grid-stride)
+    int cb = (m / kHeavyChunk) + 1;
+    if (cb > 1024) cb = 1024;
+    int fb = (n / kHeavyEdges) * 32 / kThreads + 1;
+    if (fb > 1024) fb = 1024;
+    heavy_init_chunk_kernel<<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign, n,
+                                                         bs ? bs->gid : nullptr, ws);
+    heavy_init_final_kernel<<<fb, kThreads, 0, st>>>(row_ptr, col, w, sign, n, init, ws);
     prof_end(kProfInit, st);
 }
 
@@ -403,8 +611,119 @@ int prepare_sweep_classes(int threads, bool ratio) {
     return (ratio ? classes_grid<true>(threads) : classes_grid<false>(threads)) > 0 ? 0 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// Heavy vertices (more than kHeavyEdges out-edges).  Their edges, in the
+// order of the heavy vertices and within each in CSR order, form one sequence
+// of heavy_edges entries; chunk c holds entries [c * kHeavyChunk, ...).  One
+// block per chunk finds the best candidate of each heavy vertex the chunk
+// meets (at most two: the vertex holding its first entry, slot 0, and the
+// next one, slot 1), and one warp per heavy vertex combines its chunks and
+// takes the switch decision exactly as the lane-group sweep does.
+
+template <bool RATIO>
+__global__ void __launch_bounds__(kHeavyThreads)
+improve_heavy_chunk_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                           const int *__restrict__ w, int sign, int nchunks, Workspace ws) {
+    __shared__ Cand s_b[2][kHeavyThreads / 32];
+    const int H = ws.ctrl->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
+    const int total = ws.ctrl->heavy_edges;
+    const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Cand none{INT_MIN, INT_MAX, LLONG_MIN};
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int g0 = c * kHeavyChunk, g1 = min(g0 + kHeavyChunk, total);
+        // the heavy vertex holding entry g0: largest i with heavy_off[i] <= g0
+        int lo = 0, hi = H;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ws.heavy_off[mid] <= g0) lo = mid; else hi = mid;
+        }
+        const int split = min(ws.heavy_off[lo + 1], g1);   // entries below: vertex lo
+        const int base0 = __ldg(&row_ptr[hv[lo]]) - ws.heavy_off[lo];
+        const int base1 = split < g1 ? __ldg(&row_ptr[hv[lo + 1]]) - ws.heavy_off[lo + 1] : 0;
+        Cand b0 = none, b1 = none;
+        for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) {
+            const bool first = g < split;
+            const Cand x = edge_cand<RATIO>(col, w, rec, ws, sign, (first ? base0 : base1) + g);
+            if (first) {
+                if (better(x, b0)) b0 = x;
+            } else if (better(x, b1)) {
+                b1 = x;
+            }
+        }
+        b0 = warp_best(b0);
+        b1 = warp_best(b1);
+        if (lane == 0) {
+            s_b[0][warp] = b0;
+            s_b[1][warp] = b1;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Cand x0 = lane < kHeavyThreads / 32 ? s_b[0][lane] : none;
+            Cand x1 = lane < kHeavyThreads / 32 ? s_b[1][lane] : none;
+            x0 = warp_best(x0);
+            x1 = warp_best(x1);
+            if (lane == 0) {
+                ws.heavy_part[2 * c] = x0;
+                ws.heavy_part[2 * c + 1] = x1;
+            }
+        }
+        __syncthreads();   // s_b is reused by the next chunk
+    }
+}
+
+template <bool RATIO>
+__global__ void __launch_bounds__(kThreads)
+improve_heavy_final_kernel(const int *__restrict__ col, const int *__restrict__ w, int sign,
+                           Workspace ws, BatchState bs) {
+    const int H = ws.ctrl->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
+    const int next_eval = ws.ctrl->iter + 1;
+    const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    int switched = 0;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
+        const int v = hv[i];
+        const int a = ws.heavy_off[i], b = ws.heavy_off[i + 1];
+        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        for (int c = a / kHeavyChunk + lane; c <= (b - 1) / kHeavyChunk; c += 32) {
+            const Cand x = ws.heavy_part[2 * c + ((long long)c * kHeavyChunk >= a ? 0 : 1)];
+            if (better(x, best)) best = x;
+        }
+        best = warp_best(best);
+        if (lane == 0 && !(bs.G && bs.gconv[bs.gid[v]])) {
+            const int t = ws.succ[v];
+            const int4 r = __ldg(&rec[t]);
+            const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
+            long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
+            if (RATIO) cur_key -= __ldg(&ws.recp[t]) * (long long)ws.tpi[v];
+            if (best.rank > r.z || (best.rank == r.z && best.key > cur_key)) {
+                ws.pi[v] = best.e;
+                ws.succ[v] = __ldg(&col[best.e]);
+                ws.wpi[v] = sign * __ldg(&w[best.e]);
+                if (RATIO) ws.tpi[v] = __ldg(&ws.transit[best.e]);
+                ws.sw_iter[v] = next_eval;
+                if (bs.G) {
+                    const int g = bs.gid[v];
+                    if (bs.gsw[g] != next_eval) bs.gsw[g] = next_eval;
+                }
+                ++switched;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) switched += __shfl_xor_sync(0xffffffffu, switched, o);
+    if (lane == 0 && switched) {
+        atomicAdd(&ws.ctrl->switched, switched);
+        ws.ctrl->changed = 1;
+    }
+}
+
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
-                 Workspace ws, const int *cls_cnt, BatchState bs, int threads, cudaStream_t st) {
+                 Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
+                 cudaStream_t st) {
     ClassGrid cg;
     int tasks = 0;
     for (int c = 0; c < kClasses; ++c) {
@@ -413,7 +732,6 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
         tasks += (int)((lanes + 31) / 32);
     }
     cg.task_off[kClasses] = tasks;
-    if (tasks == 0) return 0;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
     const bool ratio = ws.transit != nullptr;
     const int grid_blocks = ratio ? classes_grid<true>(threads) : classes_grid<false>(threads);
@@ -421,13 +739,32 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     const int wpb = threads / 32;
     int blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;
+    if (blocks < 1) blocks = 1;   // block 0 also publishes the evaluation's best cycle
     prof_begin(kProfSweep, st);
     if (ratio)
         improve_kernel<true><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
     else
         improve_kernel<false><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
+    int launches = 1;
+    const int H = cls_cnt[kClasses];
+    if (H > 0 && heavy_edges > 0) {
+        const int nchunks = (heavy_edges + kHeavyChunk - 1) / kHeavyChunk;
+        int cb = nchunks < 4096 ? nchunks : 4096;
+        int fb = (H * 32 + kThreads - 1) / kThreads;
+        if (fb > 4096) fb = 4096;
+        if (ratio) {
+            improve_heavy_chunk_kernel<true><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
+                                                                          nchunks, ws);
+            improve_heavy_final_kernel<true><<<fb, kThreads, 0, st>>>(col, w, sign, ws, bs);
+        } else {
+            improve_heavy_chunk_kernel<false><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
+                                                                           nchunks, ws);
+            improve_heavy_final_kernel<false><<<fb, kThreads, 0, st>>>(col, w, sign, ws, bs);
+        }
+        launches += 2;
+    }
     prof_end(kProfSweep, st);
-    return 1;
+    return launches;
 }
 
 }  // namespace ocm
