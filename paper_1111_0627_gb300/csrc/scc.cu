@@ -197,15 +197,40 @@ csc_count_kernel(const int *__restrict__ col, int m, int *in_ptr) {
         atomicAdd(&in_ptr[col[e] + 1], 1);
 }
 
+// Largest u in [lo, hi] with row_ptr[u] <= e (row_ptr[lo] <= e assumed).
+static __device__ __forceinline__ int source_of(const int *__restrict__ row_ptr, int e, int lo,
+                                                int hi) {
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo + 1) >> 1);
+        if (__ldg(&row_ptr[mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Edge-parallel: each warp takes 32 consecutive edges, finds the sources of
+// its first and last edge over the whole row_ptr, and every lane then finds
+// its own source between those two (a vertex with millions of edges is spread
+// over many warps instead of one thread).
 __global__ void __launch_bounds__(kThreads)
-csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n,
+csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n, int m,
                    const int *__restrict__ in_ptr, int *in_src, int *cursor) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
-        for (int e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+         base += warps * 32) {
+        const int last = min(base + 31, m - 1);
+        int lo = 0, hi = 0;
+        if (lane == 0) lo = source_of(row_ptr, base, 0, n - 1);
+        if (lane == 1) hi = source_of(row_ptr, last, 0, n - 1);
+        lo = __shfl_sync(0xffffffffu, lo, 0);
+        hi = __shfl_sync(0xffffffffu, hi, 1);
+        const int e = base + lane;
+        if (e < m) {
+            const int u = source_of(row_ptr, e, lo, hi);
             const int x = col[e];
             in_src[in_ptr[x] + atomicAdd(&cursor[x], 1)] = u;
         }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -231,7 +256,7 @@ int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, in
     csc_zero_kernel<<<blocks, kThreads, 0, st>>>(n, in_ptr, cursor);
     if (m > 0) csc_count_kernel<<<eb, kThreads, 0, st>>>(col, m, in_ptr);
     inclusive_scan(in_ptr + 1, n, bsum, st);
-    csc_scatter_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, in_ptr, in_src, cursor);
+    if (m > 0) csc_scatter_kernel<<<eb, kThreads, 0, st>>>(row_ptr, col, n, m, in_ptr, in_src, cursor);
     return 6;
 }
 

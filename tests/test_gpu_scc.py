@@ -139,3 +139,21 @@ def test_edge_cases():
     with pytest.raises(ocm.OCMError) as e:
         ocm.scc(bad, torch.zeros(1, dtype=torch.int32, device=d))
     assert e.value.status == -2
+
+
+def test_hubs_with_sinks():
+    """Vertices with thousands of out-edges (the transposed graph is built
+    edge-parallel) next to vertices without out-edges."""
+    rng = np.random.default_rng(1111062796)
+    n = 20000
+    deg = rng.poisson(1.2, size=n).astype(np.int64)
+    deg[rng.random(n) < 0.1] = 0
+    hubs = rng.choice(n, 6, replace=False)
+    deg[hubs] = rng.integers(2000, 60000, size=6)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(deg, out=rp[1:])
+    col = rng.integers(0, n, int(rp[-1])).astype(np.int32)
+    w = rng.integers(-50, 51, int(rp[-1])).astype(np.int32)
+    g = synth.Graph(rp.astype(np.int32), col, w, "max", "hubs_with_sinks")
+    _check_labels(g)
+    _check_solve(g)
