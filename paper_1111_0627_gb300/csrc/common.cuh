@@ -105,6 +105,7 @@ struct Ctrl {
     int maxt;                 // cycle ratio: largest transit time
     int qmax;                 // cycle ratio: largest ratio denominator of the current cycles
     int fcnt[3];              // single-lambda rebuild: rotating frontier counters
+    int hcnt[2][3];           // SCC searches: rotating counters of the heavy frontiers (fw, bw)
     int connect_levels;       // single-lambda rebuild: backward-search levels, all iterations
 };
 

@@ -38,6 +38,9 @@ constexpr int kSortThreads = 512;
 constexpr int kScanBlock = 1024;
 constexpr int kTrimRounds = 8;
 constexpr int kActive = 1, kFw = 2, kBw = 4;
+// A frontier vertex with more edges than this in the search direction goes to
+// a heavy frontier, whose vertices are expanded by the whole grid together.
+constexpr int kSccHeavy = 2048;
 
 // Workspace of the decomposition, carved from one caller buffer.
 struct SccWs {
@@ -50,6 +53,7 @@ struct SccWs {
     int *piv;        // [3n + 1] pivot of each class
     int *minv;       // [n] smallest vertex of the component found from pivot p
     int *q[4];       // [n] BFS frontiers: forward 0/1, backward 2/3
+    int *hq[4];      // [m / kSccHeavy + 2] heavy frontiers, the same order
     Ctrl *ctrl;
 };
 
@@ -75,6 +79,7 @@ static size_t carve_scc(void *base, int n, int m, SccWs *ws) {
     w.piv = static_cast<int *>(take(4 * (3 * N + 1)));
     w.minv = static_cast<int *>(take(4 * N));
     for (int i = 0; i < 4; ++i) w.q[i] = static_cast<int *>(take(4 * N));
+    for (int i = 0; i < 4; ++i) w.hq[i] = static_cast<int *>(take(4 * (M / kSccHeavy + 2)));
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align256(off);
@@ -331,6 +336,8 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
         for (int k = 0; k < 3; ++k) {
             c->cnt[k] = 0;
             c->pending[k] = 0;
+            c->hcnt[0][k] = 0;
+            c->hcnt[1][k] = 0;
         }
     }
     // 1. trimming: no active out- or in-neighbour in the own class
@@ -372,12 +379,17 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const int v = base + threadIdx.x;
         const bool pv = v < n && (s.flags[v] & kActive) && s.piv[s.color[v]] == v;
+        bool hf = false, hb = false;
         if (pv) {
             s.minv[v] = INT_MAX;
             s.flags[v] = kActive | kFw | kBw;
+            hf = row_ptr[v + 1] - row_ptr[v] > kSccHeavy;
+            hb = s.in_ptr[v + 1] - s.in_ptr[v] > kSccHeavy;
         }
-        frontier_append(s.q[0], &c->cnt[0], pv, v, lane);
-        frontier_append(s.q[2], &c->pending[0], pv, v, lane);
+        frontier_append(s.q[0], &c->cnt[0], pv && !hf, v, lane);
+        frontier_append(s.hq[0], &c->hcnt[0][0], pv && hf, v, lane);
+        frontier_append(s.q[2], &c->pending[0], pv && !hb, v, lane);
+        frontier_append(s.hq[2], &c->hcnt[1][0], pv && hb, v, lane);
     }
     if (!grid_barrier(c, nb)) return;
     // 3. forward and backward searches inside the classes, level by level;
@@ -386,13 +398,31 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
         const int cur = lvl % 3, nxt = (lvl + 1) % 3, old = (lvl + 2) % 3;
         const int nf = load_volatile(&c->cnt[cur]);
         const int nbk = load_volatile(&c->pending[cur]);
+        const int nhf = load_volatile(&c->hcnt[0][cur]);
+        const int nhb = load_volatile(&c->hcnt[1][cur]);
         if (leader) {
             c->cnt[old] = 0;
             c->pending[old] = 0;
+            c->hcnt[0][old] = 0;
+            c->hcnt[1][old] = 0;
         }
         const int *qf = s.q[lvl & 1], *qb = s.q[2 + (lvl & 1)];
         int *qf2 = s.q[(lvl + 1) & 1], *qb2 = s.q[2 + ((lvl + 1) & 1)];
+        const int *hqf = s.hq[lvl & 1], *hqb = s.hq[2 + (lvl & 1)];
+        int *hqf2 = s.hq[(lvl + 1) & 1], *hqb2 = s.hq[2 + ((lvl + 1) & 1)];
         int added = 0;
+        // a newly reached vertex joins the next heavy frontier of its search
+        // direction when it has more than kSccHeavy edges in that direction
+        auto push = [&](bool fwd, bool take, int x) {
+            bool heavy = false;
+            if (take)
+                heavy = (fwd ? row_ptr[x + 1] - row_ptr[x] : s.in_ptr[x + 1] - s.in_ptr[x]) >
+                        kSccHeavy;
+            frontier_append(fwd ? qf2 : qb2, fwd ? &c->cnt[nxt] : &c->pending[nxt],
+                            take && !heavy, x, lane);
+            frontier_append(fwd ? hqf2 : hqb2, &c->hcnt[fwd ? 0 : 1][nxt], take && heavy, x,
+                            lane);
+        };
         // groups of LG lanes per frontier vertex (32 / LG vertices per warp
         // task, forward tasks first, then backward ones); a group strides
         // over its vertex's edges
@@ -405,8 +435,6 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
             const int i = (fwd ? task : task - ntf) * kPer + grp;
             const int bit = fwd ? kFw : kBw;
             const int *adj = fwd ? col : s.in_src;
-            int *qout = fwd ? qf2 : qb2;
-            int *cout = fwd ? &c->cnt[nxt] : &c->pending[nxt];
             int e = 0, e1 = 0, cu = 0;
             if (i < (fwd ? nf : nbk)) {
                 const int u = fwd ? qf[i] : qb[i];
@@ -426,7 +454,33 @@ scc_iteration_kernel(const int *__restrict__ row_ptr, const int *__restrict__ co
                     if ((f & kActive) && !(f & bit) && s.color[x] == cu)
                         take = !(atomicOr(&s.flags[x], bit) & bit);
                 }
-                frontier_append(qout, cout, take, x, lane);
+                push(fwd, take, x);
+                added += take;
+            }
+        }
+        // heavy frontier vertices: every warp of the grid takes a strided
+        // share of each one's edges
+        for (int j = 0; j < nhf + nhb; ++j) {
+            const bool fwd = j < nhf;
+            const int u = fwd ? hqf[j] : hqb[j - nhf];
+            const int bit = fwd ? kFw : kBw;
+            const int *adj = fwd ? col : s.in_src;
+            const int cu = s.color[u];
+            int e = (fwd ? row_ptr[u] : s.in_ptr[u]) + gtid;
+            const int e1 = fwd ? row_ptr[u + 1] : s.in_ptr[u + 1];
+            for (;;) {
+                const bool more = e < e1;
+                if (!__any_sync(0xffffffffu, more)) break;
+                bool take = false;
+                int x = 0;
+                if (more) {
+                    x = adj[e];
+                    e += stride;
+                    const int f = s.flags[x];
+                    if ((f & kActive) && !(f & bit) && s.color[x] == cu)
+                        take = !(atomicOr(&s.flags[x], bit) & bit);
+                }
+                push(fwd, take, x);
                 added += take;
             }
         }
@@ -737,6 +791,8 @@ struct CompWs {
     int *col2;      // [m]
     int *w2;        // [m]
     int *emap;      // [m] original edge of each kept edge
+    int *eflag;     // [m] edge stays inside its component, then the inclusive scan of that
+    int *ebsum;     // [m / 1024 + 2] block sums of that scan
     int *cyc2;      // [n] cycles in kept-edge indices
     void *batch_ws; // batched solve
     size_t batch_bytes;
@@ -767,6 +823,8 @@ static size_t carve_comp(void *base, int n, int m, int hist_blocks, CompWs *ws) 
     w.col2 = static_cast<int *>(take(4 * M));
     w.w2 = static_cast<int *>(take(4 * M));
     w.emap = static_cast<int *>(take(4 * M));
+    w.eflag = static_cast<int *>(take(4 * M));
+    w.ebsum = static_cast<int *>(take(4 * (M / kScanBlock + 2)));
     w.cyc2 = static_cast<int *>(take(4 * N));
     w.batch_bytes = ocm_workspace_size_batch(n, n, m > 0 ? m : 1);
     w.batch_ws = take(w.batch_bytes);
@@ -776,17 +834,41 @@ static size_t carve_comp(void *base, int n, int m, int hist_blocks, CompWs *ws) 
 
 constexpr int kMaxSortBlocks = 1024;   // histogram capacity of the component sort
 
+// The edges that stay inside their component (edge-parallel: warps of 32
+// consecutive edges, sources as in csc_scatter_kernel); their inclusive scan
+// then gives every vertex its internal degree and every internal edge its
+// place among its vertex's internal edges, without a per-vertex edge loop.
+__global__ void __launch_bounds__(kThreads)
+comp_flag_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                 const int *__restrict__ scc, int n, int m, CompWs cw) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+         base += warps * 32) {
+        const int last = min(base + 31, m - 1);
+        int lo = 0, hi = 0;
+        if (lane == 0) lo = source_of(row_ptr, base, 0, n - 1);
+        if (lane == 1) hi = source_of(row_ptr, last, 0, n - 1);
+        lo = __shfl_sync(0xffffffffu, lo, 0);
+        hi = __shfl_sync(0xffffffffu, hi, 1);
+        const int e = base + lane;
+        if (e < m) {
+            const int u = source_of(row_ptr, e, lo, hi);
+            cw.eflag[e] = scc[col[e]] == scc[u] ? 1 : 0;
+        }
+    }
+}
+
 // internal degree of every vertex; components with an internal edge hold a cycle
 __global__ void __launch_bounds__(kThreads)
-comp_degree_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-                   const int *__restrict__ scc, int n, CompWs cw) {
+comp_degree_kernel(const int *__restrict__ row_ptr, const int *__restrict__ scc, int n,
+                   CompWs cw) {
     const int stride = gridDim.x * blockDim.x;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int lv = scc[v];
-        int d = 0;
-        for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) d += scc[col[e]] == lv;
+        const int a = row_ptr[v], b = row_ptr[v + 1];
+        const int d = b > a ? cw.eflag[b - 1] - (a > 0 ? cw.eflag[a - 1] : 0) : 0;
         cw.ideg[v] = d;
-        if (d) cw.cyclic[lv] = 1;
+        if (d) cw.cyclic[scc[v]] = 1;
     }
 }
 
@@ -840,20 +922,30 @@ comp_vptr_kernel(int len, CompWs cw) {
 
 __global__ void __launch_bounds__(kThreads)
 comp_edges_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-                  const int *__restrict__ w, const int *__restrict__ scc, int len,
-                  const int *__restrict__ sid, CompWs cw) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < len; k += stride) {
-        const int v = sid[k];
-        const int lv = scc[v];
-        int o = cw.rp2[k];
-        for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-            const int x = col[e];
-            if (scc[x] != lv) continue;
-            cw.col2[o] = cw.newid[x];
-            cw.w2[o] = w[e];
-            cw.emap[o] = e;
-            ++o;
+                  const int *__restrict__ w, int n, int m, CompWs cw) {
+    // edge-parallel like comp_flag_kernel; an internal edge's place is its
+    // vertex's first kept position plus the internal edges before it
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+         base += warps * 32) {
+        const int last = min(base + 31, m - 1);
+        int lo = 0, hi = 0;
+        if (lane == 0) lo = source_of(row_ptr, base, 0, n - 1);
+        if (lane == 1) hi = source_of(row_ptr, last, 0, n - 1);
+        lo = __shfl_sync(0xffffffffu, lo, 0);
+        hi = __shfl_sync(0xffffffffu, hi, 1);
+        const int e = base + lane;
+        if (e < m) {
+            const int incl = cw.eflag[e];
+            if (incl - (e > 0 ? cw.eflag[e - 1] : 0)) {
+                const int u = source_of(row_ptr, e, lo, hi);
+                const int a = row_ptr[u];
+                const int pos = cw.rp2[cw.newid[u]] + incl - 1 - (a > 0 ? cw.eflag[a - 1] : 0);
+                cw.col2[pos] = cw.newid[col[e]];
+                cw.w2[pos] = w[e];
+                cw.emap[pos] = e;
+            }
         }
     }
 }
@@ -939,11 +1031,19 @@ int ocm_solve_scc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t 
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 4096) blocks = 4096;
     comp_zero_kernel<<<blocks, kThreads, 0, st>>>(n, cw);
-    if (m > 0) comp_degree_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col_idx, scc, n, cw);
+    int eb = (m + kThreads - 1) / kThreads;
+    if (eb > 8192) eb = 8192;
+    if (eb < 1) eb = 1;
+    if (m > 0) {
+        comp_flag_kernel<<<eb, kThreads, 0, st>>>(row_ptr, col_idx, scc, n, m, cw);
+        inclusive_scan(cw.eflag, m, cw.ebsum, st);
+        comp_degree_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, scc, n, cw);
+        launches += 5;
+    }
     comp_select_kernel<<<blocks, kThreads, 0, st>>>(scc, n, cw);
     inclusive_scan(cw.sel, n, sw.bsum, st);
     comp_compact_kernel<<<blocks, kThreads, 0, st>>>(scc, n, cw);
-    launches += 7;
+    launches += 6;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     int len = 0;
     rc = read_int(cw.sel + (n - 1), &len, st);
@@ -991,7 +1091,7 @@ int ocm_solve_scc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t 
     // rp2[0] = 0, rp2[k+1] = kept degree of position k -> inclusive scan
     if (cudaMemsetAsync(cw.rp2, 0, sizeof(int), st) != cudaSuccess) return OCM_ERR_CUDA;
     inclusive_scan(cw.rp2 + 1, len, sw.bsum, st);
-    comp_edges_kernel<<<lb, kThreads, 0, st>>>(row_ptr, col_idx, w, scc, len, sid, cw);
+    if (m > 0) comp_edges_kernel<<<eb, kThreads, 0, st>>>(row_ptr, col_idx, w, n, m, cw);
     launches += 9;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     int G = 0, M2 = 0;
