@@ -305,7 +305,7 @@ int ocm_profile_collect(double *ms_out, int64_t *launches_out);
  * The scratch space is a fixed array of OCM_STATIC_WORKSPACE_BYTES inside
  * the library's GPU image: every device that loads the library holds it
  * until the process exits.  Graphs with ocm_workspace_size(n, m) larger than
- * that (about 195,000 vertices at mean out-degree 4) are rejected with
+ * that (about 192,000 vertices at mean out-degree 4) are rejected with
  * OCM_ERR_WORKSPACE before any device work.  The call allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine (benchmark
  * instrumentation is paused while it runs).  Arguments, outputs,
