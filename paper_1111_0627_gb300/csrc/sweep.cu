@@ -15,9 +15,11 @@
 // class c is served by a group of 2^c lanes that stride over its edges with
 // coalesced loads, gather each target's 16-byte record (V, rank, q), and
 // reduce by warp shuffles -- no shared memory and no block barriers, so the
-// warps of an SM keep many independent loads in flight.  The initial policy
-// (no records yet) is a plain thread-per-vertex pass that also validates the
-// input.
+// warps of an SM keep many independent loads in flight.  A vertex with more
+// than kHeavyEdges out-edges takes the heavy path instead (chunks of its
+// edges, one block each, combined per vertex).  The initial policy (no
+// records yet) is a thread-per-vertex pass that also validates the input, with
+// the same heavy path for heavy vertices.
 #include "common.cuh"
 
 namespace ocm {
