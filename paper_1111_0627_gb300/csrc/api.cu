@@ -226,7 +226,10 @@ __global__ void loop_control_kernel(Ctrl *c, long long max_iters, int use_cond,
     // the next step's cooperative launches count their barriers from zero
     for (int i = 0; i < 2; ++i) {
         c->bar[i].arrive = 0;
-        for (int j = 0; j < 4; ++j) c->bar[i].sum[j] = 0;
+        for (int j = 0; j < 4; ++j) {
+            c->bar[i].sum[j] = 0;
+            c->bar[i].sum2[j] = 0;
+        }
     }
     c->switched_total += c->switched;
     int more = 0;

@@ -65,6 +65,7 @@ struct __align__(16) JLS {
 struct GridBar {
     unsigned long long arrive;
     int sum[4];
+    int sum2[4];          // a second count (grid_sum2_barrier)
     int pad[2];
 };
 

@@ -266,7 +266,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         JM *out = ws.jm[(r + 1) & 1];
         int *lin = (r & 1) ? LB : LA;
         int *lout = (r & 1) ? LA : LB;
-        int pend = 0;
+        int pend = 0, kept = 0;
         for (int i0 = 0; i0 < cnt; i0 += kU * blockDim.x) {
             int item[kU];
             JM s[kU], t[kU];
@@ -337,6 +337,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                     }
                 }
                 block_append(lout, &s_cnt, keep || resolved, keep ? v : ~v, lane);
+                kept += keep;
                 const int pos = warp_append(&c->nrep, is_root, lane);
                 if (is_root) ws.cyc_root[pos] = v;
             }
@@ -346,13 +347,26 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         __syncthreads();
         if (threadIdx.x == 0) s_cnt = 0;
         bool ok;
-        const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+        int still;   // vertices still unresolved after this round
+        const int left = grid_sum2_barrier(c, nblocks, pend, kept, &still, &ok);
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds_detect += 1;
             c->items_detect += left;
         }
         if (left == 0) break;
+        if (still == 0) {
+            // all resolved: instead of a round that only copies the states
+            // resolved in this one into the other buffer, each block copies
+            // its own (the list it just built) -- nothing reads another
+            // block's jump state before the kernel ends
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const int v = ~lout[i];
+                ws.jm[r & 1][v] = out[v];
+            }
+            __syncthreads();
+            break;
+        }
         if (r + 1 >= max_detect) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
             return;
@@ -407,6 +421,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         left0 = grid_sum_barrier(c, nblocks, pend, &ok);
         if (!ok) return;
     }
+    int F = 0;   // a value buffer holding every final state (both, once copied forward)
     if (left0 != 0) {
         for (int j = 1;; ++j) {
             const JLS *in = ws.jls[(j + 1) & 1];
@@ -416,7 +431,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
             long long *tout = ws.jt[j & 1];
             int *lin = (j & 1) ? LA : LB;
             int *lout = (j & 1) ? LB : LA;
-            int pend = 0;
+            int pend = 0, kept = 0;
             for (int i0 = 0; i0 < cnt; i0 += kU * blockDim.x) {
                 int item[kU];
                 JLS s[kU], t[kU];
@@ -460,6 +475,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
                         }
                     }
                     block_append(lout, &s_cnt, keep || fin, keep ? v : ~v, lane);
+                    kept += keep;
                 }
             }
             __syncthreads();
@@ -467,13 +483,27 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
             __syncthreads();
             if (threadIdx.x == 0) s_cnt = 0;
             bool ok;
-            const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+            int still;
+            const int left = grid_sum2_barrier(c, nblocks, pend, kept, &still, &ok);
             if (!ok) return;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 c->rounds_value += 1;
                 c->items_value += left;
             }
             if (left == 0) break;
+            if (still == 0) {
+                // all final: the phases below read buffer F, which holds
+                // every final state; each block copies the states its
+                // vertices reached in this round into the other buffer
+                // (read by no one before the kernel ends)
+                F = j & 1;
+                for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                    const int v = ~lout[i];
+                    ws.jls[(j + 1) & 1][v] = out[v];
+                    if (ratio) ws.jt[(j + 1) & 1][v] = tout[v];
+                }
+                break;
+            }
             if (j + 1 > max_value) {
                 if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
                 return;
@@ -488,10 +518,10 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     for (int i = first + threadIdx.x; i < K; i += stride) {
         int root = ws.cyc_root[i];
         int x = ws.succ[root];
-        JLS st = ws.jls[0][x];
+        JLS st = ws.jls[F][x];
         long long W = (long long)ws.wpi[root] + st.S;
         long long L = 1 + (long long)st.len;
-        const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[0][x] : L;
+        const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[F][x] : L;
         long long g = gcd_ll(W, Tc);
         long long p = W / g, q = Tc / g;
         ws.cyc_p[i] = p;
@@ -580,12 +610,12 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     }
     for (int v = first + threadIdx.x; v < n; v += stride) {
         if (bs.G && bs.gconv[bs.gid[v]]) continue;
-        JLS st = ws.jls[0][v];
+        JLS st = ws.jls[F][v];
         int i = ws.cid_of_root[~st.J];
         long long p = ws.cyc_p[i];
         int q = ws.cyc_q[i];
         Rec rec;
-        const long long T = ratio ? ws.jt[0][v] : (long long)st.len;
+        const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
         rec.V = (long long)q * st.S - p * T;
         rec.rank = ws.cyc_rank[i];
         rec.q = q;

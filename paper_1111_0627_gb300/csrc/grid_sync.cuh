@@ -38,16 +38,27 @@ static __device__ __forceinline__ void grid_sync_start() {
 // barrier g - 1 completed and is next written after barrier g + 1 completes.
 // Waits are bounded by an SM-clock limit; on expiry every block records
 // kErrTimeout and *ok becomes false.  `which` selects the kernel's GridBar.
-static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok,
-                                       long long limit = kBarrierClockLimit, int which = 0) {
-    __shared__ int s_sum;
-    __shared__ int s_total;
+template <bool TWO>
+static __device__ __forceinline__ int grid_sum_barrier_impl(Ctrl *c, unsigned nblocks, int x,
+                                                            int y, int *ysum, bool *ok,
+                                                            long long limit, int which) {
+    __shared__ int s_sum, s_sum2;
+    __shared__ int s_total, s_total2;
     __shared__ int s_ok;
-    if (threadIdx.x == 0) s_sum = 0;
+    if (threadIdx.x == 0) {
+        s_sum = 0;
+        if (TWO) s_sum2 = 0;
+    }
     __syncthreads();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_sum, x);
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (TWO) y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (x) atomicAdd(&s_sum, x);
+        if (TWO && y) atomicAdd(&s_sum2, y);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         GridBar *b = &c->bar[which];
@@ -55,7 +66,11 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
         const unsigned g = *rp;
         const int slot = (int)(g & 3u);
         if (s_sum) atomicAdd(&b->sum[slot], s_sum);
-        if (blockIdx.x == 0) b->sum[(g + 2) & 3u] = 0;
+        if (TWO && s_sum2) atomicAdd(&b->sum2[slot], s_sum2);
+        if (blockIdx.x == 0) {
+            b->sum[(g + 2) & 3u] = 0;
+            b->sum2[(g + 2) & 3u] = 0;
+        }
         __threadfence();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;"
                      :: "l"(&b->arrive), "l"(1ULL) : "memory");
@@ -78,12 +93,31 @@ static __device__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *o
         asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];"
                      : "=r"(t) : "l"(&b->sum[slot]) : "memory");
         s_total = t;
+        if (TWO) {
+            asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];"
+                         : "=r"(t) : "l"(&b->sum2[slot]) : "memory");
+            s_total2 = t;
+        }
         s_ok = okv;
         *rp = g + 1;
     }
     __syncthreads();
     *ok = s_ok != 0;
+    if (TWO) *ysum = s_total2;
     return s_total;
+}
+
+static __device__ __forceinline__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok,
+                                                       long long limit = kBarrierClockLimit,
+                                                       int which = 0) {
+    return grid_sum_barrier_impl<false>(c, nblocks, x, 0, nullptr, ok, limit, which);
+}
+
+// The same barrier summing two counts: returns the sum of x, *ysum gets the
+// sum of y.
+static __device__ __forceinline__ int grid_sum2_barrier(Ctrl *c, unsigned nblocks, int x, int y,
+                                                        int *ysum, bool *ok) {
+    return grid_sum_barrier_impl<true>(c, nblocks, x, y, ysum, ok, kBarrierClockLimit, 0);
 }
 
 static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks,
