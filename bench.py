@@ -57,6 +57,8 @@ def _workloads():
                         "locality graph n=2^25, deg 4/16/64, targets i+1+|N(0,4096)|, "
                         "w U[-1000,1000], min"),
         "diff1m": (synth.diff1m_base, "ring + U{0..7} extra edges, n=2^20, w 1024*U[0,1000], max"),
+        "hub4m": (synth.hub4m, "ring + 3 uniform extra edges, n=2^20, one vertex with 4,000,000 more "
+                               "(skewed degrees), w U[-1000,1000], max"),
     }
 
 

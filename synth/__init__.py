@@ -259,6 +259,24 @@ def diff1m_base(n: int = 1 << 20) -> Graph:
                       name="diff1m" if n == 1 << 20 else f"diff(n={n})")
 
 
+def hub4m(n: int = 1 << 20, hub_deg: int = 4_000_000, seed: int = SEED_BASE + 5) -> Graph:
+    """A ring plus 3 uniform extra out-edges per vertex, and one vertex (chosen
+    by the seed) with hub_deg more: the skewed-degree workload (numpy PCG64,
+    the same bytes on every platform)."""
+    rng = np.random.default_rng(seed)
+    deg = np.full(n, 4, np.int64)
+    hub = int(rng.integers(0, n))
+    deg[hub] += hub_deg
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(deg, out=rp[1:])
+    m = int(rp[-1])
+    col = rng.integers(0, n, m).astype(np.int32)
+    col[rp[:-1]] = (np.arange(n) + 1) % n
+    w = rng.integers(-1000, 1001, m).astype(np.int32)
+    return Graph(rp.astype(np.int32), col, w, "max", "hub4m" if (n, hub_deg) == (1 << 20, 4_000_000)
+                 else f"hub(n={n},deg={hub_deg})")
+
+
 def digest(a: np.ndarray) -> int:
     a = np.ascontiguousarray(a, dtype=np.int32)
     return int(_load().synth_digest_i32(_p(a), a.shape[0]))

@@ -141,3 +141,18 @@ def test_errors_on_heavy_edges():
     assert ex.value.status == -1
     # the device stays usable
     _check(g, ocm.solve(rp, c2, w2, g.mode))
+
+
+def test_heavy_graph_loop_equals_host_loop():
+    from paper_1111_0627_gb300.ocm import OCM_FLAG_HOST_LOOP
+    rng = np.random.default_rng(1111062826)
+    g = hub_graph(rng, 20000, 5, 1500, 40000)
+    rp, col, w = _dev(g.row_ptr, g.col_idx, g.w)
+    a = ocm.solve(rp, col, w, g.mode, certificate=True)
+    b = ocm.solve(rp, col, w, g.mode, certificate=True, flags=OCM_FLAG_HOST_LOOP)
+    assert a.stats["graph_loop"] == 1 and b.stats["graph_loop"] == 0
+    for k in ("iterations", "cycles", "detect_rounds", "value_rounds", "switched", "detect_items",
+              "value_items"):
+        assert a.stats[k] == b.stats[k], k
+    assert torch.equal(a.cycle, b.cycle) and torch.equal(a.potential, b.potential)
+    assert torch.equal(a.policy, b.policy)
