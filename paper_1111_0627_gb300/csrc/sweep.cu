@@ -37,6 +37,28 @@ static __device__ __forceinline__ Cand warp_best(Cand b) {
     return b;
 }
 
+// Best candidate of heavy vertex i over its chunks' partial results, by the
+// whole block (kHeavyThreads threads); the result is valid in thread 0.
+static __device__ __forceinline__ Cand heavy_combine(const Workspace &ws, int i, Cand *s_w) {
+    const int a = ws.heavy_off[i], b = ws.heavy_off[i + 1];
+    Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+    for (int c = a / kHeavyChunk + (int)threadIdx.x; c <= (b - 1) / kHeavyChunk;
+         c += blockDim.x) {
+        const Cand x = ws.heavy_part[2 * c + ((long long)c * kHeavyChunk >= a ? 0 : 1)];
+        if (better(x, best)) best = x;
+    }
+    best = warp_best(best);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        Cand x = threadIdx.x < kHeavyThreads / 32 ? s_w[threadIdx.x]
+                                                  : Cand{INT_MIN, INT_MAX, LLONG_MIN};
+        best = warp_best(x);
+    }
+    __syncthreads();   // s_w is reused for the next vertex
+    return best;
+}
+
 __global__ void __launch_bounds__(kThreads)
 check_row_ptr_kernel(const int *__restrict__ row_ptr, int n, int m, Ctrl *ctrl) {
     int stride = gridDim.x * blockDim.x;
@@ -529,24 +551,17 @@ heavy_init_chunk_kernel(const int *__restrict__ row_ptr, const int *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kHeavyThreads)
 heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                         const int *__restrict__ w, int sign, int n,
                         const int *__restrict__ init, Workspace ws) {
+    __shared__ Cand s_w[kHeavyThreads / 32];
     const int H = ws.ctrl->cls_cnt[kClasses];
     const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
+    for (int i = blockIdx.x; i < H; i += gridDim.x) {   // one block per heavy vertex
         const int v = hv[i];
-        const int a = ws.heavy_off[i], b = ws.heavy_off[i + 1];
-        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
-        for (int c = a / kHeavyChunk + lane; c <= (b - 1) / kHeavyChunk; c += 32) {
-            const Cand x = ws.heavy_part[2 * c + ((long long)c * kHeavyChunk >= a ? 0 : 1)];
-            if (better(x, best)) best = x;
-        }
-        best = warp_best(best);
-        if (lane == 0) {
+        const Cand best = heavy_combine(ws, i, s_w);
+        if (threadIdx.x == 0) {
             int e = best.e;
             if (init) {
                 const int ei = __ldg(&init[v]);
@@ -579,11 +594,11 @@ void launch_init_policy(const int *row_ptr, const int *col, const int *w, int si
     // heavy vertices (their count is on the device: fixed grids, grid-stride)
     int cb = (m / kHeavyChunk) + 1;
     if (cb > 1024) cb = 1024;
-    int fb = (n / kHeavyEdges) * 32 / kThreads + 1;
+    int fb = (m / kHeavyEdges) + 1;
     if (fb > 1024) fb = 1024;
     heavy_init_chunk_kernel<<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign, n,
                                                          bs ? bs->gid : nullptr, ws);
-    heavy_init_final_kernel<<<fb, kThreads, 0, st>>>(row_ptr, col, w, sign, n, init, ws);
+    heavy_init_final_kernel<<<fb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign, n, init, ws);
     prof_end(kProfInit, st);
 }
 
@@ -676,26 +691,19 @@ improve_heavy_chunk_kernel(const int *__restrict__ row_ptr, const int *__restric
 }
 
 template <bool RATIO>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kHeavyThreads)
 improve_heavy_final_kernel(const int *__restrict__ col, const int *__restrict__ w, int sign,
                            Workspace ws, BatchState bs) {
+    __shared__ Cand s_w[kHeavyThreads / 32];
     const int H = ws.ctrl->cls_cnt[kClasses];
     const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
     const int next_eval = ws.ctrl->iter + 1;
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
     int switched = 0;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
+    for (int i = blockIdx.x; i < H; i += gridDim.x) {   // one block per heavy vertex
         const int v = hv[i];
-        const int a = ws.heavy_off[i], b = ws.heavy_off[i + 1];
-        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
-        for (int c = a / kHeavyChunk + lane; c <= (b - 1) / kHeavyChunk; c += 32) {
-            const Cand x = ws.heavy_part[2 * c + ((long long)c * kHeavyChunk >= a ? 0 : 1)];
-            if (better(x, best)) best = x;
-        }
-        best = warp_best(best);
-        if (lane == 0 && !(bs.G && bs.gconv[bs.gid[v]])) {
+        const Cand best = heavy_combine(ws, i, s_w);
+        if (threadIdx.x == 0 && !(bs.G && bs.gconv[bs.gid[v]])) {
             const int t = ws.succ[v];
             const int4 r = __ldg(&rec[t]);
             const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
@@ -715,9 +723,7 @@ improve_heavy_final_kernel(const int *__restrict__ col, const int *__restrict__ 
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) switched += __shfl_xor_sync(0xffffffffu, switched, o);
-    if (lane == 0 && switched) {
+    if (threadIdx.x == 0 && switched) {
         atomicAdd(&ws.ctrl->switched, switched);
         ws.ctrl->changed = 1;
     }
@@ -752,16 +758,15 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     if (H > 0 && heavy_edges > 0) {
         const int nchunks = (heavy_edges + kHeavyChunk - 1) / kHeavyChunk;
         int cb = nchunks < 4096 ? nchunks : 4096;
-        int fb = (H * 32 + kThreads - 1) / kThreads;
-        if (fb > 4096) fb = 4096;
+        int fb = H < 4096 ? H : 4096;
         if (ratio) {
             improve_heavy_chunk_kernel<true><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
                                                                           nchunks, ws);
-            improve_heavy_final_kernel<true><<<fb, kThreads, 0, st>>>(col, w, sign, ws, bs);
+            improve_heavy_final_kernel<true><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
         } else {
             improve_heavy_chunk_kernel<false><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
                                                                            nchunks, ws);
-            improve_heavy_final_kernel<false><<<fb, kThreads, 0, st>>>(col, w, sign, ws, bs);
+            improve_heavy_final_kernel<false><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
         }
         launches += 2;
     }
