@@ -22,7 +22,9 @@
 //             over the transposed graph, plain stores, then every marked
 //             vertex picks its edge) -- and a smaller one through compact
 //             lists (atomic claims and appends), so small levels cost no pass
-//             over the graph;
+//             over the graph; a heavy vertex (more than kHeavyEdges
+//             out-edges) is left out of the per-vertex edge scans and its
+//             edges are scanned by the whole grid in chunks instead;
 //   values    a vertex connected at level k gets its path sums from its new
 //             successor, final since level k-1: (len, S) = (len(t) + 1,
 //             S(t) + s*w(e)) and V = q*S - p*len relative to the chosen
@@ -66,6 +68,53 @@ size_t carve_single(void *base, int n, int m, SingleWs *sw) {
 static __device__ __forceinline__ void append(int *q, int *cnt, bool pred, int item, int lane) {
     const int pos = warp_append(cnt, pred, lane);
     if (pred) q[pos] = item;
+}
+
+// The heavy vertices (listed by the classify step, their edges numbered in
+// one sequence by heavy_off) whose level is `want` look for their smallest
+// out-edge into levels < k: one warp per chunk of kHeavyChunk entries of the
+// sequence, four edges per lane in flight, the chunk's first hit lowering
+// pick[i] (atomicMin; a chunk above an edge already found is skipped).  No
+// level below k changes while this runs, and a vertex that joins level k
+// concurrently fails the test either way, so the picks are the smallest
+// qualifying edges whatever the order of the chunks.
+static __device__ __forceinline__ void heavy_scan(int want, int k, const int *__restrict__ row_ptr,
+                                                  const int *__restrict__ col, const Workspace &ws,
+                                                  const SingleWs &sg, int *pick, int H,
+                                                  const int *hv, int total, int warp_id,
+                                                  int nwarps, int lane) {
+    const int nchunks = (total + kHeavyChunk - 1) / kHeavyChunk;
+    for (int ch = warp_id; ch < nchunks; ch += nwarps) {
+        const int g0 = ch * kHeavyChunk, g1 = min(g0 + kHeavyChunk, total);
+        int lo = 0, hi = H;   // the heavy vertex holding entry g0
+        while (hi - lo > 1) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if (ws.heavy_off[mid] <= g0) lo = mid; else hi = mid;
+        }
+        // at most two heavy vertices meet in a chunk: each has more edges
+        for (int i = lo; i < H && ws.heavy_off[i] < g1; ++i) {
+            const int v = hv[i];
+            if (sg.lev[v] != want) continue;   // stable during the scan: warp-uniform
+            const int a = max(g0, ws.heavy_off[i]), b = min(g1, ws.heavy_off[i + 1]);
+            const int base = row_ptr[v] - ws.heavy_off[i];
+            int known = 0;
+            if (lane == 0) known = load_volatile(&pick[i]);
+            known = __shfl_sync(0xffffffffu, known, 0);
+            if (known < base + a) continue;
+            int best = INT_MAX;
+            for (int g = a + lane; g < b && best == INT_MAX; g += 128) {
+                int l[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) l[j] = g + 32 * j < b ? sg.lev[col[base + g + 32 * j]] : -1;
+#pragma unroll
+                for (int j = 3; j >= 0; --j)
+                    if (l[j] >= 0 && l[j] < k) best = base + g + 32 * j;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (lane == 0 && best != INT_MAX) atomicMin(&pick[i], best);
+        }
+    }
 }
 
 
@@ -135,17 +184,48 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         c->fcnt[2] = 0;
     }
 
+    // heavy vertices: their picks live in the CSC scatter cursors, free once
+    // the transposed graph is built
+    const int H = c->cls_cnt[kClasses];
+    const int *hv = ws.cls_list + c->cls_off[kClasses];
+    const int htotal = c->heavy_edges;
+    int *pick = sg.cursor;
+
     // level 0: the vertices whose policy path ends on the chosen cycle
-    int mine = 0;
+    int mine = 0, hmine = 0;
     for (int v = gtid; v < n; v += stride) {
         const bool in0 = (~ws.jls[0][v].J == rstar);
         sg.lev[v] = in0 ? 0 : -1;
         mine += !in0;
     }
+    for (int i = gtid; i < H; i += stride) {
+        pick[i] = INT_MAX;
+        hmine += ~ws.jls[0][hv[i]].J != rstar;
+    }
     bool ok;
-    // vertices still unconnected
-    int left = grid_sum_barrier(c, nb, mine, &ok, kBarrierClockLimit, kBarConnect);
+    // vertices still unconnected, heavy ones among them
+    int hleft = 0;
+    int left = grid_sum_barrier_impl<true>(c, nb, mine, hmine, &hleft, &ok, kBarrierClockLimit,
+                                           kBarConnect);
     if (!ok) return;
+    // the heavy vertices at level `want` take the edges heavy_scan found
+    // (and reset their picks); the sum of takes ends the phase
+    auto heavy_take = [&](int want, int k, bool must) -> int {
+        int took = 0;
+        for (int i = gtid; i < H; i += stride) {
+            const int v = hv[i];
+            const int e = pick[i];
+            pick[i] = INT_MAX;
+            if (sg.lev[v] != want) continue;
+            if (e != INT_MAX) {
+                take_edge(v, e, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                ++took;
+            } else if (must) {
+                atomicOr(&c->err, kErrConnect);   // a marked vertex has the edge
+            }
+        }
+        return grid_sum_barrier(c, nb, took, &ok, kBarrierClockLimit, kBarConnect);
+    };
     constexpr int kPer = 32 / kConnectLanes;
     const int warp_id = gtid >> 5, nwarps = stride >> 5;
     const int grp = lane / kConnectLanes, sub = lane % kConnectLanes;
@@ -196,25 +276,35 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             const int want = pull ? -1 : -2;
             for (int u = gtid; u < n; u += stride) {
                 if (sg.lev[u] != want) continue;
-                const int e1 = row_ptr[u + 1];
-                int pick = -1;
-                for (int e = row_ptr[u]; e < e1 && pick < 0; e += 4) {
+                const int e0 = row_ptr[u], e1 = row_ptr[u + 1];
+                if (e1 - e0 > kHeavyEdges) continue;   // heavy_scan
+                int pk = -1;
+                for (int e = e0; e < e1 && pk < 0; e += 4) {
                     int l[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) l[j] = e + j < e1 ? sg.lev[col[e + j]] : -1;
 #pragma unroll
                     for (int j = 3; j >= 0; --j)
-                        if (l[j] >= 0 && l[j] < k) pick = e + j;   // the smallest index wins
+                        if (l[j] >= 0 && l[j] < k) pk = e + j;   // the smallest index wins
                 }
-                if (pick >= 0) {
-                    take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                if (pk >= 0) {
+                    take_edge(u, pk, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
                     ++found;
                 } else if (!pull) {
                     atomicOr(&c->err, kErrConnect);   // a marked vertex has the edge
                 }
             }
+            if (hleft > 0)
+                heavy_scan(want, k, row_ptr, col, ws, sg, pick, H, hv, htotal, warp_id, nwarps,
+                           lane);
             nf = grid_sum_barrier(c, nb, found, &ok, kBarrierClockLimit, kBarConnect);
             if (!ok) return;
+            if (hleft > 0) {
+                const int took = heavy_take(want, k, !pull);
+                if (!ok) return;
+                nf += took;
+                hleft -= took;
+            }
             have_list = false;
         } else {
             // push through lists: list level k-1 first if a pass made it
@@ -226,7 +316,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
             }
             // (a) the unconnected in-neighbours of level k-1 are reached ...
-            int added = 0;
+            int added = 0, hadded = 0;
             const int ntask = (nf + kPer - 1) / kPer;
             for (int task = warp_id; task < ntask; task += nwarps) {
                 const int i = task * kPer + grp;
@@ -248,9 +338,12 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     }
                     append(Fn, &c->fcnt[k % 3], take, u, lane);
                     added += take;
+                    if (take) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
                 }
             }
-            const int reached = grid_sum_barrier(c, nb, added, &ok, kBarrierClockLimit, kBarConnect);
+            int hreached = 0;
+            const int reached = grid_sum_barrier_impl<true>(c, nb, added, hadded, &hreached, &ok,
+                                                            kBarrierClockLimit, kBarConnect);
             if (!ok) return;
             // ... (b) and each takes its smallest out-edge into levels < k
             const int ntask2 = (reached + kPer - 1) / kPer;
@@ -261,26 +354,38 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     u = Fn[i];
                     e = row_ptr[u] + sub;
                     e1 = row_ptr[u + 1];
+                    if (e1 - (e - sub) > kHeavyEdges) {   // heavy_scan
+                        u = -1;
+                        e1 = e;
+                    }
                 }
-                int pick = INT_MAX;
+                int pk = INT_MAX;
                 for (; e < e1; e += kConnectLanes) {
                     const int l = sg.lev[col[e]];
                     if (l >= 0 && l < k) {
-                        pick = e;
+                        pk = e;
                         break;
                     }
                 }
 #pragma unroll
                 for (int o = kConnectLanes / 2; o > 0; o >>= 1)
-                    pick = min(pick, __shfl_xor_sync(0xffffffffu, pick, o));
+                    pk = min(pk, __shfl_xor_sync(0xffffffffu, pk, o));
                 if (u >= 0 && sub == 0) {
-                    if (pick == INT_MAX)
+                    if (pk == INT_MAX)
                         atomicOr(&c->err, kErrConnect);
                     else
-                        take_edge(u, pick, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
+                        take_edge(u, pk, k, rstar, P, Q, RK, ratio, sign, col, w, ws, sg);
                 }
             }
+            if (hreached > 0)
+                heavy_scan(-2, k, row_ptr, col, ws, sg, pick, H, hv, htotal, warp_id, nwarps,
+                           lane);
             if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+            if (hreached > 0) {
+                heavy_take(-2, k, true);
+                if (!ok) return;
+                hleft -= hreached;
+            }
             nf = reached;
             have_list = true;
         }

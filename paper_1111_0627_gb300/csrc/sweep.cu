@@ -453,7 +453,7 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 // The initial pass for heavy vertices (after the classes are known): each
 // chunk of the heavy edge sequence validates its edges as init_policy_kernel
 // does and keeps the heaviest edge (ties: smallest index) of each heavy vertex
-// it meets; one warp per heavy vertex combines its chunks.  Grid-stride over
+// it meets; one block per heavy vertex combines its chunks.  Grid-stride over
 // the chunk and vertex counts in the control block (nothing to do without
 // heavy vertices).
 __global__ void __launch_bounds__(kHeavyThreads)
@@ -634,7 +634,7 @@ int prepare_sweep_classes(int threads, bool ratio) {
 // of heavy_edges entries; chunk c holds entries [c * kHeavyChunk, ...).  One
 // block per chunk finds the best candidate of each heavy vertex the chunk
 // meets (at most two: the vertex holding its first entry, slot 0, and the
-// next one, slot 1), and one warp per heavy vertex combines its chunks and
+// next one, slot 1), and one block per heavy vertex combines its chunks and
 // takes the switch decision exactly as the lane-group sweep does.
 
 template <bool RATIO>

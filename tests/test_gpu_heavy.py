@@ -3,11 +3,12 @@
 Such a vertex leaves the lane-group classes of the improvement sweep: the
 edges of all heavy vertices form one sequence cut into chunks of 1,024, each
 chunk's block keeps the best candidate of the (at most two) heavy vertices it
-meets, and one warp per heavy vertex combines them; the initial policy and
+meets, and one block per heavy vertex combines them; the initial policy and
 the input checks of heavy vertices run the same way.  Results must equal the
 oracle's exactly (value, critical cycle, iteration count, certificate) in
 every form -- mean and ratio, both senses, warm start, batch, single-lambda
--- and errors on heavy edges must be reported as on any other edge."""
+(whose rebuild scans heavy vertices' edges grid-wide) -- and errors on heavy
+edges must be reported as on any other edge."""
 import numpy as np
 import pytest
 import torch
@@ -102,15 +103,68 @@ def test_heavy_vertices_in_a_batch():
                                                for x in h.cycle], k
 
 
-def test_heavy_vertices_in_the_single_lambda_form():
-    rng = np.random.default_rng(1111062824)
-    g = hub_graph(rng, 6000, 4, 2000, 12000)
+def _check_single(g, sol, t=None):
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode, transit=t)
+    assert (sol.num, sol.den, sol.stats["iterations"]) == (s.num, s.den, s.iterations), g.name
+    assert sol.cycle.cpu().tolist() == s.cycle.tolist(), g.name
+    assert sol.policy.cpu().tolist() == s.policy.tolist(), g.name
+    assert sol.potential.cpu().tolist() == s.V.tolist(), g.name
+
+
+@pytest.mark.parametrize("n,hubs,lo,hi", CASES + [(6000, 4, 2000, 12000)])
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_heavy_vertices_in_the_single_lambda_form(n, hubs, lo, hi, mode):
+    """The rebuild scans a heavy vertex's out-edges grid-wide, in chunks; the
+    edge it takes must still be its smallest-index edge into the connected
+    levels, as in the oracle."""
+    rng = np.random.default_rng(1111062824 + n + hubs + (mode == "min"))
+    g = hub_graph(rng, n, hubs, lo, hi, mode=mode)
+    rp, col, w = _dev(g.row_ptr, g.col_idx, g.w)
+    _check_single(g, ocm.solve(rp, col, w, mode, single_lambda=True, certificate=True))
+
+
+def chain_hub_graph(L, hub_deg, hits):
+    """The chosen cycle (a 5-ring of weight 100) is reached from the rest only
+    through a chain c_1..c_L of one-vertex levels; S (self-loop of weight 10)
+    leaves through c_L, and two heavy vertices start on S and reach the chain
+    only through their edges to c_L at the positions `hits` (different
+    chunks).  In the first rebuild S and the two heavy vertices form level
+    L + 1, a level of three reached through the frontier lists."""
+    c = lambda i: 0 if i == 0 else 4 + i
+    S, h1, h2 = 5 + L, 6 + L, 7 + L
+    rows = [[((i + 1) % 5, 100)] for i in range(5)]
+    rows += [[(S, 50), (c(i - 1), 0)] for i in range(1, L + 1)]
+    rows.append([(S, 10), (c(L), -100)])
+    for shift in (0, 333):
+        row = [(S, 60)] + [(S, 0)] * hub_deg
+        for p in hits:
+            row[1 + (p + shift) % hub_deg] = (c(L), 0)
+        rows.append(row)
+    edges = [(v, t, wt) for v, row in enumerate(rows) for t, wt in row]
+    g = synth.from_edges(len(rows), edges)
+    assert g.n == h2 + 1
+    return g
+
+
+def test_heavy_vertices_join_a_listed_level_in_the_single_lambda_form():
+    g = chain_hub_graph(2000, 3000, [2600, 1500])
     rp, col, w = _dev(g.row_ptr, g.col_idx, g.w)
     sol = ocm.solve(rp, col, w, g.mode, single_lambda=True, certificate=True)
-    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
-    assert (sol.num, sol.den, sol.stats["iterations"]) == (s.num, s.den, s.iterations)
-    assert sol.cycle.cpu().tolist() == s.cycle.tolist()
-    assert sol.potential.cpu().tolist() == s.V.tolist()
+    assert sol.stats["rebuild_levels"] >= 2001
+    _check_single(g, sol)
+    rng = np.random.default_rng(1111062826)
+    t = rng.integers(1, 9, size=g.m).astype(np.int32)
+    _check_single(g, ocm.solve(rp, col, w, g.mode, single_lambda=True, transit=_dev(t)[0],
+                               certificate=True), t=t)
+
+
+def test_heavy_vertices_in_the_single_lambda_ratio_form():
+    rng = np.random.default_rng(1111062827)
+    g = hub_graph(rng, 8000, 6, 1100, 20000)
+    t = rng.integers(1, 50, size=g.m).astype(np.int32)
+    rp, col, w, tt = _dev(g.row_ptr, g.col_idx, g.w, t)
+    _check_single(g, ocm.solve(rp, col, w, g.mode, single_lambda=True, transit=tt,
+                               certificate=True), t=t)
 
 
 def test_errors_on_heavy_edges():
