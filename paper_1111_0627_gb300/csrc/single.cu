@@ -24,7 +24,10 @@
 //             lists (atomic claims and appends), so small levels cost no pass
 //             over the graph; a heavy vertex (more than kHeavyEdges
 //             out-edges) is left out of the per-vertex edge scans and its
-//             edges are scanned by the whole grid in chunks instead;
+//             edges are scanned by the whole grid in chunks instead, and a
+//             pushing vertex with more than kInHeavy in-edges is listed and
+//             its in-edges spread over a block (over the grid above
+//             kInHeavyGrid);
 //   values    a vertex connected at level k gets its path sums from its new
 //             successor, final since level k-1: (len, S) = (len(t) + 1,
 //             S(t) + s*w(e)) and V = q*S - p*len relative to the chosen
@@ -42,6 +45,8 @@ namespace ocm {
 constexpr int kConnectThreads = 1024;   // one block per SM: few arrivals per barrier
 constexpr int kConnectLanes = 8;        // lanes serving one frontier vertex
 constexpr int kBarConnect = 1;          // this kernel's GridBar in the control block
+constexpr int kInHeavy = 4096;          // in-edges above which a push is spread over a block
+constexpr int kInHeavyGrid = 65536;     // ... and above which over the whole grid
 
 size_t carve_single(void *base, int n, int m, SingleWs *sw) {
     char *b = static_cast<char *>(base);
@@ -179,17 +184,21 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const bool ratio = ws.transit != nullptr;
     // the frontier counters are first used after the barrier ending level 0
     if (leader) {
-        c->fcnt[0] = 0;
-        c->fcnt[1] = 0;
-        c->fcnt[2] = 0;
+        for (int j = 0; j < 3; ++j) {
+            c->fcnt[j] = 0;
+            c->hcnt[0][j] = 0;   // listed pushing vertices with many in-edges
+        }
     }
 
-    // heavy vertices: their picks live in the CSC scatter cursors, free once
-    // the transposed graph is built
+    // heavy vertices: their picks, then the list of pushing vertices with
+    // many in-edges, live in the CSC scatter cursors, free once the
+    // transposed graph is built
     const int H = c->cls_cnt[kClasses];
     const int *hv = ws.cls_list + c->cls_off[kClasses];
     const int htotal = c->heavy_edges;
     int *pick = sg.cursor;
+    int *hin = sg.cursor + H;
+    const int hcap = n - H;   // a vertex that finds the list full is walked where it is met
 
     // level 0: the vertices whose policy path ends on the chosen cycle
     int mine = 0, hmine = 0;
@@ -226,6 +235,40 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         }
         return grid_sum_barrier(c, nb, took, &ok, kBarrierClockLimit, kBarConnect);
     };
+    // the listed pushing vertices hin[0, nh): each one's in-edges spread over
+    // one block (blocks take the list round-robin) or, above kInHeavyGrid,
+    // over the whole grid; the loops run on block- or grid-uniform bounds so
+    // that whole warps append.  claim: the list form (CAS claims, appended to
+    // Fn, counted in added / hadded); else the pass form (plain marks).
+    auto spread_push = [&](int nh, bool claim, int *Fn, int *cnt, int &added, int &hadded) {
+        for (int j = 0; j < nh; ++j) {
+            const int f = hin[j];
+            const int e0 = sg.in_ptr[f], e1 = sg.in_ptr[f + 1];
+            const bool grid = e1 - e0 > kInHeavyGrid;
+            if (!grid && j % (int)gridDim.x != (int)blockIdx.x) continue;
+            const int t0 = grid ? gtid : (int)threadIdx.x;
+            const int step = grid ? stride : (int)blockDim.x;
+            for (int base = e0; base < e1; base += step) {
+                const int e = base + t0;
+                bool take = false;
+                int u = 0;
+                if (e < e1) {
+                    u = sg.in_src[e];
+                    if (sg.lev[u] == -1) {
+                        if (claim)
+                            take = atomicCAS(&sg.lev[u], -1, -2) == -1;
+                        else
+                            sg.lev[u] = -2;
+                    }
+                }
+                if (claim) {
+                    append(Fn, cnt, take, u, lane);
+                    added += take;
+                    if (take) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
+                }
+            }
+        }
+    };
     constexpr int kPer = 32 / kConnectLanes;
     const int warp_id = gtid >> 5, nwarps = stride >> 5;
     const int grp = lane / kConnectLanes, sub = lane % kConnectLanes;
@@ -241,7 +284,11 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         int *Fn = sg.fr[k & 1];
         // counters rotate over three slots: the one reset here was last
         // appended to two levels ago and is next appended to at level k+1
-        if (leader) c->fcnt[(k + 1) % 3] = 0;
+        if (leader) {
+            c->fcnt[(k + 1) % 3] = 0;
+            c->hcnt[0][(k + 1) % 3] = 0;
+        }
+        int *hcount = &c->hcnt[0][k % 3];
         // A level of more than n/64 vertices is handled by passes over all
         // vertices (at most 64 such levels: the levels are disjoint), a
         // smaller one through a compact list.
@@ -259,8 +306,15 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             if (!pull) {
                 for (int v = gtid; v < n; v += stride) {
                     if (sg.lev[v] != k - 1) continue;
-                    const int e1 = sg.in_ptr[v + 1];
-                    for (int e = sg.in_ptr[v]; e < e1; e += 4) {
+                    const int e0 = sg.in_ptr[v], e1 = sg.in_ptr[v + 1];
+                    if (e1 - e0 > kInHeavy) {   // spread_push
+                        const int pos = atomicAdd(hcount, 1);
+                        if (pos < hcap) {
+                            hin[pos] = v;
+                            continue;
+                        }
+                    }
+                    for (int e = e0; e < e1; e += 4) {
                         int u[4], l[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) u[j] = e + j < e1 ? sg.in_src[e + j] : -1;
@@ -272,6 +326,12 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     }
                 }
                 if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+                const int nh = min(load_volatile(hcount), hcap);
+                if (nh > 0) {
+                    int unused = 0, unused2 = 0;
+                    spread_push(nh, false, nullptr, nullptr, unused, unused2);
+                    if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+                }
             }
             const int want = pull ? -1 : -2;
             for (int u = gtid; u < n; u += stride) {
@@ -320,11 +380,20 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             const int ntask = (nf + kPer - 1) / kPer;
             for (int task = warp_id; task < ntask; task += nwarps) {
                 const int i = task * kPer + grp;
-                int e = 0, e1 = 0;
+                int e = 0, e1 = 0, f = -1;
                 if (i < nf) {
-                    const int f = F[i];
+                    f = F[i];
                     e = sg.in_ptr[f] + sub;
                     e1 = sg.in_ptr[f + 1];
+                }
+                // a vertex with many in-edges goes to spread_push
+                const bool spread = f >= 0 && e1 - (e - sub) > kInHeavy;
+                int pos = 0;
+                if (spread && sub == 0) pos = atomicAdd(hcount, 1);
+                pos = __shfl_sync(0xffffffffu, pos, grp * kConnectLanes);
+                if (spread && pos < hcap) {
+                    if (sub == 0) hin[pos] = f;
+                    e1 = e;
                 }
                 for (;;) {
                     const bool more = e < e1;
@@ -342,9 +411,18 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 }
             }
             int hreached = 0;
-            const int reached = grid_sum_barrier_impl<true>(c, nb, added, hadded, &hreached, &ok,
-                                                            kBarrierClockLimit, kBarConnect);
+            int reached = grid_sum_barrier_impl<true>(c, nb, added, hadded, &hreached, &ok,
+                                                      kBarrierClockLimit, kBarConnect);
             if (!ok) return;
+            const int nh = min(load_volatile(hcount), hcap);
+            if (nh > 0) {
+                int added2 = 0, hadded2 = 0, hreached2 = 0;
+                spread_push(nh, true, Fn, &c->fcnt[k % 3], added2, hadded2);
+                reached += grid_sum_barrier_impl<true>(c, nb, added2, hadded2, &hreached2, &ok,
+                                                       kBarrierClockLimit, kBarConnect);
+                if (!ok) return;
+                hreached += hreached2;
+            }
             // ... (b) and each takes its smallest out-edge into levels < k
             const int ntask2 = (reached + kPer - 1) / kPer;
             for (int task = warp_id; task < ntask2; task += nwarps) {
