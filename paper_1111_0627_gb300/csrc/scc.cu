@@ -195,11 +195,20 @@ scc_init_kernel(int n, SccWs s, int *scc) {
     }
 }
 
+// In-degrees, warp-uniform over 32 consecutive edges: the lanes that share a
+// target add their count with one atomic (a vertex with a million in-edges
+// would otherwise serialise a million atomics on one address).
 __global__ void __launch_bounds__(kThreads)
 csc_count_kernel(const int *__restrict__ col, int m, int *in_ptr) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-        atomicAdd(&in_ptr[col[e] + 1], 1);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+         base += warps * 32) {
+        const int e = base + lane;
+        const int x = e < m ? col[e] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, x);
+        if (x >= 0 && lane == __ffs(peers) - 1) atomicAdd(&in_ptr[x + 1], __popc(peers));
+    }
 }
 
 // Largest u in [lo, hi] with row_ptr[u] <= e (row_ptr[lo] <= e assumed).
@@ -230,11 +239,14 @@ csc_scatter_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         lo = __shfl_sync(0xffffffffu, lo, 0);
         hi = __shfl_sync(0xffffffffu, hi, 1);
         const int e = base + lane;
-        if (e < m) {
-            const int u = source_of(row_ptr, e, lo, hi);
-            const int x = col[e];
-            in_src[in_ptr[x] + atomicAdd(&cursor[x], 1)] = u;
-        }
+        const int x = e < m ? col[e] : -1;
+        // lanes sharing a target claim their slots with one atomic
+        const unsigned peers = __match_any_sync(0xffffffffu, x);
+        const int first = __ffs(peers) - 1;
+        int pos = 0;
+        if (x >= 0 && lane == first) pos = atomicAdd(&cursor[x], __popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, first) + __popc(peers & ((1u << lane) - 1u));
+        if (x >= 0) in_src[in_ptr[x] + pos] = source_of(row_ptr, e, lo, hi);
     }
 }
 
