@@ -236,3 +236,29 @@ def test_sinks_with_many_in_edges(sinks, wlo, whi):
     w[rp[1:] - 1] = rng.integers(wlo, whi + 1, n)
     g = synth.Graph(rp.astype(np.int32), col, w, "max", f"sinks({sinks},{wlo}..{whi})")
     _check(g, _solve(g, certificate=True))
+
+
+def test_random_hubs_in_both_directions():
+    """Random graphs mixing vertices with many out-edges (chunk scans) and
+    sinks with many in-edges (block- and grid-spread pushes), both senses:
+    the single-lambda iteration must equal the oracle's exactly."""
+    rng = np.random.default_rng(1111062816)
+    for trial in range(16):
+        n = int(rng.integers(3000, 30000))
+        extra = int(rng.integers(1, 4))
+        out_hubs = rng.choice(n, int(rng.integers(0, 4)), replace=False)
+        sinks = rng.choice(n, int(rng.integers(1, 4)), replace=False)
+        to_sink = int(rng.integers(0, 6))     # parallel edges from every vertex to a sink
+        deg = np.full(n, 1 + extra + to_sink, np.int64)
+        deg[out_hubs] += rng.integers(1025, 20000, size=out_hubs.size)
+        rp = np.zeros(n + 1, np.int64)
+        np.cumsum(deg, out=rp[1:])
+        m = int(rp[-1])
+        col = rng.integers(0, n, m).astype(np.int32)
+        col[rp[:-1]] = (np.arange(n) + 1) % n
+        for j in range(to_sink):
+            col[rp[1:] - 1 - j] = rng.choice(sinks, n)
+        w = rng.integers(-1000, 1001, m).astype(np.int32)
+        mode = "max" if trial % 2 == 0 else "min"
+        g = synth.Graph(rp.astype(np.int32), col, w, mode, f"random_hubs#{trial}")
+        _check(g, _solve(g, certificate=trial % 4 == 0))
