@@ -339,9 +339,11 @@ int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream
 // 32 / 2^c consecutive entries of the class list, one lane group per vertex.
 // The lanes of a group stride over the vertex's edges (coalesced), gather the
 // 16-byte record of every target, keep the lexicographic best (rank, key,
-// -edge), and combine by shuffles inside the group.  The group leader compares
-// with the current policy edge, whose key it computes from the record of
-// succ(v), and switches only on strict improvement.  A persistent grid walks
+// -edge), and combine by shuffles inside the group.  The current policy edge
+// is one of the vertex's edges, so the lane that meets it keeps its candidate
+// (no second gather for the record of succ(v)); after the butterfly every lane
+// holds the best, and that lane switches only on strict improvement in
+// (rank, key).  A persistent grid walks
 // the tasks; switches are counted in registers and published with one atomic
 // per block (same-address atomics per warp would serialise the whole sweep).
 struct ClassGrid {
@@ -366,7 +368,7 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 }
 
 template <bool RATIO>
-__global__ void __launch_bounds__(kSweepMaxThreads)
+__global__ void __launch_bounds__(kSweepMaxThreads, 3)   // 40 registers: 48 warps per SM
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, Workspace ws,
                BatchState bs) {
@@ -396,17 +398,22 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         // again (its records do not change), so its vertices are skipped
         if (valid && bs.G && bs.gconv[bs.gid[v]]) valid = false;
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        Cand own{INT_MIN, INT_MAX, LLONG_MIN};   // the current policy edge, in one lane
         if (valid) {
             const int a = __ldg(&row_ptr[v]), e_end = __ldg(&row_ptr[v + 1]);
+            const int pv = ws.pi[v];
             int e = a + sub;
             for (; e + g < e_end; e += 2 * g) {   // two independent gathers in flight
                 Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
                 Cand x1 = edge_cand<RATIO>(col, w, rec, ws, sign, e + g);
+                if (e == pv) own = x0;
+                if (e + g == pv) own = x1;
                 if (better(x0, best)) best = x0;
                 if (better(x1, best)) best = x1;
             }
             if (e < e_end) {
                 Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
+                if (e == pv) own = x0;
                 if (better(x0, best)) best = x0;
             }
         }
@@ -420,13 +427,9 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 if (better(other, best)) best = other;
             }
         }
-        if (valid && sub == 0) {
-            const int t = ws.succ[v];
-            const int4 r = __ldg(&rec[t]);
-            const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
-            long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
-            if (RATIO) cur_key -= __ldg(&ws.recp[t]) * (long long)ws.tpi[v];
-            if (best.rank > r.z || (best.rank == r.z && best.key > cur_key)) {
+        // own.e == INT_MAX except in the lane that met the policy edge
+        if (valid && own.e != INT_MAX) {
+            if (best.rank > own.rank || (best.rank == own.rank && best.key > own.key)) {
                 ws.pi[v] = best.e;
                 ws.succ[v] = __ldg(&col[best.e]);
                 ws.wpi[v] = sign * __ldg(&w[best.e]);
