@@ -264,7 +264,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 if (claim) {
                     append(Fn, cnt, take, u, lane);
                     added += take;
-                    if (take) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
+                    if (take && H > 0) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
                 }
             }
         }
@@ -407,7 +407,8 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     }
                     append(Fn, &c->fcnt[k % 3], take, u, lane);
                     added += take;
-                    if (take) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
+                    // (the degree loads only where heavy vertices exist)
+                    if (take && H > 0) hadded += row_ptr[u + 1] - row_ptr[u] > kHeavyEdges;
                 }
             }
             int hreached = 0;
