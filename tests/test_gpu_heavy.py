@@ -15,6 +15,7 @@ import torch
 
 import oracle
 import synth
+from hub_graphs import chain_hub_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -121,29 +122,6 @@ def test_heavy_vertices_in_the_single_lambda_form(n, hubs, lo, hi, mode):
     g = hub_graph(rng, n, hubs, lo, hi, mode=mode)
     rp, col, w = _dev(g.row_ptr, g.col_idx, g.w)
     _check_single(g, ocm.solve(rp, col, w, mode, single_lambda=True, certificate=True))
-
-
-def chain_hub_graph(L, hub_deg, hits):
-    """The chosen cycle (a 5-ring of weight 100) is reached from the rest only
-    through a chain c_1..c_L of one-vertex levels; S (self-loop of weight 10)
-    leaves through c_L, and two heavy vertices start on S and reach the chain
-    only through their edges to c_L at the positions `hits` (different
-    chunks).  In the first rebuild S and the two heavy vertices form level
-    L + 1, a level of three reached through the frontier lists."""
-    c = lambda i: 0 if i == 0 else 4 + i
-    S, h1, h2 = 5 + L, 6 + L, 7 + L
-    rows = [[((i + 1) % 5, 100)] for i in range(5)]
-    rows += [[(S, 50), (c(i - 1), 0)] for i in range(1, L + 1)]
-    rows.append([(S, 10), (c(L), -100)])
-    for shift in (0, 333):
-        row = [(S, 60)] + [(S, 0)] * hub_deg
-        for p in hits:
-            row[1 + (p + shift) % hub_deg] = (c(L), 0)
-        rows.append(row)
-    edges = [(v, t, wt) for v, row in enumerate(rows) for t, wt in row]
-    g = synth.from_edges(len(rows), edges)
-    assert g.n == h2 + 1
-    return g
 
 
 def test_heavy_vertices_join_a_listed_level_in_the_single_lambda_form():

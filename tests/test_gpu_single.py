@@ -16,6 +16,7 @@ import torch
 import oracle
 import synth
 from golden_io import GOLDEN, single_lambda_traces
+from hub_graphs import in_hub_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -193,32 +194,13 @@ def test_bounded_wait_expires_cleanly_in_the_single_lambda_form():
     _check(g, _solve(g))
 
 
-def _in_hub(ring, chain, leaves):
-    """A target vertex with `leaves` + 1 in-edges that pushes in the rebuild.
-    The chosen cycle is a ring of `ring` vertices (weight 100) entered through
-    a chain c_1..c_chain of one-vertex levels (chain = 0: through ring vertex
-    0 directly).  S (self-loop 10) and every leaf start on S (weight 60 / 50)
-    and reach the chain's last vertex only through their second edge, so
-    that vertex's level pushes over all their in-edges at once: through the
-    frontier lists after a chain, through a pass over all vertices when the
-    ring is a large first level."""
-    c = lambda i: 0 if i == 0 else ring - 1 + i
-    S = ring + chain
-    rows = [[((i + 1) % ring, 100)] for i in range(ring)]
-    rows += [[(S, 50), (c(i - 1), 0)] for i in range(1, chain + 1)]
-    rows.append([(S, 10), (c(chain), -100)])
-    rows += [[(S, 60), (c(chain), 0)] for _ in range(leaves)]
-    edges = [(v, t, wt) for v, row in enumerate(rows) for t, wt in row]
-    return synth.from_edges(len(rows), edges, name=f"in_hub({ring},{chain},{leaves})")
-
-
 @pytest.mark.parametrize("ring,chain,leaves", [(5, 300, 10000), (5, 300, 70000),
                                                (2000, 0, 10000), (2000, 0, 70000)])
 def test_pushing_vertex_with_many_in_edges(ring, chain, leaves):
     """10,000 in-edges: spread over one block; 70,000: over the whole grid;
     after a chain the push runs through the frontier lists, from a large ring
     as a pass over all vertices.  The rebuild must equal the oracle's."""
-    g = _in_hub(ring, chain, leaves)
+    g = in_hub_graph(ring, chain, leaves)
     _check(g, _solve(g, certificate=True))
 
 

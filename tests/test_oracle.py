@@ -14,6 +14,7 @@ import pytest
 import oracle
 import synth
 from golden_io import closed_forms, fig1, ratio_closed_forms, relabel, single_lambda_traces
+import hub_graphs
 
 
 def _frac(num, den):
@@ -555,3 +556,36 @@ def test_single_lambda_warm_start_reaches_the_optimum():
         r = oracle.howard_single(g.row_ptr, g.col_idx, g.w, mode, init_policy=s.policy)
         assert (r.num, r.den, r.iterations) == (s.num, s.den, 0), trial
         assert r.cycle.tolist() == s.cycle.tolist() and r.V.tolist() == s.V.tolist()
+
+
+@pytest.mark.parametrize("args", [(2000, 3000, (2600, 1500)), (3, 1100, (7,)),
+                                  (1, 2048, (1024, 1023, 2047))])
+def test_single_lambda_rebuild_closed_form_heavy_sources(args):
+    """Alg. 1's rebuild re-points every vertex to its smallest-index edge into
+    the levels below it (reading: smallest index).  On the chain graph of
+    hub_graphs the result is known edge by edge: the ring keeps lambda* = 100,
+    each heavy vertex takes its first edge to c_L (wherever it lies among
+    its 1,024-edge chunks), and V(v) = w(pi(v)) + V(succ(v)) - 100."""
+    L, deg, hits = args
+    g = hub_graphs.chain_hub_graph(L, deg, list(hits))
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
+    pi, V = hub_graphs.chain_hub_expected(g, L, deg, list(hits))
+    assert (s.num, s.den, s.iterations) == (100, 1, 0)
+    assert s.cycle.tolist() == [0, 1, 2, 3, 4]
+    assert s.policy.tolist() == pi.tolist()
+    assert s.V.tolist() == V.tolist()
+
+
+@pytest.mark.parametrize("args", [(5, 300, 10000), (2000, 0, 70000), (1, 0, 5), (3, 2, 1)])
+def test_single_lambda_rebuild_closed_form_many_in_edges(args):
+    """The same rule on a vertex whose level pushes over all its in-edges at
+    once (after a chain, or straight from the ring; also a one-vertex ring,
+    i.e. a self-loop, as the chosen cycle)."""
+    ring, chain, leaves = args
+    g = hub_graphs.in_hub_graph(ring, chain, leaves)
+    s = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
+    pi, V = hub_graphs.in_hub_expected(g, ring, chain, leaves)
+    assert (s.num, s.den, s.iterations) == (100, 1, 0)
+    assert s.cycle.tolist() == list(range(ring))
+    assert s.policy.tolist() == pi.tolist()
+    assert s.V.tolist() == V.tolist()
