@@ -277,6 +277,89 @@ def test_gradient_is_one_over_cycle_length():
         assert oracle.howard(g.row_ptr, g.col_idx, w2).value - h.value == Fraction(1, 5)
 
 
+# Gradient pins on closed forms with edges OFF the critical cycle (ring5 has
+# none).  The expected gradient comes from the fixture alone: 1/|C*| on the
+# fixture's hand-derived cycle and exactly 0 on every other edge (ratio:
+# 1/t(C*)).  The weights are scaled by K first (lambda(K w) = K lambda(w), same
+# critical cycle), so that +1 on any single edge cannot change which cycle is
+# optimal: the finite difference of the oracle's exact value must then equal
+# the gradient exactly, edge by edge.
+_K = 1000
+_GRAD_FORMS = ["ring5", "selfloop", "tworings_max", "tworings_min", "k3", "k3_min"]
+
+
+def _exact_fd(g, w, mode, base, transit=None):
+    out = []
+    for e in range(g.m):
+        w2 = w.copy()
+        w2[e] += 1
+        out.append(oracle.howard(g.row_ptr, g.col_idx, w2, mode, transit=transit).value - base)
+    return out
+
+
+def _hand_gradient(m, cycle, denom):
+    g = np.zeros(m, np.float64)
+    g[list(cycle)] = 1.0 / denom
+    return g
+
+
+@pytest.mark.parametrize("name", _GRAD_FORMS)
+def test_gradient_pinned_by_exact_finite_differences(name):
+    cf = {c.name: c for c in closed_forms()}[name]
+    g = cf.graph
+    wk = (g.w.astype(np.int64) * _K).astype(np.int32)
+    base = oracle.howard(g.row_ptr, g.col_idx, wk, g.mode)
+    assert base.value == Fraction(cf.num * _K, cf.den)
+    L = len(cf.cycle)
+    expected = _hand_gradient(g.m, cf.cycle, L)
+    assert np.array_equal(oracle.gradient(g.m, base.cycle), expected)
+    fd = _exact_fd(g, wk, g.mode, base.value)
+    for e in range(g.m):
+        assert fd[e] == (Fraction(1, L) if e in cf.cycle else 0), (name, e)
+        assert float(fd[e]) == expected[e]
+
+
+def test_gradient_pin_rejects_planted_mistakes():
+    """The finite-difference pin above tells a right gradient from plausible
+    wrong ones: 1/|C*| on every edge, 1/m everywhere, 1/(|C*|+1) on C*, and the
+    right value on all but one edge of C*."""
+    cf = {c.name: c for c in closed_forms()}["tworings_max"]
+    g = cf.graph
+    wk = (g.w.astype(np.int64) * _K).astype(np.int32)
+    base = oracle.howard(g.row_ptr, g.col_idx, wk, g.mode)
+    fd = np.array([float(x) for x in _exact_fd(g, wk, g.mode, base.value)])
+    L = len(cf.cycle)
+    assert np.array_equal(oracle.gradient(g.m, base.cycle), fd)
+    dropped = _hand_gradient(g.m, cf.cycle, L)
+    dropped[cf.cycle[0]] = 0.0
+    for bad in (np.full(g.m, 1.0 / L), np.full(g.m, 1.0 / g.m),
+                _hand_gradient(g.m, cf.cycle, L + 1), dropped):
+        assert not np.array_equal(bad, fd)
+
+
+_RATIO_GRAD_FORMS = ["ring3", "mean_vs_ratio_max", "mean_vs_ratio_min", "ring5_t4",
+                     "negative_max", "negative_min"]
+
+
+@pytest.mark.parametrize("name", _RATIO_GRAD_FORMS)
+def test_gradient_ratio_pinned_by_exact_finite_differences(name):
+    rf = {r.name: r for r in ratio_closed_forms()}[name]
+    g = rf.graph
+    wk = (g.w.astype(np.int64) * _K).astype(np.int32)
+    base = oracle.howard(g.row_ptr, g.col_idx, wk, g.mode, transit=rf.transit)
+    assert base.value == Fraction(rf.num * _K, rf.den)
+    tC = int(sum(int(rf.transit[e]) for e in rf.cycle))
+    expected = _hand_gradient(g.m, rf.cycle, tC)
+    assert np.array_equal(oracle.gradient_ratio(g.m, base.cycle, rf.transit), expected)
+    fd = _exact_fd(g, wk, g.mode, base.value, transit=rf.transit)
+    for e in range(g.m):
+        assert fd[e] == (Fraction(1, tC) if e in rf.cycle else 0), (name, e)
+        assert float(fd[e]) == expected[e]
+    # a gradient that ignored the times (1/|C*|) is told apart wherever t != 1
+    if tC != len(rf.cycle):
+        assert not np.array_equal(oracle.gradient(g.m, base.cycle), expected)
+
+
 # ----------------------------------------------------------------- warm start
 # Policy iteration reaches an optimal policy from any start (Sec. 2.4): the
 # value from a random start policy must still be the brute-force optimum and
@@ -589,3 +672,26 @@ def test_single_lambda_rebuild_closed_form_many_in_edges(args):
     assert s.cycle.tolist() == list(range(ring))
     assert s.policy.tolist() == pi.tolist()
     assert s.V.tolist() == V.tolist()
+
+
+def test_stored_batch_answers_match_a_fresh_oracle_run():
+    """tests/golden/batch4096_values.txt (written by make_batch_values.py) holds
+    the oracle's answer for each member of the batched workload; a seeded
+    sample of the small members is re-solved here and must match line by line
+    (value, cycle length, iterations, cycle digest, first edge)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "batch4096_values.txt")
+    rows = [tuple(int(x) for x in l.split()) for l in open(path) if not l.startswith("#")]
+    assert [r[0] for r in rows] == list(range(4096))
+    sizes = synth.loguniform_sizes(4096, 100, 200000, synth.SEED_BASE + 3)
+    assert [r[1] for r in rows] == [int(s) for s in sizes]
+    small = [g for g in range(4096) if sizes[g] <= 3000]
+    pick = np.random.default_rng(1111062704).choice(small, 12, replace=False)
+    for g in sorted(int(x) for x in pick):
+        gr = synth.ring_extra(int(sizes[g]), 0, 7, 1, 10000, 1, seed=synth.SEED_BASE + 3,
+                              tag=1000 + g, mode="max")
+        h = oracle.howard(gr.row_ptr, gr.col_idx, gr.w, gr.mode)
+        cyc = np.asarray(h.cycle, np.int32)
+        assert rows[g] == (g, gr.n, gr.m, h.num, h.den, len(cyc), h.iterations,
+                           synth.digest(cyc), int(cyc[0])), g
