@@ -311,13 +311,20 @@ int ocm_profile_collect(double *ms_out, int64_t *launches_out);
  * instrumentation is paused while it runs).  Arguments, outputs,
  * synchronisation and errors are those of ocm_solve.
  *
- * The first call on each device looks up the array's device address (with
- * that device current) and caches it; make that first call before any stream
- * capture.  All calls on a device share the one array: calls whose GPU work
- * overlaps (several host threads or streams at once) race and corrupt each
- * other, so serialise them.  The array keeps the last call's contents, which
- * the next call does not need: everything the solver reads is initialised by
- * the solver first.
+ * Every call looks up the array's device address in the current context
+ * (the device must be current, as for every entry point) instead of caching
+ * it, so a context that was reset and created again is handled.  With lazy
+ * module loading (CUDA_MODULE_LOADING=LAZY, the CUDA default) the array is
+ * created when the library's GPU code is first loaded on the device, which
+ * may be the first call of this function: a caller whose device memory is
+ * capped should make one call at start-up (any small graph), before its
+ * budget is handed out, so that later calls find the array in place.  Like
+ * ocm_solve it synchronises the stream, so it is not called while that
+ * stream is being captured.  All calls on a device share the one array:
+ * calls whose GPU work overlaps (several host threads or streams at once)
+ * race and corrupt each other, so serialise them.  The array keeps the last
+ * call's contents, which the next call does not need: everything the solver
+ * reads is initialised by the solver first.
  */
 #define OCM_STATIC_WORKSPACE_BYTES (32u << 20)
 int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w,
@@ -383,7 +390,8 @@ const char *ocm_status_string(int status);
 /* ABI version: 100 * major + minor (101: ocm_options.init_policy; 102:
  * ocm_options.transit and ocm_backward_ratio; 103: ocm_scc and
  * ocm_solve_scc; 104: OCM_FLAG_SINGLE_LAMBDA, ocm_workspace_size_single,
- * ocm_stats.rebuild_levels). */
+ * ocm_stats.rebuild_levels; 105: ocm_solve_static,
+ * OCM_STATIC_WORKSPACE_BYTES). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -167,15 +167,22 @@ cudaEvent_t prof_event() {
 }
 }  // namespace
 
+thread_local bool t_prof_paused = false;
+
+bool prof_active() { return g_prof_on && !t_prof_paused; }
+
+ProfilePause::ProfilePause() : prev(t_prof_paused) { t_prof_paused = true; }
+ProfilePause::~ProfilePause() { t_prof_paused = prev; }
+
 void prof_begin(int cls, cudaStream_t st) {
     (void)cls;
-    if (!g_prof_on) return;
+    if (!prof_active()) return;
     g_prof_open = prof_event();
     if (g_prof_open) cudaEventRecord(g_prof_open, st);
 }
 
 void prof_end(int cls, cudaStream_t st) {
-    if (!g_prof_on || !g_prof_open) return;
+    if (!prof_active() || !g_prof_open) return;
     cudaEvent_t b = prof_event();
     if (!b) return;
     cudaEventRecord(b, st);
@@ -462,7 +469,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 104; }
+int ocm_version(void) { return 105; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -605,7 +612,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
                                  : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
-    const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || g_prof_on;
+    const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || prof_active();
     const int slot = host_loop ? -1 : acquire_loop(sa);
     if (slot >= 0) {
         const cudaError_t e = cudaGraphLaunch(g_loops[slot].exec, st);

@@ -283,6 +283,14 @@ __device__ __forceinline__ long long mean_key(long long p, long long q, long lon
 enum ProfClass : int { kProfInit = 0, kProfSweep = 1, kProfEvaluate = 2, kProfExtract = 3, kProfCount = 4 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
+// Pauses the instrumentation for the calling host thread while in scope
+// (the solve without allocation must not create CUDA events).
+struct ProfilePause {
+    ProfilePause();
+    ~ProfilePause();
+    bool prev;
+};
+bool prof_active();
 
 // kernel launchers (defined in the .cu files)
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);

@@ -13,7 +13,6 @@
 // The entry point only adds the workspace; the solve itself is ocm_solve,
 // unchanged.
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -22,26 +21,21 @@ static __device__ __align__(256) unsigned char g_static_workspace[OCM_STATIC_WOR
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-void *g_static_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_static_workspace on the current device.  In host code
+// Device address of g_static_workspace in the current context.  In host code
 // the array's name only stands for the host-side shadow symbol, so the real
-// address must come from the runtime, once per device, with that device
-// current.
+// address must come from the runtime, with the device current.  It is looked
+// up on every call rather than cached: a context that was torn down and
+// created again (cudaDeviceReset, a reset of the primary context) reloads the
+// module, and the array may then sit elsewhere.  Once the module is loaded the
+// lookup allocates nothing.
 int static_workspace_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return OCM_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return OCM_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (g_static_addr[dev] == nullptr) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
-        if (e != cudaSuccess || p == nullptr) return OCM_ERR_CUDA;
-        g_static_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return OCM_ERR_CUDA;
     }
-    *out = g_static_addr[dev];
+    *out = p;
     return OCM_OK;
 }
 
@@ -68,9 +62,7 @@ extern "C" int ocm_solve_static(const int32_t *row_ptr, const int32_t *col_idx, 
     ocm_options o;
     if (opt) o = *opt; else memset(&o, 0, sizeof o);
     o.flags |= OCM_FLAG_HOST_LOOP;
-    const int prof = ocm_profile_enable(0);
-    rc = ocm_solve(row_ptr, col_idx, w, n, m, mode, num, den, cycle_out, cycle_len, ws,
-                   (size_t)OCM_STATIC_WORKSPACE_BYTES, stream, &o, stats);
-    ocm_profile_enable(prof);
-    return rc;
+    ocm::ProfilePause pause;   // this thread only; other threads keep their events
+    return ocm_solve(row_ptr, col_idx, w, n, m, mode, num, den, cycle_out, cycle_len, ws,
+                     (size_t)OCM_STATIC_WORKSPACE_BYTES, stream, &o, stats);
 }

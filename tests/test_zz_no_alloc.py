@@ -92,3 +92,29 @@ def test_static_entry_in_the_single_lambda_form():
     assert (int(num.value), int(den.value)) == (ref.num, ref.den)
     assert out[:int(clen.value)].cpu().tolist() == ref.cycle.cpu().tolist()
     assert st.iterations == ref.stats["iterations"] and st.rebuild_levels > 0
+
+
+def test_static_entry_allocates_nothing_after_the_first_call():
+    """The promise itself: once the array exists (the first call may load the
+    library's GPU code and with it the array), a call takes no device memory.
+    Free device memory is read right before and right after the C call, with
+    every buffer the call uses already in place."""
+    lib = ocm.load()
+    g = synth.locality32m(1 << 16)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col_idx).cuda()
+    w = torch.from_numpy(g.w).cuda()
+    mode = 0 if g.mode == "max" else 1
+    assert _static_solve(lib, rp, col, w, g.n, g.m, mode)[0] == 0      # warm-up
+    num, den, clen = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    out = torch.full((g.n,), -1, dtype=torch.int32, device="cuda")
+    stream = int(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    rc = lib.ocm_solve_static(rp.data_ptr(), col.data_ptr(), w.data_ptr(), g.n, g.m, mode,
+                              ctypes.byref(num), ctypes.byref(den), out.data_ptr(),
+                              ctypes.byref(clen), stream, None, None)
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert rc == 0
+    assert free_after == free_before
