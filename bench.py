@@ -3,10 +3,17 @@
 
 One step = one complete solve (initial policy, every Howard iteration of
 evaluation + improvement sweep, critical-cycle extraction) of the workload,
-with its CSR graph already resident in HBM.  The metric is edge-iterations
-per second: m * (number of improvement sweeps) / solve time, summed over all
-GPUs for multi-GPU runs (each GPU solves its own replica: one graph does not
-shard, so N > 1 is replicas only).
+with its CSR graph already resident in HBM.  The default workload is the
+largest single graph, locality32m (n = 2^25, m = 2.68e8, minimum cycle
+mean).  The metric is edge-iterations per second: m * (number of improvement
+sweeps) / solve time, summed over all GPUs for multi-GPU runs (each GPU solves
+its own replica: one graph does not shard, so N > 1 is replicas only).
+
+The same JSON line carries two sub-records for the other forms of the solver:
+``batch4096`` (the batched form: graphs/s of one batched call against a loop
+of the plain solver, every member compared with the oracle's stored answer;
+sharded over the ranks by edge count when N > 1) and ``diff1m_grad`` (forward
++ backward against the finite-difference loop of plain solves).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference     # the CPU oracle on the same workload
@@ -174,38 +181,45 @@ def run_reference(args, g, desc):
 # our arm
 # --------------------------------------------------------------------------
 
-def algorithmic_bytes(cls: str, n: int, m: int, st_total: dict, launches: int) -> float:
+def algorithmic_bytes(cls: str, n: int, m: int, launches: int) -> float:
     """Bytes a kernel class must move at least, summed over its launches.
 
-    sweep:    row_ptr 4(n+1) + col_idx/w 8m + target records 16n (each once) +
-              own policy 4n per sweep, + 12 B per switched vertex (pi, succ, w_pi)
-    evaluate: per vertex-round of cycle detection 40 B (own state 8, target
-              state 8, previous window minimum 4+4, new state 8, done bitmap and
-              succ 8), per vertex-round of value propagation 48 B (own 16,
-              target 16, new 16), per evaluation 68n (value initialisation:
-              rep, succ, rep of succ, w_pi, state 16 + 16; materialisation:
-              state 16, cycle id 4, record 16)
+    sweep:    row_ptr 4(n+1) + col_idx and w 8m + the record {V, rank} of
+              every target vertex once 12n + the policy read and written 8n,
+              i.e. 8m + 24n + 4 per sweep
+    evaluate: floor of an O(n) evaluation of one policy, 40 B per vertex:
+              policy edge, its target and weight read (12), root, value,
+              rank and cycle flag written (28)
     """
     if cls == "sweep":
-        return launches * (4.0 * (n + 1) + 8.0 * m + 20.0 * n) + 12.0 * st_total["switched"]
+        return launches * (4.0 * (n + 1) + 8.0 * m + 12.0 * n + 8.0 * n)
     if cls == "evaluate":
-        return (40.0 * st_total["detect_items"] + 48.0 * st_total["value_items"]
-                + 68.0 * n * launches)
+        return launches * 40.0 * n
     return 0.0
+
+
+def round_bytes(n: int, st_total: dict, launches: int) -> float:
+    """Bytes the pointer-jumping evaluation moves by its own count: 40 B per
+    vertex-round of cycle detection (own state 8, target state 8, previous
+    window minimum 4 + 4, new state 8, done bitmap and succ 8), 48 B per
+    vertex-round of value propagation (own 16, target 16, new 16), and 68 B
+    per vertex per evaluation (value set-up and materialisation)."""
+    return (40.0 * st_total["detect_items"] + 48.0 * st_total["value_items"]
+            + 68.0 * n * launches)
 
 
 CLASSES = ["init", "sweep", "evaluate", "extract"]
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged over
-# every launch of the kernel in one host-driven solve captured by ncu, with the
-# sha256 prefix of the kernel's sources at the time (see profiles/).  Reported only
-# while the sources are unchanged.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
+# ncu capture of the kernel, with the sha256 prefix of its sources at the time;
+# reported only while the sources are unchanged.  The locality32m figures are
+# taken on the same recipe at n = 2^23 (a capture of the full 2^25 graph holds
+# too much device memory for ncu's save-and-restore passes) and scaled by 4,
+# the ratio of the vertex and edge counts; the traffic of both kernels grows in
+# proportion to n (evaluation) and n + m (sweep) once the graph exceeds L2.
 KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
                   "sweep": ("sweep.cu", "common.cuh")}
-TRAFFIC = {
-    ("product4", "evaluate"): (54.777e6 + 159.118e6, "5f19543ca3438799"),
-    ("product4", "sweep"): (268.411e6 + 13.967e6, "3ecf6bcb5b196af9"),
-}
+TRAFFIC = {}
 
 
 def job_rate(units_per_step: float, steps: int, local_ms: float, world: int, device):
@@ -239,6 +253,43 @@ def measured_traffic(workload: str, kernel: str):
     if entry is None or _source_hash(kernel) != entry[1]:
         return None
     return entry[0]
+
+
+def _stored_answer(workload: str):
+    """(num, den, cycle length, cycle digest) of the oracle's stored answer for
+    a single-graph workload (tests/golden/oracle_values.txt, written by
+    tests/golden/make_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_values.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                tok = line.split()
+                if tok and tok[0] == workload:
+                    kv = dict(t.split("=", 1) for t in tok[1:] if "=" in t)
+                    return (int(kv["num"]), int(kv["den"]), int(kv["len"]),
+                            int(kv["cycle_digest"]))
+    except OSError:
+        pass
+    return None
+
+
+def cpu_sample(g, workload: str, single: bool, iters: int) -> dict:
+    """The oracle's first `iters` Howard iterations (evaluation + improvement
+    sweep each) on the full graph, single-threaded: edge-iterations/s."""
+    import oracle
+    t0 = time.perf_counter()
+    fn = oracle.howard_single if single else oracle.howard
+    sweeps = iters
+    try:
+        h = fn(g.row_ptr, g.col_idx, g.w, g.mode, max_iter=iters)
+        sweeps = h.iterations + 1          # converged inside the sample
+    except oracle.OracleError as e:
+        if e.code != -5:          # not converged within the sample: expected
+            raise
+    dt = time.perf_counter() - t0
+    return {"value": g.m * sweeps / dt, "unit": "edge-iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {iters} Howard iterations of the oracle on the full {workload} graph "
+                      f"({dt:.1f} s, single-threaded, initial pass included)"}
 
 
 def run_ours(args, g, desc):
@@ -327,21 +378,28 @@ def run_ours(args, g, desc):
     classes = {c: {"ms_total": ms_arr[i], "launches": int(n_arr[i])} for i, c in enumerate(CLASSES)}
     peak, peak_kind = _peaks()
     for c, d in classes.items():
-        b = algorithmic_bytes(c, g.n, g.m, st_total, d["launches"])
+        b = algorithmic_bytes(c, g.n, g.m, d["launches"])
         d["algorithmic_bytes"] = b
         d["gbs"] = (b / (d["ms_total"] / 1e3) / 1e9) if d["ms_total"] > 0 and b > 0 else None
     dom = max(classes, key=lambda c: classes[c]["ms_total"])
-    sweep = classes["sweep"]
-    d = classes[dom]
-    achieved = d["gbs"]
-    roofline = {"bound": "hbm", "kernel": dom,
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
+
+    def kernel_roofline(c):
+        d = classes[c]
+        achieved = d["gbs"]
+        return {"bound": "hbm", "kernel": c, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 # (the counters were taken on the default form's launches)
-                "traffic": None if single else measured_traffic(args.workload, dom),
+                "traffic": None if single else measured_traffic(args.workload, c),
                 "peak_kind": peak_kind,
                 "avg_launch_us": d["ms_total"] * 1e3 / max(d["launches"], 1),
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(d["launches"], 1)}
+
+    roofline = kernel_roofline(dom)
+    n_eval = max(classes["evaluate"]["launches"], 1)
+    eval_rounds = round_bytes(g.n, st_total, classes["evaluate"]["launches"])
+    roofline["eval_round_bytes_per_launch"] = eval_rounds / n_eval
+    roofline["eval_bytes_over_floor"] = eval_rounds / (40.0 * g.n * n_eval)
+    roofline_sweep = kernel_roofline("sweep")
     share = {c: round(v["ms_total"] / max(sum(x["ms_total"] for x in classes.values()), 1e-12), 4)
              for c, v in classes.items()}
 
@@ -371,18 +429,29 @@ def run_ours(args, g, desc):
     barrier()
     e2e_value, _ = job_rate(units, e2e_steps, sum(a.elapsed_time(b) for a, b in e_ev), world, dev)
 
-    # ---- CPU baseline: the oracle as it stands, rank 0 at N = 1
+    # ---- the answer against the oracle's stored answer for this graph
+    stored = _stored_answer(args.workload if args.locality_log2 == 25 or
+                            args.workload != "locality32m" else "")
+    matches = None
+    if stored is not None and not single:
+        c = sol.cycle.cpu().numpy().astype(np.int32)
+        matches = (sol.num, sol.den, int(c.shape[0]), synth.digest(c)) == stored
+
+    # ---- CPU baseline: the oracle as it stands, rank 0 at N = 1, on a bounded
+    #      sample of the same workload: its first Howard iterations on the
+    #      full graph (about 10-30 s of one host core)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        h = (oracle.howard_single if single else oracle.howard)(g.row_ptr, g.col_idx, g.w, g.mode)
-        dt = time.perf_counter() - t0
-        cpu = {"value": g.m * (h.iterations + 1) / dt, "unit": "edge-iters/s", "cores": 1,
-               "kind": "oracle",
-               "sample": f"one complete oracle solve of the same {args.workload} graph "
-                         f"({h.iterations + 1} sweeps, {dt:.1f} s, single-threaded)"}
-        assert (h.num, h.den) == (sol.num, sol.den), "oracle and GPU disagree"
+        cpu = cpu_sample(g, args.workload, single, args.cpu_iters)
+
+    # ---- the other forms of the solver, as sub-records of the same line
+    sub = {}
+    if args.subrecords:
+        del rp, col, w, ws, cyc, d_rp, d_col, d_w
+        torch.cuda.empty_cache()
+        sub["batch4096"] = measure_batch(args, "batch4096", dev, world, rank, local,
+                                         steps=min(args.steps, 5), compare_loop=world == 1)
+        sub["diff1m_grad"] = measure_grad(args, dev, world, rank, steps=min(args.steps, 10))
 
     if rank == 0:
         out = {
@@ -393,6 +462,7 @@ def run_ours(args, g, desc):
             "config": {"workload": f"{args.workload}: {desc}", "n": g.n, "m": g.m,
                        "mode": g.mode, "sweeps_per_solve": sweeps,
                        "lambda": f"{sol.num}/{sol.den}", "critical_cycle_len": int(sol.cycle.numel()),
+                       "matches_stored_oracle_answer": matches,
                        "l2": "flushed before every timed step (256 MiB write, outside the timing)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "step_ms_median": statistics.median(step_ms),
@@ -402,11 +472,11 @@ def run_ours(args, g, desc):
                        "iteration": ("single-lambda (Alg. 1 rebuild around the chosen cycle)"
                                      if single else "multichain (one mean per policy cycle)")},
             "roofline": roofline,
+            "roofline_sweep": roofline_sweep,
             "kernel_share": share,
             "kernels": {c: {"ms_per_solve": v["ms_total"] / prof_steps,
                             "launches_per_solve": v["launches"] / prof_steps,
                             "gbs": v["gbs"]} for c, v in classes.items()},
-            "sweep_gbs": sweep["gbs"],
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "edge-iters/s",
                     "h2d_bytes_per_step": 4 * (g.n + 1) + 8 * g.m, "d2h_bytes_per_step": d2h},
@@ -414,6 +484,7 @@ def run_ours(args, g, desc):
             "clocks": clocks.summary(),
             "stats": sol.stats,
         }
+        out.update(sub)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -432,16 +503,55 @@ def _gpu_setup():
     return torch, dist, world, rank, local, torch.device("cuda", local)
 
 
-def run_batch(args):
-    """Batched form: graphs/s of one ocm_solve_batch call over G graphs, against
-    a loop of ocm_solve over the same graphs (same stream, warm workspace)."""
+def _batch_golden() -> dict:
+    """The oracle's stored per-member answers of batch4096 (written by
+    tests/golden/make_batch_values.py): g -> (num, den, len, digest, first edge)."""
+    rows = {}
+    path = os.path.join(ROOT, "tests", "golden", "batch4096_values.txt")
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            g, n, m, num, den, L, iters, digest, first = (int(x) for x in line.split())
+            rows[g] = (num, den, L, digest, first)
+    return rows
+
+
+def _member_answers(vptr, rp, num, den, clen, cyc_all):
+    """(num, den, len, digest, first edge) of every member, cycle edges local
+    to the member graph, as the stored oracle answers hold them."""
+    out = {}
+    for g in range(vptr.shape[0] - 1):
+        v0 = int(vptr[g])
+        e0 = int(rp[v0])
+        c = (np.asarray(cyc_all[v0:v0 + int(clen[g])], dtype=np.int64) - e0).astype(np.int32)
+        out[g] = (int(num[g]), int(den[g]), int(clen[g]), synth.digest(c),
+                  int(c[0]) if c.shape[0] else -1)
+    return out
+
+
+def measure_batch(args, workload, dev, world, rank, local, steps, compare_loop=True,
+                  warmup=3) -> dict:
+    """Batched form: graphs/s of one ocm_solve_batch call over the G graphs
+    (N > 1: each rank solves its LPT share by edge count, the job rate counts
+    all G graphs over the slowest rank), against a loop of ocm_solve over the
+    same graphs (same stream, warm workspace; N = 1 only).  batch4096 members
+    are compared with the oracle's stored answers."""
+    import torch
+    import torch.distributed as dist
+
     import paper_1111_0627_gb300 as ocm
-    torch, dist, world, rank, local, dev = _gpu_setup()
-    G, nmax, desc = BATCH_WORKLOADS[args.workload]
+    from paper_1111_0627_gb300 import shard
+    G, nmax, desc = BATCH_WORKLOADS[workload]
     graphs = synth.batch_graphs(G=G, nmin=100, nmax=nmax)
-    b = synth.concat(graphs, name=args.workload)
+    full = synth.concat(graphs, name=workload)
+    costs = full.row_ptr[full.graph_vptr[1:]].astype(np.int64) - \
+        full.row_ptr[full.graph_vptr[:-1]]
+    mine = shard.lpt_partition(costs, world)[rank]
+    sub = shard.take_graphs(full.graph_vptr, full.row_ptr, full.col_idx, full.w, mine)
+    b = synth.Batch(sub.graph_vptr, sub.row_ptr, sub.col_idx, sub.w, full.mode)
     vp, rp, col, w = [torch.from_numpy(x).to(dev) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
-    ws = torch.empty(ocm.workspace_bytes_batch(G, b.N, b.M), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ocm.workspace_bytes_batch(b.G, b.N, b.M), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -450,90 +560,123 @@ def run_batch(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(max(3, warmup)):
         sol = ocm.solve_batch(vp, rp, col, w, b.mode, workspace=ws, stream=stream)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     launches = 0
-    with ClockSampler(local) as clocks:
-        barrier()
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            sol = ocm.solve_batch(vp, rp, col, w, b.mode, workspace=ws, stream=stream)
-            ev[k][1].record(stream)
-            launches += sol.stats["launches"]
-        barrier()
-    value, total_ms = job_rate(G, args.steps, sum(a.elapsed_time(bb) for a, bb in ev), world, dev)
+    barrier()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        sol = ocm.solve_batch(vp, rp, col, w, b.mode, workspace=ws, stream=stream)
+        ev[k][1].record(stream)
+        launches += sol.stats["launches"]
+    barrier()
+    local_ms = sum(a.elapsed_time(bb) for a, bb in ev)
+    value, total_ms = job_rate(G / world, steps, local_ms, world, dev)
 
-    # the same graphs through the plain solver, one call each
-    num_b, den_b = sol.num.cpu().numpy(), sol.den.cpu().numpy()
-    wsl = torch.empty(max(ocm.workspace_bytes(g.n, g.m) for g in graphs), dtype=torch.uint8,
-                      device=dev)
-    cyc = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
-    devg = [tuple(torch.from_numpy(x).to(dev) for x in (g.row_ptr, g.col_idx, g.w)) for g in graphs]
-    for r_, c_, w_ in devg[:3]:
-        ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
-    identical = True
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # every graph of the loop is new to the solver's loop-graph cache, so the
-    # loop is timed both with the CUDA-graph loop and host-driven, and the
-    # faster of the two is the baseline
-    loop_ms_by = {}
-    for loop_name, flags in (("cuda_graph", 0), ("host", ocm.ocm.OCM_FLAG_HOST_LOOP)):
-        barrier()
-        e0.record(stream)
-        for i, (r_, c_, w_) in enumerate(devg):
-            x = ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream,
-                          flags=flags)
-            identical &= (x.num, x.den) == (int(num_b[i]), int(den_b[i]))
-            if i < 64:   # cycles of a sample of graphs compared edge by edge
-                off = int(b.row_ptr[int(b.graph_vptr[i])])
-                identical &= (sol.cycle(i).cpu() - off).tolist() == x.cycle.cpu().tolist()
-        e1.record(stream)
-        barrier()
-        loop_ms_by[loop_name] = e0.elapsed_time(e1)
-    loop_ms = min(loop_ms_by.values())
+    # results of every graph, gathered on the host in the input order
+    parts = shard.gather(shard.local_results(sub, sol.num.cpu().numpy(), sol.den.cpu().numpy(),
+                                             sol.cycle_len.cpu().numpy(),
+                                             sol.cycle_out.cpu().numpy()))
+    res = shard.assemble(parts, full.graph_vptr)
+    matches = None
+    if workload == "batch4096":
+        gold = _batch_golden()
+        got = _member_answers(full.graph_vptr, full.row_ptr, res.num, res.den, res.cycle_len,
+                              res.cycle_out)
+        matches = sum(1 for gi in range(G) if got[gi] == gold[gi])
+
+    loop = None
+    if compare_loop:
+        wsl = torch.empty(max(ocm.workspace_bytes(gr.n, gr.m) for gr in graphs),
+                          dtype=torch.uint8, device=dev)
+        cyc = torch.empty(max(gr.n for gr in graphs), dtype=torch.int32, device=dev)
+        devg = [tuple(torch.from_numpy(x).to(dev) for x in (gr.row_ptr, gr.col_idx, gr.w))
+                for gr in graphs]
+        for r_, c_, w_ in devg[:3]:
+            ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream)
+        identical = True
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # every graph of the loop is new to the solver's loop-graph cache, so
+        # the loop is timed both with the CUDA-graph loop and host-driven, and
+        # the faster of the two is the baseline
+        loop_ms_by = {}
+        for loop_name, flags in (("cuda_graph", 0), ("host", ocm.ocm.OCM_FLAG_HOST_LOOP)):
+            barrier()
+            e0.record(stream)
+            for i, (r_, c_, w_) in enumerate(devg):
+                x = ocm.solve(r_, c_, w_, b.mode, workspace=wsl, cycle_out=cyc, stream=stream,
+                              flags=flags)
+                identical &= (x.num, x.den) == (int(res.num[i]), int(res.den[i]))
+                if i < 64:   # cycles of a sample of graphs compared edge by edge
+                    off = int(full.row_ptr[int(full.graph_vptr[i])])
+                    identical &= (res.cycle(i, full.graph_vptr) - off).tolist() == \
+                        x.cycle.cpu().tolist()
+            e1.record(stream)
+            barrier()
+            loop_ms_by[loop_name] = e0.elapsed_time(e1)
+        loop_ms = min(loop_ms_by.values())
+        loop = {"graphs_per_s": G / (loop_ms / 1e3), "ms": loop_ms, "ms_by_loop": loop_ms_by,
+                "identical_results": bool(identical)}
+        del devg, wsl
 
     # end to end: host CSR -> device, batched solve, results back
     h = [torch.from_numpy(x).pin_memory() for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
     d = [torch.empty_like(x) for x in (vp, rp, col, w)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     for src, dst in zip(h, d):
         dst.copy_(src, non_blocking=True)
     s2 = ocm.solve_batch(*d, b.mode, workspace=ws, stream=stream)
-    out = [s2.num.cpu(), s2.den.cpu(), s2.cycle_len.cpu(), s2.cycle_out.cpu()]
+    outs = [s2.num.cpu(), s2.den.cpu(), s2.cycle_len.cpu(), s2.cycle_out.cpu()]
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_value, _ = job_rate(G / world, 1, e0.elapsed_time(e1), world, dev)
+    ms_batch = total_ms / steps
+    return {
+        "metric": "graphs/s", "value": value, "unit": "graphs/s", "n_gpus": world,
+        "steps": steps, "ms_per_step": ms_batch,
+        "config": {"workload": f"{workload}: {desc}", "G": G, "N": full.N, "M": full.M,
+                   "mode": full.mode, "iterations": sol.stats["iterations"],
+                   "loop": "cuda_graph" if sol.stats["graph_loop"] else "host",
+                   "parallelism": (f"sharded over {world} GPUs by edge count (LPT), host gather"
+                                   if world > 1 else "single GPU"),
+                   "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
+        "members_matching_oracle": matches,
+        "loop_of_plain_solver": loop,
+        "speedup_vs_loop": (loop["ms"] / ms_batch) if loop else None,
+        "e2e": {"value": e2e_value, "unit": "graphs/s",
+                "h2d_bytes_per_step": sum(x.numel() * 4 for x in h),
+                "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in outs)},
+        "gpu_launches": launches, "stats": sol.stats}
+
+
+def run_batch(args):
+    torch, dist, world, rank, local, dev = _gpu_setup()
+    with ClockSampler(local) as clocks:
+        r = measure_batch(args, args.workload, dev, world, rank, local, args.steps,
+                          compare_loop=world == 1, warmup=args.warmup)
     if rank == 0:
-        print(json.dumps({
-            "metric": "graphs/s", "value": value, "unit": "graphs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {desc}", "G": G, "N": b.N, "M": b.M,
-                       "mode": b.mode, "iterations": sol.stats["iterations"],
-                       "loop": "cuda_graph" if sol.stats["graph_loop"] else "host",
-                       "l2": "flushed before every timed step (256 MiB write, outside the timing)"},
-            "loop_of_plain_solver": {"graphs_per_s": G / (loop_ms / 1e3), "ms": loop_ms,
-                                     "ms_by_loop": loop_ms_by,
-                                     "identical_results": bool(identical)},
-            "speedup_vs_loop": (loop_ms / 1e3) / (total_ms / args.steps / 1e3),
-            "e2e": {"value": G / (e2e_ms / 1e3), "unit": "graphs/s",
-                    "h2d_bytes_per_step": sum(x.numel() * 4 for x in h),
-                    "d2h_bytes_per_step": sum(x.numel() * x.element_size() for x in out)},
-            "gpu_launches": launches, "clocks": clocks.summary(), "stats": sol.stats}), flush=True)
+        r.update({"warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                  "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                  "clocks": clocks.summary()})
+        print(json.dumps(r), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
-def run_grad(args):
+def measure_grad(args, dev, world, rank, steps, warmup=3) -> dict:
     """Differentiation form on diff1m: forward + backward kernel against finite
     differences by looping the plain solver over 64 random edges plus the
     critical cycle (integer +1 perturbations, exact)."""
+    import torch
+    import torch.distributed as dist
+
     import paper_1111_0627_gb300 as ocm
-    torch, dist, world, rank, local, dev = _gpu_setup()
     base = synth.diff1m_base()
     # the unique-optimum construction needs the base graph's critical cycle; the
     # solver's own answer is used here (the tests check it against the oracle)
@@ -545,7 +688,7 @@ def run_grad(args):
     w[c0] += 1
     stream = torch.cuda.current_stream(dev)
     gl = torch.ones(1, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(max(3, warmup)):
         sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
         g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
     if world > 1:
@@ -553,22 +696,22 @@ def run_grad(args):
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         sol = ocm.solve(rp, col, w, "max", workspace=ws, stream=stream)
         g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
     e1.record(stream)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    rate, job_ms = job_rate(1, args.steps, e0.elapsed_time(e1), world, dev)
-    fb_ms = job_ms / args.steps
+    rate, job_ms = job_rate(1, steps, e0.elapsed_time(e1), world, dev)
+    fb_ms = job_ms / steps
     eb = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     eb[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         g = ocm.backward(sol.cycle, gl, base.m, stream=stream)
     eb[1].record(stream)
     torch.cuda.synchronize(dev)
-    bw_ms = eb[0].elapsed_time(eb[1]) / args.steps
+    bw_ms = eb[0].elapsed_time(eb[1]) / steps
     rng = np.random.default_rng(1111062704)
     edges = np.unique(np.concatenate([rng.integers(0, base.m, 64), sol.cycle.cpu().numpy()]))
     lam0 = sol.value
@@ -587,20 +730,28 @@ def run_grad(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     fd_ms = e0.elapsed_time(e1)
+    return {
+        "metric": "gradient evaluations/s", "value": rate, "unit": "1/s",
+        "n_gpus": world, "steps": steps, "ms_per_step": fb_ms,
+        "config": {"workload": "diff1m: n=2^20, ring + U{0..7} extras, w 1024*U[0,1000] with +1 "
+                               "on the critical cycle (unique optimum), max",
+                   "n": base.n, "m": base.m, "critical_cycle_len": int(sol.cycle.numel()),
+                   "fd_edges": int(len(edges))},
+        "backward_kernel_ms": bw_ms,
+        "finite_difference_loop": {"ms": fd_ms, "solves": int(len(edges)),
+                                   "max_rel_err_vs_gradient": max_rel},
+        "speedup_vs_fd_loop": fd_ms / fb_ms}
+
+
+def run_grad(args):
+    torch, dist, world, rank, local, dev = _gpu_setup()
+    r = measure_grad(args, dev, world, rank, args.steps, warmup=args.warmup)
     if rank == 0:
-        print(json.dumps({
-            "metric": "gradient evaluations/s", "value": rate, "unit": "1/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fb_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32",
-            "data": "synthetic",
-            "config": {"workload": "diff1m: n=2^20, ring + U{0..7} extras, w 1024*U[0,1000] with +1 "
-                                   "on the critical cycle (unique optimum), max",
-                       "n": base.n, "m": base.m, "critical_cycle_len": int(sol.cycle.numel()),
-                       "fd_edges": int(len(edges))},
-            "backward_kernel_ms": bw_ms,
-            "finite_difference_loop": {"ms": fd_ms, "solves": int(len(edges)),
-                                       "max_rel_err_vs_gradient": max_rel},
-            "speedup_vs_fd_loop": fd_ms / fb_ms}), flush=True)
+        r.update({"warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                  "vs_baseline": None, "dtype": "int64+f32", "data": "synthetic"})
+        print(json.dumps(r), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -690,11 +841,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="product4",
+    ap.add_argument("--workload", default="locality32m",
                     choices=sorted(_workloads()) + sorted(BATCH_WORKLOADS) +
                     ["diff1m-grad", "digraph-scc"])
-    ap.add_argument("--ref-iters", type=int, default=2,
-                    help="Howard iterations per reference (oracle) step")
+    ap.add_argument("--ref-iters", type=int, default=0,
+                    help="Howard iterations per reference (oracle) step (0: 1 on locality32m, "
+                         "else 2)")
+    ap.add_argument("--cpu-iters", type=int, default=2,
+                    help="Howard iterations of the oracle in the cpu_baseline sample")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the batch4096 and diff1m_grad sub-records of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-lambda", action="store_true",
                     help="the paper's single-lambda form of the iteration (single-graph workloads)")
@@ -702,6 +858,11 @@ def main():
                     help="log2 of the vertex count of the locality workload (default 25)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    if args.ref_iters <= 0:
+        args.ref_iters = 1 if args.workload == "locality32m" else 2
+    # the sub-records ride on the default single-graph line only
+    args.subrecords = (not args.no_subrecords and args.workload == "locality32m"
+                       and args.locality_log2 == 25 and not args.single_lambda)
     LOCALITY_LOG2[0] = args.locality_log2
     if args.workload in BATCH_WORKLOADS and args.impl == "ours":
         return run_batch(args)

@@ -142,3 +142,19 @@ def test_full_batch_config_every_member_against_oracle():
         if got != (gnum, gden, L, digest, first):
             bad.append((g, got, (gnum, gden, L, digest, first)))
     assert not bad, bad[:5]
+
+
+def test_sharded_batch_on_one_rank_equals_the_batched_call():
+    """paper_1111_0627_gb300.shard on a single rank (no process group): the LPT
+    share is the whole batch, and the gathered host results equal one
+    ocm_solve_batch call graph by graph."""
+    from paper_1111_0627_gb300 import shard
+    graphs = synth.batch_graphs(G=48, nmin=20, nmax=4000)
+    b = synth.concat(graphs)
+    res = shard.solve_batch_sharded(b.graph_vptr, b.row_ptr, b.col_idx, b.w, b.mode)
+    sol = _solve_batch(b)
+    assert (res.num == sol.num.cpu().numpy()).all() and (res.den == sol.den.cpu().numpy()).all()
+    assert (res.cycle_len == sol.cycle_len.cpu().numpy()).all()
+    for g in range(b.G):
+        assert res.cycle(g, b.graph_vptr).tolist() == sol.cycle(g).cpu().tolist()
+    assert (res.owner == 0).all()
