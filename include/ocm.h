@@ -93,7 +93,12 @@ typedef struct ocm_options {
     int32_t edges_per_lane;
     int32_t sweep_threads;
     int32_t sweep_kind;  /* OCM_SWEEP_*; 0 = library default (degree classes)      */
-    int32_t reserved0;
+    /* Limit of every device-side wait of the call (the grid barriers of the
+     * cooperative kernels), in milliseconds of GPU wall-clock time; a wait
+     * that runs out makes the call return OCM_ERR_TIMEOUT and leaves the
+     * device context usable.  <= 0: 2,000 ms (10 ms with OCM_FLAG_TEST_STALL).
+     * The SCC decomposition of ocm_scc / ocm_solve_scc keeps the default. */
+    int32_t wait_limit_ms;
     /* Warm start (optional, device [n]; [N] with global edge ids for
      * ocm_solve_batch): the policy the iteration starts from, one out-edge
      * per vertex, row_ptr[v] <= init_policy[v] < row_ptr[v+1]
@@ -137,9 +142,18 @@ typedef struct ocm_options {
 #define OCM_SWEEP_TILES 2
 
 /* Test-only: the first grid barrier of the evaluation waits for an arrival
- * that never comes, with its wait limit cut to about 10 ms, so the solve
- * exercises the bounded-wait path and returns OCM_ERR_TIMEOUT.  The device
- * context stays usable. */
+ * that never comes, with its wait limit cut to 10 ms (or to
+ * ocm_options.wait_limit_ms when set), so the solve exercises the
+ * bounded-wait path and returns OCM_ERR_TIMEOUT.  The device context stays
+ * usable.
+ *
+ * Test hook of the error paths (no GPU fault is made): when the environment
+ * variable OCM_FAULT is "launch", the solve entry points return OCM_ERR_CUDA
+ * before their first launch; "validate" makes ocm_solve, ocm_solve_batch and
+ * ocm_solve_static return OCM_ERR_BAD_CSR as if the CSR checks had failed,
+ * also before any device work; "alloc" makes the CUDA-graph loop fail to
+ * instantiate, so the solve runs the host-driven loop (same results,
+ * ocm_stats.graph_loop = 0).  Unset in normal use. */
 #define OCM_FLAG_TEST_STALL 1
 
 /* Drive the policy iteration from the host: after every improvement step the
@@ -391,7 +405,8 @@ const char *ocm_status_string(int status);
  * ocm_options.transit and ocm_backward_ratio; 103: ocm_scc and
  * ocm_solve_scc; 104: OCM_FLAG_SINGLE_LAMBDA, ocm_workspace_size_single,
  * ocm_stats.rebuild_levels; 105: ocm_solve_static,
- * OCM_STATIC_WORKSPACE_BYTES). */
+ * OCM_STATIC_WORKSPACE_BYTES; 106: ocm_options.wait_limit_ms, the OCM_FAULT
+ * test hook). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -82,7 +82,7 @@ class OcmOptions(ctypes.Structure):
                 ("eta_num", ctypes.c_void_p), ("eta_den", ctypes.c_void_p),
                 ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
                 ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
-                ("sweep_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("sweep_kind", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
                 ("init_policy", ctypes.c_void_p), ("transit", ctypes.c_void_p)]
 
 

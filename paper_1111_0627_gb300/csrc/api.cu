@@ -4,9 +4,12 @@
 // extraction of the critical cycle, and the backward scatter.
 #include <climits>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 
@@ -65,10 +68,11 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     return align_up(off, 256);
 }
 
-__global__ void ctrl_init_kernel(Ctrl *c) {
+__global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns) {
     Ctrl z;
     memset(&z, 0, sizeof z);
     z.bad_index = INT_MAX;
+    z.wait_ns = wait_ns;
     *c = z;
 }
 
@@ -188,6 +192,21 @@ void prof_end(int cls, cudaStream_t st) {
     cudaEventRecord(b, st);
     g_prof_done.push_back(ProfPair{cls, g_prof_open, b});
     g_prof_open = nullptr;
+}
+
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
+// Host-side fault injection for tests of the error paths: the environment
+// variable OCM_FAULT names one failure that the entry points then report as
+// if the runtime or the input checks had produced it, before any device work
+// of that step ("launch": a kernel launch fails, OCM_ERR_CUDA; "validate":
+// the CSR checks fail, OCM_ERR_BAD_CSR; "alloc": the loop graph cannot be
+// instantiated, so the solve falls back to the host-driven loop).  No GPU
+// fault is ever made.
+bool injected_fault(const char *what) {
+    const char *e = getenv("OCM_FAULT");
+    return e != nullptr && strcmp(e, what) == 0;
 }
 
 static int persistent_grid() {
@@ -469,7 +488,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 105; }
+int ocm_version(void) { return 106; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -532,8 +551,20 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     BatchState none{};
     BatchState b = bs ? *bs : none;
 
+    // Limit of every device-side wait: the caller's, else two seconds (10 ms
+    // for the test-only stall, which can only run out).
+    long long wait_ns = kDefaultWaitNs;
+    if (opt && opt->wait_limit_ms > 0) wait_ns = (long long)opt->wait_limit_ms * 1000000LL;
+    else if (opt && (opt->flags & OCM_FLAG_TEST_STALL)) wait_ns = kStallTestWaitNs;
+
     // 1. row_ptr (and the graph offsets) must be sane before any kernel trusts them
-    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl);
+    NvtxRange r_all(bs ? "ocm_solve_batch" : "ocm_solve");
+    if (injected_fault("launch")) return OCM_ERR_CUDA;
+    if (injected_fault("validate")) return OCM_ERR_BAD_CSR;
+    auto phase = [](const char *name) { nvtxRangePop(); nvtxRangePushA(name); };
+    nvtxRangePushA("ocm:validate");
+    struct PopOnExit { ~PopOnExit() { nvtxRangePop(); } } pop_phase;
+    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl, wait_ns);
     launch_check_row_ptr(row_ptr, n, m, ws.ctrl, st);
     launches += 2;
     if (bs) launches += launch_batch_prepare(n, m, b, ws, st);
@@ -542,6 +573,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (rc) return rc;
     if (h.err) return map_err_bits(h.err);
 
+    phase("ocm:init_policy");
     // 2. degree classes of the improvement sweep (and the heavy vertices), then
     //    the initial policy (the paper's first pass from val = 0, lambda = 0),
     //    which also validates col_idx and w and measures max|w|
@@ -585,6 +617,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     }
 
+    phase("ocm:iterate");
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable --
     //    as one launch of the cached loop graph, or driven from the host
     StepArgs sa;
@@ -613,7 +646,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
                                  : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
     const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || prof_active();
-    const int slot = host_loop ? -1 : acquire_loop(sa);
+    // (a failed instantiation of the loop graph falls back to the host loop)
+    const int slot = (host_loop || injected_fault("alloc")) ? -1 : acquire_loop(sa);
     if (slot >= 0) {
         const cudaError_t e = cudaGraphLaunch(g_loops[slot].exec, st);
         rc = (e == cudaSuccess) ? read_ctrl(ws.ctrl, &h, st) : OCM_ERR_CUDA;
@@ -635,6 +669,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (h.not_converged) return OCM_ERR_NOT_CONVERGED;
     const long long it = h.iter;
 
+    phase("ocm:extract");
     // 4. critical cycle(s) of the final policy
     int Lstar = 0;
     if (bs) {

@@ -108,7 +108,13 @@ struct Ctrl {
     int fcnt[3];              // single-lambda rebuild: rotating frontier counters
     int hcnt[2][3];           // SCC searches: rotating counters of the heavy frontiers (fw, bw)
     int connect_levels;       // single-lambda rebuild: backward-search levels, all iterations
+    long long wait_ns;        // limit of every device-side wait (grid barriers), nanoseconds
 };
+
+// Default limit of a device-side wait, and the one the test-only stall flag
+// uses unless the caller sets ocm_options.wait_limit_ms.
+constexpr long long kDefaultWaitNs = 2000000000LL;   // two seconds
+constexpr long long kStallTestWaitNs = 10000000LL;   // 10 ms
 
 enum : int {
     kErrRowPtr = 1,
@@ -291,6 +297,13 @@ struct ProfilePause {
     bool prev;
 };
 bool prof_active();
+bool injected_fault(const char *what);
+// NVTX range over a host-side phase of an entry point (visible in Nsight
+// Systems timelines; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name);
+    ~NvtxRange();
+};
 
 // kernel launchers (defined in the .cu files)
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);

@@ -252,7 +252,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
     // nothing), and gbest only at the end.
     __syncthreads();
     // (test only: wait for one block more than exists, so the wait expires)
-    if (stall_test && !grid_barrier(c, nblocks + 1u, kStallTestClockLimit)) return;
+    if (stall_test && !grid_barrier(c, nblocks + 1u)) return;
 
     // ------------------------------------------------------------ detect
     // State: unresolved {J >= 0, M | dirty << 31}; resolved {~root, dirty}.

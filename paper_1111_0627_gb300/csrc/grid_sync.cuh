@@ -1,16 +1,24 @@
 // grid_sync.cuh -- the bounded grid-wide barrier of the library's cooperative
 // kernels (policy evaluation, single-lambda rebuild, SCC decomposition and its
 // sort).  Every block of a cooperative launch is co-resident, so a counter in
-// device memory can act as a barrier; waits are bounded by an SM-clock limit,
-// after which the kernel records kErrTimeout and returns instead of hanging.
+// device memory can act as a barrier; waits are bounded by a wall-clock limit
+// (the GPU's global nanosecond timer), after which the kernel records
+// kErrTimeout and returns instead of hanging.
 #pragma once
 
 #include "common.cuh"
 
 namespace ocm {
 
-constexpr long long kBarrierClockLimit = 4000000000LL;   // SM cycles: about two seconds
-constexpr long long kStallTestClockLimit = 20000000LL;   // about 10 ms (OCM_FLAG_TEST_STALL)
+// Limit argument of the barriers below: 0 = the control block's wait_ns (set
+// per call from ocm_options.wait_limit_ms, two seconds by default).
+constexpr long long kWaitFromCtrl = 0;
+
+static __device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 static __device__ __forceinline__ int load_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
@@ -36,8 +44,9 @@ static __device__ __forceinline__ void grid_sync_start() {
 // second round trip a last-arriver scheme needs.  Block 0 clears the slot of
 // barrier g + 2 before it arrives at g: that slot was last read before
 // barrier g - 1 completed and is next written after barrier g + 1 completes.
-// Waits are bounded by an SM-clock limit; on expiry every block records
-// kErrTimeout and *ok becomes false.  `which` selects the kernel's GridBar.
+// Waits are bounded by `limit` nanoseconds (kWaitFromCtrl: the control
+// block's wait_ns); on expiry every block records kErrTimeout and *ok becomes
+// false.  `which` selects the kernel's GridBar.
 template <bool TWO>
 static __device__ __forceinline__ int grid_sum_barrier_impl(Ctrl *c, unsigned nblocks, int x,
                                                             int y, int *ysum, bool *ok,
@@ -62,6 +71,7 @@ static __device__ __forceinline__ int grid_sum_barrier_impl(Ctrl *c, unsigned nb
     __syncthreads();
     if (threadIdx.x == 0) {
         GridBar *b = &c->bar[which];
+        const long long lim = limit > 0 ? limit : c->wait_ns;
         unsigned *rp = bar_round();
         const unsigned g = *rp;
         const int slot = (int)(g & 3u);
@@ -76,14 +86,14 @@ static __device__ __forceinline__ int grid_sum_barrier_impl(Ctrl *c, unsigned nb
                      :: "l"(&b->arrive), "l"(1ULL) : "memory");
         const unsigned long long target = (unsigned long long)nblocks * (g + 1);
         int okv = 1;
-        const long long t0 = clock64();
+        const long long t0 = global_ns();
         for (unsigned it = 1;; ++it) {
             unsigned long long a;
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
                          : "=l"(a) : "l"(&b->arrive) : "memory");
             if (a >= target) break;
             if ((it & 63u) == 0 &&
-                (clock64() - t0 > limit || (load_volatile(&c->err) & kErrTimeout))) {
+                (global_ns() - t0 > lim || (load_volatile(&c->err) & kErrTimeout))) {
                 atomicOr(&c->err, kErrTimeout);
                 okv = 0;
                 break;
@@ -108,7 +118,7 @@ static __device__ __forceinline__ int grid_sum_barrier_impl(Ctrl *c, unsigned nb
 }
 
 static __device__ __forceinline__ int grid_sum_barrier(Ctrl *c, unsigned nblocks, int x, bool *ok,
-                                                       long long limit = kBarrierClockLimit,
+                                                       long long limit = kWaitFromCtrl,
                                                        int which = 0) {
     return grid_sum_barrier_impl<false>(c, nblocks, x, 0, nullptr, ok, limit, which);
 }
@@ -117,11 +127,11 @@ static __device__ __forceinline__ int grid_sum_barrier(Ctrl *c, unsigned nblocks
 // sum of y.
 static __device__ __forceinline__ int grid_sum2_barrier(Ctrl *c, unsigned nblocks, int x, int y,
                                                         int *ysum, bool *ok) {
-    return grid_sum_barrier_impl<true>(c, nblocks, x, y, ysum, ok, kBarrierClockLimit, 0);
+    return grid_sum_barrier_impl<true>(c, nblocks, x, y, ysum, ok, kWaitFromCtrl, 0);
 }
 
 static __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned nblocks,
-                                                    long long limit = kBarrierClockLimit,
+                                                    long long limit = kWaitFromCtrl,
                                                     int which = 0) {
     bool ok;
     grid_sum_barrier(c, nblocks, 0, &ok, limit, which);

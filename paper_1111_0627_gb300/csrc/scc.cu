@@ -548,6 +548,7 @@ __global__ void scc_ctrl_init_kernel(Ctrl *c) {
     Ctrl z;
     memset(&z, 0, sizeof z);
     z.bad_index = INT_MAX;
+    z.wait_ns = kDefaultWaitNs;
     *c = z;
 }
 
@@ -671,6 +672,8 @@ int ocm_scc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t m
     if (!workspace || ws_bytes < scc_workspace_size(n, m) ||
         (reinterpret_cast<uintptr_t>(workspace) & 255u))
         return OCM_ERR_WORKSPACE;
+    NvtxRange range("ocm_scc");
+    if (injected_fault("launch")) return OCM_ERR_CUDA;
     int count = 0;
     const int rc = scc_decompose(row_ptr, col_idx, n, m, scc, &count, workspace,
                                  static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr);
@@ -1027,6 +1030,8 @@ int ocm_solve_scc(const int32_t *row_ptr, const int32_t *col_idx, const int32_t 
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->init_policy || opt->transit || (opt->flags & OCM_FLAG_TEST_STALL)))
         return OCM_ERR_INVALID_ARG;
+    NvtxRange range("ocm_solve_scc");
+    if (injected_fault("launch")) return OCM_ERR_CUDA;
     if (!workspace || ws_bytes < comp_workspace_size(n, m) ||
         (reinterpret_cast<uintptr_t>(workspace) & 255u))
         return OCM_ERR_WORKSPACE;

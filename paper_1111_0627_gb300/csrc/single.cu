@@ -214,7 +214,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     bool ok;
     // vertices still unconnected, heavy ones among them
     int hleft = 0;
-    int left = grid_sum_barrier_impl<true>(c, nb, mine, hmine, &hleft, &ok, kBarrierClockLimit,
+    int left = grid_sum_barrier_impl<true>(c, nb, mine, hmine, &hleft, &ok, kWaitFromCtrl,
                                            kBarConnect);
     if (!ok) return;
     // the heavy vertices at level `want` take the edges heavy_scan found
@@ -233,7 +233,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 atomicOr(&c->err, kErrConnect);   // a marked vertex has the edge
             }
         }
-        return grid_sum_barrier(c, nb, took, &ok, kBarrierClockLimit, kBarConnect);
+        return grid_sum_barrier(c, nb, took, &ok, kWaitFromCtrl, kBarConnect);
     };
     // the listed pushing vertices hin[0, nh): each one's in-edges spread over
     // one block (blocks take the list round-robin) or, above kInHeavyGrid,
@@ -325,12 +325,12 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                             if (l[j] == -1) sg.lev[u[j]] = -2;
                     }
                 }
-                if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+                if (!grid_barrier(c, nb, kWaitFromCtrl, kBarConnect)) return;
                 const int nh = min(load_volatile(hcount), hcap);
                 if (nh > 0) {
                     int unused = 0, unused2 = 0;
                     spread_push(nh, false, nullptr, nullptr, unused, unused2);
-                    if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+                    if (!grid_barrier(c, nb, kWaitFromCtrl, kBarConnect)) return;
                 }
             }
             const int want = pull ? -1 : -2;
@@ -357,7 +357,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             if (hleft > 0)
                 heavy_scan(want, k, row_ptr, col, ws, sg, pick, H, hv, htotal, warp_id, nwarps,
                            lane);
-            nf = grid_sum_barrier(c, nb, found, &ok, kBarrierClockLimit, kBarConnect);
+            nf = grid_sum_barrier(c, nb, found, &ok, kWaitFromCtrl, kBarConnect);
             if (!ok) return;
             if (hleft > 0) {
                 const int took = heavy_take(want, k, !pull);
@@ -373,7 +373,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     const int v = base + threadIdx.x;
                     append(F, &c->fcnt[(k - 1) % 3], v < n && sg.lev[v] == k - 1, v, lane);
                 }
-                if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+                if (!grid_barrier(c, nb, kWaitFromCtrl, kBarConnect)) return;
             }
             // (a) the unconnected in-neighbours of level k-1 are reached ...
             int added = 0, hadded = 0;
@@ -413,14 +413,14 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             }
             int hreached = 0;
             int reached = grid_sum_barrier_impl<true>(c, nb, added, hadded, &hreached, &ok,
-                                                      kBarrierClockLimit, kBarConnect);
+                                                      kWaitFromCtrl, kBarConnect);
             if (!ok) return;
             const int nh = min(load_volatile(hcount), hcap);
             if (nh > 0) {
                 int added2 = 0, hadded2 = 0, hreached2 = 0;
                 spread_push(nh, true, Fn, &c->fcnt[k % 3], added2, hadded2);
                 reached += grid_sum_barrier_impl<true>(c, nb, added2, hadded2, &hreached2, &ok,
-                                                       kBarrierClockLimit, kBarConnect);
+                                                       kWaitFromCtrl, kBarConnect);
                 if (!ok) return;
                 hreached += hreached2;
             }
@@ -459,7 +459,7 @@ connect_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             if (hreached > 0)
                 heavy_scan(-2, k, row_ptr, col, ws, sg, pick, H, hv, htotal, warp_id, nwarps,
                            lane);
-            if (!grid_barrier(c, nb, kBarrierClockLimit, kBarConnect)) return;
+            if (!grid_barrier(c, nb, kWaitFromCtrl, kBarConnect)) return;
             if (hreached > 0) {
                 heavy_take(-2, k, true);
                 if (!ok) return;

@@ -117,7 +117,7 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
           sweep_kind: int = 0, tune: bool = False,
           init_policy: torch.Tensor | None = None,
           transit: torch.Tensor | None = None,
-          single_lambda: bool = False) -> Solution:
+          single_lambda: bool = False, wait_limit_ms: int = 0) -> Solution:
     """Optimal cycle mean of a CSR graph on the GPU (``ocm_solve``).
 
     Returns the exact reduced mean num/den (max or min sense) and a critical
@@ -128,7 +128,8 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     graphs of this shape (results never depend on them).  ``single_lambda``
     runs the paper's own form of the iteration (one lambda, the policy graph
     rebuilt around the chosen cycle each time); every vertex must reach that
-    cycle, as in a strongly connected graph."""
+    cycle, as in a strongly connected graph.  ``wait_limit_ms`` bounds every
+    device-side wait of the call (0: two seconds)."""
     lib = _native.load()
     rp = _dev_i32(row_ptr, "row_ptr")
     col = _dev_i32(col_idx, "col_idx")
@@ -146,6 +147,7 @@ def solve(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="m
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
+    opt.wait_limit_ms = int(wait_limit_ms)
     if tune and not (edges_per_lane or sweep_threads or sweep_kind):
         from .autotune import lookup
         found = lookup(rp)
@@ -204,7 +206,7 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
                 w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
                 stream=None, max_iters: int = 0, flags: int = 0,
                 init_policy: torch.Tensor | None = None,
-                transit: torch.Tensor | None = None) -> BatchSolution:
+                transit: torch.Tensor | None = None, wait_limit_ms: int = 0) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
     (``ocm_solve_batch``); each result equals solving that graph alone.
     ``init_policy`` (int32 [N], global edge ids) warm-starts every graph;
@@ -228,6 +230,7 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     opt = _native.OcmOptions()
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
+    opt.wait_limit_ms = int(wait_limit_ms)
     init = _init_policy(init_policy, N)
     if init is not None:
         opt.init_policy = init.data_ptr()

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_only_entry_points():
     lib = ocm.load()
-    assert lib.ocm_version() == 105
+    assert lib.ocm_version() == 106
     assert lib.ocm_workspace_size(0, 5) == 0
     assert lib.ocm_workspace_size(5, 0) == 0
     small = lib.ocm_workspace_size(1000, 4000)
@@ -103,3 +103,63 @@ def test_no_cpu_fallback_in_the_package():
             if f.endswith(".py"):
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+@pytest.fixture
+def fault_env():
+    old = os.environ.get("OCM_FAULT")
+    yield os.environ
+    if old is None:
+        os.environ.pop("OCM_FAULT", None)
+    else:
+        os.environ["OCM_FAULT"] = old
+
+
+def _host_csr_call(lib, fn_name):
+    """Calls an entry point with valid sizes and 256-byte aligned host
+    addresses: with OCM_FAULT set it must return before any device work, so
+    the addresses are never dereferenced (no GPU is needed)."""
+    import numpy as np
+    n, m = 8, 16
+    buf = np.zeros(1 << 20, np.uint8)
+    base = (buf.ctypes.data + 255) // 256 * 256
+    num, den, clen = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    if fn_name == "ocm_solve":
+        ws = lib.ocm_workspace_size(n, m)
+        return lib.ocm_solve(base, base, base, n, m, 0, ctypes.byref(num), ctypes.byref(den),
+                             base, ctypes.byref(clen), base, ws, None, None, None), (num, den)
+    if fn_name == "ocm_solve_batch":
+        ws = lib.ocm_workspace_size_batch(2, n, m)
+        return lib.ocm_solve_batch(base, base, base, base, 2, n, m, 0, base, base, base, base,
+                                   base, ws, None, None, None), (num, den)
+    if fn_name == "ocm_scc":
+        cnt = ctypes.c_int32(-1)
+        ws = lib.ocm_workspace_size_scc(n, m)
+        return lib.ocm_scc(base, base, n, m, base, ctypes.byref(cnt), base, ws, None), (cnt, den)
+    raise ValueError(fn_name)
+
+
+@pytest.mark.parametrize("fn_name", ["ocm_solve", "ocm_solve_batch", "ocm_scc"])
+def test_injected_launch_failure_returns_cuda_error_without_device_work(fault_env, fn_name):
+    lib = ocm.load()
+    fault_env["OCM_FAULT"] = "launch"
+    rc, (a, b) = _host_csr_call(lib, fn_name)
+    assert rc == -8                                  # OCM_ERR_CUDA
+    assert lib.ocm_status_string(rc) == b"CUDA runtime error"
+    assert a.value in (0, -1) and b.value == 0       # outputs untouched
+
+
+@pytest.mark.parametrize("fn_name", ["ocm_solve", "ocm_solve_batch"])
+def test_injected_validation_failure_returns_bad_csr(fault_env, fn_name):
+    lib = ocm.load()
+    fault_env["OCM_FAULT"] = "validate"
+    rc, (num, den) = _host_csr_call(lib, fn_name)
+    assert rc == -2                                  # OCM_ERR_BAD_CSR
+    assert (num.value, den.value) == (0, 0)
+
+
+def test_python_layer_maps_injected_failures_to_ocm_error(fault_env):
+    """ocm.OCMError carries the status and its text (the Python layer adds no
+    recovery of its own)."""
+    err = ocm.OCMError(-8, "ocm_solve")
+    assert err.status == -8 and "CUDA" in str(err)

@@ -124,6 +124,44 @@ def test_graph_loop_bounded_wait_expires_cleanly():
     assert sol.stats["graph_loop"] == 1
 
 
+def test_wait_limit_option_bounds_the_stalled_wait():
+    """ocm_options.wait_limit_ms sets the limit of every device-side wait: the
+    stalled barrier of the test flag gives up after about that long (GPU wall
+    clock), in both loop forms, and the context stays usable."""
+    import time
+    g = synth.ring10k()
+    rp, col, w = _dev(g)
+    for flags in (OCM_FLAG_TEST_STALL, OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP):
+        took = {}
+        for ms in (5, 400):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            with pytest.raises(ocm.OCMError) as ei:
+                ocm.solve(rp, col, w, g.mode, flags=flags, wait_limit_ms=ms)
+            took[ms] = time.perf_counter() - t
+            assert ei.value.status == -6
+        assert took[400] >= 0.38, took
+        assert took[5] < 0.25, took
+    h = oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode)
+    sol = ocm.solve(rp, col, w, g.mode, wait_limit_ms=50)
+    assert (sol.num, sol.den) == (h.num, h.den)
+
+
+def test_injected_loop_graph_failure_falls_back_to_the_host_loop(monkeypatch):
+    """OCM_FAULT=alloc: the loop graph cannot be instantiated, the solve runs
+    the host-driven loop and gives the same answer."""
+    g = synth.ring10k()
+    rp, col, w = _dev(g)
+    monkeypatch.setenv("OCM_FAULT", "alloc")
+    sol = ocm.solve(rp, col, w, g.mode)
+    monkeypatch.delenv("OCM_FAULT")
+    ref = ocm.solve(rp, col, w, g.mode)
+    assert sol.stats["graph_loop"] == 0 and ref.stats["graph_loop"] == 1
+    assert (sol.num, sol.den) == (ref.num, ref.den)
+    assert sol.cycle.tolist() == ref.cycle.tolist()
+    assert sol.stats["iterations"] == ref.stats["iterations"]
+
+
 def test_batch_graph_loop_equals_host_loop():
     graphs = synth.batch_graphs(G=48, nmin=20, nmax=4000)
     b = synth.concat(graphs)
