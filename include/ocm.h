@@ -121,6 +121,19 @@ typedef struct ocm_options {
      * 4 n^2 max|w| max t < 2^62 and n max t < 2^31 (OCM_ERR_OVERFLOW).  The
      * improvement sweep always uses OCM_SWEEP_CLASSES in this mode.         */
     const int32_t *transit;
+    /* ocm_solve_batch only: graphs with at most this many vertices (and at
+     * most 16 times as many edges) are solved by a persistent kernel in which
+     * one thread block runs every iteration of one graph, blocks taking the
+     * graphs largest first from a queue; the larger graphs are solved
+     * together as one disjoint union afterwards.  0 = automatic: every graph
+     * with at most max(4,096, 4 N / B) vertices, B the number of resident
+     * blocks of that kernel (304 on a GB300), so that only graphs large next
+     * to the batch's share per block take the union path; < 0 = every graph
+     * takes the union path.  Results do not depend on it.  Not used with
+     * transit times or per-vertex outputs (every graph then takes the union
+     * path).                                                                */
+    int32_t batch_small_vertices;
+    int32_t reserved1;
 } ocm_options;
 
 /* Layouts of the improvement sweep (results do not depend on the choice).
@@ -191,6 +204,9 @@ typedef struct ocm_stats {
     int32_t graph_loop;     /* 1: the iteration ran as a CUDA graph, 0: host-driven */
     int32_t rebuild_levels; /* OCM_FLAG_SINGLE_LAMBDA: backward-search levels of the
                                rebuilds, summed over iterations; 0 otherwise         */
+    int32_t batch_small_graphs; /* ocm_solve_batch: graphs solved one per thread block
+                                   (see ocm_options.batch_small_vertices)          */
+    int32_t reserved2;
 } ocm_stats;
 
 /* Bytes of device workspace ocm_solve needs for a graph with n vertices and m
@@ -406,7 +422,8 @@ const char *ocm_status_string(int status);
  * ocm_solve_scc; 104: OCM_FLAG_SINGLE_LAMBDA, ocm_workspace_size_single,
  * ocm_stats.rebuild_levels; 105: ocm_solve_static,
  * OCM_STATIC_WORKSPACE_BYTES; 106: ocm_options.wait_limit_ms, the OCM_FAULT
- * test hook). */
+ * test hook; 107: ocm_options.batch_small_vertices,
+ * ocm_stats.batch_small_graphs). */
 int ocm_version(void);
 
 #ifdef __cplusplus

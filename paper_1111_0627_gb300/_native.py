@@ -19,8 +19,8 @@ CSRC = os.path.join(_PKG, "csrc")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
-SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "api.cu", "static_ws.cu",
-           "scc.cu", "single.cu"]
+SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "batch_small.cu", "api.cu",
+           "static_ws.cu", "scc.cu", "single.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -83,7 +83,8 @@ class OcmOptions(ctypes.Structure):
                 ("potential", ctypes.c_void_p), ("policy", ctypes.c_void_p),
                 ("edges_per_lane", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
                 ("sweep_kind", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
-                ("init_policy", ctypes.c_void_p), ("transit", ctypes.c_void_p)]
+                ("init_policy", ctypes.c_void_p), ("transit", ctypes.c_void_p),
+                ("batch_small_vertices", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class OcmStats(ctypes.Structure):
@@ -91,7 +92,8 @@ class OcmStats(ctypes.Structure):
                 ("detect_rounds", ctypes.c_int32), ("value_rounds", ctypes.c_int32),
                 ("switched", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("detect_items", ctypes.c_int64), ("value_items", ctypes.c_int64),
-                ("graph_loop", ctypes.c_int32), ("rebuild_levels", ctypes.c_int32)]
+                ("graph_loop", ctypes.c_int32), ("rebuild_levels", ctypes.c_int32),
+                ("batch_small_graphs", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

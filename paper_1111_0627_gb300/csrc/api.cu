@@ -488,7 +488,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 106; }
+int ocm_version(void) { return 107; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -618,6 +618,21 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     }
 
     phase("ocm:iterate");
+    // 2b. batch: the small graphs, one thread block each for all their
+    //     iterations (largest first); the union loop below skips them.  Not
+    //     with transit times or per-vertex outputs, which the union path
+    //     serves for every graph.
+    if (bs) {
+        const int small_n = opt ? opt->batch_small_vertices : 0;   // 0: automatic
+        const bool outputs = opt && (opt->eta_num || opt->eta_den || opt->potential || opt->policy);
+        if (small_n >= 0 && !ratio && !outputs) {
+            const int k = launch_batch_small(row_ptr, col_idx, w, sign, small_n, n, max_iters,
+                                             b.small_queue, ws, b, st);
+            if (k < 0) return OCM_ERR_CUDA;
+            launches += k;
+        }
+    }
+
     // 3. Howard iteration: evaluate the policy, sweep, stop when stable --
     //    as one launch of the cached loop graph, or driven from the host
     StepArgs sa;
@@ -698,7 +713,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         *out.cycle_len = Lstar;
     }
     if (stats) {
-        stats->iterations = (int32_t)it;
+        stats->iterations = (int32_t)(it > fin.small_iters ? it : fin.small_iters);
         stats->cycles = h.res_cycles;
         stats->detect_rounds = fin.rounds_detect;
         stats->value_rounds = fin.rounds_value;
@@ -708,6 +723,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         stats->value_items = fin.items_value;
         stats->graph_loop = slot >= 0 ? 1 : 0;
         stats->rebuild_levels = fin.connect_levels;
+        stats->batch_small_graphs = fin.small_total;
     }
     return OCM_OK;
 }
@@ -732,6 +748,7 @@ static size_t batch_extra(int G, int N, BatchState *bs, char *base) {
     b.gq = static_cast<int *>(take(4 * (size_t)G));
     b.gconv = static_cast<int *>(take(4 * (size_t)G));
     b.gsw = static_cast<int *>(take(4 * (size_t)G));
+    b.small_queue = static_cast<int *>(take(4 * (size_t)G));
     b.G = G;
     if (bs) *bs = b;
     return align_up(off, 256);

@@ -1,0 +1,559 @@
+// batch_small.cu -- the batched form's persistent per-graph solver.
+//
+// The regions of Sec. 3.3 are independent; for the small ones a whole Howard
+// iteration (Alg. 1: evaluate the policy, improve it, stop when stable) fits
+// one thread block.  A persistent grid of blocks pops graph tasks from a queue
+// ordered by decreasing size (a log2 bucket per size class, the largest
+// first, so the longest tasks start first), and every block runs all
+// iterations of its graph with block barriers only: no grid barrier and no
+// launch per iteration.  Each graph converges on its own (the paper's per-
+// region "work" flag becomes the end of the block's loop) and leaves its
+// answer in the per-graph records of the batch; the larger graphs go through
+// the disjoint-union path of batch.cu / evaluate.cu / sweep.cu, which skips
+// the graphs solved here.
+//
+// Every step computes what the union path computes, with the same order and
+// tie rules (cycle root = smallest vertex, V = q*S - p*len, improvement key
+// q_t*s*w(e) + V(t) compared within equal mean rank, strict switching, ties to
+// the smaller edge index), so every graph follows the trajectory the oracle
+// follows for that graph alone.  State lives in the batch workspace at the
+// graph's own vertex range (and its cycle records at the same offsets), where
+// it stays in L1/L2 while the block works on it.
+#include <climits>
+
+#include "common.cuh"
+#include "grid_sync.cuh"
+
+namespace ocm {
+
+constexpr int kSmallThreads = 512;
+constexpr int kSU = 2;   // vertices per thread per pass of a jump round (64 registers)
+constexpr int kSmallBuckets = 32;
+
+// Size buckets of the queue: floor(log2(n_g)), largest first.
+static __device__ __forceinline__ int size_bucket(int n) { return 31 - __clz(n); }
+
+static __device__ __forceinline__ bool small_eligible(const BatchState &bs,
+                                                      const int *__restrict__ row_ptr, int g,
+                                                      int max_n, int *n_out) {
+    const int a = bs.vptr[g], b = bs.vptr[g + 1];
+    const int n = b - a;
+    const long long m = (long long)row_ptr[b] - row_ptr[a];
+    *n_out = n;
+    return n <= max_n && m <= 16LL * max_n;
+}
+
+__global__ void __launch_bounds__(kThreads)
+small_count_kernel(const int *__restrict__ row_ptr, BatchState bs, int max_n, Ctrl *c) {
+    __shared__ int s_cnt[kSmallBuckets];
+    if (threadIdx.x < kSmallBuckets) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < bs.G; g += gridDim.x * blockDim.x) {
+        int n;
+        if (small_eligible(bs, row_ptr, g, max_n, &n)) atomicAdd(&s_cnt[size_bucket(n)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kSmallBuckets && s_cnt[threadIdx.x])
+        atomicAdd(&c->small_bucket[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// Queue positions: bucket b (larger b first) starts after all larger buckets;
+// within a bucket the order is that of the atomics (it decides only which
+// block solves which graph, never a result).
+__global__ void __launch_bounds__(kThreads)
+small_fill_kernel(const int *__restrict__ row_ptr, BatchState bs, int max_n, Ctrl *c,
+                  int *queue) {
+    __shared__ int s_start[kSmallBuckets];
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = kSmallBuckets - 1; b >= 0; --b) {
+            s_start[b] = run;
+            run += c->small_bucket[b];
+        }
+        if (blockIdx.x == 0) c->small_total = run;
+    }
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < bs.G; g += gridDim.x * blockDim.x) {
+        int n;
+        if (small_eligible(bs, row_ptr, g, max_n, &n)) {
+            const int b = size_bucket(n);
+            queue[s_start[b] + atomicAdd(&c->small_cursor[b], 1)] = g;
+        }
+    }
+}
+
+// Block-wide sum (all threads call it).
+static __device__ __forceinline__ int block_sum(int x, int *s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k];
+    __syncthreads();
+    return t;
+}
+
+// Appends item to the block's list (warp-aggregated shared-memory counter).
+static __device__ __forceinline__ void small_append(int *list, int *s_cnt, bool pred, int item) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    int base = 0;
+    if (mask) {
+        const int leader = __ffs(mask) - 1;
+        if (lane == leader) base = atomicAdd(s_cnt, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
+constexpr int kMinMaskS = 0x7fffffff;
+
+// Policy evaluation number `eval` of graph [v0, v1) inside one block, the
+// steps and state encodings of evaluate_kernel: detection by window minima
+// with a "switched in the last sweep" bit ORed over the windows; value
+// propagation only for vertices whose path or cycle holds a switched vertex
+// (the others keep the last evaluation's (root, len, S), which both value
+// buffers hold); worklists of unfinished vertices (lists 0 and 1 at the
+// graph's offset), a vertex finished in a round copied into the other buffer
+// in the next one, so no buffer is written while it is read.  On return every
+// vertex has its final (~root, len, S) in jls[0] and jls[1] and its record
+// {V, rank, q}; the cycle records sit at [v0, v0 + K) and the packed best
+// (rank, INT_MAX - root) in *s_best.  Returns false on an error (recorded in
+// the control block).
+static __device__ bool small_evaluate(int v0, int v1, int eval, const Workspace &ws, int *s_red,
+                                      int *s_k, int *s_cnt, unsigned long long *s_best) {
+    const int n = v1 - v0;
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    Ctrl *c = ws.ctrl;
+    int *LA = ws.list[0] + v0, *LB = ws.list[1] + v0;
+    const unsigned W = blockDim.x;
+    // ---- cycle detection.  Unresolved {J, M | dirty << 31}; resolved
+    //      {~root, dirty}.
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    int cnt = n;
+    for (int r = 0;; ++r) {
+        const JM *in = ws.jm[r & 1];
+        JM *out = ws.jm[(r + 1) & 1];
+        const int *lin = (r & 1) ? LB : LA;
+        int *lout = (r & 1) ? LA : LB;
+        int work = 0, kept = 0;
+        for (int i0 = 0; i0 < cnt; i0 += kSU * W) {
+            int item[kSU], ap[kSU];
+            JM s[kSU], t[kSU];
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) {
+                const int i = i0 + u * (int)W + (int)threadIdx.x;
+                item[u] = i < cnt ? ((r == 0) ? v0 + i : lin[i]) : INT_MIN;
+            }
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) {
+                const int it = item[u];
+                if (it == INT_MIN) continue;
+                const int v = it < 0 ? ~it : it;
+                if (r == 0) {
+                    s[u] = JM{ws.succ[v], v | ((ws.sw_iter[v] == eval) ? INT_MIN : 0)};
+                } else {
+                    s[u] = in[v];
+                    ap[u] = it >= 0 ? ws.aprev[v] : 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) {
+                const int it = item[u];
+                if (it == INT_MIN || it < 0) continue;
+                const int J = s[u].J;
+                t[u] = (r == 0) ? JM{ws.succ[J], J | ((ws.sw_iter[J] == eval) ? INT_MIN : 0)}
+                                : in[J];
+            }
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) {
+                const int it = item[u];
+                bool keep = false, resolved = false;
+                int v = 0;
+                if (it != INT_MIN) {
+                    v = it < 0 ? ~it : it;
+                    if (it < 0) {
+                        out[v] = s[u];        // resolved last round: copy forward
+                    } else {
+                        const int sdirty = (int)((unsigned)s[u].M >> 31);
+                        int root = -1, dirty = 0;
+                        if (t[u].J < 0) {
+                            root = ~t[u].J;
+                            dirty = sdirty | t[u].M;
+                        } else if (r > 0 && (t[u].M & kMinMaskS) == ap[u]) {
+                            root = ap[u];
+                            dirty = sdirty | (int)((unsigned)t[u].M >> 31);
+                        } else {
+                            const int m = min(s[u].M & kMinMaskS, t[u].M & kMinMaskS);
+                            out[v] = JM{t[u].J, m | ((s[u].M | t[u].M) & INT_MIN)};
+                            ws.aprev[v] = t[u].M & kMinMaskS;
+                            keep = true;
+                        }
+                        if (root >= 0) {
+                            out[v] = JM{~root, dirty};
+                            ws.rep[v] = root;
+                            resolved = true;
+                        }
+                        ++work;
+                    }
+                }
+                small_append(lout, s_cnt, keep || resolved, keep ? v : ~v);
+                kept += keep;
+            }
+        }
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left = block_sum(work, s_red);
+        const int still = block_sum(kept, s_red);   // (its barriers order the counter reset)
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        if (left == 0) break;
+        if (still == 0) {
+            // all resolved: the states resolved in this round go into the
+            // buffer this round read, so that both hold every final state
+            for (int i = threadIdx.x; i < cnt; i += W) {
+                const int v = ~lout[i];
+                ws.jm[r & 1][v] = out[v];
+            }
+            __syncthreads();
+            break;
+        }
+        if (r + 1 >= lg + 4) {
+            if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
+            return false;
+        }
+    }
+    // ---- values: only dirty vertices; dirty roots are final at once, as is
+    //      a dirty vertex whose successor is a root; the rest jump
+    cnt = 0;
+    {
+        int work = 0;
+        for (int v = v0 + (int)threadIdx.x; v < v1 + (int)((W - (n % W)) % W); v += W) {
+            bool keep = false;
+            if (v < v1) {
+                const JM d = ws.jm[0][v];
+                if (d.M) {
+                    const int root = ~d.J;
+                    JLS st;
+                    bool fin = true;
+                    if (root == v) {
+                        st = JLS{~v, 0, 0};
+                    } else {
+                        const int sv = ws.succ[v];
+                        fin = (ws.rep[sv] == sv);
+                        st = JLS{fin ? ~sv : sv, 1, (long long)ws.wpi[v]};
+                    }
+                    ws.jls[0][v] = st;
+                    if (fin) ws.jls[1][v] = st;
+                    keep = !fin;
+                }
+            }
+            small_append(LA, s_cnt, keep, v);
+            work += keep;
+        }
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left0 = block_sum(work, s_red);
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        if (left0 != 0) {
+            for (int j = 1;; ++j) {
+                const JLS *in = ws.jls[(j + 1) & 1];
+                JLS *out = ws.jls[j & 1];
+                const int *lin = (j & 1) ? LA : LB;
+                int *lout = (j & 1) ? LB : LA;
+                int work2 = 0, kept = 0;
+                for (int i0 = 0; i0 < cnt; i0 += kSU * W) {
+                    int item[kSU];
+                    JLS s[kSU], t[kSU];
+#pragma unroll
+                    for (int u = 0; u < kSU; ++u) {
+                        const int i = i0 + u * (int)W + (int)threadIdx.x;
+                        item[u] = i < cnt ? lin[i] : INT_MIN;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSU; ++u)
+                        if (item[u] != INT_MIN) s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
+#pragma unroll
+                    for (int u = 0; u < kSU; ++u)
+                        if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
+#pragma unroll
+                    for (int u = 0; u < kSU; ++u) {
+                        const int it = item[u];
+                        bool keep = false, fin = false;
+                        int v = 0;
+                        if (it != INT_MIN) {
+                            v = it < 0 ? ~it : it;
+                            if (it < 0) {
+                                out[v] = s[u];    // final last round: copy forward
+                            } else {
+                                const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                                out[v] = nu;
+                                fin = nu.J < 0;
+                                keep = !fin;
+                                ++work2;
+                            }
+                        }
+                        small_append(lout, s_cnt, keep || fin, keep ? v : ~v);
+                        kept += keep;
+                    }
+                }
+                __syncthreads();
+                cnt = *s_cnt;
+                const int left = block_sum(work2, s_red);
+                const int still = block_sum(kept, s_red);
+                if (threadIdx.x == 0) *s_cnt = 0;
+                __syncthreads();
+                if (left == 0) break;
+                if (still == 0) {
+                    for (int i = threadIdx.x; i < cnt; i += W) {
+                        const int v = ~lout[i];
+                        ws.jls[(j + 1) & 1][v] = out[v];
+                    }
+                    __syncthreads();
+                    break;
+                }
+                if (j + 1 > lg + 3) {
+                    if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+                    return false;
+                }
+            }
+        }
+        // both buffers hold every final state from here on
+    }
+    const JLS *A = ws.jls[0];
+    // ---- cycles: mean W/L reduced, exact key, rank among this graph's cycles
+    if (threadIdx.x == 0) {
+        *s_k = 0;
+        *s_best = 0;
+    }
+    __syncthreads();
+    const long long N2 = (long long)n * n;
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += W) {
+        if (ws.rep[v] != v) continue;
+        const int x = ws.succ[v];
+        const JLS st = A[x];
+        const long long Wc = (long long)ws.wpi[v] + st.S;
+        const long long L = 1 + (long long)st.len;
+        const long long g = gcd_ll(Wc, L);
+        const int i = v0 + atomicAdd(s_k, 1);
+        ws.cyc_root[i] = v;
+        ws.cyc_p[i] = Wc / g;
+        ws.cyc_q[i] = (int)(L / g);
+        ws.cyc_L[i] = (int)L;
+        ws.cyc_key[i] = mean_key(Wc / g, L / g, N2);
+        ws.cid_of_root[v] = i;
+    }
+    __syncthreads();
+    const int K = *s_k;
+    for (int i = v0 + (int)threadIdx.x; i < v0 + K; i += W) {
+        const long long key = ws.cyc_key[i];
+        int rank = 0;
+        for (int j = v0; j < v0 + K; ++j) rank += ws.cyc_key[j] < key;
+        ws.cyc_rank[i] = rank;
+        const unsigned long long packed =
+            ((unsigned long long)(unsigned)rank << 32) | (unsigned)(INT_MAX - ws.cyc_root[i]);
+        atomicMax(s_best, packed);
+    }
+    __syncthreads();
+    // ---- materialise the records the sweep gathers
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += W) {
+        const JLS st = A[v];
+        const int i = ws.cid_of_root[~st.J];
+        const long long p = ws.cyc_p[i];
+        const int q = ws.cyc_q[i];
+        Rec rec;
+        rec.V = (long long)q * st.S - p * (long long)st.len;
+        rec.rank = ws.cyc_rank[i];
+        rec.q = q;
+        ws.rec[v] = rec;
+    }
+    __syncthreads();
+    return true;
+}
+
+// Switch decision of vertex v given the best candidate and the candidate of
+// its current policy edge (strict improvement, Alg. 1).
+static __device__ __forceinline__ int small_switch(int v, int eval, const Cand &best,
+                                                   const Cand &own, const int *__restrict__ col,
+                                                   const int *__restrict__ w, int sign,
+                                                   const Workspace &ws) {
+    if (own.e == INT_MAX) {
+        atomicOr(&ws.ctrl->err, kErrSweep);
+        return 0;
+    }
+    if (best.rank > own.rank || (best.rank == own.rank && best.key > own.key)) {
+        ws.pi[v] = best.e;
+        ws.succ[v] = col[best.e];
+        ws.wpi[v] = sign * w[best.e];
+        ws.sw_iter[v] = eval + 1;   // changed for the next evaluation
+        return 1;
+    }
+    return 0;
+}
+
+static __device__ __forceinline__ Cand small_cand(const int *__restrict__ col,
+                                                  const int *__restrict__ w, int sign,
+                                                  const Workspace &ws, int e) {
+    const Rec r = ws.rec[col[e]];
+    return Cand{r.rank, e, (long long)r.q * (long long)(sign * w[e]) + r.V};
+}
+
+// One improvement sweep of graph [v0, v1) (the candidate order of
+// improve_kernel): a thread per vertex of out-degree <= 32, a warp per vertex
+// with more (lanes stride its edges, shuffles combine); returns the number of
+// switches.
+static __device__ int small_sweep(int v0, int v1, int eval, const int *__restrict__ row_ptr,
+                                  const int *__restrict__ col, const int *__restrict__ w,
+                                  int sign, const Workspace &ws, int *s_red) {
+    int sw = 0;
+    bool heavy_seen = false;
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
+        const int a = row_ptr[v], b = row_ptr[v + 1];
+        if (b - a > 32) {
+            heavy_seen = true;
+            continue;
+        }
+        const int pv = ws.pi[v];
+        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        Cand own{INT_MIN, INT_MAX, LLONG_MIN};
+        for (int e = a; e < b; ++e) {
+            const Cand x = small_cand(col, w, sign, ws, e);
+            if (e == pv) own = x;
+            if (better(x, best)) best = x;
+        }
+        sw += small_switch(v, eval, best, own, col, w, sign, ws);
+    }
+    if (__syncthreads_or(heavy_seen)) {
+        const int lane = threadIdx.x & 31;
+        const int nw = blockDim.x >> 5;
+        for (int v = v0 + (int)(threadIdx.x >> 5); v < v1; v += nw) {
+            const int a = row_ptr[v], b = row_ptr[v + 1];
+            if (b - a <= 32) continue;   // the same decision in every lane
+            const int pv = ws.pi[v];
+            Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+            Cand own{INT_MIN, INT_MAX, LLONG_MIN};
+            for (int e = a + lane; e < b; e += 32) {
+                const Cand x = small_cand(col, w, sign, ws, e);
+                if (e == pv) own = x;
+                if (better(x, best)) best = x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                Cand y;
+                y.rank = __shfl_xor_sync(0xffffffffu, best.rank, o);
+                y.e = __shfl_xor_sync(0xffffffffu, best.e, o);
+                y.key = __shfl_xor_sync(0xffffffffu, best.key, o);
+                if (better(y, best)) best = y;
+                Cand z;
+                z.rank = __shfl_xor_sync(0xffffffffu, own.rank, o);
+                z.e = __shfl_xor_sync(0xffffffffu, own.e, o);
+                z.key = __shfl_xor_sync(0xffffffffu, own.key, o);
+                if (z.e != INT_MAX) own = z;   // one lane met the policy edge
+            }
+            if (lane == 0) sw += small_switch(v, eval, best, own, col, w, sign, ws);
+        }
+    }
+    return block_sum(sw, s_red);
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 2)
+small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
+                   const int *__restrict__ w, int sign, const int *__restrict__ queue,
+                   long long max_iters, Workspace ws, BatchState bs) {
+    __shared__ int s_red[kSmallThreads / 32];
+    __shared__ int s_task, s_k, s_stop, s_cnt;
+    __shared__ unsigned long long s_best;
+    Ctrl *c = ws.ctrl;
+    const int total = c->small_total;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&c->small_head, 1);
+        __syncthreads();
+        const int qi = s_task;
+        __syncthreads();
+        if (qi >= total) break;
+        const int g = queue[qi];
+        const int v0 = bs.vptr[g], v1 = bs.vptr[g + 1];
+        long long it = 0;
+        bool ok = true;
+        for (;;) {
+            if (!small_evaluate(v0, v1, (int)it, ws, s_red, &s_k, &s_cnt, &s_best)) {
+                ok = false;
+                break;
+            }
+            const int sw = small_sweep(v0, v1, (int)it, row_ptr, col, w, sign, ws, s_red);
+            if (sw == 0) break;
+            if (++it >= max_iters) {
+                if (threadIdx.x == 0) c->not_converged = 1;
+                ok = false;
+                break;
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (ok) {
+                const unsigned long long packed = s_best;
+                const int root = INT_MAX - (int)(unsigned)(packed & 0xffffffffu);
+                const int i = ws.cid_of_root[root];
+                bs.gbest[g] = packed;
+                bs.groot[g] = root;
+                bs.glen[g] = ws.cyc_L[i];
+                bs.gp[g] = ws.cyc_p[i];
+                bs.gq[g] = ws.cyc_q[i];
+                bs.gconv[g] = 1;
+                atomicMax(&c->small_iters, (int)it);
+            }
+        }
+        // an error anywhere fails the whole call: stop (the same decision in
+        // every thread of the block)
+        if (threadIdx.x == 0) s_stop = (load_volatile(&c->err) != 0) || load_volatile(&c->not_converged);
+        __syncthreads();
+        if (s_stop) break;
+    }
+}
+
+// Builds the queue of graphs with at most max_n vertices (and at most 16 max_n
+// edges) and solves them, one block per graph at a time; returns the number
+// of kernel launches, or -1.  max_n == 0 picks the size limit from the batch:
+// a graph goes to a block of its own unless it holds more than four times the
+// batch's vertices per resident block (a few huge graphs are faster on the
+// whole grid, the rest of the batch is not worth a launch per iteration), and
+// never below kBatchSmallDefault.
+int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sign, int max_n,
+                       long long N, long long max_iters, int *queue, Workspace ws, BatchState bs,
+                       cudaStream_t st) {
+    static int cached_dev = -1, cached_blocks = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (dev != cached_dev) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_graph_kernel,
+                                                          kSmallThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            return -1;
+        cached_blocks = sms * per_sm;
+        cached_dev = dev;
+    }
+    if (max_n == 0) {
+        const long long auto_n = 4 * N / cached_blocks;
+        max_n = (int)(auto_n > INT_MAX / 16 ? INT_MAX / 16
+                                            : (auto_n < kBatchSmallDefault ? kBatchSmallDefault
+                                                                           : auto_n));
+    }
+    int gb = (bs.G + kThreads - 1) / kThreads;
+    if (gb > 1024) gb = 1024;
+    prof_begin(kProfEvaluate, st);
+    small_count_kernel<<<gb, kThreads, 0, st>>>(row_ptr, bs, max_n, ws.ctrl);
+    small_fill_kernel<<<gb, kThreads, 0, st>>>(row_ptr, bs, max_n, ws.ctrl, queue);
+    small_graph_kernel<<<cached_blocks, kSmallThreads, 0, st>>>(row_ptr, col, w, sign, queue,
+                                                                max_iters, ws, bs);
+    prof_end(kProfEvaluate, st);
+    return cudaGetLastError() == cudaSuccess ? 3 : -1;
+}
+
+}  // namespace ocm

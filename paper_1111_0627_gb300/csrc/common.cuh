@@ -34,6 +34,7 @@ constexpr int kEdgesPerLane = 8;       // default; ocm_options.edges_per_lane ov
 constexpr int kSweepMaxThreads = 512;  // largest sweep block (ocm_options.sweep_threads)
 constexpr int kSweepThreads = 512;     // default sweep block
 constexpr int kClassifyBlock = 1024;   // vertices per classification block
+constexpr int kBatchSmallDefault = 4096;   // batch: smallest automatic per-block size limit
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
 // the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
@@ -109,6 +110,12 @@ struct Ctrl {
     int hcnt[2][3];           // SCC searches: rotating counters of the heavy frontiers (fw, bw)
     int connect_levels;       // single-lambda rebuild: backward-search levels, all iterations
     long long wait_ns;        // limit of every device-side wait (grid barriers), nanoseconds
+    // batch: the per-graph solver of the small graphs (batch_small.cu)
+    int small_bucket[32];     // graphs per size bucket floor(log2 n_g)
+    int small_cursor[32];     // fill cursors of the buckets
+    int small_total;          // graphs in the queue
+    int small_head;           // next queue position to pop
+    int small_iters;          // largest iteration count among them
 };
 
 // Default limit of a device-side wait, and the one the test-only stall flag
@@ -213,6 +220,7 @@ struct BatchState {
     int *gq;                      //     and denominator
     int *gconv;                   // [G] 1 once the graph's policy is final
     int *gsw;                     // [G] evaluation index after the last sweep that switched in g
+    int *small_queue;             // [G] graphs solved by one block each, largest first
     int G;
 };
 
@@ -328,6 +336,9 @@ int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
                     cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
+int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sign, int max_n,
+                       long long N, long long max_iters, int *queue, Workspace ws, BatchState bs,
+                       cudaStream_t st);
 int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws, int64_t *num,
                         int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,
                         cudaStream_t st);

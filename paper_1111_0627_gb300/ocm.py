@@ -206,11 +206,14 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
                 w: torch.Tensor, mode="max", *, workspace: torch.Tensor | None = None,
                 stream=None, max_iters: int = 0, flags: int = 0,
                 init_policy: torch.Tensor | None = None,
-                transit: torch.Tensor | None = None, wait_limit_ms: int = 0) -> BatchSolution:
+                transit: torch.Tensor | None = None, wait_limit_ms: int = 0,
+                small_vertices: int = 0) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
     (``ocm_solve_batch``); each result equals solving that graph alone.
     ``init_policy`` (int32 [N], global edge ids) warm-starts every graph;
-    ``transit`` (int32 [M]) gives optimal cycle ratios."""
+    ``transit`` (int32 [M]) gives optimal cycle ratios.  Graphs with at most
+    ``small_vertices`` vertices (0: the library default, < 0: none) are solved
+    one per thread block by the persistent per-graph kernel."""
     lib = _native.load()
     vp = _dev_i32(graph_vptr, "graph_vptr")
     rp = _dev_i32(row_ptr, "row_ptr")
@@ -231,6 +234,7 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
     opt.wait_limit_ms = int(wait_limit_ms)
+    opt.batch_small_vertices = int(small_vertices)
     init = _init_policy(init_policy, N)
     if init is not None:
         opt.init_policy = init.data_ptr()

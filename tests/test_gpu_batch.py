@@ -158,3 +158,63 @@ def test_sharded_batch_on_one_rank_equals_the_batched_call():
     for g in range(b.G):
         assert res.cycle(g, b.graph_vptr).tolist() == sol.cycle(g).cpu().tolist()
     assert (res.owner == 0).all()
+
+
+@pytest.mark.parametrize("small", [-1, 64, 1500, 1 << 20])
+def test_per_block_path_and_union_path_agree(small):
+    """The persistent per-graph kernel (one block runs every iteration of a
+    graph) and the disjoint-union path give every graph the same value and
+    cycle as the oracle, whatever the size threshold that splits the batch
+    between them (-1: union only; 1 << 20: every graph per block)."""
+    rng = np.random.default_rng(1111062777)
+    graphs = synth.batch_graphs(G=40, nmin=10, nmax=6000)
+    graphs += [synth.tiny_random(rng, int(rng.integers(1, 12)), max_extra=3, wlo=-50, whi=50)
+               for _ in range(40)]
+    b = synth.concat(graphs)
+    d = torch.device("cuda")
+    args = [torch.from_numpy(x).to(d) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    sol = ocm.solve_batch(*args, b.mode, small_vertices=small)
+    _check_against_oracle(b, sol, graphs)
+    sizes = np.diff(b.graph_vptr)
+    edges = np.diff(b.row_ptr[b.graph_vptr])
+    expect = int(((sizes <= small) & (edges <= 16 * small)).sum()) if small > 0 else 0
+    assert sol.stats["batch_small_graphs"] == expect
+    # the iteration count is the largest over the graphs, on either path
+    iters = max(oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode).iterations for g in graphs)
+    assert sol.stats["iterations"] == iters
+
+
+def test_per_block_path_reports_the_iteration_cap():
+    graphs = synth.batch_graphs(G=12, nmin=200, nmax=900)
+    b = synth.concat(graphs)
+    d = torch.device("cuda")
+    args = [torch.from_numpy(x).to(d) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    need = max(oracle.howard(g.row_ptr, g.col_idx, g.w, g.mode).iterations for g in graphs)
+    with pytest.raises(ocm.OCMError) as ei:
+        ocm.solve_batch(*args, b.mode, small_vertices=1 << 20, max_iters=need)
+    assert ei.value.status == -5
+    sol = ocm.solve_batch(*args, b.mode, small_vertices=1 << 20, max_iters=need + 1)
+    _check_against_oracle(b, sol, graphs)
+
+
+@pytest.mark.parametrize("small", [-1, 1 << 20])
+def test_batch_members_with_hub_vertices(small):
+    """Members with a vertex of thousands of out-edges: the per-block sweep
+    serves such a vertex with a whole warp; values and cycles are the oracle's."""
+    graphs = [synth.hub4m(n=n, hub_deg=deg, seed=1111062790 + i)
+              for i, (n, deg) in enumerate([(300, 40), (2000, 5000), (50, 33), (4000, 70000)])]
+    graphs += synth.batch_graphs(G=6, nmin=30, nmax=500)
+    b = synth.concat(graphs)
+    d = torch.device("cuda")
+    args = [torch.from_numpy(x).to(d) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    sol = ocm.solve_batch(*args, b.mode, small_vertices=small)
+    _check_against_oracle(b, sol, graphs)
+    if small > 0:
+        assert sol.stats["batch_small_graphs"] == len(graphs)
+
+
+def test_automatic_split_sends_a_batch_of_small_graphs_to_the_per_block_path():
+    graphs = synth.batch_graphs(G=30, nmin=50, nmax=3000)
+    b = synth.concat(graphs)
+    sol = _solve_batch(b)
+    assert sol.stats["batch_small_graphs"] == len(graphs)
