@@ -127,7 +127,7 @@ typedef struct ocm_options {
      * graphs largest first from a queue; the larger graphs are solved
      * together as one disjoint union afterwards.  0 = automatic: every graph
      * with at most max(4,096, 4 N / B) vertices, B the number of resident
-     * blocks of that kernel (304 on a GB300), so that only graphs large next
+     * blocks of that kernel (152 on a GB300), so that only graphs large next
      * to the batch's share per block take the union path; < 0 = every graph
      * takes the union path.  Results do not depend on it.  Not used with
      * transit times or per-vertex outputs (every graph then takes the union

@@ -117,3 +117,80 @@ def tune(row_ptr: torch.Tensor, col_idx: torch.Tensor, w: torch.Tensor, mode="ma
                                                                "sweep_threads", "sweep_ms")}
             _save_table(tab)
     return result
+
+
+# ----------------------------------------------------------------------------
+# Batched form: the size limit of the per-block path (ocm_options.
+# batch_small_vertices: 0 automatic, < 0 union only, else a vertex count) and
+# the union path's sweep layout, timed as whole ocm_solve_batch calls.
+# ----------------------------------------------------------------------------
+BATCH_CANDIDATES = ([(small, CLASSES, 8, 512) for small in (0, -1, 4096, 65536)] +
+                    [(-1, CLASSES, epl, thr) for epl in (4, 16) for thr in (256, 512)])
+
+
+def batch_signature(graph_vptr: torch.Tensor, row_ptr: torch.Tensor) -> str:
+    """Batch shape buckets: log2 of the graph count, of the total vertex count,
+    of the largest graph and of the mean degree (half steps)."""
+    sizes = (graph_vptr[1:] - graph_vptr[:-1]).to(torch.float64)
+    G = int(sizes.numel())
+    N = int(row_ptr.numel() - 1)
+    M = int(row_ptr[-1])
+    mean = M / max(N, 1)
+    return (f"batch_g{math.ceil(math.log2(max(G, 2)))}_n{math.ceil(math.log2(max(N, 2)))}"
+            f"_x{math.ceil(math.log2(max(float(sizes.max()), 2.0)))}"
+            f"_d{round(2 * math.log2(max(mean, 1.0)))}")
+
+
+def lookup_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor):
+    with _lock:
+        entry = _load_table().get(batch_signature(graph_vptr, row_ptr))
+    if not entry or "batch_small_vertices" not in entry:
+        return None
+    return (int(entry["batch_small_vertices"]), int(entry["sweep_kind"]),
+            int(entry["edges_per_lane"]), int(entry["sweep_threads"]))
+
+
+def tune_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor,
+               w: torch.Tensor, mode="max", *, candidates=BATCH_CANDIDATES, reps: int = 2,
+               save: bool = True) -> dict:
+    """Time ocm_solve_batch (CUDA events on the current stream, best of
+    `reps` after a warm-up) for every (batch_small_vertices, sweep_kind,
+    edges_per_lane, sweep_threads) candidate, check that every candidate gives
+    the same results, and record the fastest for this batch's signature."""
+    from .ocm import solve_batch, workspace_bytes_batch
+    G, N, M = graph_vptr.numel() - 1, row_ptr.numel() - 1, col_idx.numel()
+    ws = torch.empty(workspace_bytes_batch(G, N, M), dtype=torch.uint8, device=row_ptr.device)
+    stream = torch.cuda.current_stream(row_ptr.device)
+    timings, ref = {}, None
+    for small, kind, epl, thr in candidates:
+        kw = dict(workspace=ws, stream=stream, small_vertices=small, sweep_kind=kind,
+                  edges_per_lane=epl, sweep_threads=thr)
+        sol = solve_batch(graph_vptr, row_ptr, col_idx, w, mode, **kw)
+        got = (sol.num.clone(), sol.den.clone(), sol.cycle_len.clone())
+        if ref is None:
+            ref = got
+        elif not all(torch.equal(a, b) for a, b in zip(ref, got)):
+            raise RuntimeError("launch parameters changed the result")
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solve_batch(graph_vptr, row_ptr, col_idx, w, mode, **kw)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        timings[f"{small}x{kind}x{epl}x{thr}"] = best
+    pick = min(timings, key=timings.get)
+    small, kind, epl, thr = (int(x) for x in pick.split("x"))
+    result = {"batch_small_vertices": small, "sweep_kind": kind, "edges_per_lane": epl,
+              "sweep_threads": thr, "batch_ms": timings[pick], "timings_ms": timings,
+              "signature": batch_signature(graph_vptr, row_ptr)}
+    if save:
+        with _lock:
+            tab = _load_table()
+            tab[result["signature"]] = {k: result[k] for k in (
+                "batch_small_vertices", "sweep_kind", "edges_per_lane", "sweep_threads",
+                "batch_ms")}
+            _save_table(tab)
+    return result

@@ -26,8 +26,8 @@
 
 namespace ocm {
 
-constexpr int kSmallThreads = 512;
-constexpr int kSU = 2;   // vertices per thread per pass of a jump round (64 registers)
+constexpr int kSmallThreads = 1024;
+constexpr int kSU = 4;   // vertices per thread per pass of a jump round (64 registers)
 constexpr int kSmallBuckets = 32;
 
 // Size buckets of the queue: floor(log2(n_g)), largest first.
@@ -95,237 +95,88 @@ static __device__ __forceinline__ int block_sum(int x, int *s_red) {
     return t;
 }
 
-// Appends item to the block's list (warp-aggregated shared-memory counter).
-static __device__ __forceinline__ void small_append(int *list, int *s_cnt, bool pred, int item) {
-    const int lane = threadIdx.x & 31;
-    const unsigned mask = __ballot_sync(0xffffffffu, pred);
-    int base = 0;
-    if (mask) {
-        const int leader = __ffs(mask) - 1;
-        if (lane == leader) base = atomicAdd(s_cnt, __popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-    }
-    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = item;
-}
-
-constexpr int kMinMaskS = 0x7fffffff;
-
-// Policy evaluation number `eval` of graph [v0, v1) inside one block, the
-// steps and state encodings of evaluate_kernel: detection by window minima
-// with a "switched in the last sweep" bit ORed over the windows; value
-// propagation only for vertices whose path or cycle holds a switched vertex
-// (the others keep the last evaluation's (root, len, S), which both value
-// buffers hold); worklists of unfinished vertices (lists 0 and 1 at the
-// graph's offset), a vertex finished in a round copied into the other buffer
-// in the next one, so no buffer is written while it is read.  On return every
-// vertex has its final (~root, len, S) in jls[0] and jls[1] and its record
-// {V, rank, q}; the cycle records sit at [v0, v0 + K) and the packed best
-// (rank, INT_MAX - root) in *s_best.  Returns false on an error (recorded in
-// the control block).
-static __device__ bool small_evaluate(int v0, int v1, int eval, const Workspace &ws, int *s_red,
-                                      int *s_k, int *s_cnt, unsigned long long *s_best) {
+// Policy evaluation of graph [v0, v1) inside one block, the steps of
+// evaluate_kernel over every vertex of the graph in every round (no
+// worklists: a graph's state stays in L1/L2 while its block works on it, and
+// a dense pass costs less than keeping lists): cycle detection by doubling
+// with window minima, resolved vertices holding J = ~root; then value
+// propagation with (len, S) until the root, which is terminal.  On return
+// every vertex has its root (rep), its final (~root, len, S) in jls[0], its
+// record {V, rank, q}; the cycle records sit at [v0, v0 + K) and the packed
+// best (rank, INT_MAX - root) in *s_best.  Returns false on an error
+// (recorded in the control block).
+static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *s_red, int *s_k,
+                                      unsigned long long *s_best) {
     const int n = v1 - v0;
     int lg = 0;
     while ((1 << lg) < n) ++lg;
     Ctrl *c = ws.ctrl;
-    int *LA = ws.list[0] + v0, *LB = ws.list[1] + v0;
-    const unsigned W = blockDim.x;
-    // ---- cycle detection.  Unresolved {J, M | dirty << 31}; resolved
-    //      {~root, dirty}.
-    if (threadIdx.x == 0) *s_cnt = 0;
+    JM *X = ws.jm[0], *Y = ws.jm[1];
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) X[v] = JM{ws.succ[v], v};
     __syncthreads();
-    int cnt = n;
     for (int r = 0;; ++r) {
-        const JM *in = ws.jm[r & 1];
-        JM *out = ws.jm[(r + 1) & 1];
-        const int *lin = (r & 1) ? LB : LA;
-        int *lout = (r & 1) ? LA : LB;
-        int work = 0, kept = 0;
-        for (int i0 = 0; i0 < cnt; i0 += kSU * W) {
-            int item[kSU], ap[kSU];
+        int pend = 0;
+        for (int base = v0 + (int)threadIdx.x; base < v1; base += kSU * blockDim.x) {
             JM s[kSU], t[kSU];
 #pragma unroll
             for (int u = 0; u < kSU; ++u) {
-                const int i = i0 + u * (int)W + (int)threadIdx.x;
-                item[u] = i < cnt ? ((r == 0) ? v0 + i : lin[i]) : INT_MIN;
+                const int v = base + u * (int)blockDim.x;
+                s[u] = v < v1 ? X[v] : JM{-1, 0};
             }
 #pragma unroll
-            for (int u = 0; u < kSU; ++u) {
-                const int it = item[u];
-                if (it == INT_MIN) continue;
-                const int v = it < 0 ? ~it : it;
-                if (r == 0) {
-                    s[u] = JM{ws.succ[v], v | ((ws.sw_iter[v] == eval) ? INT_MIN : 0)};
-                } else {
-                    s[u] = in[v];
-                    ap[u] = it >= 0 ? ws.aprev[v] : 0;
-                }
-            }
+            for (int u = 0; u < kSU; ++u)
+                if (s[u].J >= 0) t[u] = X[s[u].J];
 #pragma unroll
             for (int u = 0; u < kSU; ++u) {
-                const int it = item[u];
-                if (it == INT_MIN || it < 0) continue;
-                const int J = s[u].J;
-                t[u] = (r == 0) ? JM{ws.succ[J], J | ((ws.sw_iter[J] == eval) ? INT_MIN : 0)}
-                                : in[J];
-            }
-#pragma unroll
-            for (int u = 0; u < kSU; ++u) {
-                const int it = item[u];
-                bool keep = false, resolved = false;
-                int v = 0;
-                if (it != INT_MIN) {
-                    v = it < 0 ? ~it : it;
-                    if (it < 0) {
-                        out[v] = s[u];        // resolved last round: copy forward
-                    } else {
-                        const int sdirty = (int)((unsigned)s[u].M >> 31);
-                        int root = -1, dirty = 0;
-                        if (t[u].J < 0) {
-                            root = ~t[u].J;
-                            dirty = sdirty | t[u].M;
-                        } else if (r > 0 && (t[u].M & kMinMaskS) == ap[u]) {
-                            root = ap[u];
-                            dirty = sdirty | (int)((unsigned)t[u].M >> 31);
-                        } else {
-                            const int m = min(s[u].M & kMinMaskS, t[u].M & kMinMaskS);
-                            out[v] = JM{t[u].J, m | ((s[u].M | t[u].M) & INT_MIN)};
-                            ws.aprev[v] = t[u].M & kMinMaskS;
-                            keep = true;
-                        }
-                        if (root >= 0) {
-                            out[v] = JM{~root, dirty};
-                            ws.rep[v] = root;
-                            resolved = true;
-                        }
-                        ++work;
-                    }
-                }
-                small_append(lout, s_cnt, keep || resolved, keep ? v : ~v);
-                kept += keep;
+                const int v = base + u * (int)blockDim.x;
+                if (v >= v1) continue;
+                if (s[u].J < 0) { Y[v] = s[u]; continue; }
+                int root = -1;
+                if (t[u].J < 0) root = ~t[u].J;
+                else if (r > 0 && t[u].M == ws.aprev[v]) root = t[u].M;
+                if (root >= 0) { Y[v] = JM{~root, 0}; ws.rep[v] = root; }
+                else { Y[v] = JM{t[u].J, min(s[u].M, t[u].M)}; ws.aprev[v] = t[u].M; ++pend; }
             }
         }
-        __syncthreads();
-        cnt = *s_cnt;
-        const int left = block_sum(work, s_red);
-        const int still = block_sum(kept, s_red);   // (its barriers order the counter reset)
-        if (threadIdx.x == 0) *s_cnt = 0;
-        __syncthreads();
-        if (left == 0) break;
-        if (still == 0) {
-            // all resolved: the states resolved in this round go into the
-            // buffer this round read, so that both hold every final state
-            for (int i = threadIdx.x; i < cnt; i += W) {
-                const int v = ~lout[i];
-                ws.jm[r & 1][v] = out[v];
-            }
-            __syncthreads();
-            break;
-        }
-        if (r + 1 >= lg + 4) {
-            if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
-            return false;
-        }
+        JM *tmp = X; X = Y; Y = tmp;
+        if (block_sum(pend, s_red) == 0) break;
+        if (r + 1 > lg + 4) { if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect); return false; }
     }
-    // ---- values: only dirty vertices; dirty roots are final at once, as is
-    //      a dirty vertex whose successor is a root; the rest jump
-    cnt = 0;
-    {
-        int work = 0;
-        for (int v = v0 + (int)threadIdx.x; v < v1 + (int)((W - (n % W)) % W); v += W) {
-            bool keep = false;
-            if (v < v1) {
-                const JM d = ws.jm[0][v];
-                if (d.M) {
-                    const int root = ~d.J;
-                    JLS st;
-                    bool fin = true;
-                    if (root == v) {
-                        st = JLS{~v, 0, 0};
-                    } else {
-                        const int sv = ws.succ[v];
-                        fin = (ws.rep[sv] == sv);
-                        st = JLS{fin ? ~sv : sv, 1, (long long)ws.wpi[v]};
-                    }
-                    ws.jls[0][v] = st;
-                    if (fin) ws.jls[1][v] = st;
-                    keep = !fin;
-                }
-            }
-            small_append(LA, s_cnt, keep, v);
-            work += keep;
-        }
-        __syncthreads();
-        cnt = *s_cnt;
-        const int left0 = block_sum(work, s_red);
-        if (threadIdx.x == 0) *s_cnt = 0;
-        __syncthreads();
-        if (left0 != 0) {
-            for (int j = 1;; ++j) {
-                const JLS *in = ws.jls[(j + 1) & 1];
-                JLS *out = ws.jls[j & 1];
-                const int *lin = (j & 1) ? LA : LB;
-                int *lout = (j & 1) ? LB : LA;
-                int work2 = 0, kept = 0;
-                for (int i0 = 0; i0 < cnt; i0 += kSU * W) {
-                    int item[kSU];
-                    JLS s[kSU], t[kSU];
-#pragma unroll
-                    for (int u = 0; u < kSU; ++u) {
-                        const int i = i0 + u * (int)W + (int)threadIdx.x;
-                        item[u] = i < cnt ? lin[i] : INT_MIN;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kSU; ++u)
-                        if (item[u] != INT_MIN) s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
-#pragma unroll
-                    for (int u = 0; u < kSU; ++u)
-                        if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
-#pragma unroll
-                    for (int u = 0; u < kSU; ++u) {
-                        const int it = item[u];
-                        bool keep = false, fin = false;
-                        int v = 0;
-                        if (it != INT_MIN) {
-                            v = it < 0 ? ~it : it;
-                            if (it < 0) {
-                                out[v] = s[u];    // final last round: copy forward
-                            } else {
-                                const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
-                                out[v] = nu;
-                                fin = nu.J < 0;
-                                keep = !fin;
-                                ++work2;
-                            }
-                        }
-                        small_append(lout, s_cnt, keep || fin, keep ? v : ~v);
-                        kept += keep;
-                    }
-                }
-                __syncthreads();
-                cnt = *s_cnt;
-                const int left = block_sum(work2, s_red);
-                const int still = block_sum(kept, s_red);
-                if (threadIdx.x == 0) *s_cnt = 0;
-                __syncthreads();
-                if (left == 0) break;
-                if (still == 0) {
-                    for (int i = threadIdx.x; i < cnt; i += W) {
-                        const int v = ~lout[i];
-                        ws.jls[(j + 1) & 1][v] = out[v];
-                    }
-                    __syncthreads();
-                    break;
-                }
-                if (j + 1 > lg + 3) {
-                    if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
-                    return false;
-                }
-            }
-        }
-        // both buffers hold every final state from here on
+    JLS *A = ws.jls[0], *B = ws.jls[1];
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
+        const int root = ws.rep[v];
+        JLS st;
+        if (root == v) st = JLS{~v, 0, 0};
+        else { const int sv = ws.succ[v]; st = JLS{ws.rep[sv] == sv ? ~sv : sv, 1, (long long)ws.wpi[v]}; }
+        A[v] = st;
     }
-    const JLS *A = ws.jls[0];
+    __syncthreads();
+    for (int r = 0;; ++r) {
+        int pend = 0;
+        for (int base = v0 + (int)threadIdx.x; base < v1; base += kSU * blockDim.x) {
+            JLS s[kSU], t[kSU];
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) { const int v = base + u * (int)blockDim.x; s[u] = v < v1 ? A[v] : JLS{-1, 0, 0}; }
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) if (s[u].J >= 0) t[u] = A[s[u].J];
+#pragma unroll
+            for (int u = 0; u < kSU; ++u) {
+                const int v = base + u * (int)blockDim.x;
+                if (v >= v1) continue;
+                if (s[u].J < 0) { B[v] = s[u]; continue; }
+                const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                B[v] = nu; pend += nu.J >= 0;
+            }
+        }
+        JLS *tmp = A; A = B; B = tmp;
+        if (block_sum(pend, s_red) == 0) break;
+        if (r + 1 > lg + 3) { if (threadIdx.x == 0) atomicOr(&c->err, kErrValue); return false; }
+    }
+    if (A != ws.jls[0])
+        for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) ws.jls[0][v] = A[v];
+    __syncthreads();
+    const unsigned W = blockDim.x;
+    A = ws.jls[0];
     // ---- cycles: mean W/L reduced, exact key, rank among this graph's cycles
     if (threadIdx.x == 0) {
         *s_k = 0;
@@ -378,7 +229,7 @@ static __device__ bool small_evaluate(int v0, int v1, int eval, const Workspace 
 
 // Switch decision of vertex v given the best candidate and the candidate of
 // its current policy edge (strict improvement, Alg. 1).
-static __device__ __forceinline__ int small_switch(int v, int eval, const Cand &best,
+static __device__ __forceinline__ int small_switch(int v, const Cand &best,
                                                    const Cand &own, const int *__restrict__ col,
                                                    const int *__restrict__ w, int sign,
                                                    const Workspace &ws) {
@@ -390,7 +241,6 @@ static __device__ __forceinline__ int small_switch(int v, int eval, const Cand &
         ws.pi[v] = best.e;
         ws.succ[v] = col[best.e];
         ws.wpi[v] = sign * w[best.e];
-        ws.sw_iter[v] = eval + 1;   // changed for the next evaluation
         return 1;
     }
     return 0;
@@ -407,7 +257,7 @@ static __device__ __forceinline__ Cand small_cand(const int *__restrict__ col,
 // improve_kernel): a thread per vertex of out-degree <= 32, a warp per vertex
 // with more (lanes stride its edges, shuffles combine); returns the number of
 // switches.
-static __device__ int small_sweep(int v0, int v1, int eval, const int *__restrict__ row_ptr,
+static __device__ int small_sweep(int v0, int v1, const int *__restrict__ row_ptr,
                                   const int *__restrict__ col, const int *__restrict__ w,
                                   int sign, const Workspace &ws, int *s_red) {
     int sw = 0;
@@ -426,7 +276,7 @@ static __device__ int small_sweep(int v0, int v1, int eval, const int *__restric
             if (e == pv) own = x;
             if (better(x, best)) best = x;
         }
-        sw += small_switch(v, eval, best, own, col, w, sign, ws);
+        sw += small_switch(v, best, own, col, w, sign, ws);
     }
     if (__syncthreads_or(heavy_seen)) {
         const int lane = threadIdx.x & 31;
@@ -455,18 +305,18 @@ static __device__ int small_sweep(int v0, int v1, int eval, const int *__restric
                 z.key = __shfl_xor_sync(0xffffffffu, own.key, o);
                 if (z.e != INT_MAX) own = z;   // one lane met the policy edge
             }
-            if (lane == 0) sw += small_switch(v, eval, best, own, col, w, sign, ws);
+            if (lane == 0) sw += small_switch(v, best, own, col, w, sign, ws);
         }
     }
     return block_sum(sw, s_red);
 }
 
-__global__ void __launch_bounds__(kSmallThreads, 2)
+__global__ void __launch_bounds__(kSmallThreads, 1)
 small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, const int *__restrict__ queue,
                    long long max_iters, Workspace ws, BatchState bs) {
     __shared__ int s_red[kSmallThreads / 32];
-    __shared__ int s_task, s_k, s_stop, s_cnt;
+    __shared__ int s_task, s_k, s_stop;
     __shared__ unsigned long long s_best;
     Ctrl *c = ws.ctrl;
     const int total = c->small_total;
@@ -481,11 +331,11 @@ small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         long long it = 0;
         bool ok = true;
         for (;;) {
-            if (!small_evaluate(v0, v1, (int)it, ws, s_red, &s_k, &s_cnt, &s_best)) {
+            if (!small_evaluate(v0, v1, ws, s_red, &s_k, &s_best)) {
                 ok = false;
                 break;
             }
-            const int sw = small_sweep(v0, v1, (int)it, row_ptr, col, w, sign, ws, s_red);
+            const int sw = small_sweep(v0, v1, row_ptr, col, w, sign, ws, s_red);
             if (sw == 0) break;
             if (++it >= max_iters) {
                 if (threadIdx.x == 0) c->not_converged = 1;

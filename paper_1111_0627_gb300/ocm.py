@@ -207,13 +207,17 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
                 stream=None, max_iters: int = 0, flags: int = 0,
                 init_policy: torch.Tensor | None = None,
                 transit: torch.Tensor | None = None, wait_limit_ms: int = 0,
-                small_vertices: int = 0) -> BatchSolution:
+                small_vertices: int = 0, sweep_kind: int = 0, edges_per_lane: int = 0,
+                sweep_threads: int = 0, tune: bool = False) -> BatchSolution:
     """Optimal cycle means of G graphs given as one disjoint-union CSR
     (``ocm_solve_batch``); each result equals solving that graph alone.
     ``init_policy`` (int32 [N], global edge ids) warm-starts every graph;
     ``transit`` (int32 [M]) gives optimal cycle ratios.  Graphs with at most
     ``small_vertices`` vertices (0: the library default, < 0: none) are solved
-    one per thread block by the persistent per-graph kernel."""
+    one per thread block by the persistent per-graph kernel.  ``tune=True``
+    uses the split and sweep launch parameters that
+    :func:`paper_1111_0627_gb300.autotune.tune_batch` recorded for batches of
+    this shape (results never depend on them)."""
     lib = _native.load()
     vp = _dev_i32(graph_vptr, "graph_vptr")
     rp = _dev_i32(row_ptr, "row_ptr")
@@ -234,7 +238,15 @@ def solve_batch(graph_vptr: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.
     opt.max_iters = int(max_iters)
     opt.flags = int(flags)
     opt.wait_limit_ms = int(wait_limit_ms)
+    if tune and not (small_vertices or sweep_kind or edges_per_lane or sweep_threads):
+        from .autotune import lookup_batch
+        found = lookup_batch(vp, rp)
+        if found:
+            small_vertices, sweep_kind, edges_per_lane, sweep_threads = found
     opt.batch_small_vertices = int(small_vertices)
+    opt.sweep_kind = int(sweep_kind)
+    opt.edges_per_lane = int(edges_per_lane)
+    opt.sweep_threads = int(sweep_threads)
     init = _init_policy(init_policy, N)
     if init is not None:
         opt.init_policy = init.data_ptr()

@@ -218,3 +218,22 @@ def test_automatic_split_sends_a_batch_of_small_graphs_to_the_per_block_path():
     b = synth.concat(graphs)
     sol = _solve_batch(b)
     assert sol.stats["batch_small_graphs"] == len(graphs)
+
+
+def test_batch_autotuner_picks_a_candidate_and_results_stay_exact(tmp_path, monkeypatch):
+    """autotune.tune_batch times the per-block/union split and the union's
+    sweep layout on the caller's batch, checks that every candidate gives the
+    same results, and solve_batch(tune=True) uses the recorded choice."""
+    monkeypatch.setenv("OCM_TUNE_FILE", str(tmp_path / "tune.json"))
+    graphs = synth.batch_graphs(G=40, nmin=20, nmax=5000)
+    b = synth.concat(graphs)
+    d = torch.device("cuda")
+    args = [torch.from_numpy(x).to(d) for x in (b.graph_vptr, b.row_ptr, b.col_idx, b.w)]
+    cands = [(0, 1, 8, 512), (-1, 1, 4, 256), (1000, 1, 16, 512)]
+    res = ocm.autotune.tune_batch(*args, b.mode, candidates=cands)
+    picked = (res["batch_small_vertices"], res["sweep_kind"], res["edges_per_lane"],
+              res["sweep_threads"])
+    assert picked in cands and len(res["timings_ms"]) == 3
+    assert ocm.autotune.lookup_batch(args[0], args[1]) == picked
+    sol = ocm.solve_batch(*args, b.mode, tune=True)
+    _check_against_oracle(b, sol, graphs)
