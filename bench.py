@@ -219,7 +219,11 @@ CLASSES = ["init", "sweep", "evaluate", "extract"]
 # proportion to n (evaluation) and n + m (sweep) once the graph exceeds L2.
 KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
                   "sweep": ("sweep.cu", "common.cuh")}
-TRAFFIC = {}
+TRAFFIC = {
+    # n = 2^23 capture (3 launches from the middle of a solve, mean) x 4
+    ("locality32m", "evaluate"): (4 * (4.237341e9 + 4.036051e9), "eaf1269e9732e595"),
+    ("locality32m", "sweep"): (4 * (1.728532e9 + 0.177541e9), "85bcbfdb571c126c"),
+}
 
 
 def job_rate(units_per_step: float, steps: int, local_ms: float, world: int, device):
