@@ -191,6 +191,22 @@ typedef struct ocm_options {
  * may differ from the default form's. */
 #define OCM_FLAG_SINGLE_LAMBDA 4
 
+/* Choice of the policy evaluation (results are the same bits either way).
+ * By default ocm_solve measures, once per solve, the fraction of edges whose
+ * target lies in the same block range of the evaluation grid as its source
+ * (ranges of about n / 152 consecutive vertices on a GB300); graphs of at
+ * least 2^18 vertices with at least 85% of such edges get the two-level
+ * evaluation: every block first resolves the policy paths inside its own
+ * range with block barriers only, leaving the vertices whose successor lies
+ * outside it ("exits"), and the cycles that cross ranges are then found and
+ * valued on the much smaller graph of the exits.  OCM_FLAG_EVAL_LOCAL forces
+ * the two-level evaluation, OCM_FLAG_EVAL_GLOBAL forbids it (setting both is
+ * OCM_ERR_INVALID_ARG).  The two-level form serves ocm_solve without transit
+ * times and without OCM_FLAG_SINGLE_LAMBDA; the other calls always use the
+ * one-level evaluation. */
+#define OCM_FLAG_EVAL_LOCAL 8
+#define OCM_FLAG_EVAL_GLOBAL 16
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */

@@ -62,6 +62,7 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.jt[0] = static_cast<long long *>(take(8 * N));
     w.jt[1] = static_cast<long long *>(take(8 * N));
     w.recp = static_cast<long long *>(take(8 * N));
+    w.root_mark = static_cast<int *>(take(4 * N));
     w.transit = nullptr;
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
@@ -281,6 +282,7 @@ struct StepArgs {
     BatchState bs;
     bool batch;
     bool single;              // the paper's single-lambda form: rebuild after each evaluation
+    bool local;               // the two-level evaluation (locality of the policy graph)
     SingleWs sg;
     int cls_cnt[kClassSlots];
     int heavy_edges;
@@ -289,7 +291,7 @@ struct StepArgs {
 // Launches one step; returns the number of kernels, or -1.
 static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHandle handle,
                        cudaStream_t st) {
-    int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st);
+    int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st, a.local);
     if (le < 0) return -1;
     if (a.single) {
         if (launch_connect(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.sg, st) < 0) return -1;
@@ -315,13 +317,13 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges;
+    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local;
     long long N2, max_iters;
     int cls_cnt[kClassSlots];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
             ctrl != o.ctrl || vptr != o.vptr || transit != o.transit || n != o.n || m != o.m ||
-            sign != o.sign || single != o.single ||
+            sign != o.sign || single != o.single || local != o.local ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters || heavy_edges != o.heavy_edges)
             return false;
@@ -365,6 +367,7 @@ LoopKey make_key(const StepArgs &a) {
     k.stall = a.stall;
     k.G = a.bs.G;
     k.single = a.single ? 1 : 0;
+    k.local = a.local ? 1 : 0;
     k.N2 = a.N2;
     k.max_iters = a.max_iters;
     for (int c = 0; c < kClassSlots; ++c) k.cls_cnt[c] = a.cls_cnt[c];
@@ -589,6 +592,17 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
                        bs ? &b : nullptr, st);
     launches += 3;
+    // the two-level evaluation serves single graphs whose edges mostly stay
+    // inside the evaluation grid's block ranges (or when forced)
+    const int eval_flags = opt ? opt->flags & (OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL) : 0;
+    const bool local_ok = !bs && !ratio && !single && !(eval_flags & OCM_FLAG_EVAL_GLOBAL);
+    int local_R = 0;
+    if (local_ok) {
+        const int blocks = evaluate_local_blocks(n);
+        if (blocks <= 0) return OCM_ERR_CUDA;
+        local_R = (n + blocks - 1) / blocks;
+        launches += launch_locality_count(row_ptr, col_idx, n, local_R, ws, st);
+    }
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;
@@ -653,10 +667,14 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.bs = b;
     sa.batch = bs != nullptr;
     sa.single = single;
+    sa.local = local_ok && ((eval_flags & OCM_FLAG_EVAL_LOCAL) ||
+                            (n >= kLocalEvalMinN &&
+                             (double)h.local_edges >= kLocalEvalMinFraction * (double)m));
     sa.sg = sg;
     for (int c = 0; c < kClassSlots; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
     sa.heavy_edges = (kind == OCM_SWEEP_TILES) ? 0 : h.heavy_edges;
     if ((single && prepare_connect() != 0) || prepare_evaluate(ratio) != 0 ||
+        (sa.local && prepare_evaluate_local() != 0) ||
         (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
                                  : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
@@ -769,7 +787,10 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
               const ocm_options *opt, ocm_stats *stats) {
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA)))
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA |
+                               OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL)))
+        return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
         return OCM_ERR_INVALID_ARG;
     const bool single = opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA);
     if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))

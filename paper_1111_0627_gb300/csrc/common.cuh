@@ -35,6 +35,10 @@ constexpr int kSweepMaxThreads = 512;  // largest sweep block (ocm_options.sweep
 constexpr int kSweepThreads = 512;     // default sweep block
 constexpr int kClassifyBlock = 1024;   // vertices per classification block
 constexpr int kBatchSmallDefault = 4096;   // batch: smallest automatic per-block size limit
+// The two-level evaluation is chosen for graphs of at least this many
+// vertices with at least this fraction of edges inside their block range.
+constexpr int kLocalEvalMinN = 1 << 18;
+constexpr double kLocalEvalMinFraction = 0.85;
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
 // the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
@@ -116,6 +120,8 @@ struct Ctrl {
     int small_total;          // graphs in the queue
     int small_head;           // next queue position to pop
     int small_iters;          // largest iteration count among them
+    int node_cnt;             // two-level evaluation: exits listed (nodes of the contracted graph)
+    long long local_edges;    // edges whose target lies in the source's block range
 };
 
 // Default limit of a device-side wait, and the one the test-only stall flag
@@ -177,6 +183,7 @@ struct Workspace {
     int *tpi;             // [n] transit time of the policy edge
     long long *jt[2];     // [n] value jumping: transit time of the path from v to J
     long long *recp;      // [n] numerator p of the ratio of v's cycle (gathered by the sweep)
+    int *root_mark;       // [n] two-level evaluation: evaluation stamp of a root found on the node graph
     Ctrl *ctrl;
 };
 
@@ -334,7 +341,11 @@ int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sig
 int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
-                    cudaStream_t st);
+                    cudaStream_t st, bool local = false);
+int prepare_evaluate_local();
+int evaluate_local_blocks(int n);
+int launch_locality_count(const int *row_ptr, const int *col, int n, int R, Workspace ws,
+                          cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sign, int max_n,
                        long long N, long long max_iters, int *queue, Workspace ws, BatchState bs,

@@ -215,6 +215,133 @@ static __device__ bool radix_ranks(int K, const Workspace &ws, Ctrl *c, unsigned
     return grid_barrier(c, nblocks);
 }
 
+// The phases after every vertex has its final (~root, len, S) in jls[F]
+// (and, for the cycle ratio, its path time in jt[F]) and the roots are listed
+// in cyc_root[0, nrep): per-cycle means, exact keys and ranks, the best cycle
+// (per graph for a batch), and the records {V, rank, q} the next sweep
+// gathers.  Called by every thread of a cooperative evaluation kernel.
+template <bool RATIO>
+static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace &ws,
+                                     const BatchState &bs, long long *s_key) {
+    Ctrl *c = ws.ctrl;
+    const unsigned nblocks = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    const int first = blockIdx.x * blockDim.x;
+    constexpr bool ratio = RATIO;
+    // ------------------------------------------------------------ cycles
+    // mean W/L, or for the cycle ratio W/T with T the cycle's transit time
+    const int K = load_volatile(&c->nrep);
+    int qmax = 0;
+    for (int i = first + threadIdx.x; i < K; i += stride) {
+        int root = ws.cyc_root[i];
+        int x = ws.succ[root];
+        JLS st = ws.jls[F][x];
+        long long W = (long long)ws.wpi[root] + st.S;
+        long long L = 1 + (long long)st.len;
+        const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[F][x] : L;
+        long long g = gcd_ll(W, Tc);
+        long long p = W / g, q = Tc / g;
+        ws.cyc_p[i] = p;
+        ws.cyc_q[i] = (int)q;
+        ws.cyc_L[i] = (int)L;
+        if (!ratio) ws.cyc_key[i] = mean_key(p, q, N2);
+        ws.cyc_rank[i] = 0;   // summed into by the spread all-pairs count
+        qmax = max(qmax, (int)q);
+        ws.cid_of_root[root] = i;
+    }
+    if (ratio) {
+        // the order keys need N2 >= (largest denominator)^2 to separate
+        // distinct ratios; the current cycles' largest one keeps them small
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+        if (lane == 0 && qmax) atomicMax(&c->qmax, qmax);
+    }
+    if (!grid_barrier(c, nblocks)) return;
+    if (ratio) {
+        const long long qm = load_volatile(&c->qmax);
+        const long long N2r = qm * qm;
+        // |key| <= max|w| * N2r (every ratio is at most max|w| in size, t >= 1)
+        if ((__int128)N2r * (__int128)(c->maxabsw + 1) >= ((__int128)1 << 62)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrRatioKey);
+            return;
+        }
+        for (int i = first + threadIdx.x; i < K; i += stride)
+            ws.cyc_key[i] = mean_key(ws.cyc_p[i], ws.cyc_q[i], N2r);
+        if (!grid_barrier(c, nblocks)) return;
+    }
+    if (K > kRankDirectMax && n >= 2 * 256 * (int)gridDim.x) {
+        if (!radix_ranks(K, ws, c, nblocks)) return;
+    } else if (K >= kRankSplitMin) {
+        // all pairs, spread: (kEvalThreads cycles x kRankPairTile keys)
+        // pieces over every block, each adding its count of smaller keys to
+        // the cycle's rank (integer sums: the order of the adds is immaterial)
+        const int nI = (K + kEvalThreads - 1) / kEvalThreads;
+        const int nT = (K + kRankPairTile - 1) / kRankPairTile;
+        for (int wi = blockIdx.x; wi < nI * nT; wi += gridDim.x) {
+            const int t0 = (wi % nT) * kRankPairTile;
+            const int tn = min(kRankPairTile, K - t0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
+            __syncthreads();
+            const int i = (wi / nT) * kEvalThreads + threadIdx.x;
+            if (i < K) {
+                const long long key = ws.cyc_key[i];
+                int cnt = 0;
+                for (int q = 0; q < tn; ++q) cnt += (s_key[q] < key);
+                if (cnt) atomicAdd(&ws.cyc_rank[i], cnt);
+            }
+        }
+        if (!grid_barrier(c, nblocks)) return;
+    } else {
+        // all pairs: rank(i) = number of cycle keys below key(i)
+        for (int base = first; base < K; base += stride) {
+            const int i = base + threadIdx.x;
+            const long long key = i < K ? ws.cyc_key[i] : 0;
+            int rank = 0;
+            for (int t0 = 0; t0 < K; t0 += kRankTile) {
+                int tn = min(kRankTile, K - t0);
+                __syncthreads();
+                for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
+                __syncthreads();
+                for (int q = 0; q < tn; ++q) rank += (s_key[q] < key);
+            }
+            if (i < K) ws.cyc_rank[i] = rank;
+        }
+    }
+    for (int i = first + threadIdx.x; i < K; i += stride) {
+        const int rank = ws.cyc_rank[i];
+        const int root = ws.cyc_root[i];
+        unsigned long long packed = ((unsigned long long)(unsigned)rank << 32) |
+                                    (unsigned)(INT_MAX - root);
+        atomicMax(&c->best, packed);
+        // batched: Alg. 4's region-specific vote, one region per graph,
+        // deterministic because the packed key is a total order
+        if (bs.G) atomicMax(&bs.gbest[bs.gid[root]], packed);
+    }
+    if (!grid_barrier(c, nblocks)) return;
+
+    // ------------------------------------------------------- materialise
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->changed = 0;
+        c->switched = 0;
+    }
+    for (int v = first + threadIdx.x; v < n; v += stride) {
+        if (bs.G && bs.gconv[bs.gid[v]]) continue;
+        JLS st = ws.jls[F][v];
+        int i = ws.cid_of_root[~st.J];
+        long long p = ws.cyc_p[i];
+        int q = ws.cyc_q[i];
+        Rec rec;
+        const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
+        rec.V = (long long)q * st.S - p * T;
+        rec.rank = ws.cyc_rank[i];
+        rec.q = q;
+        ws.rec[v] = rec;
+        if (ratio) ws.recp[v] = p;
+    }
+}
+
 constexpr int kMinMask = 0x7fffffff;
 
 // RATIO: optimal cycle ratio (transit times carried through values and
@@ -511,117 +638,7 @@ evaluate_kernel(int n, long long N2, int max_detect, int max_value, int stall_te
         }
     }
 
-    // ------------------------------------------------------------ cycles
-    // mean W/L, or for the cycle ratio W/T with T the cycle's transit time
-    const int K = load_volatile(&c->nrep);
-    int qmax = 0;
-    for (int i = first + threadIdx.x; i < K; i += stride) {
-        int root = ws.cyc_root[i];
-        int x = ws.succ[root];
-        JLS st = ws.jls[F][x];
-        long long W = (long long)ws.wpi[root] + st.S;
-        long long L = 1 + (long long)st.len;
-        const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[F][x] : L;
-        long long g = gcd_ll(W, Tc);
-        long long p = W / g, q = Tc / g;
-        ws.cyc_p[i] = p;
-        ws.cyc_q[i] = (int)q;
-        ws.cyc_L[i] = (int)L;
-        if (!ratio) ws.cyc_key[i] = mean_key(p, q, N2);
-        ws.cyc_rank[i] = 0;   // summed into by the spread all-pairs count
-        qmax = max(qmax, (int)q);
-        ws.cid_of_root[root] = i;
-    }
-    if (ratio) {
-        // the order keys need N2 >= (largest denominator)^2 to separate
-        // distinct ratios; the current cycles' largest one keeps them small
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
-        if (lane == 0 && qmax) atomicMax(&c->qmax, qmax);
-    }
-    if (!grid_barrier(c, nblocks)) return;
-    if (ratio) {
-        const long long qm = load_volatile(&c->qmax);
-        const long long N2r = qm * qm;
-        // |key| <= max|w| * N2r (every ratio is at most max|w| in size, t >= 1)
-        if ((__int128)N2r * (__int128)(c->maxabsw + 1) >= ((__int128)1 << 62)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrRatioKey);
-            return;
-        }
-        for (int i = first + threadIdx.x; i < K; i += stride)
-            ws.cyc_key[i] = mean_key(ws.cyc_p[i], ws.cyc_q[i], N2r);
-        if (!grid_barrier(c, nblocks)) return;
-    }
-    if (K > kRankDirectMax && n >= 2 * 256 * (int)gridDim.x) {
-        if (!radix_ranks(K, ws, c, nblocks)) return;
-    } else if (K >= kRankSplitMin) {
-        // all pairs, spread: (kEvalThreads cycles x kRankPairTile keys)
-        // pieces over every block, each adding its count of smaller keys to
-        // the cycle's rank (integer sums: the order of the adds is immaterial)
-        const int nI = (K + kEvalThreads - 1) / kEvalThreads;
-        const int nT = (K + kRankPairTile - 1) / kRankPairTile;
-        for (int wi = blockIdx.x; wi < nI * nT; wi += gridDim.x) {
-            const int t0 = (wi % nT) * kRankPairTile;
-            const int tn = min(kRankPairTile, K - t0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
-            __syncthreads();
-            const int i = (wi / nT) * kEvalThreads + threadIdx.x;
-            if (i < K) {
-                const long long key = ws.cyc_key[i];
-                int cnt = 0;
-                for (int q = 0; q < tn; ++q) cnt += (s_key[q] < key);
-                if (cnt) atomicAdd(&ws.cyc_rank[i], cnt);
-            }
-        }
-        if (!grid_barrier(c, nblocks)) return;
-    } else {
-        // all pairs: rank(i) = number of cycle keys below key(i)
-        for (int base = first; base < K; base += stride) {
-            const int i = base + threadIdx.x;
-            const long long key = i < K ? ws.cyc_key[i] : 0;
-            int rank = 0;
-            for (int t0 = 0; t0 < K; t0 += kRankTile) {
-                int tn = min(kRankTile, K - t0);
-                __syncthreads();
-                for (int q = threadIdx.x; q < tn; q += blockDim.x) s_key[q] = ws.cyc_key[t0 + q];
-                __syncthreads();
-                for (int q = 0; q < tn; ++q) rank += (s_key[q] < key);
-            }
-            if (i < K) ws.cyc_rank[i] = rank;
-        }
-    }
-    for (int i = first + threadIdx.x; i < K; i += stride) {
-        const int rank = ws.cyc_rank[i];
-        const int root = ws.cyc_root[i];
-        unsigned long long packed = ((unsigned long long)(unsigned)rank << 32) |
-                                    (unsigned)(INT_MAX - root);
-        atomicMax(&c->best, packed);
-        // batched: Alg. 4's region-specific vote, one region per graph,
-        // deterministic because the packed key is a total order
-        if (bs.G) atomicMax(&bs.gbest[bs.gid[root]], packed);
-    }
-    if (!grid_barrier(c, nblocks)) return;
-
-    // ------------------------------------------------------- materialise
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->changed = 0;
-        c->switched = 0;
-    }
-    for (int v = first + threadIdx.x; v < n; v += stride) {
-        if (bs.G && bs.gconv[bs.gid[v]]) continue;
-        JLS st = ws.jls[F][v];
-        int i = ws.cid_of_root[~st.J];
-        long long p = ws.cyc_p[i];
-        int q = ws.cyc_q[i];
-        Rec rec;
-        const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
-        rec.V = (long long)q * st.S - p * T;
-        rec.rank = ws.cyc_rank[i];
-        rec.q = q;
-        ws.rec[v] = rec;
-        if (ratio) ws.recp[v] = p;
-    }
+    evaluate_tail<RATIO>(n, N2, F, ws, bs, s_key);
 }
 
 static int ceil_log2(long long x) {
@@ -653,11 +670,37 @@ int prepare_evaluate(bool ratio) {
     return (ratio ? evaluate_grid<true>() : evaluate_grid<false>()) > 0 ? 0 : -1;
 }
 
+__global__ void __launch_bounds__(kEvalThreads, 1)
+evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
+                      Workspace ws, BatchState bs);
+int evaluate_local_blocks(int n);
+
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
-// launch failure.
+// launch failure.  local: the two-level evaluation (single graphs without
+// transit times only).
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool local) {
     const bool ratio = ws.transit != nullptr;
+    if (local && !ratio && bs.G == 0) {
+        const int blocks = evaluate_local_blocks(n);
+        if (blocks <= 0) return -1;
+        const int R = (n + blocks - 1) / blocks;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kEvalThreads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        prof_begin(kProfEvaluate, st);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, evaluate_local_kernel, n, N2,
+                                                 ceil_log2(R) + 4, ceil_log2(n) + 4, stall_test,
+                                                 ws, bs);
+        prof_end(kProfEvaluate, st);
+        return e == cudaSuccess ? 1 : -1;
+    }
     int blocks = ratio ? evaluate_grid<true>() : evaluate_grid<false>();
     if (blocks <= 0) return -1;
     int need = (n + kEvalThreads - 1) / kEvalThreads;
@@ -790,6 +833,536 @@ void launch_outputs(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int
     prof_begin(kProfExtract, st);
     outputs_kernel<<<blocks, kThreads, 0, st>>>(n, ws, eta_num, eta_den, potential, policy);
     prof_end(kProfExtract, st);
+}
+
+}  // namespace ocm
+
+namespace ocm {
+
+// ---------------------------------------------------------------------------
+// Two-level evaluation, for policy graphs whose edges mostly stay inside the
+// contiguous vertex range a block of the cooperative grid owns (graphs with
+// locality, like the synthetic locality graph, where a policy path runs for
+// tens of steps inside a range before it leaves it).  Same results as
+// evaluate_kernel (root = smallest vertex of the cycle, (len, S) to its first
+// occurrence, the same records), computed in fewer jump rounds:
+//   local:  every block runs detection and value propagation on its own range
+//           with block barriers only, a vertex whose successor lies outside
+//           the range (an "exit") being terminal: each vertex ends with the
+//           root of a cycle inside the range, or with the exit its path
+//           leaves by, the path's length and weight to it, and the smallest
+//           vertex on the way;
+//   nodes:  the exits form a functional graph of their own (exit x -> the
+//           exit that succ(x)'s local path ends at, with the segment's length,
+//           weight and smallest vertex); detection by window minima on it
+//           finds the roots of the cycles that cross ranges (the smallest
+//           segment minimum on the node cycle is the cycle's smallest vertex);
+//   fix:    a block whose range holds such a root repeats its local phase with
+//           the root as one more terminal, so that every path reaching it
+//           stops at its first occurrence;
+//   values: (len, S) of every exit to its root by jumping on the node graph;
+//   expand: each vertex adds its local part to its exit's value.
+// The local rounds are O(log) of the path length inside a range instead of
+// the whole depth and cycle length, and need no grid barrier.
+// ---------------------------------------------------------------------------
+
+static __device__ __forceinline__ int block_sum_int(int x, int *s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_red[k];
+    __syncthreads();
+    return t;
+}
+
+// The local phase of block range [lo, hi).  Detection states: unresolved
+// {J, window minimum}, resolved {~tag, aux} with tag = a root (< n) or n + x
+// for exit x, aux = the smallest vertex on the path to the exit (exits: none,
+// INT_MAX).  Value states {~tag, len, S} once final.  Both jump buffers hold
+// every final state on return, rep[v] = tag.  rerun: vertices with rep[v] == v
+// (roots) are terminals too and no root is listed again.  Returns false on an
+// error (recorded in the control block).
+static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_rounds,
+                                   const Workspace &ws, int *LA, int *LB, int *s_cnt, int *s_red,
+                                   int *work_total) {
+    Ctrl *c = ws.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int W = blockDim.x;
+    const int pad = (W - ((hi - lo) % W)) % W;   // uniform trip counts for the warp votes
+    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
+        bool is_exit = false;
+        if (v < hi) {
+            const int sv = ws.succ[v];
+            is_exit = sv < lo || sv >= hi;
+            if (rerun && ws.rep[v] == v) {
+                const JM t{~v, 0};
+                ws.jm[0][v] = t;
+                ws.jm[1][v] = t;
+                is_exit = false;
+            } else if (is_exit) {
+                const JM t{~(n + v), INT_MAX};
+                ws.jm[0][v] = t;
+                ws.jm[1][v] = t;
+                ws.rep[v] = n + v;
+            } else {
+                ws.jm[0][v] = JM{sv, v};
+            }
+        }
+        if (!rerun) {   // the node list: every exit once
+            const int pos = warp_append(&c->node_cnt, is_exit, lane);
+            if (is_exit) ws.list[2][pos] = v;
+        }
+    }
+    __syncthreads();
+    int work = 0;
+    // ---- detection
+    int cnt = hi - lo;
+    for (int r = 0;; ++r) {
+        const JM *in = ws.jm[r & 1];
+        JM *out = ws.jm[(r + 1) & 1];
+        const int *lin = (r & 1) ? LB : LA;
+        int *lout = (r & 1) ? LA : LB;
+        int done_work = 0, kept = 0;
+        for (int i0 = 0; i0 < cnt; i0 += kU * W) {
+            int item[kU], ap[kU];
+            JM s[kU], t[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + u * W + (int)threadIdx.x;
+                item[u] = i < cnt ? ((r == 0) ? lo + i : lin[i]) : INT_MIN;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int it = item[u];
+                if (it == INT_MIN) continue;
+                const int v = it < 0 ? ~it : it;
+                s[u] = in[v];
+                ap[u] = (r > 0 && it >= 0) ? ws.aprev[v] : 0;
+                if (r == 0 && s[u].J < 0) item[u] = INT_MIN;   // a terminal
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int it = item[u];
+                bool keep = false, resolved = false, is_root = false;
+                int v = 0;
+                if (it != INT_MIN) {
+                    v = it < 0 ? ~it : it;
+                    if (it < 0) {
+                        out[v] = s[u];        // resolved last round: copy forward
+                    } else {
+                        int tag = -1, aux = 0;
+                        if (t[u].J < 0) {
+                            tag = ~t[u].J;    // the target is finished: v's path reaches it
+                            aux = tag >= n ? min(s[u].M, t[u].M) : 0;
+                        } else if (r > 0 && t[u].M == ap[u]) {
+                            tag = ap[u];      // a cycle inside the range: its smallest vertex
+                        } else {
+                            out[v] = JM{t[u].J, min(s[u].M, t[u].M)};
+                            ws.aprev[v] = t[u].M;
+                            keep = true;
+                        }
+                        if (tag >= 0) {
+                            out[v] = JM{~tag, aux};
+                            ws.rep[v] = tag;
+                            resolved = true;
+                            is_root = !rerun && tag == v;
+                        }
+                        ++done_work;
+                    }
+                }
+                block_append(lout, s_cnt, keep || resolved, keep ? v : ~v, lane);
+                kept += keep;
+                const int pos = warp_append(&c->nrep, is_root, lane);
+                if (is_root) ws.cyc_root[pos] = v;
+            }
+        }
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left = block_sum_int(done_work, s_red);
+        const int still = block_sum_int(kept, s_red);
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        work += left;
+        if (left == 0) break;
+        if (still == 0) {
+            for (int i = threadIdx.x; i < cnt; i += W) {
+                const int v = ~lout[i];
+                ws.jm[r & 1][v] = out[v];
+            }
+            __syncthreads();
+            break;
+        }
+        if (r + 1 >= max_rounds) {
+            if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
+            return false;
+        }
+    }
+    // ---- values: terminals (roots, exits) are final at once, as is a vertex
+    //      whose successor is one; the rest jump
+    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
+        bool keep = false;
+        if (v < hi) {
+            const int tag = ws.rep[v];
+            if (tag == v || tag == n + v) {
+                const JLS f{~tag, 0, 0};
+                ws.jls[0][v] = f;
+                ws.jls[1][v] = f;
+            } else {
+                const int sv = ws.succ[v];
+                const int ts = ws.rep[sv];
+                const bool fin = ts == sv || ts == n + sv;
+                const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
+                ws.jls[0][v] = st;
+                if (fin) ws.jls[1][v] = st;
+                keep = !fin;
+            }
+        }
+        block_append(LA, s_cnt, keep, v, lane);
+    }
+    __syncthreads();
+    cnt = *s_cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    for (int j = 1; cnt > 0; ++j) {
+        const JLS *in = ws.jls[(j + 1) & 1];
+        JLS *out = ws.jls[j & 1];
+        const int *lin = (j & 1) ? LA : LB;
+        int *lout = (j & 1) ? LB : LA;
+        int done_work = 0, kept = 0;
+        for (int i0 = 0; i0 < cnt; i0 += kU * W) {
+            int item[kU];
+            JLS s[kU], t[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + u * W + (int)threadIdx.x;
+                item[u] = i < cnt ? lin[i] : INT_MIN;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (item[u] != INT_MIN) s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[s[u].J];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int it = item[u];
+                bool keep = false, fin = false;
+                int v = 0;
+                if (it != INT_MIN) {
+                    v = it < 0 ? ~it : it;
+                    if (it < 0) {
+                        out[v] = s[u];        // final last round: copy forward
+                    } else {
+                        const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
+                        out[v] = nu;
+                        fin = nu.J < 0;
+                        keep = !fin;
+                        ++done_work;
+                    }
+                }
+                block_append(lout, s_cnt, keep || fin, keep ? v : ~v, lane);
+                kept += keep;
+            }
+        }
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left = block_sum_int(done_work, s_red);
+        const int still = block_sum_int(kept, s_red);
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        work += left;
+        if (left == 0) break;
+        if (still == 0) {
+            for (int i = threadIdx.x; i < cnt; i += W) {
+                const int v = ~lout[i];
+                ws.jls[(j + 1) & 1][v] = out[v];
+            }
+            __syncthreads();
+            break;
+        }
+        if (j + 1 > max_rounds) {
+            if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+            return false;
+        }
+    }
+    *work_total += work;
+    return true;
+}
+
+__global__ void __launch_bounds__(kEvalThreads, 1)
+evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
+                      Workspace ws, BatchState bs) {
+    __shared__ long long s_key[kRankTile];
+    __shared__ int s_cnt;
+    __shared__ int s_red[kEvalThreads / 32];
+    __shared__ int s_rerun;
+    grid_sync_start();
+    Ctrl *c = ws.ctrl;
+    const unsigned nblocks = gridDim.x;
+    const int stride = gridDim.x * blockDim.x;
+    const int first = blockIdx.x * blockDim.x;
+    const int R = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = min((int)blockIdx.x * R, n), hi = min(lo + R, n);
+    int *LA = ws.list[0] + lo, *LB = ws.list[1] + lo;
+    const int stamp = c->iter + 1;   // marks the roots found on the node graph in this evaluation
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->nrep = 0;
+        c->best = 0;
+        c->qmax = 0;
+        c->node_cnt = 0;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    // (the counters reset above are first used after this barrier)
+    if (!grid_barrier(c, nblocks)) return;
+    if (stall_test && !grid_barrier(c, nblocks + 1u)) return;
+
+    // ---- local phase of every block (block barriers only)
+    int work = 0;
+    if (!local_phase(lo, hi, n, false, max_local, ws, LA, LB, &s_cnt, s_red, &work)) return;
+    if (!grid_barrier(c, nblocks)) return;
+    const int K_exit = load_volatile(&c->node_cnt);
+    const int K_local = load_volatile(&c->nrep);
+    const int *X = ws.list[2];
+
+    // ---- node graph: detection by window minima over segment minima
+    for (int i = first + threadIdx.x; i < K_exit; i += stride) {
+        const int x = X[i];
+        const int y = ws.succ[x];
+        const int ty = ws.rep[y];
+        JM node;
+        if (ty < n) {
+            node = JM{~ty, 0};   // succ(x)'s path ends on a cycle inside its range
+        } else {
+            const JM d = ws.jm[1][y];   // y's local final: aux = smallest vertex before its exit
+            node = JM{ty - n, min(x, d.M)};
+        }
+        ws.jm[0][x] = node;
+    }
+    if (!grid_barrier(c, nblocks)) return;
+    int nr = 0;
+    for (int r = 0;; ++r) {
+        const JM *in = ws.jm[r & 1];
+        JM *out = ws.jm[(r + 1) & 1];
+        int pend = 0;
+        for (int i = first + threadIdx.x; i < K_exit; i += stride) {
+            const int x = X[i];
+            const JM s = in[x];
+            if (s.J < 0) {
+                out[x] = s;
+                continue;
+            }
+            const JM t = in[s.J];
+            int root = -1;
+            if (t.J < 0) {
+                root = ~t.J;
+            } else if (r > 0 && t.M == ws.aprev[x]) {
+                root = t.M;   // the cycle's smallest vertex (it may lie inside a segment)
+                if (atomicExch(&ws.root_mark[root], stamp) != stamp) {
+                    const int pos = atomicAdd(&c->nrep, 1);
+                    ws.cyc_root[pos] = root;
+                }
+            }
+            if (root >= 0) {
+                out[x] = JM{~root, 0};
+            } else {
+                out[x] = JM{t.J, min(s.M, t.M)};
+                ws.aprev[x] = t.M;
+                ++pend;
+            }
+        }
+        bool ok;
+        const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+        if (!ok) return;
+        ++nr;
+        if (left == 0) break;
+        if (r + 1 >= max_node) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrDetect);
+            return;
+        }
+    }
+    const int K_all = load_volatile(&c->nrep);
+    // the roots found on the node graph become terminals: a block whose range
+    // holds one repeats its local phase
+    for (int i = K_local + first + threadIdx.x; i < K_all; i += stride) ws.rep[ws.cyc_root[i]] =
+        ws.cyc_root[i];
+    if (!grid_barrier(c, nblocks)) return;
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int i = K_local; i < K_all && !any; ++i) {
+            const int rt = ws.cyc_root[i];
+            any = rt >= lo && rt < hi;
+        }
+        s_rerun = any;
+    }
+    __syncthreads();
+    if (s_rerun && !local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work))
+        return;
+    if (!grid_barrier(c, nblocks)) return;
+
+    // ---- node graph: (len, S) of every exit to its root
+    for (int i = first + threadIdx.x; i < K_exit; i += stride) {
+        const int x = X[i];
+        JLS node;
+        bool fin = true;
+        if (ws.rep[x] == x) {
+            node = JLS{~x, 0, 0};   // an exit that is itself a root
+        } else {
+            const int y = ws.succ[x];
+            const int ty = ws.rep[y];
+            const int ylo = (y / R) * R, yhi = min(ylo + R, n);
+            const int sy = ws.succ[y];
+            long long ll = 0, ls = 0;
+            if (!(sy < ylo || sy >= yhi) || ty == y) {   // y is no exit, or a root
+                const JLS f = ws.jls[1][y];
+                ll = f.len;
+                ls = f.S;
+            }
+            const int len = 1 + (int)ll;
+            const long long S = (long long)ws.wpi[x] + ls;
+            if (ty < n) {
+                node = JLS{~ty, len, S};
+            } else {
+                const int xn = ty - n;
+                fin = ws.rep[xn] == xn;
+                node = JLS{fin ? ~xn : xn, len, S};
+            }
+        }
+        ws.jls[0][x] = node;
+        if (fin) ws.jls[1][x] = node;
+    }
+    if (!grid_barrier(c, nblocks)) return;
+    int FN = 0;
+    for (int j = 1;; ++j) {
+        const JLS *in = ws.jls[(j + 1) & 1];
+        JLS *out = ws.jls[j & 1];
+        int pend = 0;
+        for (int i = first + threadIdx.x; i < K_exit; i += stride) {
+            const int x = X[i];
+            const JLS s = in[x];
+            if (s.J < 0) {
+                out[x] = s;
+                continue;
+            }
+            const JLS t = in[s.J];
+            const JLS nu{t.J, s.len + t.len, s.S + t.S};
+            out[x] = nu;
+            pend += nu.J >= 0;
+        }
+        bool ok;
+        const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+        if (!ok) return;
+        ++nr;
+        FN = j & 1;
+        if (left == 0) break;
+        if (j + 1 > max_node) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+            return;
+        }
+    }
+    for (int i = first + threadIdx.x; i < K_exit; i += stride) {
+        const int x = X[i];
+        ws.jls[FN ^ 1][x] = ws.jls[FN][x];
+    }
+    if (!grid_barrier(c, nblocks)) return;
+
+    // ---- expand: every vertex adds its local part to its exit's value
+    for (int v = lo + (int)threadIdx.x; v < hi; v += blockDim.x) {
+        const int tag = ws.rep[v];
+        if (tag < n) continue;                 // its path ends at a root inside the range
+        const int sv = ws.succ[v];
+        if (sv < lo || sv >= hi) {             // an exit: its node value is final
+            ws.rep[v] = ~ws.jls[0][v].J;
+            continue;
+        }
+        const JLS nf = ws.jls[0][tag - n];
+        const JLS lf = ws.jls[0][v];
+        const JLS f{nf.J, lf.len + nf.len, lf.S + nf.S};
+        ws.jls[0][v] = f;
+        ws.jls[1][v] = f;
+        ws.rep[v] = ~nf.J;
+    }
+    if (threadIdx.x == 0 && work)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&c->items_detect),
+                  (unsigned long long)work);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->rounds_detect += nr;
+    if (!grid_barrier(c, nblocks)) return;
+    evaluate_tail<false>(n, N2, 0, ws, bs, s_key);
+}
+
+}  // namespace ocm
+
+namespace ocm {
+
+// Counts the edges whose target lies in the block range of their source (the
+// ranges of the evaluation grid, R vertices each), the measure of locality
+// that chooses the two-level evaluation; also clears the root stamps of the
+// two-level evaluation for the solve.
+__global__ void __launch_bounds__(kThreads)
+locality_count_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n, int R,
+                      int *root_mark, Ctrl *ctrl) {
+    __shared__ long long s_sum[kThreads / 32];
+    long long local = 0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        root_mark[v] = 0;
+        const int b = v / R;
+        const int e1 = row_ptr[v + 1];
+        for (int e = row_ptr[v]; e < e1; ++e) local += (__ldg(&col[e]) / R) == b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int k = 0; k < kThreads / 32; ++k) t += s_sum[k];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&ctrl->local_edges),
+                         (unsigned long long)t);
+    }
+}
+
+int launch_locality_count(const int *row_ptr, const int *col, int n, int R, Workspace ws,
+                          cudaStream_t st) {
+    int blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    prof_begin(kProfInit, st);
+    locality_count_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, R, ws.root_mark, ws.ctrl);
+    prof_end(kProfInit, st);
+    return 1;
+}
+
+// Co-resident CTAs of the two-level evaluation kernel on the current device.
+static int evaluate_local_grid() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev == cached_dev && cached > 0) return cached;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_local_kernel,
+                                                      kEvalThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    cached_dev = dev;
+    cached = sms * per_sm;
+    return cached;
+}
+
+int prepare_evaluate_local() { return evaluate_local_grid() > 0 ? 0 : -1; }
+
+// Blocks of the two-level evaluation for n vertices (its ranges are n / blocks).
+int evaluate_local_blocks(int n) {
+    int blocks = evaluate_local_grid();
+    const int need = (n + kEvalThreads - 1) / kEvalThreads;
+    if (blocks > need) blocks = need;
+    return blocks;
 }
 
 }  // namespace ocm

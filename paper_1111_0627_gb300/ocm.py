@@ -25,6 +25,8 @@ OCM_MAX, OCM_MIN = 0, 1
 OCM_FLAG_TEST_STALL = 1
 OCM_FLAG_HOST_LOOP = 2
 OCM_FLAG_SINGLE_LAMBDA = 4
+OCM_FLAG_EVAL_LOCAL = 8     # force the two-level evaluation (include/ocm.h)
+OCM_FLAG_EVAL_GLOBAL = 16   # forbid it
 OCM_SWEEP_DEFAULT, OCM_SWEEP_CLASSES, OCM_SWEEP_TILES = 0, 1, 2
 
 

@@ -69,7 +69,11 @@ def test_argument_errors_are_reported_before_any_device_work():
                        ctypes.byref(clen), ctypes.c_void_p(256 + 8), 10**9, None, None, None)
     assert rc == -7                                      # workspace misaligned
     opt = _native.OcmOptions()
-    opt.flags = 8                                        # no such flag
+    opt.flags = 32                                       # no such flag
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
+    assert rc == -1
+    opt.flags = 8 | 16                                   # both evaluation forms at once
     rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
                        ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
     assert rc == -1
