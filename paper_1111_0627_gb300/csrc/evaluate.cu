@@ -1096,6 +1096,111 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_ro
     return true;
 }
 
+constexpr int kRerunMaxRoots = 32;   // roots on the node graph per range fixed by the short rerun
+
+// The roots roots[0, k) found on the node graph lie in range [lo, hi) and are
+// terminals now (rep[r] = r).  The only vertices whose local result changes
+// are those whose local path passes such a root, and every one of them ends
+// at the same exit as the root: the vertices tagged with one of tags[0, k)
+// (the roots' former tags).  They repeat the local value jumping with the
+// roots as extra terminals; a vertex whose path meets a root first takes it as
+// its tag.  Returns false on an error.
+static __device__ bool local_rerun(int lo, int hi, int n, const int *roots, const int *tags,
+                                   int k, int max_rounds, const Workspace &ws, int *LA, int *LB,
+                                   int *s_cnt, int *s_red) {
+    Ctrl *c = ws.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int W = blockDim.x;
+    const int pad = (W - ((hi - lo) % W)) % W;
+    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
+        bool keep = false;
+        if (v < hi) {
+            const int tag = ws.rep[v];
+            bool root = false, member = false;
+            for (int i = 0; i < k; ++i) {
+                root |= roots[i] == v;
+                member |= tags[i] == tag;
+            }
+            const int sv = ws.succ[v];
+            if (root) {
+                const JLS f{~v, 0, 0};
+                ws.jls[0][v] = f;
+                ws.jls[1][v] = f;
+            } else if (member && sv >= lo && sv < hi) {   // (an exit stays final)
+                const int ts = ws.rep[sv];
+                const bool fin = ts == sv || ts == n + sv;
+                const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
+                ws.jls[0][v] = st;
+                if (fin) ws.jls[1][v] = st;
+                keep = !fin;
+            }
+        }
+        block_append(LA, s_cnt, keep, v, lane);
+    }
+    __syncthreads();
+    int cnt = *s_cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    for (int j = 1; cnt > 0; ++j) {
+        const JLS *in = ws.jls[(j + 1) & 1];
+        JLS *out = ws.jls[j & 1];
+        const int *lin = (j & 1) ? LA : LB;
+        int *lout = (j & 1) ? LB : LA;
+        int done_work = 0, kept = 0;
+        for (int i = threadIdx.x; i < cnt + ((W - cnt % W) % W); i += W) {
+            const int it = i < cnt ? lin[i] : INT_MIN;
+            bool keep = false, fin = false;
+            int v = 0;
+            if (it != INT_MIN) {
+                v = it < 0 ? ~it : it;
+                const JLS sv = in[v];
+                if (it < 0) {
+                    out[v] = sv;
+                } else {
+                    const JLS t = in[sv.J];
+                    const JLS nu{t.J, sv.len + t.len, sv.S + t.S};
+                    out[v] = nu;
+                    fin = nu.J < 0;
+                    keep = !fin;
+                    ++done_work;
+                }
+            }
+            block_append(lout, s_cnt, keep || fin, keep ? v : ~v, lane);
+            kept += keep;
+        }
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left = block_sum_int(done_work, s_red);
+        const int still = block_sum_int(kept, s_red);
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        if (left == 0) break;
+        if (still == 0) {
+            for (int i = threadIdx.x; i < cnt; i += W) {
+                const int v = ~lout[i];
+                ws.jls[(j + 1) & 1][v] = out[v];
+            }
+            __syncthreads();
+            break;
+        }
+        if (j + 1 > max_rounds) {
+            if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+            return false;
+        }
+    }
+    // the new tags: a root met on the way, or the exit as before
+    for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+        const int tag = ws.rep[v];
+        bool member = false;
+        for (int i = 0; i < k; ++i) member |= tags[i] == tag;
+        const int sv = ws.succ[v];
+        if (member && sv >= lo && sv < hi) ws.rep[v] = ~ws.jls[0][v].J;
+    }
+    __syncthreads();
+    return true;
+}
+
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       Workspace ws, BatchState bs) {
@@ -1103,6 +1208,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     __shared__ int s_cnt;
     __shared__ int s_red[kEvalThreads / 32];
     __shared__ int s_rerun;
+    __shared__ int s_roots[kRerunMaxRoots], s_tags[kRerunMaxRoots];
     grid_sync_start();
     Ctrl *c = ws.ctrl;
     const unsigned nblocks = gridDim.x;
@@ -1188,22 +1294,36 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         }
     }
     const int K_all = load_volatile(&c->nrep);
-    // the roots found on the node graph become terminals: a block whose range
-    // holds one repeats its local phase
+    // the roots found on the node graph become terminals: in a range that
+    // holds some, the vertices draining to their exits repeat their local
+    // values (the whole local phase when a range holds very many)
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int i = K_local; i < K_all; ++i) {
+            const int rt = ws.cyc_root[i];
+            if (rt >= lo && rt < hi) {
+                if (k < kRerunMaxRoots) {
+                    s_roots[k] = rt;
+                    s_tags[k] = ws.rep[rt];   // its former tag: n + its exit
+                }
+                ++k;
+            }
+        }
+        s_rerun = k;
+    }
+    __syncthreads();
+    const int k_roots = s_rerun;
+    if (!grid_barrier(c, nblocks)) return;   // every block has read the former tags
     for (int i = K_local + first + threadIdx.x; i < K_all; i += stride) ws.rep[ws.cyc_root[i]] =
         ws.cyc_root[i];
     if (!grid_barrier(c, nblocks)) return;
-    if (threadIdx.x == 0) {
-        int any = 0;
-        for (int i = K_local; i < K_all && !any; ++i) {
-            const int rt = ws.cyc_root[i];
-            any = rt >= lo && rt < hi;
-        }
-        s_rerun = any;
+    if (k_roots > kRerunMaxRoots) {
+        if (!local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work)) return;
+    } else if (k_roots > 0) {
+        if (!local_rerun(lo, hi, n, s_roots, s_tags, k_roots, max_local, ws, LA, LB, &s_cnt,
+                         s_red))
+            return;
     }
-    __syncthreads();
-    if (s_rerun && !local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work))
-        return;
     if (!grid_barrier(c, nblocks)) return;
 
     // ---- node graph: (len, S) of every exit to its root
