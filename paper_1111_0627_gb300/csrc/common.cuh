@@ -121,6 +121,10 @@ struct Ctrl {
     int small_head;           // next queue position to pop
     int small_iters;          // largest iteration count among them
     int node_cnt;             // two-level evaluation: exits listed (nodes of the contracted graph)
+    int fix_k;                // two-level evaluation: roots found on the node graph (capped)
+    int fix_cnt;              // two-level evaluation: vertices listed for the root fix
+    int fix_root[32];         // those roots
+    int fix_tag[32];          // and their tags before the fix (n + their exit)
     long long local_edges;    // edges whose target lies in the source's block range
 };
 

@@ -220,7 +220,22 @@ static __device__ bool radix_ranks(int K, const Workspace &ws, Ctrl *c, unsigned
 // in cyc_root[0, nrep): per-cycle means, exact keys and ranks, the best cycle
 // (per graph for a batch), and the records {V, rank, q} the next sweep
 // gathers.  Called by every thread of a cooperative evaluation kernel.
-template <bool RATIO>
+//
+// LOCAL (the two-level evaluation): a vertex whose local path ends at an exit
+// (rep[v] = n + x, v itself no exit) still holds its local (len, S) to x; its
+// final state adds x's node value and is written back to jls[0] here, in the
+// pass that also writes its record, instead of in a pass of its own.
+template <bool LOCAL>
+static __device__ __forceinline__ JLS final_state(const Workspace &ws, int n, int F, int v) {
+    const JLS st = ws.jls[F][v];
+    if (!LOCAL) return st;
+    const int tag = ws.rep[v];
+    if (tag < n || tag == n + v) return st;
+    const JLS nf = ws.jls[0][tag - n];
+    return JLS{nf.J, st.len + nf.len, st.S + nf.S};
+}
+
+template <bool RATIO, bool LOCAL = false>
 static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace &ws,
                                      const BatchState &bs, long long *s_key) {
     Ctrl *c = ws.ctrl;
@@ -236,7 +251,7 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     for (int i = first + threadIdx.x; i < K; i += stride) {
         int root = ws.cyc_root[i];
         int x = ws.succ[root];
-        JLS st = ws.jls[F][x];
+        JLS st = final_state<LOCAL>(ws, n, F, x);
         long long W = (long long)ws.wpi[root] + st.S;
         long long L = 1 + (long long)st.len;
         const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[F][x] : L;
@@ -328,7 +343,8 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     }
     for (int v = first + threadIdx.x; v < n; v += stride) {
         if (bs.G && bs.gconv[bs.gid[v]]) continue;
-        JLS st = ws.jls[F][v];
+        JLS st = final_state<LOCAL>(ws, n, F, v);
+        if (LOCAL && ws.rep[v] >= n && ws.rep[v] != n + v) ws.jls[0][v] = st;
         int i = ws.cid_of_root[~st.J];
         long long p = ws.cyc_p[i];
         int q = ws.cyc_q[i];
@@ -1096,110 +1112,7 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_ro
     return true;
 }
 
-constexpr int kRerunMaxRoots = 32;   // roots on the node graph per range fixed by the short rerun
-
-// The roots roots[0, k) found on the node graph lie in range [lo, hi) and are
-// terminals now (rep[r] = r).  The only vertices whose local result changes
-// are those whose local path passes such a root, and every one of them ends
-// at the same exit as the root: the vertices tagged with one of tags[0, k)
-// (the roots' former tags).  They repeat the local value jumping with the
-// roots as extra terminals; a vertex whose path meets a root first takes it as
-// its tag.  Returns false on an error.
-static __device__ bool local_rerun(int lo, int hi, int n, const int *roots, const int *tags,
-                                   int k, int max_rounds, const Workspace &ws, int *LA, int *LB,
-                                   int *s_cnt, int *s_red) {
-    Ctrl *c = ws.ctrl;
-    const int lane = threadIdx.x & 31;
-    const int W = blockDim.x;
-    const int pad = (W - ((hi - lo) % W)) % W;
-    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
-        bool keep = false;
-        if (v < hi) {
-            const int tag = ws.rep[v];
-            bool root = false, member = false;
-            for (int i = 0; i < k; ++i) {
-                root |= roots[i] == v;
-                member |= tags[i] == tag;
-            }
-            const int sv = ws.succ[v];
-            if (root) {
-                const JLS f{~v, 0, 0};
-                ws.jls[0][v] = f;
-                ws.jls[1][v] = f;
-            } else if (member && sv >= lo && sv < hi) {   // (an exit stays final)
-                const int ts = ws.rep[sv];
-                const bool fin = ts == sv || ts == n + sv;
-                const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
-                ws.jls[0][v] = st;
-                if (fin) ws.jls[1][v] = st;
-                keep = !fin;
-            }
-        }
-        block_append(LA, s_cnt, keep, v, lane);
-    }
-    __syncthreads();
-    int cnt = *s_cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) *s_cnt = 0;
-    __syncthreads();
-    for (int j = 1; cnt > 0; ++j) {
-        const JLS *in = ws.jls[(j + 1) & 1];
-        JLS *out = ws.jls[j & 1];
-        const int *lin = (j & 1) ? LA : LB;
-        int *lout = (j & 1) ? LB : LA;
-        int done_work = 0, kept = 0;
-        for (int i = threadIdx.x; i < cnt + ((W - cnt % W) % W); i += W) {
-            const int it = i < cnt ? lin[i] : INT_MIN;
-            bool keep = false, fin = false;
-            int v = 0;
-            if (it != INT_MIN) {
-                v = it < 0 ? ~it : it;
-                const JLS sv = in[v];
-                if (it < 0) {
-                    out[v] = sv;
-                } else {
-                    const JLS t = in[sv.J];
-                    const JLS nu{t.J, sv.len + t.len, sv.S + t.S};
-                    out[v] = nu;
-                    fin = nu.J < 0;
-                    keep = !fin;
-                    ++done_work;
-                }
-            }
-            block_append(lout, s_cnt, keep || fin, keep ? v : ~v, lane);
-            kept += keep;
-        }
-        __syncthreads();
-        cnt = *s_cnt;
-        const int left = block_sum_int(done_work, s_red);
-        const int still = block_sum_int(kept, s_red);
-        if (threadIdx.x == 0) *s_cnt = 0;
-        __syncthreads();
-        if (left == 0) break;
-        if (still == 0) {
-            for (int i = threadIdx.x; i < cnt; i += W) {
-                const int v = ~lout[i];
-                ws.jls[(j + 1) & 1][v] = out[v];
-            }
-            __syncthreads();
-            break;
-        }
-        if (j + 1 > max_rounds) {
-            if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
-            return false;
-        }
-    }
-    // the new tags: a root met on the way, or the exit as before
-    for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
-        const int tag = ws.rep[v];
-        bool member = false;
-        for (int i = 0; i < k; ++i) member |= tags[i] == tag;
-        const int sv = ws.succ[v];
-        if (member && sv >= lo && sv < hi) ws.rep[v] = ~ws.jls[0][v].J;
-    }
-    __syncthreads();
-    return true;
-}
+constexpr int kRerunMaxRoots = 32;   // roots on the node graph fixed by the grid-wide rerun
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
@@ -1294,35 +1207,112 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         }
     }
     const int K_all = load_volatile(&c->nrep);
-    // the roots found on the node graph become terminals: in a range that
-    // holds some, the vertices draining to their exits repeat their local
-    // values (the whole local phase when a range holds very many)
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int i = K_local; i < K_all; ++i) {
-            const int rt = ws.cyc_root[i];
-            if (rt >= lo && rt < hi) {
-                if (k < kRerunMaxRoots) {
-                    s_roots[k] = rt;
-                    s_tags[k] = ws.rep[rt];   // its former tag: n + its exit
-                }
-                ++k;
-            }
+    // ---- the roots found on the node graph become terminals.  The vertices
+    //      whose local result changes are those draining to a root's exit
+    //      (the root's former tag); the whole grid repeats their local value
+    //      jumping with the roots as extra terminals.  Too many roots: every
+    //      block holding one repeats its whole local phase instead.
+    const int k_new = K_all - K_local;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int k = min(k_new, kRerunMaxRoots);
+        for (int i = 0; i < k; ++i) {
+            const int rt = ws.cyc_root[K_local + i];
+            c->fix_root[i] = rt;
+            c->fix_tag[i] = ws.rep[rt];
         }
-        s_rerun = k;
+        c->fix_k = k;
+        c->fix_cnt = 0;
     }
-    __syncthreads();
-    const int k_roots = s_rerun;
-    if (!grid_barrier(c, nblocks)) return;   // every block has read the former tags
+    if (!grid_barrier(c, nblocks)) return;   // the former tags are read
     for (int i = K_local + first + threadIdx.x; i < K_all; i += stride) ws.rep[ws.cyc_root[i]] =
         ws.cyc_root[i];
     if (!grid_barrier(c, nblocks)) return;
-    if (k_roots > kRerunMaxRoots) {
-        if (!local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work)) return;
-    } else if (k_roots > 0) {
-        if (!local_rerun(lo, hi, n, s_roots, s_tags, k_roots, max_local, ws, LA, LB, &s_cnt,
-                         s_red))
+    if (k_new > kRerunMaxRoots) {
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int i = K_local; i < K_all && !any; ++i) {
+                const int rt = ws.cyc_root[i];
+                any = rt >= lo && rt < hi;
+            }
+            s_rerun = any;
+        }
+        __syncthreads();
+        if (s_rerun &&
+            !local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work))
             return;
+    } else if (k_new > 0) {
+        if (threadIdx.x < kRerunMaxRoots) {
+            s_roots[threadIdx.x] = threadIdx.x < k_new ? c->fix_root[threadIdx.x] : -1;
+            s_tags[threadIdx.x] = threadIdx.x < k_new ? c->fix_tag[threadIdx.x] : -1;
+        }
+        __syncthreads();
+        // the members: vertices of the roots' ranges tagged with a root's exit
+        int *FL = ws.list[0];
+        const long long span = (long long)k_new * R;
+        for (long long q = first + threadIdx.x; q < span; q += stride) {
+            const int ri = (int)(q / R);
+            const int rlo = (s_roots[ri] / R) * R;
+            bool seen = false;   // a range holding several roots is scanned once
+            for (int i = 0; i < ri; ++i) seen |= (s_roots[i] / R) * R == rlo;
+            const int v = rlo + (int)(q % R);
+            if (seen || v >= n) continue;
+            bool root = false, member = false;
+            const int tag = ws.rep[v];
+            for (int i = 0; i < k_new; ++i) {
+                root |= s_roots[i] == v;
+                member |= s_tags[i] == tag;
+            }
+            if (root) {
+                const JLS f{~v, 0, 0};
+                ws.jls[0][v] = f;
+                ws.jls[1][v] = f;
+                continue;
+            }
+            const int sv = ws.succ[v];
+            if (!member || sv < rlo || sv >= min(rlo + R, n)) continue;   // exits stay final
+            const int ts = ws.rep[sv];
+            const bool fin = ts == sv || ts == n + sv;
+            const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
+            ws.jls[0][v] = st;
+            ws.jls[1][v] = st;
+            if (fin) ws.rep[v] = ts;   // (its successor is a root or the exit)
+            else FL[atomicAdd(&c->fix_cnt, 1)] = v;
+        }
+        if (!grid_barrier(c, nblocks)) return;
+        const int K_fix = load_volatile(&c->fix_cnt);
+        for (int j = 1; K_fix > 0; ++j) {
+            const JLS *in = ws.jls[(j + 1) & 1];
+            JLS *out = ws.jls[j & 1];
+            int pend = 0;
+            for (int i = first + threadIdx.x; i < K_fix; i += stride) {
+                const int v = FL[i];
+                const JLS sv = in[v];
+                if (sv.J < 0) {
+                    out[v] = sv;
+                    continue;
+                }
+                const JLS t = in[sv.J];
+                const JLS nu{t.J, sv.len + t.len, sv.S + t.S};
+                out[v] = nu;
+                pend += nu.J >= 0;
+            }
+            bool ok;
+            const int left = grid_sum_barrier(c, nblocks, pend, &ok);
+            if (!ok) return;
+            if (left == 0) {
+                for (int i = first + threadIdx.x; i < K_fix; i += stride) {
+                    const int v = FL[i];
+                    const JLS f = out[v];
+                    ws.jls[(j + 1) & 1][v] = f;
+                    ws.rep[v] = ~f.J;   // a root met on the way, or the exit as before
+                }
+                break;
+            }
+            if (j + 1 > max_local) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+                return;
+            }
+        }
     }
     if (!grid_barrier(c, nblocks)) return;
 
@@ -1392,28 +1382,12 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     }
     if (!grid_barrier(c, nblocks)) return;
 
-    // ---- expand: every vertex adds its local part to its exit's value
-    for (int v = lo + (int)threadIdx.x; v < hi; v += blockDim.x) {
-        const int tag = ws.rep[v];
-        if (tag < n) continue;                 // its path ends at a root inside the range
-        const int sv = ws.succ[v];
-        if (sv < lo || sv >= hi) {             // an exit: its node value is final
-            ws.rep[v] = ~ws.jls[0][v].J;
-            continue;
-        }
-        const JLS nf = ws.jls[0][tag - n];
-        const JLS lf = ws.jls[0][v];
-        const JLS f{nf.J, lf.len + nf.len, lf.S + nf.S};
-        ws.jls[0][v] = f;
-        ws.jls[1][v] = f;
-        ws.rep[v] = ~nf.J;
-    }
+    // (the expansion of exit-bound vertices happens in the tail)
     if (threadIdx.x == 0 && work)
         atomicAdd(reinterpret_cast<unsigned long long *>(&c->items_detect),
                   (unsigned long long)work);
     if (blockIdx.x == 0 && threadIdx.x == 0) c->rounds_detect += nr;
-    if (!grid_barrier(c, nblocks)) return;
-    evaluate_tail<false>(n, N2, 0, ws, bs, s_key);
+    evaluate_tail<false, true>(n, N2, 0, ws, bs, s_key);
 }
 
 }  // namespace ocm
