@@ -901,9 +901,9 @@ static __device__ __forceinline__ int block_sum_int(int x, int *s_red) {
 // every final state on return, rep[v] = tag.  rerun: vertices with rep[v] == v
 // (roots) are terminals too and no root is listed again.  Returns false on an
 // error (recorded in the control block).
-static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_rounds,
-                                   const Workspace &ws, int *LA, int *LB, int *s_cnt, int *s_red,
-                                   int *work_total) {
+static __device__ bool local_phase(int lo, int hi, int n, bool rerun, bool list_exits,
+                                   int max_rounds, const Workspace &ws, int *LA, int *LB,
+                                   int *s_cnt, int *s_red, int *work_total) {
     Ctrl *c = ws.ctrl;
     const int lane = threadIdx.x & 31;
     const int W = blockDim.x;
@@ -927,7 +927,7 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_ro
                 ws.jm[0][v] = JM{sv, v};
             }
         }
-        if (!rerun) {   // the node list: every exit once
+        if (list_exits) {   // the node list: every exit once
             const int pos = warp_append(&c->node_cnt, is_exit, lane);
             if (is_exit) ws.list[2][pos] = v;
         }
@@ -1112,6 +1112,161 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, int max_ro
     return true;
 }
 
+// One-pass local phase for ranges without a cycle of their own: a single
+// jumping pass carries, for every vertex, its jump target, the length and
+// weight of the path to it and the smallest vertex on the way, so the exit a
+// path leaves by (its tag), the path's (len, S) and the path minimum the node
+// graph needs all come out of the same rounds (the two-pass phase finds the
+// tags in a detection pass first and jumps for the values afterwards).  The
+// state is packed into 16 bytes: bits 0-20 the jump target, 21-41 the path
+// length (saturating), 42-62 the path minimum (local indices; all ones: none),
+// bit 63 finished, then the weight.  Ping-pong buffers: the records (dead
+// until this evaluation writes them again) and the second value buffer; a
+// finished vertex writes its final {~tag, len, S} to jls[0], its tag and its
+// {~tag, path minimum} for the node graph once (jls[1] then holds final
+// states only for the exits).  A path still unfinished after
+// as many steps as the range has vertices lies in the basin of a cycle inside
+// the range: the block then reports it and runs the two-pass phase instead.
+// Needs ranges of fewer than 2^21 - 1 vertices.  Returns 1 done, 0 a cycle
+// inside the range, -1 an error.
+struct __align__(16) PackedState {
+    unsigned long long a;
+    long long S;
+};
+constexpr unsigned long long kPkMask = (1ULL << 21) - 1;
+constexpr unsigned long long kPkNone = kPkMask;            // "no vertex" / saturated length
+constexpr int kMaxOnePassRange = (1 << 21) - 2;
+
+static __device__ __forceinline__ PackedState pk_make(unsigned J, unsigned len, unsigned M,
+                                                     bool fin, long long S) {
+    return PackedState{(unsigned long long)J | ((unsigned long long)len << 21) |
+                           ((unsigned long long)M << 42) | (fin ? (1ULL << 63) : 0ULL),
+                       S};
+}
+
+static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const Workspace &ws,
+                                    int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
+                                    int *work_total) {
+    Ctrl *c = ws.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int W = blockDim.x;
+    const int nv = hi - lo;
+    const int pad = (W - (nv % W)) % W;
+    PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec),
+                         reinterpret_cast<PackedState *>(ws.jls[1])};
+    if (threadIdx.x == 0) *s_flag = 0;
+    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
+        bool is_exit = false, keep = false;
+        if (v < hi) {
+            const int sv = ws.succ[v];
+            is_exit = sv < lo || sv >= hi;
+            if (is_exit) {
+                const PackedState f = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
+                P[0][v] = f;
+                P[1][v] = f;
+                ws.jls[0][v] = JLS{~(n + v), 0, 0};
+                ws.rep[v] = n + v;
+                ws.jm[1][v] = JM{~(n + v), INT_MAX};
+            } else {
+                P[0][v] = pk_make((unsigned)(sv - lo), 1, (unsigned)(v - lo), false,
+                                  (long long)ws.wpi[v]);
+                keep = true;
+            }
+        }
+        const int pos = warp_append(&c->node_cnt, is_exit, lane);
+        if (is_exit) ws.list[2][pos] = v;
+        block_append(LA, s_cnt, keep, v, lane);
+    }
+    __syncthreads();
+    int cnt = *s_cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    int work = 0;
+    for (int r = 0; cnt > 0; ++r) {
+        const PackedState *in = P[r & 1];
+        PackedState *out = P[(r + 1) & 1];
+        const int *lin = (r & 1) ? LB : LA;
+        int *lout = (r & 1) ? LA : LB;
+        int done_work = 0, kept = 0;
+        bool basin = false;
+        for (int i0 = 0; i0 < cnt; i0 += kU * W) {
+            int item[kU];
+            PackedState s[kU], t[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + u * W + (int)threadIdx.x;
+                item[u] = i < cnt ? lin[i] : INT_MIN;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (item[u] != INT_MIN) s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[lo + (int)(s[u].a & kPkMask)];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int it = item[u];
+                bool keep = false, fin = false;
+                int v = 0;
+                if (it != INT_MIN) {
+                    v = it < 0 ? ~it : it;
+                    if (it < 0) {
+                        out[v] = s[u];        // finished last round: copy forward
+                    } else {
+                        const unsigned J = (unsigned)(t[u].a & kPkMask);
+                        const unsigned len = min((unsigned)((s[u].a >> 21) & kPkMask) +
+                                                     (unsigned)((t[u].a >> 21) & kPkMask),
+                                                 (unsigned)kPkNone);
+                        const unsigned M = min((unsigned)((s[u].a >> 42) & kPkMask),
+                                               (unsigned)((t[u].a >> 42) & kPkMask));
+                        fin = (t[u].a >> 63) != 0;
+                        const long long S = s[u].S + t[u].S;
+                        out[v] = pk_make(J, len, M, fin, S);
+                        if (fin) {
+                            const int tag = n + lo + (int)J;   // the exit the path leaves by
+                            ws.jls[0][v] = JLS{~tag, (int)len, S};
+                            ws.rep[v] = tag;
+                            ws.jm[1][v] = JM{~tag, M == kPkNone ? INT_MAX : lo + (int)M};
+                        } else if ((int)len >= nv) {
+                            basin = true;     // no exit within the range: a cycle inside it
+                        } else {
+                            keep = true;
+                        }
+                        ++done_work;
+                    }
+                }
+                block_append(lout, s_cnt, keep || fin, keep ? v : ~v, lane);
+                kept += keep;
+            }
+        }
+        if (basin) *s_flag = 1;
+        __syncthreads();
+        cnt = *s_cnt;
+        const int left = block_sum_int(done_work, s_red);
+        const int still = block_sum_int(kept, s_red);
+        if (threadIdx.x == 0) *s_cnt = 0;
+        __syncthreads();
+        work += left;
+        if (*s_flag) return 0;   // (the same decision in every thread)
+        if (left == 0) break;
+        if (still == 0) break;   // (the finished states are in jls[0] already)
+        if (r + 1 > max_rounds) {
+            if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+            return -1;
+        }
+    }
+    // jls[0] holds every final state; jls[1] served as a ping-pong buffer and
+    // gets the final state of the exits only (the root fix reads them there)
+    for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+        const int sv = ws.succ[v];
+        if (sv < lo || sv >= hi) ws.jls[1][v] = JLS{~(n + v), 0, 0};
+    }
+    __syncthreads();
+    *work_total += work;
+    return 1;
+}
+
 constexpr int kRerunMaxRoots = 32;   // roots on the node graph fixed by the grid-wide rerun
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
@@ -1142,9 +1297,20 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     if (!grid_barrier(c, nblocks)) return;
     if (stall_test && !grid_barrier(c, nblocks + 1u)) return;
 
-    // ---- local phase of every block (block barriers only)
+    // ---- local phase of every block (block barriers only): one pass, or
+    //      two where the range holds a cycle of its own
     int work = 0;
-    if (!local_phase(lo, hi, n, false, max_local, ws, LA, LB, &s_cnt, s_red, &work)) return;
+    {
+        const int one = (hi - lo <= kMaxOnePassRange)
+                            ? local_onepass(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red,
+                                            &s_rerun, &work)
+                            : 0;
+        if (one < 0) return;
+        if (one == 0 &&
+            !local_phase(lo, hi, n, false, hi - lo > kMaxOnePassRange, max_local, ws, LA, LB,
+                         &s_cnt, s_red, &work))
+            return;
+    }
     if (!grid_barrier(c, nblocks)) return;
     const int K_exit = load_volatile(&c->node_cnt);
     const int K_local = load_volatile(&c->nrep);
@@ -1238,7 +1404,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         }
         __syncthreads();
         if (s_rerun &&
-            !local_phase(lo, hi, n, true, max_local, ws, LA, LB, &s_cnt, s_red, &work))
+            !local_phase(lo, hi, n, true, false, max_local, ws, LA, LB, &s_cnt, s_red, &work))
             return;
     } else if (k_new > 0) {
         if (threadIdx.x < kRerunMaxRoots) {
@@ -1330,7 +1496,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
             const int sy = ws.succ[y];
             long long ll = 0, ls = 0;
             if (!(sy < ylo || sy >= yhi) || ty == y) {   // y is no exit, or a root
-                const JLS f = ws.jls[1][y];
+                const JLS f = ws.jls[0][y];
                 ll = f.len;
                 ls = f.S;
             }
