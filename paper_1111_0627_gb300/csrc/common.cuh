@@ -273,6 +273,21 @@ __device__ __forceinline__ void publish_result(const Workspace &ws, int n) {
     }
 }
 
+// Final value state (J = ~root, len, S) of vertex v from the evaluation's
+// value buffer.  After the two-level evaluation a vertex whose path leaves its
+// block range holds its state to the exit x it leaves by (J = ~(n + x)), and
+// its final state adds x's (an exit's own state is final); after the one-level
+// evaluation every state is final and this is a plain load.
+__device__ __forceinline__ JLS final_value(const JLS *jls0, int n, int v) {
+    JLS st = jls0[v];
+    const int tag = ~st.J;
+    if (tag >= n) {
+        const JLS nf = jls0[tag - n];
+        st = JLS{nf.J, st.len + nf.len, st.S + nf.S};
+    }
+    return st;
+}
+
 __device__ __forceinline__ int warp_append(int *counter, bool pred, int lane) {
     unsigned mask = __ballot_sync(0xffffffffu, pred);
     int base = 0;

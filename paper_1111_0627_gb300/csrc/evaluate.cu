@@ -222,19 +222,7 @@ static __device__ bool radix_ranks(int K, const Workspace &ws, Ctrl *c, unsigned
 // gathers.  Called by every thread of a cooperative evaluation kernel.
 //
 // LOCAL (the two-level evaluation): a vertex whose local path ends at an exit
-// (rep[v] = n + x, v itself no exit) still holds its local (len, S) to x; its
-// final state adds x's node value and is written back to jls[0] here, in the
-// pass that also writes its record, instead of in a pass of its own.
-template <bool LOCAL>
-static __device__ __forceinline__ JLS final_state(const Workspace &ws, int n, int F, int v) {
-    const JLS st = ws.jls[F][v];
-    if (!LOCAL) return st;
-    const int tag = ws.rep[v];
-    if (tag < n || tag == n + v) return st;
-    const JLS nf = ws.jls[0][tag - n];
-    return JLS{nf.J, st.len + nf.len, st.S + nf.S};
-}
-
+// holds its state to that exit, completed on the fly (final_value).
 template <bool RATIO, bool LOCAL = false>
 static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace &ws,
                                      const BatchState &bs, long long *s_key) {
@@ -251,7 +239,7 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     for (int i = first + threadIdx.x; i < K; i += stride) {
         int root = ws.cyc_root[i];
         int x = ws.succ[root];
-        JLS st = final_state<LOCAL>(ws, n, F, x);
+        JLS st = LOCAL ? final_value(ws.jls[0], n, x) : ws.jls[F][x];
         long long W = (long long)ws.wpi[root] + st.S;
         long long L = 1 + (long long)st.len;
         const long long Tc = ratio ? (long long)ws.tpi[root] + ws.jt[F][x] : L;
@@ -343,8 +331,7 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     }
     for (int v = first + threadIdx.x; v < n; v += stride) {
         if (bs.G && bs.gconv[bs.gid[v]]) continue;
-        JLS st = final_state<LOCAL>(ws, n, F, v);
-        if (LOCAL && ws.rep[v] >= n && ws.rep[v] != n + v) ws.jls[0][v] = st;
+        JLS st = LOCAL ? final_value(ws.jls[0], n, v) : ws.jls[F][v];
         int i = ws.cid_of_root[~st.J];
         long long p = ws.cyc_p[i];
         int q = ws.cyc_q[i];
@@ -688,7 +675,8 @@ int prepare_evaluate(bool ratio) {
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
-                      Workspace ws, BatchState bs);
+                      int nwords, Workspace ws, BatchState bs);
+constexpr int kLocalBitmapWords = 40960;   // 160 KB: ranges up to 1,310,720 vertices
 int evaluate_local_blocks(int n);
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
@@ -701,9 +689,12 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         const int blocks = evaluate_local_blocks(n);
         if (blocks <= 0) return -1;
         const int R = (n + blocks - 1) / blocks;
+        const int words = (R + 31) / 32;
+        const int nwords = words <= kLocalBitmapWords ? words : 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
         cfg.blockDim = dim3(kEvalThreads);
+        cfg.dynamicSmemBytes = (size_t)nwords * 4;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -713,7 +704,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         prof_begin(kProfEvaluate, st);
         const cudaError_t e = cudaLaunchKernelEx(&cfg, evaluate_local_kernel, n, N2,
                                                  ceil_log2(R) + 4, ceil_log2(n) + 4, stall_test,
-                                                 ws, bs);
+                                                 nwords, ws, bs);
         prof_end(kProfEvaluate, st);
         return e == cudaSuccess ? 1 : -1;
     }
@@ -763,7 +754,7 @@ extract_candidates_kernel(int n, Workspace ws) {
         const int v = base + threadIdx.x;
         bool cand = false;
         if (v < n) {
-            JLS st = ws.jls[0][v];
+            const JLS st = final_value(ws.jls[0], n, v);
             cand = (~st.J == root) && st.len < L;
             if (cand) cur[v] = v;
         }
@@ -790,7 +781,7 @@ extract_round_kernel(int b, Workspace ws) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-extract_scatter_kernel(Workspace ws, int *cycle_out) {
+extract_scatter_kernel(int n, Workspace ws, int *cycle_out) {
     Ctrl *c = ws.ctrl;
     const int K = load_volatile(&c->ncand);
     const int L = c->res_len;
@@ -799,7 +790,7 @@ extract_scatter_kernel(Workspace ws, int *cycle_out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
         int v = ws.list[0][i];
         if (ws.aprev[v] == v) {
-            int len = ws.jls[0][v].len;
+            int len = final_value(ws.jls[0], n, v).len;
             int pos = (len == 0) ? 0 : L - len;
             cycle_out[pos] = ws.pi[v];
             ++found;
@@ -823,7 +814,7 @@ int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cud
     int bits = 0;
     while ((1LL << bits) <= Lstar) ++bits;
     for (int b = 0; b < bits; ++b, ++launches) extract_round_kernel<<<grid, kThreads, 0, st>>>(b, ws);
-    extract_scatter_kernel<<<grid, kThreads, 0, st>>>(ws, cycle_out);
+    extract_scatter_kernel<<<grid, kThreads, 0, st>>>(n, ws, cycle_out);
     prof_end(kProfExtract, st);
     return launches + 1;
 }
@@ -833,7 +824,7 @@ outputs_kernel(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t 
                int32_t *policy) {
     const int stride = gridDim.x * blockDim.x;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        JLS st = ws.jls[0][v];
+        const JLS st = final_value(ws.jls[0], n, v);
         int i = ws.cid_of_root[~st.J];
         if (eta_num) eta_num[v] = ws.cyc_p[i];
         if (eta_den) eta_den[v] = ws.cyc_q[i];
@@ -1144,9 +1135,13 @@ static __device__ __forceinline__ PackedState pk_make(unsigned J, unsigned len, 
                        S};
 }
 
+// Leaves (vertices no vertex of the range points to, about a third of them in
+// a random policy graph) are never a jump target, so when the range's
+// predecessor bitmap fits in shared memory (bits words) they stay out of the
+// rounds and take their successor's final state at the end.
 static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const Workspace &ws,
                                     int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
-                                    int *work_total) {
+                                    unsigned *bits, int nwords, int *work_total) {
     Ctrl *c = ws.ctrl;
     const int lane = threadIdx.x & 31;
     const int W = blockDim.x;
@@ -1155,12 +1150,25 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
     PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec),
                          reinterpret_cast<PackedState *>(ws.jls[1])};
     if (threadIdx.x == 0) *s_flag = 0;
+    const bool trim = nwords > 0 && (nv + 31) / 32 <= nwords;
+    if (trim) {
+        for (int i = threadIdx.x; i < (nv + 31) / 32; i += W) bits[i] = 0u;
+        __syncthreads();
+        for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+            const int sv = ws.succ[v];
+            if (sv >= lo && sv < hi) atomicOr(&bits[(sv - lo) >> 5], 1u << ((sv - lo) & 31));
+        }
+        __syncthreads();
+    }
     for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
         bool is_exit = false, keep = false;
         if (v < hi) {
             const int sv = ws.succ[v];
             is_exit = sv < lo || sv >= hi;
-            if (is_exit) {
+            const bool leaf = trim && !is_exit && !((bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u);
+            if (leaf) {
+                // finished after the rounds, from its successor
+            } else if (is_exit) {
                 const PackedState f = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
                 P[0][v] = f;
                 P[1][v] = f;
@@ -1256,11 +1264,21 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             return -1;
         }
     }
-    // jls[0] holds every final state; jls[1] served as a ping-pong buffer and
-    // gets the final state of the exits only (the root fix reads them there)
+    // the leaves: one step to the successor, whose state is final; jls[0] then
+    // holds every final state, and jls[1] (a ping-pong buffer above) gets the
+    // final state of the exits (the root fix reads them there)
     for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
         const int sv = ws.succ[v];
-        if (sv < lo || sv >= hi) ws.jls[1][v] = JLS{~(n + v), 0, 0};
+        if (sv < lo || sv >= hi) {
+            ws.jls[1][v] = JLS{~(n + v), 0, 0};
+        } else if (trim && !((bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u)) {
+            const JLS f = ws.jls[0][sv];
+            const JM d = ws.jm[1][sv];
+            const int tag = ~f.J;
+            ws.jls[0][v] = JLS{f.J, f.len + 1, f.S + (long long)ws.wpi[v]};
+            ws.rep[v] = tag;
+            ws.jm[1][v] = JM{f.J, min(v, d.M)};
+        }
     }
     __syncthreads();
     *work_total += work;
@@ -1271,7 +1289,8 @@ constexpr int kRerunMaxRoots = 32;   // roots on the node graph fixed by the gri
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
-                      Workspace ws, BatchState bs) {
+                      int nwords, Workspace ws, BatchState bs) {
+    extern __shared__ unsigned s_bits[];   // nwords: the local predecessor bitmap
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     __shared__ int s_red[kEvalThreads / 32];
@@ -1303,7 +1322,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     {
         const int one = (hi - lo <= kMaxOnePassRange)
                             ? local_onepass(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red,
-                                            &s_rerun, &work)
+                                            &s_rerun, s_bits, nwords, &work)
                             : 0;
         if (one < 0) return;
         if (one == 0 &&
@@ -1606,8 +1625,12 @@ static int evaluate_local_grid() {
     if (dev == cached_dev && cached > 0) return cached;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_local_kernel,
-                                                      kEvalThreads, 0) != cudaSuccess ||
+    // co-resident with the largest bitmap any launch uses
+    if (cudaFuncSetAttribute(evaluate_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kLocalBitmapWords * 4) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_local_kernel,
+                                                      kEvalThreads, kLocalBitmapWords * 4) !=
+            cudaSuccess ||
         per_sm < 1)
         return 0;
     cached_dev = dev;
