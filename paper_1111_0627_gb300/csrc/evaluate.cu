@@ -676,7 +676,7 @@ int prepare_evaluate(bool ratio) {
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       int nwords, Workspace ws, BatchState bs);
-constexpr int kLocalBitmapWords = 40960;   // 160 KB: ranges up to 1,310,720 vertices
+constexpr int kLocalBitmapWords = 40960;   // 160 KB: bitmap and prefix counts of ranges up to 655,360 vertices
 int evaluate_local_blocks(int n);
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
@@ -689,7 +689,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         const int blocks = evaluate_local_blocks(n);
         if (blocks <= 0) return -1;
         const int R = (n + blocks - 1) / blocks;
-        const int words = (R + 31) / 32;
+        const int words = 2 * ((R + 31) / 32);   // the bitmap and its prefix counts
         const int nwords = words <= kLocalBitmapWords ? words : 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
@@ -1136,9 +1136,15 @@ static __device__ __forceinline__ PackedState pk_make(unsigned J, unsigned len, 
 }
 
 // Leaves (vertices no vertex of the range points to, about a third of them in
-// a random policy graph) are never a jump target, so when the range's
-// predecessor bitmap fits in shared memory (bits words) they stay out of the
-// rounds and take their successor's final state at the end.
+// a random policy graph) are never a jump target.  When the range's
+// predecessor bitmap fits in shared memory (bits, nwords words; the same
+// again holds per-word prefix counts), the other vertices are renumbered
+// densely in vertex order (rank = set bits before them) and the rounds run on
+// that dense index space -- states and lists stay contiguous, so a warp's
+// accesses fill whole sectors -- while the leaves take their successor's
+// final state at the end.  Without the bitmap every vertex takes part.  In
+// the packed state a pending vertex's jump target is a dense index, a
+// finished one's the local index of its exit.
 static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const Workspace &ws,
                                     int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
                                     unsigned *bits, int nwords, int *work_total) {
@@ -1146,51 +1152,79 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
     const int lane = threadIdx.x & 31;
     const int W = blockDim.x;
     const int nv = hi - lo;
-    const int pad = (W - (nv % W)) % W;
-    PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec),
-                         reinterpret_cast<PackedState *>(ws.jls[1])};
+    const int nw = (nv + 31) / 32;
+    const bool trim = nwords > 0 && 2 * nw <= nwords;
+    unsigned *pref = bits + nw;   // set bits in the words before each word
+    PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec) + lo,
+                         reinterpret_cast<PackedState *>(ws.jls[1]) + lo};
+    int *orig = ws.aprev + lo;    // dense index -> vertex
     if (threadIdx.x == 0) *s_flag = 0;
-    const bool trim = nwords > 0 && (nv + 31) / 32 <= nwords;
+    int nd = nv;                  // vertices in the dense space
     if (trim) {
-        for (int i = threadIdx.x; i < (nv + 31) / 32; i += W) bits[i] = 0u;
+        for (int i = threadIdx.x; i < nw; i += W) bits[i] = 0u;
         __syncthreads();
         for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
             const int sv = ws.succ[v];
             if (sv >= lo && sv < hi) atomicOr(&bits[(sv - lo) >> 5], 1u << ((sv - lo) & 31));
         }
         __syncthreads();
-    }
-    for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
-        bool is_exit = false, keep = false;
-        if (v < hi) {
-            const int sv = ws.succ[v];
-            is_exit = sv < lo || sv >= hi;
-            const bool leaf = trim && !is_exit && !((bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u);
-            if (leaf) {
-                // finished after the rounds, from its successor
-            } else if (is_exit) {
-                const PackedState f = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
-                P[0][v] = f;
-                P[1][v] = f;
-                ws.jls[0][v] = JLS{~(n + v), 0, 0};
-                ws.rep[v] = n + v;
-                ws.jm[1][v] = JM{~(n + v), INT_MAX};
-            } else {
-                P[0][v] = pk_make((unsigned)(sv - lo), 1, (unsigned)(v - lo), false,
-                                  (long long)ws.wpi[v]);
-                keep = true;
-            }
+        // exclusive prefix of the word popcounts: each thread a contiguous chunk
+        const int per = (nw + W - 1) / W;
+        const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+        int sum = 0;
+        for (int i = w0; i < w1; ++i) sum += __popc(bits[i]);
+        __shared__ int s_warp[32];
+        __shared__ int s_total;
+        const int incl = block_inclusive_scan(sum, s_warp);
+        int run = incl - sum;
+        for (int i = w0; i < w1; ++i) {
+            pref[i] = (unsigned)run;
+            run += __popc(bits[i]);
         }
-        const int pos = warp_append(&c->node_cnt, is_exit, lane);
-        if (is_exit) ws.list[2][pos] = v;
-        block_append(LA, s_cnt, keep, v, lane);
+        if (threadIdx.x == W - 1) s_total = incl;
+        __syncthreads();
+        nd = s_total;
     }
-    __syncthreads();
-    int cnt = *s_cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) *s_cnt = 0;
+    auto dense = [&](int v) -> int {   // dense index of a vertex that has a predecessor
+        const int l = v - lo;
+        return trim ? (int)pref[l >> 5] + __popc(bits[l >> 5] & ((1u << (l & 31)) - 1u)) : l;
+    };
+    auto has_pred = [&](int v) -> bool {
+        const int l = v - lo;
+        return !trim || ((bits[l >> 5] >> (l & 31)) & 1u);
+    };
+    for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+        const int sv = ws.succ[v];
+        const bool is_exit = sv < lo || sv >= hi;
+        if (is_exit) {
+            ws.jls[0][v] = JLS{~(n + v), 0, 0};
+            ws.rep[v] = n + v;
+            ws.jm[1][v] = JM{~(n + v), INT_MAX};
+        }
+        if (!has_pred(v)) continue;   // a leaf: finished at the end
+        const int d = dense(v);
+        orig[d] = v;
+        if (is_exit) {
+            const PackedState f = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
+            P[0][d] = f;
+            P[1][d] = f;
+        } else {
+            P[0][d] = pk_make((unsigned)dense(sv), 1, (unsigned)(v - lo), false,
+                              (long long)ws.wpi[v]);
+        }
+    }
+    // the node list: every exit once
+    {
+        const int pad = (W - (nv % W)) % W;
+        for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
+            const bool is_exit = v < hi && (ws.succ[v] < lo || ws.succ[v] >= hi);
+            const int pos = warp_append(&c->node_cnt, is_exit, lane);
+            if (is_exit) ws.list[2][pos] = v;
+        }
+    }
     __syncthreads();
     int work = 0;
+    int cnt = nd;   // round 0: every dense index (finished ones are skipped)
     for (int r = 0; cnt > 0; ++r) {
         const PackedState *in = P[r & 1];
         PackedState *out = P[(r + 1) & 1];
@@ -1204,23 +1238,26 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int i = i0 + u * W + (int)threadIdx.x;
-                item[u] = i < cnt ? lin[i] : INT_MIN;
+                item[u] = i < cnt ? ((r == 0) ? i : lin[i]) : INT_MIN;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (item[u] == INT_MIN) continue;
+                s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
+                if (r == 0 && (s[u].a >> 63)) item[u] = INT_MIN;   // an exit
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (item[u] != INT_MIN) s[u] = in[item[u] < 0 ? ~item[u] : item[u]];
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[lo + (int)(s[u].a & kPkMask)];
+                if (item[u] != INT_MIN && item[u] >= 0) t[u] = in[(int)(s[u].a & kPkMask)];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int it = item[u];
                 bool keep = false, fin = false;
-                int v = 0;
+                int d = 0;
                 if (it != INT_MIN) {
-                    v = it < 0 ? ~it : it;
+                    d = it < 0 ? ~it : it;
                     if (it < 0) {
-                        out[v] = s[u];        // finished last round: copy forward
+                        out[d] = s[u];        // finished last round: copy forward
                     } else {
                         const unsigned J = (unsigned)(t[u].a & kPkMask);
                         const unsigned len = min((unsigned)((s[u].a >> 21) & kPkMask) +
@@ -1230,8 +1267,9 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
                                                (unsigned)((t[u].a >> 42) & kPkMask));
                         fin = (t[u].a >> 63) != 0;
                         const long long S = s[u].S + t[u].S;
-                        out[v] = pk_make(J, len, M, fin, S);
+                        out[d] = pk_make(J, len, M, fin, S);
                         if (fin) {
+                            const int v = orig[d];
                             const int tag = n + lo + (int)J;   // the exit the path leaves by
                             ws.jls[0][v] = JLS{~tag, (int)len, S};
                             ws.rep[v] = tag;
@@ -1244,7 +1282,7 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
                         ++done_work;
                     }
                 }
-                block_append(lout, s_cnt, keep || fin, keep ? v : ~v, lane);
+                block_append(lout, s_cnt, keep || fin, keep ? d : ~d, lane);
                 kept += keep;
             }
         }
@@ -1271,13 +1309,12 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
         const int sv = ws.succ[v];
         if (sv < lo || sv >= hi) {
             ws.jls[1][v] = JLS{~(n + v), 0, 0};
-        } else if (trim && !((bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u)) {
+        } else if (!has_pred(v)) {
             const JLS f = ws.jls[0][sv];
-            const JM d = ws.jm[1][sv];
-            const int tag = ~f.J;
+            const JM dm = ws.jm[1][sv];
             ws.jls[0][v] = JLS{f.J, f.len + 1, f.S + (long long)ws.wpi[v]};
-            ws.rep[v] = tag;
-            ws.jm[1][v] = JM{f.J, min(v, d.M)};
+            ws.rep[v] = ~f.J;
+            ws.jm[1][v] = JM{f.J, min(v, dm.M)};
         }
     }
     __syncthreads();
