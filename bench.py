@@ -221,8 +221,8 @@ KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
                   "sweep": ("sweep.cu", "common.cuh")}
 TRAFFIC = {
     # n = 2^23 capture (3 launches from the middle of a solve, mean) x 4
-    ("locality32m", "evaluate"): (4 * (4.237341e9 + 4.036051e9), "eaf1269e9732e595"),
-    ("locality32m", "sweep"): (4 * (1.728532e9 + 0.177541e9), "85bcbfdb571c126c"),
+    ("locality32m", "evaluate"): (4 * (1.352272e9 + 1.064272e9), "2c44b1fdb208294a"),
+    ("locality32m", "sweep"): (4 * (1.728464e9 + 0.177420e9), "cda8d1022ac7c1cf"),
 }
 
 
