@@ -589,11 +589,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     const int sweep_threads = (opt && opt->sweep_threads > 0) ? opt->sweep_threads : kSweepThreads;
     launches += launch_classify(row_ptr, n, kind == OCM_SWEEP_TILES ? kEdgesPerLane : epl, ws, st);
     if (kind == OCM_SWEEP_TILES) launches += launch_tile_index(row_ptr, n, m, 32 * epl, ws, st);
-    launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
-                       bs ? &b : nullptr, st);
-    launches += 3;
     // the two-level evaluation serves single graphs whose edges mostly stay
-    // inside the evaluation grid's block ranges (or when forced)
+    // inside the evaluation grid's block ranges (or when forced); the initial
+    // pass counts those edges
     const int eval_flags = opt ? opt->flags & (OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL) : 0;
     const bool local_ok = !bs && !ratio && !single && !(eval_flags & OCM_FLAG_EVAL_GLOBAL);
     int local_R = 0;
@@ -601,8 +599,10 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         const int blocks = evaluate_local_blocks(n);
         if (blocks <= 0) return OCM_ERR_CUDA;
         local_R = (n + blocks - 1) / blocks;
-        launches += launch_locality_count(row_ptr, col_idx, n, local_R, ws, st);
     }
+    launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
+                       bs ? &b : nullptr, st, local_R);
+    launches += 3;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
     if (rc) return rc;

@@ -342,7 +342,8 @@ struct NvtxRange {
 // kernel launchers (defined in the .cu files)
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st);
+                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
+                        int local_R = 0);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
                  cudaStream_t st);
@@ -363,8 +364,6 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
                     cudaStream_t st, bool local = false);
 int prepare_evaluate_local();
 int evaluate_local_blocks(int n);
-int launch_locality_count(const int *row_ptr, const int *col, int n, int R, Workspace ws,
-                          cudaStream_t st);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);
 int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sign, int max_n,
                        long long N, long long max_iters, int *queue, Workspace ws, BatchState bs,

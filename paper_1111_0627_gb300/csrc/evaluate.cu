@@ -1616,44 +1616,6 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
 
 namespace ocm {
 
-// Counts the edges whose target lies in the block range of their source (the
-// ranges of the evaluation grid, R vertices each), the measure of locality
-// that chooses the two-level evaluation; also clears the root stamps of the
-// two-level evaluation for the solve.
-__global__ void __launch_bounds__(kThreads)
-locality_count_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col, int n, int R,
-                      int *root_mark, Ctrl *ctrl) {
-    __shared__ long long s_sum[kThreads / 32];
-    long long local = 0;
-    const int stride = gridDim.x * blockDim.x;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        root_mark[v] = 0;
-        const int b = v / R;
-        const int e1 = row_ptr[v + 1];
-        for (int e = row_ptr[v]; e < e1; ++e) local += (__ldg(&col[e]) / R) == b;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int k = 0; k < kThreads / 32; ++k) t += s_sum[k];
-        if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&ctrl->local_edges),
-                         (unsigned long long)t);
-    }
-}
-
-int launch_locality_count(const int *row_ptr, const int *col, int n, int R, Workspace ws,
-                          cudaStream_t st) {
-    int blocks = (n + kThreads - 1) / kThreads;
-    if (blocks > 4096) blocks = 4096;
-    prof_begin(kProfInit, st);
-    locality_count_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, n, R, ws.root_mark, ws.ctrl);
-    prof_end(kProfInit, st);
-    return 1;
-}
-
 // Co-resident CTAs of the two-level evaluation kernel on the current device.
 static int evaluate_local_grid() {
     static int cached_dev = -1, cached = 0;

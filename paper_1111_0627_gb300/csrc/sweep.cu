@@ -94,6 +94,11 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
     prof_end(kProfInit, st);
 }
 
+// With local_R > 0 the pass also counts the edges whose target lies in the
+// block range (local_R consecutive vertices) of their source, the locality
+// measure that chooses the two-level evaluation, and clears that
+// evaluation's root stamps (heavy vertices' edges are not counted).
+//
 // Initial policy (Alg. 1's first pass from val = 0, lambda = 0): the heaviest
 // out-edge in the s*w sense, ties to the smallest edge index (for the cycle
 // ratio too: with lambda = 0 the key w(e) - lambda t(e) is w(e)) -- or, for a
@@ -103,9 +108,11 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 __global__ void __launch_bounds__(kThreads)
 init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
-                   const int *__restrict__ init, Workspace ws) {
+                   const int *__restrict__ init, int local_R, Workspace ws) {
     __shared__ int s_maxw[kThreads / 32];
     __shared__ int s_maxt[kThreads / 32];
+    __shared__ unsigned long long s_local[kThreads / 32];
+    unsigned long long local = 0;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -113,7 +120,9 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     int maxabs = 0, maxt = 0;
     for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
         const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
+        if (local_R) ws.root_mark[v] = 0;
         if (b - a > kHeavyEdges) continue;   // the heavy path (heavy_init_*_kernel)
+        const int my_range = local_R ? v / local_R : 0;
         const int my_g = gid ? gid[v] : 0;
         int best_e = a;
         long long best_key = LLONG_MIN;
@@ -131,6 +140,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 x = 0;
             }
             maxabs = max(maxabs, x < 0 ? -x : x);
+            if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
             if (tt) {
                 const int te = __ldg(&tt[e]);
                 if (te < 1) {
@@ -166,10 +176,12 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     for (int o = 16; o > 0; o >>= 1) {
         maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
         maxt = max(maxt, __shfl_xor_sync(0xffffffffu, maxt, o));
+        local += __shfl_xor_sync(0xffffffffu, local, o);
     }
     if (lane == 0) {
         s_maxw[tid >> 5] = maxabs;
         s_maxt[tid >> 5] = maxt;
+        s_local[tid >> 5] = local;
     }
     __syncthreads();
     if (tid < 32) {
@@ -183,6 +195,12 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         if (tid == 0) {
             atomicMax(&ws.ctrl->maxabsw, x);
             if (tt) atomicMax(&ws.ctrl->maxt, y);
+            if (local_R) {
+                unsigned long long sum = 0;
+                for (int k = 0; k < kThreads / 32; ++k) sum += s_local[k];
+                if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctrl->local_edges),
+                                   sum);
+            }
         }
     }
 }
@@ -588,12 +606,13 @@ heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__
 }
 
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
-                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st) {
+                        const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
+                        int local_R) {
     int blocks = (n + kThreads - 1) / kThreads;
     if (blocks > 2048) blocks = 2048;
     prof_begin(kProfInit, st);
     init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n,
-                                                    bs ? bs->gid : nullptr, init, ws);
+                                                    bs ? bs->gid : nullptr, init, local_R, ws);
     // heavy vertices (their count is on the device: fixed grids, grid-stride)
     int cb = (m / kHeavyChunk) + 1;
     if (cb > 1024) cb = 1024;
