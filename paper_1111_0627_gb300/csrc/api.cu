@@ -63,14 +63,11 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.jt[1] = static_cast<long long *>(take(8 * N));
     w.recp = static_cast<long long *>(take(8 * N));
     w.root_mark = static_cast<int *>(take(4 * N));
-    w.recv = static_cast<long long *>(take(8 * N));
     w.transit = nullptr;
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;
     return align_up(off, 256);
 }
-
-__global__ void set_compact_ok_kernel(Ctrl *c, int ok) { c->compact_ok = ok; }
 
 __global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns) {
     Ctrl z;
@@ -625,11 +622,6 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
             return OCM_ERR_OVERFLOW;
     }
     const long long N2 = nmax * nmax;
-    // V-only records when the policy has a single cycle: single graphs, the
-    // mean, the degree-class sweep (the other forms read the full record)
-    set_compact_ok_kernel<<<1, 1, 0, st>>>(ws.ctrl, (!bs && !ratio && !single &&
-                                                      kind == OCM_SWEEP_CLASSES) ? 1 : 0);
-    launches += 1;
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
     if (single) {
         // the backward search of the rebuild walks the transposed graph

@@ -120,9 +120,6 @@ struct Ctrl {
     int small_total;          // graphs in the queue
     int small_head;           // next queue position to pop
     int small_iters;          // largest iteration count among them
-    int compact_ok;           // the solve may use V-only records (single graph, mean, class sweep)
-    int compact;              // the last evaluation wrote V-only records (one policy cycle)
-    int compact_q;            // that cycle's mean denominator
     int node_cnt;             // two-level evaluation: exits listed (nodes of the contracted graph)
     int fix_k;                // two-level evaluation: roots found on the node graph (capped)
     int fix_cnt;              // two-level evaluation: vertices listed for the root fix
@@ -191,8 +188,6 @@ struct Workspace {
     long long *jt[2];     // [n] value jumping: transit time of the path from v to J
     long long *recp;      // [n] numerator p of the ratio of v's cycle (gathered by the sweep)
     int *root_mark;       // [n] two-level evaluation: evaluation stamp of a root found on the node graph
-    long long *recv;      // [n] V only, the record when the policy has a single cycle (every
-                          //     vertex then has rank 0 and that cycle's denominator)
     Ctrl *ctrl;
 };
 

@@ -329,13 +329,6 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
         c->changed = 0;
         c->switched = 0;
     }
-    // one policy cycle: every vertex has rank 0 and its denominator, and the
-    // sweep needs V alone (half the bytes per gathered record)
-    const bool compact = !ratio && K == 1 && c->compact_ok;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->compact = compact ? 1 : 0;
-        c->compact_q = ws.cyc_q[0];
-    }
     for (int v = first + threadIdx.x; v < n; v += stride) {
         if (bs.G && bs.gconv[bs.gid[v]]) continue;
         JLS st = LOCAL ? final_value(ws.jls[0], n, v) : ws.jls[F][v];
@@ -345,10 +338,6 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
         Rec rec;
         const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
         rec.V = (long long)q * st.S - p * T;
-        if (compact) {
-            ws.recv[v] = rec.V;
-            continue;
-        }
         rec.rank = ws.cyc_rank[i];
         rec.q = q;
         ws.rec[v] = rec;
@@ -839,7 +828,7 @@ outputs_kernel(int n, Workspace ws, int64_t *eta_num, int32_t *eta_den, int64_t 
         int i = ws.cid_of_root[~st.J];
         if (eta_num) eta_num[v] = ws.cyc_p[i];
         if (eta_den) eta_den[v] = ws.cyc_q[i];
-        if (potential) potential[v] = ws.ctrl->compact ? ws.recv[v] : ws.rec[v].V;
+        if (potential) potential[v] = ws.rec[v].V;
         if (policy) policy[v] = ws.pi[v];
     }
 }

@@ -372,18 +372,12 @@ struct ClassGrid {
 // p_t * t(e), the target's ratio numerator times the edge's transit time;
 // for the mean t(e) = 1 and p_t is the same for every target of equal rank,
 // so the term is dropped.
-//
-// With a single policy cycle (compact) every target has rank 0 and the
-// cycle's denominator q, and its record is V alone (8 bytes instead of 16:
-// twice the records per sector).
 template <bool RATIO>
 static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
                                                  const int *__restrict__ w, const int4 *rec,
-                                                 const Workspace &ws, int sign, int e,
-                                                 bool compact = false, long long q = 0) {
+                                                 const Workspace &ws, int sign, int e) {
     const int t = __ldg(&col[e]);
     const int x = __ldg(&w[e]);
-    if (!RATIO && compact) return Cand{0, e, q * (long long)(sign * x) + __ldg(&ws.recv[t])};
     const int4 r = __ldg(&rec[t]);
     const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
     long long key = (long long)r.w * (long long)(sign * x) + V;
@@ -405,8 +399,6 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     if (blockIdx.x == 0 && tid == 0) publish_result(ws, n_vertices);
     __syncthreads();
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
-    const bool compact = !RATIO && ws.ctrl->compact;
-    const long long cq = ws.ctrl->compact_q;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int total = cg.task_off[kClasses];
     int switched = 0;
@@ -430,15 +422,15 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             const int pv = ws.pi[v];
             int e = a + sub;
             for (; e + g < e_end; e += 2 * g) {   // two independent gathers in flight
-                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e, compact, cq);
-                Cand x1 = edge_cand<RATIO>(col, w, rec, ws, sign, e + g, compact, cq);
+                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
+                Cand x1 = edge_cand<RATIO>(col, w, rec, ws, sign, e + g);
                 if (e == pv) own = x0;
                 if (e + g == pv) own = x1;
                 if (better(x0, best)) best = x0;
                 if (better(x1, best)) best = x1;
             }
             if (e < e_end) {
-                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e, compact, cq);
+                Cand x0 = edge_cand<RATIO>(col, w, rec, ws, sign, e);
                 if (e == pv) own = x0;
                 if (better(x0, best)) best = x0;
             }
@@ -676,8 +668,6 @@ improve_heavy_chunk_kernel(const int *__restrict__ row_ptr, const int *__restric
     const int *hv = ws.cls_list + ws.ctrl->cls_off[kClasses];
     const int total = ws.ctrl->heavy_edges;
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
-    const bool compact = !RATIO && ws.ctrl->compact;
-    const long long cq = ws.ctrl->compact_q;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Cand none{INT_MIN, INT_MAX, LLONG_MIN};
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -694,8 +684,7 @@ improve_heavy_chunk_kernel(const int *__restrict__ row_ptr, const int *__restric
         Cand b0 = none, b1 = none;
         for (int g = g0 + (int)threadIdx.x; g < g1; g += blockDim.x) {
             const bool first = g < split;
-            const Cand x = edge_cand<RATIO>(col, w, rec, ws, sign, (first ? base0 : base1) + g,
-                                            compact, cq);
+            const Cand x = edge_cand<RATIO>(col, w, rec, ws, sign, (first ? base0 : base1) + g);
             if (first) {
                 if (better(x, b0)) b0 = x;
             } else if (better(x, b1)) {
@@ -738,14 +727,7 @@ improve_heavy_final_kernel(const int *__restrict__ col, const int *__restrict__ 
         const Cand best = heavy_combine(ws, i, s_w);
         if (threadIdx.x == 0 && !(bs.G && bs.gconv[bs.gid[v]])) {
             const int t = ws.succ[v];
-            int4 r;
-            if (!RATIO && ws.ctrl->compact) {   // V only; rank 0, the cycle's q
-                const long long Vt = __ldg(&ws.recv[t]);
-                r = make_int4((int)(unsigned)(Vt & 0xffffffffLL), (int)(Vt >> 32), 0,
-                              ws.ctrl->compact_q);
-            } else {
-                r = __ldg(&rec[t]);
-            }
+            const int4 r = __ldg(&rec[t]);
             const long long V = ((long long)(unsigned)r.x) | ((long long)r.y << 32);
             long long cur_key = (long long)r.w * (long long)ws.wpi[v] + V;
             if (RATIO) cur_key -= __ldg(&ws.recp[t]) * (long long)ws.tpi[v];
