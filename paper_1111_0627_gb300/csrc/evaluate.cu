@@ -676,7 +676,7 @@ int prepare_evaluate(bool ratio) {
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       int nwords, Workspace ws, BatchState bs);
-constexpr int kLocalBitmapWords = 40960;   // 160 KB: bitmap and prefix counts of ranges up to 655,360 vertices
+constexpr int kLocalBitmapWords = 40960;   // 160 KB: the bitmaps of ranges up to 436,906 vertices
 int evaluate_local_blocks(int n);
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
@@ -689,7 +689,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         const int blocks = evaluate_local_blocks(n);
         if (blocks <= 0) return -1;
         const int R = (n + blocks - 1) / blocks;
-        const int words = 2 * ((R + 31) / 32);   // the bitmap and its prefix counts
+        const int words = 3 * ((R + 31) / 32);   // two bitmaps and the prefix counts
         const int nwords = words <= kLocalBitmapWords ? words : 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
@@ -1136,15 +1136,16 @@ static __device__ __forceinline__ PackedState pk_make(unsigned J, unsigned len, 
 }
 
 // Leaves (vertices no vertex of the range points to, about a third of them in
-// a random policy graph) are never a jump target.  When the range's
-// predecessor bitmap fits in shared memory (bits, nwords words; the same
-// again holds per-word prefix counts), the other vertices are renumbered
-// densely in vertex order (rank = set bits before them) and the rounds run on
-// that dense index space -- states and lists stay contiguous, so a warp's
-// accesses fill whole sectors -- while the leaves take their successor's
-// final state at the end.  Without the bitmap every vertex takes part.  In
-// the packed state a pending vertex's jump target is a dense index, a
-// finished one's the local index of its exit.
+// a random policy graph) are never a jump target, and neither are vertices
+// whose predecessors are all leaves.  When three bitmaps of the range fit in
+// shared memory (bits, nwords words: has a predecessor, has a predecessor that
+// is no leaf, and per-word prefix counts of the latter), the kept vertices
+// are renumbered densely in vertex order (rank = set bits before them) and
+// the rounds run on that dense index space -- states and lists stay
+// contiguous, so a warp's accesses fill whole sectors -- while the two levels
+// of leaves take their successor's final state at the end.  Without the
+// bitmaps every vertex takes part.  In the packed state a pending vertex's
+// jump target is a dense index, a finished one's the local index of its exit.
 static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const Workspace &ws,
                                     int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
                                     unsigned *bits, int nwords, int *work_total) {
@@ -1153,45 +1154,60 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
     const int W = blockDim.x;
     const int nv = hi - lo;
     const int nw = (nv + 31) / 32;
-    const bool trim = nwords > 0 && 2 * nw <= nwords;
-    unsigned *pref = bits + nw;   // set bits in the words before each word
+    const bool trim = nwords > 0 && 3 * nw <= nwords;
+    unsigned *keep_bits = bits + nw;   // vertices with a predecessor that is no leaf
+    unsigned *pref = bits + 2 * nw;    // set keep bits in the words before each word
     PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec) + lo,
                          reinterpret_cast<PackedState *>(ws.jls[1]) + lo};
     int *orig = ws.aprev + lo;    // dense index -> vertex
     if (threadIdx.x == 0) *s_flag = 0;
     int nd = nv;                  // vertices in the dense space
     if (trim) {
-        for (int i = threadIdx.x; i < nw; i += W) bits[i] = 0u;
+        for (int i = threadIdx.x; i < 2 * nw; i += W) bits[i] = 0u;
         __syncthreads();
         for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
             const int sv = ws.succ[v];
             if (sv >= lo && sv < hi) atomicOr(&bits[(sv - lo) >> 5], 1u << ((sv - lo) & 31));
         }
         __syncthreads();
+        // second level: a vertex whose predecessors are all leaves is no jump
+        // target either (jumps start at kept vertices and follow successors)
+        for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+            const int l = v - lo;
+            const int sv = ws.succ[v];
+            if (((bits[l >> 5] >> (l & 31)) & 1u) && sv >= lo && sv < hi)
+                atomicOr(&keep_bits[(sv - lo) >> 5], 1u << ((sv - lo) & 31));
+        }
+        __syncthreads();
         // exclusive prefix of the word popcounts: each thread a contiguous chunk
         const int per = (nw + W - 1) / W;
         const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
         int sum = 0;
-        for (int i = w0; i < w1; ++i) sum += __popc(bits[i]);
+        for (int i = w0; i < w1; ++i) sum += __popc(keep_bits[i]);
         __shared__ int s_warp[32];
         __shared__ int s_total;
         const int incl = block_inclusive_scan(sum, s_warp);
         int run = incl - sum;
         for (int i = w0; i < w1; ++i) {
             pref[i] = (unsigned)run;
-            run += __popc(bits[i]);
+            run += __popc(keep_bits[i]);
         }
         if (threadIdx.x == W - 1) s_total = incl;
         __syncthreads();
         nd = s_total;
     }
-    auto dense = [&](int v) -> int {   // dense index of a vertex that has a predecessor
+    auto dense = [&](int v) -> int {   // dense index of a kept vertex
         const int l = v - lo;
-        return trim ? (int)pref[l >> 5] + __popc(bits[l >> 5] & ((1u << (l & 31)) - 1u)) : l;
+        return trim ? (int)pref[l >> 5] + __popc(keep_bits[l >> 5] & ((1u << (l & 31)) - 1u))
+                    : l;
     };
-    auto has_pred = [&](int v) -> bool {
+    auto has_pred = [&](int v) -> bool {   // kept: a predecessor that is no leaf
         const int l = v - lo;
-        return !trim || ((bits[l >> 5] >> (l & 31)) & 1u);
+        return !trim || ((keep_bits[l >> 5] >> (l & 31)) & 1u);
+    };
+    auto is_leaf1 = [&](int v) -> bool {   // no predecessor at all
+        const int l = v - lo;
+        return trim && !((bits[l >> 5] >> (l & 31)) & 1u);
     };
     for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
         const int sv = ws.succ[v];
@@ -1302,22 +1318,27 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             return -1;
         }
     }
-    // the leaves: one step to the successor, whose state is final; jls[0] then
-    // holds every final state, and jls[1] (a ping-pong buffer above) gets the
-    // final state of the exits (the root fix reads them there)
-    for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
-        const int sv = ws.succ[v];
-        if (sv < lo || sv >= hi) {
-            ws.jls[1][v] = JLS{~(n + v), 0, 0};
-        } else if (!has_pred(v)) {
+    // the leaves, second level first (their successors are kept vertices or
+    // exits), then the first (their successors are kept or finished second-
+    // level leaves): one step to the successor, whose state is final.  jls[0]
+    // then holds every final state, and jls[1] (a ping-pong buffer above) gets
+    // the final state of the exits (the root fix reads them there)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+            const int sv = ws.succ[v];
+            if (sv < lo || sv >= hi) {
+                if (pass == 0) ws.jls[1][v] = JLS{~(n + v), 0, 0};
+                continue;
+            }
+            if (has_pred(v) || is_leaf1(v) != (pass == 1)) continue;
             const JLS f = ws.jls[0][sv];
             const JM dm = ws.jm[1][sv];
             ws.jls[0][v] = JLS{f.J, f.len + 1, f.S + (long long)ws.wpi[v]};
             ws.rep[v] = ~f.J;
             ws.jm[1][v] = JM{f.J, min(v, dm.M)};
         }
+        __syncthreads();
     }
-    __syncthreads();
     *work_total += work;
     return 1;
 }
