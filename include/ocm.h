@@ -207,6 +207,11 @@ typedef struct ocm_options {
 #define OCM_FLAG_EVAL_LOCAL 8
 #define OCM_FLAG_EVAL_GLOBAL 16
 
+/* Test-only: the two-level evaluation runs without its shared-memory bitmaps
+ * (every vertex of a range takes part in the jump rounds), the form it takes
+ * on its own for ranges of more than 436,906 vertices.  Same results. */
+#define OCM_FLAG_TEST_NO_BITMAP 32
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
@@ -439,7 +444,8 @@ const char *ocm_status_string(int status);
  * ocm_stats.rebuild_levels; 105: ocm_solve_static,
  * OCM_STATIC_WORKSPACE_BYTES; 106: ocm_options.wait_limit_ms, the OCM_FAULT
  * test hook; 107: ocm_options.batch_small_vertices,
- * ocm_stats.batch_small_graphs). */
+ * ocm_stats.batch_small_graphs; 108: OCM_FLAG_EVAL_LOCAL, OCM_FLAG_EVAL_GLOBAL,
+ * OCM_FLAG_TEST_NO_BITMAP). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -283,6 +283,7 @@ struct StepArgs {
     bool batch;
     bool single;              // the paper's single-lambda form: rebuild after each evaluation
     bool local;               // the two-level evaluation (locality of the policy graph)
+    bool no_bitmap;           // (test) the two-level evaluation without its bitmaps
     SingleWs sg;
     int cls_cnt[kClassSlots];
     int heavy_edges;
@@ -291,7 +292,7 @@ struct StepArgs {
 // Launches one step; returns the number of kernels, or -1.
 static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHandle handle,
                        cudaStream_t st) {
-    int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st, a.local);
+    int le = launch_evaluate(a.n, a.N2, a.ws, a.stall, a.bs, st, a.local, a.no_bitmap);
     if (le < 0) return -1;
     if (a.single) {
         if (launch_connect(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.sg, st) < 0) return -1;
@@ -317,13 +318,14 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local;
+    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local, no_bitmap;
     long long N2, max_iters;
     int cls_cnt[kClassSlots];
     bool operator==(const LoopKey &o) const {
         if (dev != o.dev || row_ptr != o.row_ptr || col_idx != o.col_idx || w != o.w ||
             ctrl != o.ctrl || vptr != o.vptr || transit != o.transit || n != o.n || m != o.m ||
             sign != o.sign || single != o.single || local != o.local ||
+            no_bitmap != o.no_bitmap ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters || heavy_edges != o.heavy_edges)
             return false;
@@ -368,6 +370,7 @@ LoopKey make_key(const StepArgs &a) {
     k.G = a.bs.G;
     k.single = a.single ? 1 : 0;
     k.local = a.local ? 1 : 0;
+    k.no_bitmap = a.no_bitmap ? 1 : 0;
     k.N2 = a.N2;
     k.max_iters = a.max_iters;
     for (int c = 0; c < kClassSlots; ++c) k.cls_cnt[c] = a.cls_cnt[c];
@@ -491,7 +494,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 107; }
+int ocm_version(void) { return 108; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -670,6 +673,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.local = local_ok && ((eval_flags & OCM_FLAG_EVAL_LOCAL) ||
                             (n >= kLocalEvalMinN &&
                              (double)h.local_edges >= kLocalEvalMinFraction * (double)m));
+    sa.no_bitmap = opt && (opt->flags & OCM_FLAG_TEST_NO_BITMAP);
     sa.sg = sg;
     for (int c = 0; c < kClassSlots; ++c) sa.cls_cnt[c] = h.cls_cnt[c];
     sa.heavy_edges = (kind == OCM_SWEEP_TILES) ? 0 : h.heavy_edges;
@@ -788,7 +792,8 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (!row_ptr || !col_idx || !w || !num || !den || !cycle_out || !cycle_len) return OCM_ERR_INVALID_ARG;
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA |
-                               OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL)))
+                               OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL |
+                               OCM_FLAG_TEST_NO_BITMAP)))
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
         return OCM_ERR_INVALID_ARG;

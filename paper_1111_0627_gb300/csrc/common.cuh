@@ -361,7 +361,7 @@ int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sig
 int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st);
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
-                    cudaStream_t st, bool local = false);
+                    cudaStream_t st, bool local = false, bool no_bitmap = false);
 int prepare_evaluate_local();
 int evaluate_local_blocks(int n);
 int launch_batch_prepare(int N, int M, BatchState bs, Workspace ws, cudaStream_t st);

@@ -683,14 +683,14 @@ int evaluate_local_blocks(int n);
 // launch failure.  local: the two-level evaluation (single graphs without
 // transit times only).
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
-                    cudaStream_t st, bool local) {
+                    cudaStream_t st, bool local, bool no_bitmap) {
     const bool ratio = ws.transit != nullptr;
     if (local && !ratio && bs.G == 0) {
         const int blocks = evaluate_local_blocks(n);
         if (blocks <= 0) return -1;
         const int R = (n + blocks - 1) / blocks;
         const int words = 3 * ((R + 31) / 32);   // two bitmaps and the prefix counts
-        const int nwords = words <= kLocalBitmapWords ? words : 0;
+        const int nwords = (words <= kLocalBitmapWords && !no_bitmap) ? words : 0;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
         cfg.blockDim = dim3(kEvalThreads);

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
     import paper_1111_0627_gb300 as ocm
-    from paper_1111_0627_gb300.ocm import OCM_FLAG_EVAL_GLOBAL, OCM_FLAG_EVAL_LOCAL, OCM_FLAG_HOST_LOOP
+    from paper_1111_0627_gb300.ocm import (OCM_FLAG_EVAL_GLOBAL, OCM_FLAG_EVAL_LOCAL,
+                                           OCM_FLAG_HOST_LOOP, OCM_FLAG_TEST_NO_BITMAP)
 
 
 def _dev(g):
@@ -51,6 +52,21 @@ def test_forced_local_evaluation_on_random_graphs(mode):
         else:                 # many short cycles, self-loops and parallel edges
             g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, mode=mode)
         _check(g, OCM_FLAG_EVAL_LOCAL)
+
+
+@pytest.mark.parametrize("mode", ["max", "min"])
+def test_local_evaluation_without_bitmaps(mode):
+    """The form large ranges take (no shared-memory bitmaps: no leaf trimming,
+    every vertex in the jump rounds), forced on small graphs."""
+    rng = np.random.default_rng(1111062930 + (mode == "min"))
+    for trial in range(6):
+        n = int(rng.integers(2000, 40000))
+        if trial % 2 == 0:
+            g = synth.locality(n, int(rng.integers(2, 400)), -1000, 1000,
+                               seed=1111062960 + trial, mode=mode)
+        else:
+            g = synth.tiny_random(rng, n, max_extra=3, wlo=-9, whi=9, mode=mode)
+        _check(g, OCM_FLAG_EVAL_LOCAL | OCM_FLAG_TEST_NO_BITMAP)
 
 
 def test_local_and_global_evaluation_agree_in_both_loop_forms():
