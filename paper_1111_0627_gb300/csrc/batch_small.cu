@@ -29,6 +29,9 @@ namespace ocm {
 constexpr int kSmallThreads = 1024;
 constexpr int kSU = 4;   // vertices per thread per pass of a jump round (64 registers)
 constexpr int kSmallBuckets = 32;
+// Shared-memory words for the leaf bitmaps of one graph (two bitmap words and
+// a prefix word per 32 vertices: graphs up to 512K vertices are trimmed).
+constexpr int kSmallBitmapWords = 49152;
 
 // Size buckets of the queue: floor(log2(n_g)), largest first.
 static __device__ __forceinline__ int size_bucket(int n) { return 31 - __clz(n); }
@@ -95,8 +98,34 @@ static __device__ __forceinline__ int block_sum(int x, int *s_red) {
     return t;
 }
 
+// Inclusive sum over the block (all threads call it).
+static __device__ __forceinline__ int block_scan_incl(int x, int *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int wv = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wv, o);
+            if (lane >= o) wv += y;
+        }
+        s_warp[lane] = wv;
+    }
+    __syncthreads();
+    const int r = x + (warp > 0 ? s_warp[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
 // Policy evaluation of graph [v0, v1) inside one block, the steps of
-// evaluate_kernel over every vertex of the graph in every round (no
+// evaluate_kernel over every vertex that is no leaf in every round (no
 // worklists: a graph's state stays in L1/L2 while its block works on it, and
 // a dense pass costs less than keeping lists): cycle detection by doubling
 // with window minima, resolved vertices holding J = ~root; then value
@@ -106,75 +135,155 @@ static __device__ __forceinline__ int block_sum(int x, int *s_red) {
 // best (rank, INT_MAX - root) in *s_best.  Returns false on an error
 // (recorded in the control block).
 static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *s_red, int *s_k,
-                                      unsigned long long *s_best) {
+                                      unsigned long long *s_best, unsigned *bits, int nwords) {
     const int n = v1 - v0;
     int lg = 0;
     while ((1 << lg) < n) ++lg;
     Ctrl *c = ws.ctrl;
-    JM *X = ws.jm[0], *Y = ws.jm[1];
-    for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) X[v] = JM{ws.succ[v], v};
+    const int Wt = blockDim.x;
+    // Vertices nobody points to (leaves), and those whose predecessors are
+    // all leaves, lie on no cycle and no other vertex jumps to them: when the
+    // graph's bitmaps fit in shared memory the others are renumbered densely
+    // (rank in the "has a predecessor that is no leaf" bitmap) and the jump
+    // rounds run on that dense space; the leaves take their successor's final
+    // state at the end.
+    const int nw = (n + 31) / 32;
+    const bool trim = nwords > 0 && 3 * nw <= nwords;
+    unsigned *keepb = bits + nw, *pref = bits + 2 * nw;
+    int nk = n;
+    if (trim) {
+        for (int i = threadIdx.x; i < 2 * nw; i += Wt) bits[i] = 0u;
+        __syncthreads();
+        for (int v = v0 + (int)threadIdx.x; v < v1; v += Wt) {
+            const int l = ws.succ[v] - v0;
+            atomicOr(&bits[l >> 5], 1u << (l & 31));
+        }
+        __syncthreads();
+        for (int v = v0 + (int)threadIdx.x; v < v1; v += Wt) {
+            const int lv = v - v0;
+            if ((bits[lv >> 5] >> (lv & 31)) & 1u) {
+                const int l = ws.succ[v] - v0;
+                atomicOr(&keepb[l >> 5], 1u << (l & 31));
+            }
+        }
+        __syncthreads();
+        const int per = (nw + Wt - 1) / Wt;
+        const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+        int sum = 0;
+        for (int i = w0; i < w1; ++i) sum += __popc(keepb[i]);
+        __shared__ int s_warp[32];
+        __shared__ int s_total;
+        const int incl = block_scan_incl(sum, s_warp);
+        int run = incl - sum;
+        for (int i = w0; i < w1; ++i) {
+            pref[i] = (unsigned)run;
+            run += __popc(keepb[i]);
+        }
+        if (threadIdx.x == Wt - 1) s_total = incl;
+        __syncthreads();
+        nk = s_total;
+    }
+    auto dense = [&](int v) -> int {
+        const int l = v - v0;
+        return trim ? (int)pref[l >> 5] + __popc(keepb[l >> 5] & ((1u << (l & 31)) - 1u)) : l;
+    };
+    auto kept = [&](int v) -> bool {
+        const int l = v - v0;
+        return !trim || ((keepb[l >> 5] >> (l & 31)) & 1u);
+    };
+    auto leaf1 = [&](int v) -> bool {
+        const int l = v - v0;
+        return trim && !((bits[l >> 5] >> (l & 31)) & 1u);
+    };
+    int *orig = ws.aprev + v0;    // dense index -> vertex
+    int *ap = ws.list[0] + v0;    // previous window minimum, per dense index
+    // ---- cycle detection on the dense space (window minima of vertex ids)
+    JM *X = ws.jm[0] + v0, *Y = ws.jm[1] + v0;
+    for (int v = v0 + (int)threadIdx.x; v < v1; v += Wt) {
+        if (!kept(v)) continue;
+        const int d = dense(v);
+        orig[d] = v;
+        X[d] = JM{dense(ws.succ[v]), v};
+    }
     __syncthreads();
     for (int r = 0;; ++r) {
         int pend = 0;
-        for (int base = v0 + (int)threadIdx.x; base < v1; base += kSU * blockDim.x) {
-            JM s[kSU], t[kSU];
+        for (int base = (int)threadIdx.x; base < nk; base += kSU * Wt) {
+            JM sj[kSU], tj[kSU];
 #pragma unroll
             for (int u = 0; u < kSU; ++u) {
-                const int v = base + u * (int)blockDim.x;
-                s[u] = v < v1 ? X[v] : JM{-1, 0};
+                const int d = base + u * Wt;
+                sj[u] = d < nk ? X[d] : JM{-1, 0};
             }
 #pragma unroll
             for (int u = 0; u < kSU; ++u)
-                if (s[u].J >= 0) t[u] = X[s[u].J];
+                if (sj[u].J >= 0) tj[u] = X[sj[u].J];
 #pragma unroll
             for (int u = 0; u < kSU; ++u) {
-                const int v = base + u * (int)blockDim.x;
-                if (v >= v1) continue;
-                if (s[u].J < 0) { Y[v] = s[u]; continue; }
+                const int d = base + u * Wt;
+                if (d >= nk) continue;
+                if (sj[u].J < 0) { Y[d] = sj[u]; continue; }
                 int root = -1;
-                if (t[u].J < 0) root = ~t[u].J;
-                else if (r > 0 && t[u].M == ws.aprev[v]) root = t[u].M;
-                if (root >= 0) { Y[v] = JM{~root, 0}; ws.rep[v] = root; }
-                else { Y[v] = JM{t[u].J, min(s[u].M, t[u].M)}; ws.aprev[v] = t[u].M; ++pend; }
+                if (tj[u].J < 0) root = ~tj[u].J;
+                else if (r > 0 && tj[u].M == ap[d]) root = tj[u].M;
+                if (root >= 0) { Y[d] = JM{~root, 0}; ws.rep[orig[d]] = root; }
+                else { Y[d] = JM{tj[u].J, min(sj[u].M, tj[u].M)}; ap[d] = tj[u].M; ++pend; }
             }
         }
         JM *tmp = X; X = Y; Y = tmp;
         if (block_sum(pend, s_red) == 0) break;
         if (r + 1 > lg + 4) { if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect); return false; }
     }
-    JLS *A = ws.jls[0], *B = ws.jls[1];
-    for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
+    // ---- values on the dense space, the root terminal (final J = ~root)
+    JLS *A = ws.jls[1] + v0, *B = reinterpret_cast<JLS *>(ws.rec) + v0;
+    for (int d = (int)threadIdx.x; d < nk; d += Wt) {
+        const int v = orig[d];
         const int root = ws.rep[v];
         JLS st;
-        if (root == v) st = JLS{~v, 0, 0};
-        else { const int sv = ws.succ[v]; st = JLS{ws.rep[sv] == sv ? ~sv : sv, 1, (long long)ws.wpi[v]}; }
-        A[v] = st;
+        if (root == v) {
+            st = JLS{~v, 0, 0};
+        } else {
+            const int sv = ws.succ[v];
+            st = ws.rep[sv] == sv ? JLS{~sv, 1, (long long)ws.wpi[v]}
+                                  : JLS{dense(sv), 1, (long long)ws.wpi[v]};
+        }
+        A[d] = st;
     }
     __syncthreads();
     for (int r = 0;; ++r) {
         int pend = 0;
-        for (int base = v0 + (int)threadIdx.x; base < v1; base += kSU * blockDim.x) {
-            JLS s[kSU], t[kSU];
+        for (int base = (int)threadIdx.x; base < nk; base += kSU * Wt) {
+            JLS sj[kSU], tj[kSU];
 #pragma unroll
-            for (int u = 0; u < kSU; ++u) { const int v = base + u * (int)blockDim.x; s[u] = v < v1 ? A[v] : JLS{-1, 0, 0}; }
+            for (int u = 0; u < kSU; ++u) { const int d = base + u * Wt; sj[u] = d < nk ? A[d] : JLS{-1, 0, 0}; }
 #pragma unroll
-            for (int u = 0; u < kSU; ++u) if (s[u].J >= 0) t[u] = A[s[u].J];
+            for (int u = 0; u < kSU; ++u) if (sj[u].J >= 0) tj[u] = A[sj[u].J];
 #pragma unroll
             for (int u = 0; u < kSU; ++u) {
-                const int v = base + u * (int)blockDim.x;
-                if (v >= v1) continue;
-                if (s[u].J < 0) { B[v] = s[u]; continue; }
-                const JLS nu{t[u].J, s[u].len + t[u].len, s[u].S + t[u].S};
-                B[v] = nu; pend += nu.J >= 0;
+                const int d = base + u * Wt;
+                if (d >= nk) continue;
+                if (sj[u].J < 0) { B[d] = sj[u]; continue; }
+                const JLS nu{tj[u].J, sj[u].len + tj[u].len, sj[u].S + tj[u].S};
+                B[d] = nu; pend += nu.J >= 0;
             }
         }
         JLS *tmp = A; A = B; B = tmp;
         if (block_sum(pend, s_red) == 0) break;
         if (r + 1 > lg + 3) { if (threadIdx.x == 0) atomicOr(&c->err, kErrValue); return false; }
     }
-    if (A != ws.jls[0])
-        for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) ws.jls[0][v] = A[v];
+    // final states at the vertices' own indices (jls[0], which the extraction
+    // reads), then the leaves: second level first, from their successors
+    for (int d = (int)threadIdx.x; d < nk; d += Wt) ws.jls[0][orig[d]] = A[d];
     __syncthreads();
+    for (int pass = 0; pass < 2 && trim; ++pass) {
+        for (int v = v0 + (int)threadIdx.x; v < v1; v += Wt) {
+            if (kept(v) || leaf1(v) != (pass == 1)) continue;
+            const JLS f = ws.jls[0][ws.succ[v]];
+            ws.jls[0][v] = JLS{f.J, f.len + 1, f.S + (long long)ws.wpi[v]};
+            ws.rep[v] = ~f.J;
+        }
+        __syncthreads();
+    }
     const unsigned W = blockDim.x;
     A = ws.jls[0];
     // ---- cycles: mean W/L reduced, exact key, rank among this graph's cycles
@@ -314,7 +423,8 @@ static __device__ int small_sweep(int v0, int v1, const int *__restrict__ row_pt
 __global__ void __launch_bounds__(kSmallThreads, 1)
 small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, const int *__restrict__ queue,
-                   long long max_iters, Workspace ws, BatchState bs) {
+                   long long max_iters, int nwords, Workspace ws, BatchState bs) {
+    extern __shared__ unsigned s_bits[];
     __shared__ int s_red[kSmallThreads / 32];
     __shared__ int s_task, s_k, s_stop;
     __shared__ unsigned long long s_best;
@@ -331,7 +441,7 @@ small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         long long it = 0;
         bool ok = true;
         for (;;) {
-            if (!small_evaluate(v0, v1, ws, s_red, &s_k, &s_best)) {
+            if (!small_evaluate(v0, v1, ws, s_red, &s_k, &s_best, s_bits, nwords)) {
                 ok = false;
                 break;
             }
@@ -382,8 +492,12 @@ int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sig
         int sms = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return -1;
+        if (cudaFuncSetAttribute(small_graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmallBitmapWords * 4) != cudaSuccess)
+            return -1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_graph_kernel,
-                                                          kSmallThreads, 0) != cudaSuccess ||
+                                                          kSmallThreads,
+                                                          kSmallBitmapWords * 4) != cudaSuccess ||
             per_sm < 1)
             return -1;
         cached_blocks = sms * per_sm;
@@ -400,8 +514,8 @@ int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sig
     prof_begin(kProfEvaluate, st);
     small_count_kernel<<<gb, kThreads, 0, st>>>(row_ptr, bs, max_n, ws.ctrl);
     small_fill_kernel<<<gb, kThreads, 0, st>>>(row_ptr, bs, max_n, ws.ctrl, queue);
-    small_graph_kernel<<<cached_blocks, kSmallThreads, 0, st>>>(row_ptr, col, w, sign, queue,
-                                                                max_iters, ws, bs);
+    small_graph_kernel<<<cached_blocks, kSmallThreads, kSmallBitmapWords * 4, st>>>(
+        row_ptr, col, w, sign, queue, max_iters, kSmallBitmapWords, ws, bs);
     prof_end(kProfEvaluate, st);
     return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
