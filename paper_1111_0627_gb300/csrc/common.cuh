@@ -273,13 +273,31 @@ __device__ __forceinline__ void publish_result(const Workspace &ws, int n) {
     }
 }
 
+// Local state of v after the two-level evaluation's local phase.  A vertex
+// that no vertex of its range jumps to (a "leaf": no predecessor in the
+// range, or leaves only) keeps the one step to its successor, J = succ(v) >= 0,
+// len 1 and its edge weight, and is completed here by following those steps:
+// at most two, since the successor of a leaf whose predecessors are all
+// leaves has a state of its own.  Every other state is returned as stored.
+__device__ __forceinline__ JLS local_state(const JLS *jls0, int v) {
+    JLS st = jls0[v];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (st.J < 0) break;
+        const JLS nx = jls0[st.J];
+        st = JLS{nx.J, st.len + nx.len, st.S + nx.S};
+    }
+    return st;
+}
+
 // Final value state (J = ~root, len, S) of vertex v from the evaluation's
 // value buffer.  After the two-level evaluation a vertex whose path leaves its
 // block range holds its state to the exit x it leaves by (J = ~(n + x)), and
-// its final state adds x's (an exit's own state is final); after the one-level
-// evaluation every state is final and this is a plain load.
+// its final state adds x's (an exit's own state is final); a leaf holds one
+// step to its successor (local_state).  After the one-level evaluation every
+// state is final and this is a plain load.
 __device__ __forceinline__ JLS final_value(const JLS *jls0, int n, int v) {
-    JLS st = jls0[v];
+    JLS st = local_state(jls0, v);
     const int tag = ~st.J;
     if (tag >= n) {
         const JLS nf = jls0[tag - n];

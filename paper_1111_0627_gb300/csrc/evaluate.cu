@@ -1113,9 +1113,9 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, bool list_
 // length (saturating), 42-62 the path minimum (local indices; all ones: none),
 // bit 63 finished, then the weight.  Ping-pong buffers: the records (dead
 // until this evaluation writes them again) and the second value buffer; a
-// finished vertex writes its final {~tag, len, S} to jls[0], its tag and its
-// {~tag, path minimum} for the node graph once (jls[1] then holds final
-// states only for the exits).  A path still unfinished after
+// finished vertex writes its final {~tag, len, S} to jls[0] and its
+// {~tag, path minimum} for the node graph once; rep holds n + x for an exit
+// x and -1 for the others (the tags are in jls[0]).  A path still unfinished after
 // as many steps as the range has vertices lies in the basin of a cycle inside
 // the range: the block then reports it and runs the two-pass phase instead.
 // Needs ranges of fewer than 2^21 - 1 vertices.  Returns 1 done, 0 a cycle
@@ -1143,8 +1143,9 @@ static __device__ __forceinline__ PackedState pk_make(unsigned J, unsigned len, 
 // are renumbered densely in vertex order (rank = set bits before them) and
 // the rounds run on that dense index space -- states and lists stay
 // contiguous, so a warp's accesses fill whole sectors -- while the two levels
-// of leaves take their successor's final state at the end.  Without the
-// bitmaps every vertex takes part.  In the packed state a pending vertex's
+// of leaves keep the one step to their successor in jls[0] (J = succ >= 0),
+// which every reader completes (local_state): no pass over the range for
+// them at the end.  Without the bitmaps every vertex takes part.  In the packed state a pending vertex's
 // jump target is a dense index, a finished one's the local index of its exit.
 static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const Workspace &ws,
                                     int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
@@ -1205,10 +1206,6 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
         const int l = v - lo;
         return !trim || ((keep_bits[l >> 5] >> (l & 31)) & 1u);
     };
-    auto is_leaf1 = [&](int v) -> bool {   // no predecessor at all
-        const int l = v - lo;
-        return trim && !((bits[l >> 5] >> (l & 31)) & 1u);
-    };
     for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
         const int sv = ws.succ[v];
         const bool is_exit = sv < lo || sv >= hi;
@@ -1216,8 +1213,13 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             ws.jls[0][v] = JLS{~(n + v), 0, 0};
             ws.rep[v] = n + v;
             ws.jm[1][v] = JM{~(n + v), INT_MAX};
+        } else {
+            ws.rep[v] = -1;   // no root, no exit (the root fix sets the roots)
         }
-        if (!has_pred(v)) continue;   // a leaf: finished at the end
+        if (!has_pred(v)) {   // a leaf: one step to its successor, completed on read
+            if (!is_exit) ws.jls[0][v] = JLS{sv, 1, (long long)ws.wpi[v]};
+            continue;
+        }
         const int d = dense(v);
         orig[d] = v;
         if (is_exit) {
@@ -1288,7 +1290,6 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
                             const int v = orig[d];
                             const int tag = n + lo + (int)J;   // the exit the path leaves by
                             ws.jls[0][v] = JLS{~tag, (int)len, S};
-                            ws.rep[v] = tag;
                             ws.jm[1][v] = JM{~tag, M == kPkNone ? INT_MAX : lo + (int)M};
                         } else if ((int)len >= nv) {
                             basin = true;     // no exit within the range: a cycle inside it
@@ -1317,27 +1318,6 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
             return -1;
         }
-    }
-    // the leaves, second level first (their successors are kept vertices or
-    // exits), then the first (their successors are kept or finished second-
-    // level leaves): one step to the successor, whose state is final.  jls[0]
-    // then holds every final state, and jls[1] (a ping-pong buffer above) gets
-    // the final state of the exits (the root fix reads them there)
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
-            const int sv = ws.succ[v];
-            if (sv < lo || sv >= hi) {
-                if (pass == 0) ws.jls[1][v] = JLS{~(n + v), 0, 0};
-                continue;
-            }
-            if (has_pred(v) || is_leaf1(v) != (pass == 1)) continue;
-            const JLS f = ws.jls[0][sv];
-            const JM dm = ws.jm[1][sv];
-            ws.jls[0][v] = JLS{f.J, f.len + 1, f.S + (long long)ws.wpi[v]};
-            ws.rep[v] = ~f.J;
-            ws.jm[1][v] = JM{f.J, min(v, dm.M)};
-        }
-        __syncthreads();
     }
     *work_total += work;
     return 1;
@@ -1397,15 +1377,25 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         const int y = ws.succ[x];
-        const int ty = ws.rep[y];
+        // y's local result: through a leaf's steps to the first vertex with a
+        // state of its own (the leaves passed count for the path minimum)
+        int z = y, mz = INT_MAX;
+        JLS f = ws.jls[0][z];
+        for (int k = 0; k < 2 && f.J >= 0; ++k) {
+            mz = min(mz, z);
+            z = f.J;
+            f = ws.jls[0][z];
+        }
+        const int ty = ~f.J;
         JM node;
         if (ty < n) {
             node = JM{~ty, 0};   // succ(x)'s path ends on a cycle inside its range
         } else {
-            const JM d = ws.jm[1][y];   // y's local final: aux = smallest vertex before its exit
-            node = JM{ty - n, min(x, d.M)};
+            const JM d = ws.jm[1][z];   // aux = smallest vertex before the exit
+            node = JM{ty - n, min(x, min(mz, d.M))};
         }
         ws.jm[0][x] = node;
+        ws.jls[1][x] = JLS{~(n + x), 0, 0};   // the exits' local state in both buffers
     }
     if (!grid_barrier(c, nblocks)) return;
     int nr = 0;
@@ -1461,7 +1451,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         for (int i = 0; i < k; ++i) {
             const int rt = ws.cyc_root[K_local + i];
             c->fix_root[i] = rt;
-            c->fix_tag[i] = ws.rep[rt];
+            c->fix_tag[i] = ~local_state(ws.jls[0], rt).J;
         }
         c->fix_k = k;
         c->fix_cnt = 0;
@@ -1500,7 +1490,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
             const int v = rlo + (int)(q % R);
             if (seen || v >= n) continue;
             bool root = false, member = false;
-            const int tag = ws.rep[v];
+            const int tag = ~ws.jls[0][v].J;   // (a leaf: no tag, completed on read)
             for (int i = 0; i < k_new; ++i) {
                 root |= s_roots[i] == v;
                 member |= s_tags[i] == tag;
@@ -1559,42 +1549,32 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     }
     if (!grid_barrier(c, nblocks)) return;
 
-    // ---- node graph: (len, S) of every exit to its root
+    // ---- node graph: (len, S) of every exit to its root (the exits' entries
+    //      of jls[0] keep their local state until the jumping below)
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         JLS node;
-        bool fin = true;
         if (ws.rep[x] == x) {
             node = JLS{~x, 0, 0};   // an exit that is itself a root
         } else {
-            const int y = ws.succ[x];
-            const int ty = ws.rep[y];
-            const int ylo = (y / R) * R, yhi = min(ylo + R, n);
-            const int sy = ws.succ[y];
-            long long ll = 0, ls = 0;
-            if (!(sy < ylo || sy >= yhi) || ty == y) {   // y is no exit, or a root
-                const JLS f = ws.jls[0][y];
-                ll = f.len;
-                ls = f.S;
-            }
-            const int len = 1 + (int)ll;
-            const long long S = (long long)ws.wpi[x] + ls;
+            const JLS f = local_state(ws.jls[0], ws.succ[x]);
+            const int ty = ~f.J;
+            const int len = 1 + f.len;
+            const long long S = (long long)ws.wpi[x] + f.S;
             if (ty < n) {
                 node = JLS{~ty, len, S};
             } else {
                 const int xn = ty - n;
-                fin = ws.rep[xn] == xn;
-                node = JLS{fin ? ~xn : xn, len, S};
+                node = JLS{ws.rep[xn] == xn ? ~xn : xn, len, S};
             }
         }
-        ws.jls[0][x] = node;
-        if (fin) ws.jls[1][x] = node;
+        ws.jls[1][x] = node;
     }
     if (!grid_barrier(c, nblocks)) return;
-    int FN = 0;
+    int FN = 1;
     for (int j = 1;; ++j) {
-        const JLS *in = ws.jls[(j + 1) & 1];
-        JLS *out = ws.jls[j & 1];
+        const JLS *in = ws.jls[j & 1];
+        JLS *out = ws.jls[(j + 1) & 1];
         int pend = 0;
         for (int i = first + threadIdx.x; i < K_exit; i += stride) {
             const int x = X[i];
@@ -1612,7 +1592,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         const int left = grid_sum_barrier(c, nblocks, pend, &ok);
         if (!ok) return;
         ++nr;
-        FN = j & 1;
+        FN = (j + 1) & 1;
         if (left == 0) break;
         if (j + 1 > max_node) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
