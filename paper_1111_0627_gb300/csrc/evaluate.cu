@@ -1162,13 +1162,16 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
                          reinterpret_cast<PackedState *>(ws.jls[1]) + lo};
     int *orig = ws.aprev + lo;    // dense index -> vertex
     if (threadIdx.x == 0) *s_flag = 0;
+    __shared__ int s_warp[32];
     int nd = nv;                  // vertices in the dense space
+    int my_exits = 0;             // exits among this thread's vertices
     if (trim) {
         for (int i = threadIdx.x; i < 2 * nw; i += W) bits[i] = 0u;
         __syncthreads();
         for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
             const int sv = ws.succ[v];
             if (sv >= lo && sv < hi) atomicOr(&bits[(sv - lo) >> 5], 1u << ((sv - lo) & 31));
+            else ++my_exits;
         }
         __syncthreads();
         // second level: a vertex whose predecessors are all leaves is no jump
@@ -1185,7 +1188,6 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
         const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
         int sum = 0;
         for (int i = w0; i < w1; ++i) sum += __popc(keep_bits[i]);
-        __shared__ int s_warp[32];
         __shared__ int s_total;
         const int incl = block_inclusive_scan(sum, s_warp);
         int run = incl - sum;
@@ -1196,6 +1198,21 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
         if (threadIdx.x == W - 1) s_total = incl;
         __syncthreads();
         nd = s_total;
+    } else {
+        for (int v = lo + (int)threadIdx.x; v < hi; v += W) {
+            const int sv = ws.succ[v];
+            my_exits += sv < lo || sv >= hi;
+        }
+    }
+    // the node list: every exit once; each thread's exits take consecutive
+    // slots (one global atomic per block)
+    int xpos;
+    {
+        __shared__ int s_xbase;
+        const int incl = block_inclusive_scan(my_exits, s_warp);
+        if (threadIdx.x == W - 1) s_xbase = atomicAdd(&c->node_cnt, incl);
+        __syncthreads();
+        xpos = s_xbase + incl - my_exits;
     }
     auto dense = [&](int v) -> int {   // dense index of a kept vertex
         const int l = v - lo;
@@ -1213,13 +1230,14 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             ws.jls[0][v] = JLS{~(n + v), 0, 0};
             ws.rep[v] = n + v;
             ws.jm[1][v] = JM{~(n + v), INT_MAX};
+            ws.list[2][xpos++] = v;
         } else {
+            // one step to the successor: final for a leaf, completed on read;
+            // a kept vertex overwrites it with its final state below
+            ws.jls[0][v] = JLS{sv, 1, (long long)ws.wpi[v]};
             ws.rep[v] = -1;   // no root, no exit (the root fix sets the roots)
         }
-        if (!has_pred(v)) {   // a leaf: one step to its successor, completed on read
-            if (!is_exit) ws.jls[0][v] = JLS{sv, 1, (long long)ws.wpi[v]};
-            continue;
-        }
+        if (!has_pred(v)) continue;   // a leaf
         const int d = dense(v);
         orig[d] = v;
         if (is_exit) {
@@ -1229,15 +1247,6 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
         } else {
             P[0][d] = pk_make((unsigned)dense(sv), 1, (unsigned)(v - lo), false,
                               (long long)ws.wpi[v]);
-        }
-    }
-    // the node list: every exit once
-    {
-        const int pad = (W - (nv % W)) % W;
-        for (int v = lo + (int)threadIdx.x; v < hi + pad; v += W) {
-            const bool is_exit = v < hi && (ws.succ[v] < lo || ws.succ[v] >= hi);
-            const int pos = warp_append(&c->node_cnt, is_exit, lane);
-            if (is_exit) ws.list[2][pos] = v;
         }
     }
     __syncthreads();
