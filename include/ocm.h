@@ -92,7 +92,7 @@ typedef struct ocm_options {
      * these.                                                                 */
     int32_t edges_per_lane;
     int32_t sweep_threads;
-    int32_t sweep_kind;  /* OCM_SWEEP_*; 0 = library default (degree classes)      */
+    int32_t sweep_kind;  /* OCM_SWEEP_*; 0 = library default (see there)           */
     /* Limit of every device-side wait of the call (the grid barriers of the
      * cooperative kernels), in milliseconds of GPU wall-clock time; a wait
      * that runs out makes the call return OCM_ERR_TIMEOUT and leaves the
@@ -149,10 +149,27 @@ typedef struct ocm_options {
  *   128 or 256 threads (512 runs as 256).
  * OCM_SWEEP_CLASSES: vertices grouped by degree class; a vertex of out-degree
  *   d is served by the smallest power-of-two lane group g <= 32 with
- *   d <= edges_per_lane * g (edges_per_lane 1..64; default 8).             */
+ *   d <= edges_per_lane * g (edges_per_lane 1..64; default 8).  The grid
+ *   takes the classes band by band (2^18 consecutive vertices at a time), so
+ *   the target records a band's edges gather stay in L2 between the class
+ *   passes.
+ * OCM_SWEEP_WINDOW: for graphs whose edges mostly point near their source in
+ *   vertex order.  One thread block per SM walks a contiguous chunk of
+ *   vertices in tiles of 2,048; bulk copies keep the records of a window of
+ *   10,240 vertices around the tile in shared memory (the window starts hb
+ *   vertices before the tile, hb in {0, 2048, ..., 8192} chosen by the
+ *   initial pass as the placement holding most edges), and targets inside
+ *   it are read from there.  Inside a tile vertices are grouped by degree
+ *   class as in OCM_SWEEP_CLASSES (edges_per_lane likewise; sweep_threads is
+ *   not used).  Not for the cycle ratio (OCM_SWEEP_CLASSES then).  On the
+ *   2^25-vertex locality graph it runs slower than OCM_SWEEP_CLASSES (fewer
+ *   warps in flight per SM), so it is never chosen by default.
+ * OCM_SWEEP_DEFAULT is OCM_SWEEP_CLASSES; ocm_stats.sweep_kind reports the
+ *   layout used.                                                           */
 #define OCM_SWEEP_DEFAULT 0
 #define OCM_SWEEP_CLASSES 1
 #define OCM_SWEEP_TILES 2
+#define OCM_SWEEP_WINDOW 3
 
 /* Test-only: the first grid barrier of the evaluation waits for an arrival
  * that never comes, with its wait limit cut to 10 ms (or to
@@ -227,7 +244,7 @@ typedef struct ocm_stats {
                                rebuilds, summed over iterations; 0 otherwise         */
     int32_t batch_small_graphs; /* ocm_solve_batch: graphs solved one per thread block
                                    (see ocm_options.batch_small_vertices)          */
-    int32_t reserved2;
+    int32_t sweep_kind;     /* OCM_SWEEP_* layout the improvement sweep used        */
 } ocm_stats;
 
 /* Bytes of device workspace ocm_solve needs for a graph with n vertices and m
@@ -445,7 +462,7 @@ const char *ocm_status_string(int status);
  * OCM_STATIC_WORKSPACE_BYTES; 106: ocm_options.wait_limit_ms, the OCM_FAULT
  * test hook; 107: ocm_options.batch_small_vertices,
  * ocm_stats.batch_small_graphs; 108: OCM_FLAG_EVAL_LOCAL, OCM_FLAG_EVAL_GLOBAL,
- * OCM_FLAG_TEST_NO_BITMAP). */
+ * OCM_FLAG_TEST_NO_BITMAP; 109: OCM_SWEEP_WINDOW, ocm_stats.sweep_kind). */
 int ocm_version(void);
 
 #ifdef __cplusplus

@@ -19,7 +19,7 @@ CSRC = os.path.join(_PKG, "csrc")
 BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libocm.so")
 INCLUDE = os.path.join(_ROOT, "include")
-SOURCES = ["sweep.cu", "sweep_tiles.cu", "evaluate.cu", "batch.cu", "batch_small.cu", "api.cu",
+SOURCES = ["sweep.cu", "sweep_tiles.cu", "sweep_window.cu", "evaluate.cu", "batch.cu", "batch_small.cu", "api.cu",
            "static_ws.cu", "scc.cu", "single.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -93,7 +93,7 @@ class OcmStats(ctypes.Structure):
                 ("switched", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("detect_items", ctypes.c_int64), ("value_items", ctypes.c_int64),
                 ("graph_loop", ctypes.c_int32), ("rebuild_levels", ctypes.c_int32),
-                ("batch_small_graphs", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("batch_small_graphs", ctypes.c_int32), ("sweep_kind", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

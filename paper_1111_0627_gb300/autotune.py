@@ -26,9 +26,10 @@ import torch
 
 from . import _native
 
-TILES, CLASSES = 2, 1   # OCM_SWEEP_TILES, OCM_SWEEP_CLASSES (include/ocm.h)
+TILES, CLASSES, WINDOW = 2, 1, 3   # OCM_SWEEP_TILES, _CLASSES, _WINDOW (include/ocm.h)
 CANDIDATES = ([(TILES, epl, thr) for epl in (4, 8) for thr in (64, 128, 256)] +
-              [(CLASSES, epl, thr) for epl in (2, 4, 8, 16, 32) for thr in (128, 256, 512)])
+              [(CLASSES, epl, thr) for epl in (2, 4, 8, 16, 32) for thr in (128, 256, 512)] +
+              [(WINDOW, epl, 512) for epl in (2, 4, 8, 16)])
 SWEEP_CLASS = 1       # profiling class of the improvement sweep (include/ocm.h)
 _lock = threading.Lock()
 

@@ -51,6 +51,8 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.sw_iter = static_cast<int *>(take(4 * N));
     w.cls_list = static_cast<int *>(take(4 * N));
     w.cls_hist = static_cast<int *>(take(4 * (size_t)kClassSlots * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.band_grp = static_cast<int4 *>(
+        take(sizeof(int4) * ((size_t)kClasses * ((N + kSweepBand - 1) / kSweepBand) + 1)));
     w.heavy_off = static_cast<int *>(take(4 * (N + 1)));
     w.heavy_part = static_cast<Cand *>(take(sizeof(Cand) * 2 * ((size_t)m / kHeavyChunk + 2)));
     w.tile_v = static_cast<int *>(take(4 * (T + 1)));
@@ -276,7 +278,8 @@ __global__ void loop_control_kernel(Ctrl *c, long long max_iters, int use_cond,
 struct StepArgs {
     const int32_t *row_ptr, *col_idx, *w;
     int n, m, sign, threads, stall;
-    int kind, epl;            // sweep layout (OCM_SWEEP_TILES or _CLASSES) and its lane load
+    int kind, epl;            // sweep layout (OCM_SWEEP_TILES, _CLASSES or _WINDOW) and its lane load
+    int win_hb;               // window sweep: the window starts this many vertices before the tile
     long long N2, max_iters;
     Workspace ws;
     BatchState bs;
@@ -301,6 +304,9 @@ static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHand
     const int ks = (a.kind == OCM_SWEEP_TILES)
                        ? launch_sweep_tiles(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.m, a.epl,
                                             a.ws, a.bs, a.threads, st)
+                   : (a.kind == OCM_SWEEP_WINDOW)
+                       ? launch_sweep_window(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.epl,
+                                             a.win_hb, a.ws, a.cls_cnt, a.heavy_edges, a.bs, st)
                        : launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt,
                                       a.heavy_edges, a.bs, a.threads, st);
     if (ks < 0) return -1;
@@ -318,7 +324,7 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local, no_bitmap;
+    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local, no_bitmap, win_hb;
     long long N2, max_iters;
     int cls_cnt[kClassSlots];
     bool operator==(const LoopKey &o) const {
@@ -327,6 +333,7 @@ struct LoopKey {
             sign != o.sign || single != o.single || local != o.local ||
             no_bitmap != o.no_bitmap ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
+            win_hb != o.win_hb ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters || heavy_edges != o.heavy_edges)
             return false;
         for (int c = 0; c < kClassSlots; ++c)
@@ -364,6 +371,7 @@ LoopKey make_key(const StepArgs &a) {
     k.m = a.m;
     k.kind = a.kind;
     k.epl = a.epl;
+    k.win_hb = a.win_hb;
     k.sign = a.sign;
     k.threads = a.threads;
     k.stall = a.stall;
@@ -494,7 +502,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 108; }
+int ocm_version(void) { return 109; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -584,8 +592,10 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     //    the initial policy (the paper's first pass from val = 0, lambda = 0),
     //    which also validates col_idx and w and measures max|w|
     // (the edge-tiled sweep has no cycle-ratio form)
-    const int kind = (opt && opt->sweep_kind == OCM_SWEEP_TILES && !ratio) ? OCM_SWEEP_TILES
-                                                                          : OCM_SWEEP_CLASSES;
+    // (the window sweep is decided after the initial pass, which measures the
+    // locality it relies on; it groups vertices by the same degree classes)
+    const int req_kind = opt ? opt->sweep_kind : OCM_SWEEP_DEFAULT;
+    int kind = (req_kind == OCM_SWEEP_TILES && !ratio) ? OCM_SWEEP_TILES : OCM_SWEEP_CLASSES;
     int epl = (opt && opt->edges_per_lane > 0) ? opt->edges_per_lane : kEdgesPerLane;
     if (epl > 64) epl = 64;
     if (kind == OCM_SWEEP_TILES) epl = epl <= 4 ? 4 : 8;
@@ -625,6 +635,16 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
             return OCM_ERR_OVERFLOW;
     }
     const long long N2 = nmax * nmax;
+    // the window sweep (asked for; the mean only): the window placement that
+    // holds the most edges
+    int win_hb = 0;
+    if (kind == OCM_SWEEP_CLASSES && !ratio && req_kind == OCM_SWEEP_WINDOW) {
+        int best = 0;
+        for (int j = 1; j < kWinShapes; ++j)
+            if (h.win_edges[j] > h.win_edges[best]) best = j;
+        kind = OCM_SWEEP_WINDOW;
+        win_hb = best * kWinTile;
+    }
     const long long max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : 4LL * n + 64;
     if (single) {
         // the backward search of the rebuild walks the transposed graph
@@ -660,6 +680,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.m = m;
     sa.kind = kind;
     sa.epl = epl;
+    sa.win_hb = win_hb;
     sa.sign = sign;
     sa.threads = (sweep_threads == 64 || sweep_threads == 128 || sweep_threads == 256 ||
                   sweep_threads == 512) ? sweep_threads : kSweepThreads;
@@ -679,8 +700,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.heavy_edges = (kind == OCM_SWEEP_TILES) ? 0 : h.heavy_edges;
     if ((single && prepare_connect() != 0) || prepare_evaluate(ratio) != 0 ||
         (sa.local && prepare_evaluate_local() != 0) ||
-        (kind == OCM_SWEEP_TILES ? prepare_sweep_tiles(epl, sa.threads)
-                                 : prepare_sweep_classes(sa.threads, ratio)) != 0)
+        (kind == OCM_SWEEP_TILES    ? prepare_sweep_tiles(epl, sa.threads)
+         : kind == OCM_SWEEP_WINDOW ? prepare_sweep_window()
+                                    : prepare_sweep_classes(sa.threads, ratio)) != 0)
         return OCM_ERR_CUDA;
     const bool host_loop = (opt && (opt->flags & OCM_FLAG_HOST_LOOP)) || prof_active();
     // (a failed instantiation of the loop graph falls back to the host loop)
@@ -746,6 +768,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         stats->graph_loop = slot >= 0 ? 1 : 0;
         stats->rebuild_levels = fin.connect_levels;
         stats->batch_small_graphs = fin.small_total;
+        stats->sweep_kind = kind;
     }
     return OCM_OK;
 }
@@ -798,7 +821,7 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
         return OCM_ERR_INVALID_ARG;
     const bool single = opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA);
-    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))
+    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_WINDOW))
         return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     SolveOut out{num, den, cycle_len, cycle_out};
@@ -820,7 +843,7 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_TILES))
+    if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_WINDOW))
         return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;
     const size_t base = ocm_workspace_size(N, M);

@@ -34,11 +34,23 @@ constexpr int kEdgesPerLane = 8;       // default; ocm_options.edges_per_lane ov
 constexpr int kSweepMaxThreads = 512;  // largest sweep block (ocm_options.sweep_threads)
 constexpr int kSweepThreads = 512;     // default sweep block
 constexpr int kClassifyBlock = 1024;   // vertices per classification block
+// The degree-class sweep takes its warp tasks band by band: all classes of
+// the vertices [b * kSweepBand, (b + 1) * kSweepBand), then the next band, so
+// that the records the band's edges gather stay in L2 across the class passes.
+constexpr int kSweepBand = 1 << 18;
 constexpr int kBatchSmallDefault = 4096;   // batch: smallest automatic per-block size limit
 // The two-level evaluation is chosen for graphs of at least this many
 // vertices with at least this fraction of edges inside their block range.
 constexpr int kLocalEvalMinN = 1 << 18;
 constexpr double kLocalEvalMinFraction = 0.85;
+// Window sweep (sweep_window.cu): tiles of kWinTile vertices, each seeing the
+// records of kWinHalo more vertices in shared memory, the window starting hb
+// before the tile; the initial pass counts, for hb = j * kWinTile (j <
+// kWinShapes), the edges whose target lies in [v - hb, v - hb + kWinHalo),
+// and the sweep takes the hb that holds the most.
+constexpr int kWinTile = 2048;
+constexpr int kWinHalo = 4 * kWinTile;
+constexpr int kWinShapes = 5;
 
 // Per-vertex record the improvement sweep gathers for every edge target t:
 // the value V(t) (scaled by the denominator q of t's cycle mean), the rank of
@@ -126,6 +138,7 @@ struct Ctrl {
     int fix_root[32];         // those roots
     int fix_tag[32];          // and their tags before the fix (n + their exit)
     long long local_edges;    // edges whose target lies in the source's block range
+    long long win_edges[kWinShapes];   // edges inside each window shape of the window sweep
 };
 
 // Default limit of a device-side wait, and the one the test-only stall flag
@@ -170,6 +183,9 @@ struct Workspace {
     int *sw_iter;         // evaluation index after the sweep that last switched v
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan
+    int4 *band_grp;       // [bands * kClasses + 1] per (band, class), band-major: first
+                          //   warp task, first class-list entry, entries, class; the
+                          //   last .x = all tasks
     int *heavy_off;       // [n+1] heavy vertex i's edges are entries heavy_off[i] .. heavy_off[i+1]
                           //       of the heavy edge sequence
     struct Cand *heavy_part;  // [2 * (m / kHeavyChunk + 2)] per chunk: best of its first and
@@ -199,6 +215,15 @@ struct Cand {
     int e;
     long long key;
 };
+
+// Degree class of a vertex of out-degree d in the lane-group sweeps (the
+// smallest c with d <= epl * 2^c, capped at kClasses - 1); kClasses: heavy.
+__device__ __forceinline__ int degree_class(int d, int epl) {
+    if (d > kHeavyEdges) return kClasses;   // the heavy path
+    int c = 0;
+    while (c < kClasses - 1 && d > (epl << c)) ++c;
+    return c;
+}
 
 __device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
     if (a.rank != b.rank) return a.rank > b.rank;
@@ -367,12 +392,18 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
                  cudaStream_t st);
 int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspace ws,
                       cudaStream_t st);
+int launch_sweep_heavy(const int *row_ptr, const int *col, const int *w, int sign, Workspace ws,
+                       int H, int heavy_edges, BatchState bs, cudaStream_t st);
+int launch_sweep_window(const int *row_ptr, const int *col, const int *w, int sign, int n,
+                        int epl, int hb, Workspace ws, const int *cls_cnt, int heavy_edges,
+                        BatchState bs, cudaStream_t st);
 // Host-side kernel configuration (shared-memory opt-in, occupancy), done
 // before the loop so that a captured loop graph holds launches only;
 // 0 on success.
 int prepare_evaluate(bool ratio);
 int prepare_sweep_classes(int threads, bool ratio);
 int prepare_sweep_tiles(int edges_per_lane, int threads);
+int prepare_sweep_window();
 int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                        int edges_per_lane, Workspace ws, BatchState bs, int threads,
                        cudaStream_t st);

@@ -112,7 +112,9 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     __shared__ int s_maxw[kThreads / 32];
     __shared__ int s_maxt[kThreads / 32];
     __shared__ unsigned long long s_local[kThreads / 32];
+    __shared__ unsigned s_win[kThreads / 32][kWinShapes];
     unsigned long long local = 0;
+    unsigned win[kWinShapes] = {};   // edges inside each window shape (window sweep)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -141,6 +143,9 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             }
             maxabs = max(maxabs, x < 0 ? -x : x);
             if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
+#pragma unroll
+            for (int j = 0; j < kWinShapes; ++j)
+                win[j] += (unsigned)(t - v + j * kWinTile) < (unsigned)kWinHalo;
             if (tt) {
                 const int te = __ldg(&tt[e]);
                 if (te < 1) {
@@ -177,11 +182,15 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         maxabs = max(maxabs, __shfl_xor_sync(0xffffffffu, maxabs, o));
         maxt = max(maxt, __shfl_xor_sync(0xffffffffu, maxt, o));
         local += __shfl_xor_sync(0xffffffffu, local, o);
+#pragma unroll
+        for (int j = 0; j < kWinShapes; ++j) win[j] += __shfl_xor_sync(0xffffffffu, win[j], o);
     }
     if (lane == 0) {
         s_maxw[tid >> 5] = maxabs;
         s_maxt[tid >> 5] = maxt;
         s_local[tid >> 5] = local;
+#pragma unroll
+        for (int j = 0; j < kWinShapes; ++j) s_win[tid >> 5][j] = win[j];
     }
     __syncthreads();
     if (tid < 32) {
@@ -201,6 +210,12 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctrl->local_edges),
                                    sum);
             }
+            for (int j = 0; j < kWinShapes; ++j) {
+                unsigned long long sum = 0;
+                for (int k = 0; k < kThreads / 32; ++k) sum += s_win[k][j];
+                if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctrl->win_edges[j]),
+                                   sum);
+            }
         }
     }
 }
@@ -212,12 +227,6 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
 // when degrees are skewed.  The partition is computed once per solve (the
 // graph does not change), stable within each class, in three passes:
 // per-block counts, one exclusive scan, and a scatter.
-static __device__ __forceinline__ int degree_class(int d, int epl) {
-    if (d > kHeavyEdges) return kClasses;   // the heavy path
-    int c = 0;
-    while (c < kClasses - 1 && d > (epl << c)) ++c;
-    return c;
-}
 
 __global__ void __launch_bounds__(kClassifyBlock)
 classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, Workspace ws) {
@@ -341,6 +350,62 @@ __global__ void __launch_bounds__(1024) heavy_prep_kernel(const int *__restrict_
     }
 }
 
+// One block: the sweep's (band, class) task groups in band-major order.  The
+// class-c vertices of band b are the class-list entries from block b * B of
+// the classification (B = kSweepBand / kClassifyBlock) up to block
+// (b + 1) * B (the class list is in vertex order within a class); a group of
+// k entries takes ceil(k * 2^c / 32) warp tasks.
+__global__ void __launch_bounds__(1024) band_tasks_kernel(int n, int nb, Workspace ws) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    constexpr int B = kSweepBand / kClassifyBlock;
+    const int bands = (n + kSweepBand - 1) / kSweepBand;
+    const int groups = bands * kClasses;
+    const Ctrl *c = ws.ctrl;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < groups; base += 1024) {
+        const int i = base + threadIdx.x;
+        int4 grp = make_int4(0, 0, 0, 0);
+        int x = 0;
+        if (i < groups) {
+            const int b = i / kClasses, q = i % kClasses;
+            const int first = ws.cls_hist[q * nb + b * B];
+            const int last = (b + 1) * B < nb ? ws.cls_hist[q * nb + (b + 1) * B]
+                                               : c->cls_off[q] + c->cls_cnt[q];
+            grp = make_int4(0, first, last - first, q);
+            x = (int)((((long long)(last - first) << q) + 31) >> 5);
+        }
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((threadIdx.x & 31) >= o) incl += y;
+        }
+        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int wv = s_warp[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wv, o);
+                if (threadIdx.x >= o) wv += y;
+            }
+            s_warp[threadIdx.x] = wv;
+        }
+        __syncthreads();
+        const int warp_prefix = (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+        if (i < groups) {
+            grp.x = s_carry + warp_prefix + incl - x;
+            ws.band_grp[i] = grp;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry += warp_prefix + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ws.band_grp[groups] = make_int4(s_carry, 0, 0, 0);
+}
+
 int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st) {
     const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
     prof_begin(kProfInit, st);
@@ -348,8 +413,9 @@ int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream
     classify_scan_kernel<<<1, 1024, 0, st>>>(nb, ws);
     classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     heavy_prep_kernel<<<1, 1024, 0, st>>>(row_ptr, ws);
+    band_tasks_kernel<<<1, 1024, 0, st>>>(n, nb, ws);
     prof_end(kProfInit, st);
-    return 4;
+    return 5;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,12 +427,13 @@ int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream
 // is one of the vertex's edges, so the lane that meets it keeps its candidate
 // (no second gather for the record of succ(v)); after the butterfly every lane
 // holds the best, and that lane switches only on strict improvement in
-// (rank, key).  A persistent grid walks
-// the tasks; switches are counted in registers and published with one atomic
-// per block (same-address atomics per warp would serialise the whole sweep).
-struct ClassGrid {
-    int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
-};
+// (rank, key).  A persistent grid walks the tasks band by band (all classes
+// of a band of kSweepBand vertices, then the next band: the band's records
+// are gathered from L2 in every class pass, not again from HBM); each warp
+// keeps a cursor on the (band, class) groups, which its grid-stride steps
+// advance by a few groups at most.  Switches are counted in registers and
+// published with one atomic per block (same-address atomics per warp would
+// serialise the whole sweep).
 
 // Candidate of edge e.  Cycle ratio (RATIO): the key also subtracts
 // p_t * t(e), the target's ratio numerator times the edge's transit time;
@@ -388,7 +455,7 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
 template <bool RATIO>
 __global__ void __launch_bounds__(kSweepMaxThreads, 3)   // 40 registers: 48 warps per SM
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, int n_vertices, ClassGrid cg, Workspace ws,
+               const int *__restrict__ w, int sign, int n_vertices, int groups, Workspace ws,
                BatchState bs) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
@@ -400,18 +467,24 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     __syncthreads();
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    const int total = cg.task_off[kClasses];
+    const int4 *__restrict__ grp_tab = ws.band_grp;
+    const int total = grp_tab[groups].x;
     int switched = 0;
+    int p = 0;          // the group holding the current task: grp_tab[p].x <= task
+    int4 grp = grp_tab[0];
+    int next_start = groups > 1 ? grp_tab[1].x : total;
     for (int task = (blockIdx.x * blockDim.x + tid) >> 5; task < total; task += warps) {
-        int c = 0;
-#pragma unroll
-        for (int k = 1; k < kClasses; ++k)
-            if (task >= cg.task_off[k]) c = k;
+        while (task >= next_start) {   // (the same steps in every lane)
+            ++p;
+            grp = grp_tab[p];
+            next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+        }
+        const int c = grp.w;
         const int g = 1 << c;
         const int sub = lane & (g - 1);
-        const int idx = (task - cg.task_off[c]) * (32 >> c) + (lane >> c);
-        bool valid = idx < ws.ctrl->cls_cnt[c];
-        const int v = valid ? ws.cls_list[ws.ctrl->cls_off[c] + idx] : 0;
+        const int idx = (task - grp.x) * (32 >> c) + (lane >> c);
+        bool valid = idx < grp.z;
+        const int v = valid ? ws.cls_list[grp.y + idx] : 0;
         // batched: a graph whose last sweep switched nothing never switches
         // again (its records do not change), so its vertices are skipped
         if (valid && bs.G && bs.gconv[bs.gid[v]]) valid = false;
@@ -751,47 +824,56 @@ improve_heavy_final_kernel(const int *__restrict__ col, const int *__restrict__ 
     }
 }
 
+// The heavy vertices' chunk and combine kernels after a lane-group sweep;
+// returns the number of launches (0 without heavy vertices).
+int launch_sweep_heavy(const int *row_ptr, const int *col, const int *w, int sign, Workspace ws,
+                       int H, int heavy_edges, BatchState bs, cudaStream_t st) {
+    if (H <= 0 || heavy_edges <= 0) return 0;
+    const bool ratio = ws.transit != nullptr;
+    const int nchunks = (heavy_edges + kHeavyChunk - 1) / kHeavyChunk;
+    const int cb = nchunks < 4096 ? nchunks : 4096;
+    const int fb = H < 4096 ? H : 4096;
+    if (ratio) {
+        improve_heavy_chunk_kernel<true><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
+                                                                      nchunks, ws);
+        improve_heavy_final_kernel<true><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
+    } else {
+        improve_heavy_chunk_kernel<false><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
+                                                                       nchunks, ws);
+        improve_heavy_final_kernel<false><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
+    }
+    return 2;
+}
+
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
                  cudaStream_t st) {
-    ClassGrid cg;
-    int tasks = 0;
-    for (int c = 0; c < kClasses; ++c) {
-        cg.task_off[c] = tasks;
-        const long long lanes = (long long)cls_cnt[c] << c;
-        tasks += (int)((lanes + 31) / 32);
-    }
-    cg.task_off[kClasses] = tasks;
+    // an upper bound on the warp tasks (each (band, class) group rounds up
+    // to whole tasks); the kernel reads the exact count from the group table
+    long long tasks = 0;
+    for (int c = 0; c < kClasses; ++c) tasks += (((long long)cls_cnt[c] << c) + 31) / 32;
+    const int groups = kClasses * ((n + kSweepBand - 1) / kSweepBand);
+    tasks += groups;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
     const bool ratio = ws.transit != nullptr;
     const int grid_blocks = ratio ? classes_grid<true>(threads) : classes_grid<false>(threads);
     if (grid_blocks <= 0) return -1;
     const int wpb = threads / 32;
-    int blocks = (tasks + wpb - 1) / wpb;
+    long long blocks = (tasks + wpb - 1) / wpb;
     if (blocks > grid_blocks) blocks = grid_blocks;
     if (blocks < 1) blocks = 1;   // block 0 also publishes the evaluation's best cycle
     prof_begin(kProfSweep, st);
     if (ratio)
-        improve_kernel<true><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
+        improve_kernel<true><<<(int)blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, ws,
+                                                              bs);
     else
-        improve_kernel<false><<<blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, cg, ws, bs);
+        improve_kernel<false><<<(int)blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, groups,
+                                                               ws, bs);
     int launches = 1;
-    const int H = cls_cnt[kClasses];
-    if (H > 0 && heavy_edges > 0) {
-        const int nchunks = (heavy_edges + kHeavyChunk - 1) / kHeavyChunk;
-        int cb = nchunks < 4096 ? nchunks : 4096;
-        int fb = H < 4096 ? H : 4096;
-        if (ratio) {
-            improve_heavy_chunk_kernel<true><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
-                                                                          nchunks, ws);
-            improve_heavy_final_kernel<true><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
-        } else {
-            improve_heavy_chunk_kernel<false><<<cb, kHeavyThreads, 0, st>>>(row_ptr, col, w, sign,
-                                                                           nchunks, ws);
-            improve_heavy_final_kernel<false><<<fb, kHeavyThreads, 0, st>>>(col, w, sign, ws, bs);
-        }
-        launches += 2;
-    }
+    const int kh = launch_sweep_heavy(row_ptr, col, w, sign, ws, cls_cnt[kClasses], heavy_edges,
+                                      bs, st);
+    if (kh < 0) return -1;
+    launches += kh;
     prof_end(kProfSweep, st);
     return launches;
 }

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_only_entry_points():
     lib = ocm.load()
-    assert lib.ocm_version() == 108
+    assert lib.ocm_version() == 109
     assert lib.ocm_workspace_size(0, 5) == 0
     assert lib.ocm_workspace_size(5, 0) == 0
     small = lib.ocm_workspace_size(1000, 4000)
