@@ -614,7 +614,9 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
         local_R = (n + blocks - 1) / blocks;
     }
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
-                       bs ? &b : nullptr, st, local_R);
+                       bs ? &b : nullptr, st, local_R,
+                       (req_kind == OCM_SWEEP_WINDOW && kind == OCM_SWEEP_CLASSES && !ratio) ? 1
+                                                                                            : 0);
     launches += 3;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);

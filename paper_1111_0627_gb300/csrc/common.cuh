@@ -386,7 +386,7 @@ struct NvtxRange {
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
-                        int local_R = 0);
+                        int local_R = 0, int count_win = 0);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
                  cudaStream_t st);

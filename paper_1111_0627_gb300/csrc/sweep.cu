@@ -105,14 +105,19 @@ void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStre
 // warm start, the caller's policy (init != nullptr), which must name an
 // out-edge of each vertex.  The same pass validates col_idx, w and the
 // transit times and measures max|w| and max t for the exactness bound.
-__global__ void __launch_bounds__(kThreads)
+//
+// Layout: the lane groups and band-major task order of the degree-class
+// sweep (improve_kernel below), so the edge loads are coalesced.
+__global__ void __launch_bounds__(kSweepMaxThreads, 3)
 init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                    const int *__restrict__ w, int sign, int n, const int *__restrict__ gid,
-                   const int *__restrict__ init, int local_R, Workspace ws) {
-    __shared__ int s_maxw[kThreads / 32];
-    __shared__ int s_maxt[kThreads / 32];
-    __shared__ unsigned long long s_local[kThreads / 32];
-    __shared__ unsigned s_win[kThreads / 32][kWinShapes];
+                   const int *__restrict__ init, int local_R, int count_win, int groups,
+                   Workspace ws) {
+    constexpr int kWarps = kSweepMaxThreads / 32;
+    __shared__ int s_maxw[kWarps];
+    __shared__ int s_maxt[kWarps];
+    __shared__ unsigned long long s_local[kWarps];
+    __shared__ unsigned s_win[kWarps][kWinShapes];
     unsigned long long local = 0;
     unsigned win[kWinShapes] = {};   // edges inside each window shape (window sweep)
     const int tid = threadIdx.x;
@@ -120,62 +125,94 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const int stride = gridDim.x * blockDim.x;
     const int *__restrict__ tt = ws.transit;
     int maxabs = 0, maxt = 0;
-    for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) {
-        const int a = __ldg(&row_ptr[v]), b = __ldg(&row_ptr[v + 1]);
-        if (local_R) ws.root_mark[v] = 0;
-        if (b - a > kHeavyEdges) continue;   // the heavy path (heavy_init_*_kernel)
-        const int my_range = local_R ? v / local_R : 0;
-        const int my_g = gid ? gid[v] : 0;
-        int best_e = a;
-        long long best_key = LLONG_MIN;
-        for (int e = a; e < b; ++e) {
-            const int t = __ldg(&col[e]);
-            int x = __ldg(&w[e]);
-            if ((unsigned)t >= (unsigned)n || (gid && gid[t] != my_g)) {
-                // out of range, or (batched) an edge between different graphs
-                atomicOr(&ws.ctrl->err, kErrCol);
-                atomicMin(&ws.ctrl->bad_index, e);
-            }
-            if (x == INT_MIN) {
-                atomicOr(&ws.ctrl->err, kErrWeightMin);
-                atomicMin(&ws.ctrl->bad_index, e);
-                x = 0;
-            }
-            maxabs = max(maxabs, x < 0 ? -x : x);
-            if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
-#pragma unroll
-            for (int j = 0; j < kWinShapes; ++j)
-                win[j] += (unsigned)(t - v + j * kWinTile) < (unsigned)kWinHalo;
-            if (tt) {
-                const int te = __ldg(&tt[e]);
-                if (te < 1) {
-                    atomicOr(&ws.ctrl->err, kErrTransit);
+    if (local_R)
+        for (int v = blockIdx.x * blockDim.x + tid; v < n; v += stride) ws.root_mark[v] = 0;
+    const int4 *__restrict__ grp_tab = ws.band_grp;
+    const int total = grp_tab[groups].x;
+    const int warps = stride >> 5;
+    int p = 0;
+    int4 grp = grp_tab[0];
+    int next_start = groups > 1 ? grp_tab[1].x : total;
+    for (int task = (blockIdx.x * blockDim.x + tid) >> 5; task < total; task += warps) {
+        while (task >= next_start) {   // (the same steps in every lane)
+            ++p;
+            grp = grp_tab[p];
+            next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+        }
+        const int c = grp.w;
+        const int g = 1 << c;
+        const int sub = lane & (g - 1);
+        const int idx = (task - grp.x) * (32 >> c) + (lane >> c);
+        const bool valid = idx < grp.z;
+        const int v = valid ? ws.cls_list[grp.y + idx] : 0;
+        Cand best{INT_MIN, INT_MAX, LLONG_MIN};
+        int a = 0, b = 0;
+        if (valid) {
+            a = __ldg(&row_ptr[v]);
+            b = __ldg(&row_ptr[v + 1]);
+            const int my_range = local_R ? v / local_R : 0;
+            const int my_g = gid ? gid[v] : 0;
+            for (int e = a + sub; e < b; e += g) {
+                const int t = __ldg(&col[e]);
+                int x = __ldg(&w[e]);
+                if ((unsigned)t >= (unsigned)n || (gid && gid[t] != my_g)) {
+                    // out of range, or (batched) an edge between different graphs
+                    atomicOr(&ws.ctrl->err, kErrCol);
                     atomicMin(&ws.ctrl->bad_index, e);
                 }
-                maxt = max(maxt, te);
-            }
-            const long long k = (long long)sign * x;
-            if (k > best_key) {
-                best_key = k;
-                best_e = e;
+                if (x == INT_MIN) {
+                    atomicOr(&ws.ctrl->err, kErrWeightMin);
+                    atomicMin(&ws.ctrl->bad_index, e);
+                    x = 0;
+                }
+                maxabs = max(maxabs, x < 0 ? -x : x);
+                if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
+                if (count_win) {
+#pragma unroll
+                    for (int j = 0; j < kWinShapes; ++j)
+                        win[j] += (unsigned)(t - v + j * kWinTile) < (unsigned)kWinHalo;
+                }
+                if (tt) {
+                    const int te = __ldg(&tt[e]);
+                    if (te < 1) {
+                        atomicOr(&ws.ctrl->err, kErrTransit);
+                        atomicMin(&ws.ctrl->bad_index, e);
+                    }
+                    maxt = max(maxt, te);
+                }
+                const Cand x0{0, e, (long long)sign * x};
+                if (better(x0, best)) best = x0;
             }
         }
-        if (init) {
-            const int e = __ldg(&init[v]);
-            if (e >= a && e < b) {
-                best_e = e;
-            } else {
-                atomicOr(&ws.ctrl->err, kErrInitPolicy);
-                atomicMin(&ws.ctrl->bad_index, v);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            if (o < g) {
+                Cand other;
+                other.rank = __shfl_xor_sync(0xffffffffu, best.rank, o);
+                other.e = __shfl_xor_sync(0xffffffffu, best.e, o);
+                other.key = __shfl_xor_sync(0xffffffffu, best.key, o);
+                if (better(other, best)) best = other;
             }
         }
-        const int t = __ldg(&col[best_e]);
-        const int x = __ldg(&w[best_e]);
-        ws.pi[v] = best_e;
-        ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
-        ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
-        if (tt) ws.tpi[v] = __ldg(&tt[best_e]);
-        ws.sw_iter[v] = 0;   // the first evaluation treats every vertex as changed
+        if (valid && sub == 0) {
+            int be = best.e;
+            if (init) {
+                const int e = __ldg(&init[v]);
+                if (e >= a && e < b) {
+                    be = e;
+                } else {
+                    atomicOr(&ws.ctrl->err, kErrInitPolicy);
+                    atomicMin(&ws.ctrl->bad_index, v);
+                }
+            }
+            const int t = __ldg(&col[be]);
+            const int x = __ldg(&w[be]);
+            ws.pi[v] = be;
+            ws.succ[v] = ((unsigned)t < (unsigned)n) ? t : 0;
+            ws.wpi[v] = sign * (x == INT_MIN ? 0 : x);
+            if (tt) ws.tpi[v] = __ldg(&tt[be]);
+            ws.sw_iter[v] = 0;   // the first evaluation treats every vertex as changed
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -194,8 +231,9 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     }
     __syncthreads();
     if (tid < 32) {
-        int x = tid < kThreads / 32 ? s_maxw[tid] : 0;
-        int y = tid < kThreads / 32 ? s_maxt[tid] : 0;
+        const int nw = blockDim.x >> 5;
+        int x = tid < nw ? s_maxw[tid] : 0;
+        int y = tid < nw ? s_maxt[tid] : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -206,13 +244,13 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             if (tt) atomicMax(&ws.ctrl->maxt, y);
             if (local_R) {
                 unsigned long long sum = 0;
-                for (int k = 0; k < kThreads / 32; ++k) sum += s_local[k];
+                for (int k = 0; k < nw; ++k) sum += s_local[k];
                 if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctrl->local_edges),
                                    sum);
             }
-            for (int j = 0; j < kWinShapes; ++j) {
+            for (int j = 0; j < kWinShapes && count_win; ++j) {
                 unsigned long long sum = 0;
-                for (int k = 0; k < kThreads / 32; ++k) sum += s_win[k][j];
+                for (int k = 0; k < nw; ++k) sum += s_win[k][j];
                 if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctrl->win_edges[j]),
                                    sum);
             }
@@ -680,12 +718,14 @@ heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__
 
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
-                        int local_R) {
-    int blocks = (n + kThreads - 1) / kThreads;
-    if (blocks > 2048) blocks = 2048;
+                        int local_R, int count_win) {
+    int blocks = (n + kSweepMaxThreads - 1) / kSweepMaxThreads;
+    if (blocks > 1024) blocks = 1024;
+    const int groups = kClasses * ((n + kSweepBand - 1) / kSweepBand);
     prof_begin(kProfInit, st);
-    init_policy_kernel<<<blocks, kThreads, 0, st>>>(row_ptr, col, w, sign, n,
-                                                    bs ? bs->gid : nullptr, init, local_R, ws);
+    init_policy_kernel<<<blocks, kSweepMaxThreads, 0, st>>>(row_ptr, col, w, sign, n,
+                                                            bs ? bs->gid : nullptr, init, local_R,
+                                                            count_win, groups, ws);
     // heavy vertices (their count is on the device: fixed grids, grid-stride)
     int cb = (m / kHeavyChunk) + 1;
     if (cb > 1024) cb = 1024;
