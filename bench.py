@@ -221,8 +221,8 @@ KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
                   "sweep": ("sweep.cu", "common.cuh")}
 TRAFFIC = {
     # n = 2^23 capture (3 launches from the middle of a solve, mean) x 4
-    ("locality32m", "evaluate"): (4 * (1.352272e9 + 1.064272e9), "2c44b1fdb208294a"),
-    ("locality32m", "sweep"): (4 * (1.728464e9 + 0.177420e9), "cda8d1022ac7c1cf"),
+    ("locality32m", "evaluate"): (4 * (0.639559e9 + 0.706099e9), "b1fbdd763e7870e3"),
+    ("locality32m", "sweep"): (4 * (0.855704e9 + 0.113074e9), "7872234484a53054"),
 }
 
 
