@@ -149,10 +149,10 @@ typedef struct ocm_options {
  *   128 or 256 threads (512 runs as 256).
  * OCM_SWEEP_CLASSES: vertices grouped by degree class; a vertex of out-degree
  *   d is served by the smallest power-of-two lane group g <= 32 with
- *   d <= edges_per_lane * g (edges_per_lane 1..64; default 8).  The grid
- *   takes the classes band by band (2^18 consecutive vertices at a time), so
- *   the target records a band's edges gather stay in L2 between the class
- *   passes.
+ *   d <= edges_per_lane * g (edges_per_lane 1..64; default 8).  On graphs
+ *   of more than 2^22 vertices the grid takes the classes band by band (2^18
+ *   consecutive vertices at a time), so the target records a band's edges
+ *   gather stay in L2 between the class passes.
  * OCM_SWEEP_WINDOW: for graphs whose edges mostly point near their source in
  *   vertex order.  One thread block per SM walks a contiguous chunk of
  *   vertices in tiles of 2,048; bulk copies keep the records of a window of
@@ -228,6 +228,11 @@ typedef struct ocm_options {
  * (every vertex of a range takes part in the jump rounds), the form it takes
  * on its own for ranges of more than 436,906 vertices.  Same results. */
 #define OCM_FLAG_TEST_NO_BITMAP 32
+
+/* Test-only: the degree-class sweep and the initial pass take their warp
+ * tasks in bands of 1,024 vertices (the band-by-band order large graphs get,
+ * with many more bands).  Same results. */
+#define OCM_FLAG_TEST_SMALL_BANDS 64
 
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
@@ -462,7 +467,8 @@ const char *ocm_status_string(int status);
  * OCM_STATIC_WORKSPACE_BYTES; 106: ocm_options.wait_limit_ms, the OCM_FAULT
  * test hook; 107: ocm_options.batch_small_vertices,
  * ocm_stats.batch_small_graphs; 108: OCM_FLAG_EVAL_LOCAL, OCM_FLAG_EVAL_GLOBAL,
- * OCM_FLAG_TEST_NO_BITMAP; 109: OCM_SWEEP_WINDOW, ocm_stats.sweep_kind). */
+ * OCM_FLAG_TEST_NO_BITMAP; 109: OCM_SWEEP_WINDOW, ocm_stats.sweep_kind; 110:
+ * OCM_FLAG_TEST_SMALL_BANDS). */
 int ocm_version(void);
 
 #ifdef __cplusplus

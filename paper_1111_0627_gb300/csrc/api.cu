@@ -52,7 +52,7 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.cls_list = static_cast<int *>(take(4 * N));
     w.cls_hist = static_cast<int *>(take(4 * (size_t)kClassSlots * ((N + kClassifyBlock - 1) / kClassifyBlock)));
     w.band_grp = static_cast<int4 *>(
-        take(sizeof(int4) * ((size_t)kClasses * ((N + kSweepBand - 1) / kSweepBand) + 1)));
+        take(sizeof(int4) * ((size_t)kClasses * ((N + kClassifyBlock - 1) / kClassifyBlock) + 1)));
     w.heavy_off = static_cast<int *>(take(4 * (N + 1)));
     w.heavy_part = static_cast<Cand *>(take(sizeof(Cand) * 2 * ((size_t)m / kHeavyChunk + 2)));
     w.tile_v = static_cast<int *>(take(4 * (T + 1)));
@@ -280,6 +280,7 @@ struct StepArgs {
     int n, m, sign, threads, stall;
     int kind, epl;            // sweep layout (OCM_SWEEP_TILES, _CLASSES or _WINDOW) and its lane load
     int win_hb;               // window sweep: the window starts this many vertices before the tile
+    int band_blocks;          // class sweep: classification blocks per band of its task order
     long long N2, max_iters;
     Workspace ws;
     BatchState bs;
@@ -308,7 +309,7 @@ static int launch_step(const StepArgs &a, int use_cond, cudaGraphConditionalHand
                        ? launch_sweep_window(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.epl,
                                              a.win_hb, a.ws, a.cls_cnt, a.heavy_edges, a.bs, st)
                        : launch_sweep(a.row_ptr, a.col_idx, a.w, a.sign, a.n, a.ws, a.cls_cnt,
-                                      a.heavy_edges, a.bs, a.threads, st);
+                                      a.heavy_edges, a.bs, a.threads, a.band_blocks, st);
     if (ks < 0) return -1;
     int k = le + ks;
     if (a.batch) k += launch_batch_converge(a.bs, a.ws, st);
@@ -324,7 +325,8 @@ namespace {
 struct LoopKey {
     int dev;
     const void *row_ptr, *col_idx, *w, *ctrl, *vptr, *transit;
-    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local, no_bitmap, win_hb;
+    int n, m, sign, threads, stall, G, kind, epl, single, heavy_edges, local, no_bitmap, win_hb,
+        band_blocks;
     long long N2, max_iters;
     int cls_cnt[kClassSlots];
     bool operator==(const LoopKey &o) const {
@@ -333,7 +335,7 @@ struct LoopKey {
             sign != o.sign || single != o.single || local != o.local ||
             no_bitmap != o.no_bitmap ||
             threads != o.threads || stall != o.stall || G != o.G || kind != o.kind ||
-            win_hb != o.win_hb ||
+            win_hb != o.win_hb || band_blocks != o.band_blocks ||
             epl != o.epl || N2 != o.N2 || max_iters != o.max_iters || heavy_edges != o.heavy_edges)
             return false;
         for (int c = 0; c < kClassSlots; ++c)
@@ -372,6 +374,7 @@ LoopKey make_key(const StepArgs &a) {
     k.kind = a.kind;
     k.epl = a.epl;
     k.win_hb = a.win_hb;
+    k.band_blocks = a.band_blocks;
     k.sign = a.sign;
     k.threads = a.threads;
     k.stall = a.stall;
@@ -502,7 +505,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 109; }
+int ocm_version(void) { return 110; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -600,7 +603,11 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     if (epl > 64) epl = 64;
     if (kind == OCM_SWEEP_TILES) epl = epl <= 4 ? 4 : 8;
     const int sweep_threads = (opt && opt->sweep_threads > 0) ? opt->sweep_threads : kSweepThreads;
-    launches += launch_classify(row_ptr, n, kind == OCM_SWEEP_TILES ? kEdgesPerLane : epl, ws, st);
+    // bands of the class sweep's task order (one band up to 2^22 vertices)
+    const int band_blocks =
+        (opt && (opt->flags & OCM_FLAG_TEST_SMALL_BANDS)) ? 1 : sweep_band_blocks(n);
+    launches += launch_classify(row_ptr, n, kind == OCM_SWEEP_TILES ? kEdgesPerLane : epl,
+                                band_blocks, ws, st);
     if (kind == OCM_SWEEP_TILES) launches += launch_tile_index(row_ptr, n, m, 32 * epl, ws, st);
     // the two-level evaluation serves single graphs whose edges mostly stay
     // inside the evaluation grid's block ranges (or when forced); the initial
@@ -616,7 +623,8 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     launch_init_policy(row_ptr, col_idx, w, sign, n, m, opt ? opt->init_policy : nullptr, ws,
                        bs ? &b : nullptr, st, local_R,
                        (req_kind == OCM_SWEEP_WINDOW && kind == OCM_SWEEP_CLASSES && !ratio) ? 1
-                                                                                            : 0);
+                                                                                            : 0,
+                       band_blocks);
     launches += 3;
     if (cudaGetLastError() != cudaSuccess) return OCM_ERR_CUDA;
     rc = read_ctrl(ws.ctrl, &h, st);
@@ -683,6 +691,7 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     sa.kind = kind;
     sa.epl = epl;
     sa.win_hb = win_hb;
+    sa.band_blocks = band_blocks;
     sa.sign = sign;
     sa.threads = (sweep_threads == 64 || sweep_threads == 128 || sweep_threads == 256 ||
                   sweep_threads == 512) ? sweep_threads : kSweepThreads;
@@ -818,7 +827,7 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA |
                                OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL |
-                               OCM_FLAG_TEST_NO_BITMAP)))
+                               OCM_FLAG_TEST_NO_BITMAP | OCM_FLAG_TEST_SMALL_BANDS)))
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
         return OCM_ERR_INVALID_ARG;
@@ -844,7 +853,8 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
     if (!graph_vptr || !row_ptr || !col_idx || !w || !num || !den || !cycle_len || !cycle_out)
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP))) return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_TEST_SMALL_BANDS)))
+        return OCM_ERR_INVALID_ARG;
     if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_WINDOW))
         return OCM_ERR_INVALID_ARG;
     if (!workspace) return OCM_ERR_WORKSPACE;

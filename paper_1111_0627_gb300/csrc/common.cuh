@@ -37,7 +37,20 @@ constexpr int kClassifyBlock = 1024;   // vertices per classification block
 // The degree-class sweep takes its warp tasks band by band: all classes of
 // the vertices [b * kSweepBand, (b + 1) * kSweepBand), then the next band, so
 // that the records the band's edges gather stay in L2 across the class passes.
+// A graph of at most kSweepOneBandN vertices (records of at most 64 MB, which
+// L2 holds anyway) is one band: class by class over the whole graph.
 constexpr int kSweepBand = 1 << 18;
+constexpr int kSweepOneBandN = 1 << 22;
+// Classification blocks per band (the default), and the sweep's (band,
+// class) groups for bands of B classification blocks.
+__host__ __device__ inline int sweep_band_blocks(int n) {
+    return n <= kSweepOneBandN ? (n + kClassifyBlock - 1) / kClassifyBlock
+                               : kSweepBand / kClassifyBlock;
+}
+__host__ __device__ inline int sweep_groups(int n, int B) {
+    const long long band = (long long)B * kClassifyBlock;
+    return kClasses * (int)((n + band - 1) / band);
+}
 constexpr int kBatchSmallDefault = 4096;   // batch: smallest automatic per-block size limit
 // The two-level evaluation is chosen for graphs of at least this many
 // vertices with at least this fraction of edges inside their block range.
@@ -386,10 +399,10 @@ struct NvtxRange {
 void launch_check_row_ptr(const int *row_ptr, int n, int m, Ctrl *ctrl, cudaStream_t st);
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
-                        int local_R = 0, int count_win = 0);
+                        int local_R = 0, int count_win = 0, int band_blocks = 1);
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
-                 cudaStream_t st);
+                 int band_blocks, cudaStream_t st);
 int launch_tile_index(const int *row_ptr, int n, int m, int tile_edges, Workspace ws,
                       cudaStream_t st);
 int launch_sweep_heavy(const int *row_ptr, const int *col, const int *w, int sign, Workspace ws,
@@ -408,7 +421,8 @@ int launch_sweep_tiles(const int *row_ptr, const int *col, const int *w, int sig
                        int edges_per_lane, Workspace ws, BatchState bs, int threads,
                        cudaStream_t st);
 int launch_batch_converge(BatchState bs, Workspace ws, cudaStream_t st);
-int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st);
+int launch_classify(const int *row_ptr, int n, int epl, int band_blocks, Workspace ws,
+                    cudaStream_t st);
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
                     cudaStream_t st, bool local = false, bool no_bitmap = false);
 int prepare_evaluate_local();

@@ -390,15 +390,13 @@ __global__ void __launch_bounds__(1024) heavy_prep_kernel(const int *__restrict_
 
 // One block: the sweep's (band, class) task groups in band-major order.  The
 // class-c vertices of band b are the class-list entries from block b * B of
-// the classification (B = kSweepBand / kClassifyBlock) up to block
+// the classification (B classification blocks a band) up to block
 // (b + 1) * B (the class list is in vertex order within a class); a group of
 // k entries takes ceil(k * 2^c / 32) warp tasks.
-__global__ void __launch_bounds__(1024) band_tasks_kernel(int n, int nb, Workspace ws) {
+__global__ void __launch_bounds__(1024) band_tasks_kernel(int n, int nb, int B, Workspace ws) {
     __shared__ int s_warp[32];
     __shared__ int s_carry;
-    constexpr int B = kSweepBand / kClassifyBlock;
-    const int bands = (n + kSweepBand - 1) / kSweepBand;
-    const int groups = bands * kClasses;
+    const int groups = sweep_groups(n, B);
     const Ctrl *c = ws.ctrl;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
@@ -444,14 +442,15 @@ __global__ void __launch_bounds__(1024) band_tasks_kernel(int n, int nb, Workspa
     if (threadIdx.x == 0) ws.band_grp[groups] = make_int4(s_carry, 0, 0, 0);
 }
 
-int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream_t st) {
+int launch_classify(const int *row_ptr, int n, int epl, int band_blocks, Workspace ws,
+                    cudaStream_t st) {
     const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
     prof_begin(kProfInit, st);
     classify_count_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     classify_scan_kernel<<<1, 1024, 0, st>>>(nb, ws);
     classify_scatter_kernel<<<nb, kClassifyBlock, 0, st>>>(row_ptr, n, nb, epl, ws);
     heavy_prep_kernel<<<1, 1024, 0, st>>>(row_ptr, ws);
-    band_tasks_kernel<<<1, 1024, 0, st>>>(n, nb, ws);
+    band_tasks_kernel<<<1, 1024, 0, st>>>(n, nb, band_blocks, ws);
     prof_end(kProfInit, st);
     return 5;
 }
@@ -469,9 +468,13 @@ int launch_classify(const int *row_ptr, int n, int epl, Workspace ws, cudaStream
 // of a band of kSweepBand vertices, then the next band: the band's records
 // are gathered from L2 in every class pass, not again from HBM); each warp
 // keeps a cursor on the (band, class) groups, which its grid-stride steps
-// advance by a few groups at most.  Switches are counted in registers and
-// published with one atomic per block (same-address atomics per warp would
-// serialise the whole sweep).
+// advance by a few groups at most (BANDED; a graph that is one band takes
+// its class of a task from the launch's per-class task offsets instead).
+// Switches are counted in registers and published with one atomic per block
+// (same-address atomics per warp would serialise the whole sweep).
+struct ClassGrid {
+    int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
+};
 
 // Candidate of edge e.  Cycle ratio (RATIO): the key also subtracts
 // p_t * t(e), the target's ratio numerator times the edge's transit time;
@@ -490,11 +493,11 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
     return Cand{r.z, e, key};
 }
 
-template <bool RATIO>
+template <bool RATIO, bool BANDED>
 __global__ void __launch_bounds__(kSweepMaxThreads, 3)   // 40 registers: 48 warps per SM
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
-               const int *__restrict__ w, int sign, int n_vertices, int groups, Workspace ws,
-               BatchState bs) {
+               const int *__restrict__ w, int sign, int n_vertices, int groups, ClassGrid cg,
+               Workspace ws, BatchState bs) {
     __shared__ int s_sw;
     const int tid = threadIdx.x;
     // a vertex switched here is "dirty" for the next evaluation
@@ -506,23 +509,37 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const int4 *rec = reinterpret_cast<const int4 *>(ws.rec);
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int4 *__restrict__ grp_tab = ws.band_grp;
-    const int total = grp_tab[groups].x;
+    const int total = BANDED ? grp_tab[groups].x : cg.task_off[kClasses];
     int switched = 0;
     int p = 0;          // the group holding the current task: grp_tab[p].x <= task
-    int4 grp = grp_tab[0];
-    int next_start = groups > 1 ? grp_tab[1].x : total;
+    int4 grp = BANDED ? grp_tab[0] : make_int4(0, 0, 0, 0);
+    int next_start = (BANDED && groups > 1) ? grp_tab[1].x : total;
     for (int task = (blockIdx.x * blockDim.x + tid) >> 5; task < total; task += warps) {
-        while (task >= next_start) {   // (the same steps in every lane)
-            ++p;
-            grp = grp_tab[p];
-            next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+        int c, first_task, list0, cnt;
+        if (BANDED) {
+            while (task >= next_start) {   // (the same steps in every lane)
+                ++p;
+                grp = grp_tab[p];
+                next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+            }
+            c = grp.w;
+            first_task = grp.x;
+            list0 = grp.y;
+            cnt = grp.z;
+        } else {
+            c = 0;
+#pragma unroll
+            for (int k = 1; k < kClasses; ++k)
+                if (task >= cg.task_off[k]) c = k;
+            first_task = cg.task_off[c];
+            list0 = ws.ctrl->cls_off[c];
+            cnt = ws.ctrl->cls_cnt[c];
         }
-        const int c = grp.w;
         const int g = 1 << c;
         const int sub = lane & (g - 1);
-        const int idx = (task - grp.x) * (32 >> c) + (lane >> c);
-        bool valid = idx < grp.z;
-        const int v = valid ? ws.cls_list[grp.y + idx] : 0;
+        const int idx = (task - first_task) * (32 >> c) + (lane >> c);
+        bool valid = idx < cnt;
+        const int v = valid ? ws.cls_list[list0 + idx] : 0;
         // batched: a graph whose last sweep switched nothing never switches
         // again (its records do not change), so its vertices are skipped
         if (valid && bs.G && bs.gconv[bs.gid[v]]) valid = false;
@@ -718,10 +735,10 @@ heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__
 
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
-                        int local_R, int count_win) {
+                        int local_R, int count_win, int band_blocks) {
     int blocks = (n + kSweepMaxThreads - 1) / kSweepMaxThreads;
     if (blocks > 1024) blocks = 1024;
-    const int groups = kClasses * ((n + kSweepBand - 1) / kSweepBand);
+    const int groups = sweep_groups(n, band_blocks);
     prof_begin(kProfInit, st);
     init_policy_kernel<<<blocks, kSweepMaxThreads, 0, st>>>(row_ptr, col, w, sign, n,
                                                             bs ? bs->gid : nullptr, init, local_R,
@@ -748,7 +765,7 @@ static int classes_grid(int threads) {
     if (cached_dev[slot] != dev) {
         int sms = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel<RATIO>, threads,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel<RATIO, true>, threads,
                                                           0) != cudaSuccess ||
             sms <= 0 || per_sm <= 0)
             return 0;
@@ -887,13 +904,20 @@ int launch_sweep_heavy(const int *row_ptr, const int *col, const int *w, int sig
 
 int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int n,
                  Workspace ws, const int *cls_cnt, int heavy_edges, BatchState bs, int threads,
-                 cudaStream_t st) {
-    // an upper bound on the warp tasks (each (band, class) group rounds up
-    // to whole tasks); the kernel reads the exact count from the group table
+                 int band_blocks, cudaStream_t st) {
+    // the warp tasks: per class (one band), else an upper bound (each (band,
+    // class) group rounds up to whole tasks; the kernel reads the exact count
+    // from the group table)
+    ClassGrid cg;
     long long tasks = 0;
-    for (int c = 0; c < kClasses; ++c) tasks += (((long long)cls_cnt[c] << c) + 31) / 32;
-    const int groups = kClasses * ((n + kSweepBand - 1) / kSweepBand);
-    tasks += groups;
+    for (int c = 0; c < kClasses; ++c) {
+        cg.task_off[c] = (int)tasks;
+        tasks += (((long long)cls_cnt[c] << c) + 31) / 32;
+    }
+    cg.task_off[kClasses] = (int)tasks;
+    const int groups = sweep_groups(n, band_blocks);
+    const bool banded = groups > kClasses;
+    if (banded) tasks += groups;
     if (threads != 128 && threads != 256 && threads != 512) threads = kSweepThreads;
     const bool ratio = ws.transit != nullptr;
     const int grid_blocks = ratio ? classes_grid<true>(threads) : classes_grid<false>(threads);
@@ -903,12 +927,19 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     if (blocks > grid_blocks) blocks = grid_blocks;
     if (blocks < 1) blocks = 1;   // block 0 also publishes the evaluation's best cycle
     prof_begin(kProfSweep, st);
-    if (ratio)
-        improve_kernel<true><<<(int)blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, ws,
-                                                              bs);
+    const int nb = (int)blocks;
+    if (ratio && banded)
+        improve_kernel<true, true><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
+                                                           ws, bs);
+    else if (ratio)
+        improve_kernel<true, false><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
+                                                            ws, bs);
+    else if (banded)
+        improve_kernel<false, true><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
+                                                            ws, bs);
     else
-        improve_kernel<false><<<(int)blocks, threads, 0, st>>>(row_ptr, col, w, sign, n, groups,
-                                                               ws, bs);
+        improve_kernel<false, false><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups,
+                                                             cg, ws, bs);
     int launches = 1;
     const int kh = launch_sweep_heavy(row_ptr, col, w, sign, ws, cls_cnt[kClasses], heavy_edges,
                                       bs, st);
