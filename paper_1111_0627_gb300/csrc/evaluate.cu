@@ -873,6 +873,17 @@ namespace ocm {
 // the whole depth and cycle length, and need no grid barrier.
 // ---------------------------------------------------------------------------
 
+// The node graph is kept in dense node order (node i is the exit list[2][i]):
+// the exits' node indices, by vertex, and the detection buffers live in the
+// cycle-ratio buffers, which the two-level evaluation (the mean only) does not
+// use; the value buffers in the records (dead until the record pass) and the
+// second value buffer (dead once the root fix is done).
+constexpr int kNU = 2;   // nodes per thread per pass of a node round
+
+static __device__ __forceinline__ int *node_index(const Workspace &ws) {
+    return reinterpret_cast<int *>(ws.recp);
+}
+
 static __device__ __forceinline__ int block_sum_int(int x, int *s_red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -920,7 +931,10 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, bool list_
         }
         if (list_exits) {   // the node list: every exit once
             const int pos = warp_append(&c->node_cnt, is_exit, lane);
-            if (is_exit) ws.list[2][pos] = v;
+            if (is_exit) {
+                ws.list[2][pos] = v;
+                node_index(ws)[v] = pos;
+            }
         }
     }
     __syncthreads();
@@ -1230,6 +1244,7 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
             ws.jls[0][v] = JLS{~(n + v), 0, 0};
             ws.rep[v] = n + v;
             ws.jm[1][v] = JM{~(n + v), INT_MAX};
+            node_index(ws)[v] = xpos;
             ws.list[2][xpos++] = v;
         } else {
             // one step to the successor: final for a leaf, completed on read;
@@ -1383,6 +1398,9 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     const int *X = ws.list[2];
 
     // ---- node graph: detection by window minima over segment minima
+    const int *node_of = node_index(ws);
+    JM *ND[2] = {reinterpret_cast<JM *>(ws.jt[0]), reinterpret_cast<JM *>(ws.jt[1])};
+    int *NAP = ws.tpi;   // previous window minimum of each node
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         const int y = ws.succ[x];
@@ -1401,41 +1419,56 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
             node = JM{~ty, 0};   // succ(x)'s path ends on a cycle inside its range
         } else {
             const JM d = ws.jm[1][z];   // aux = smallest vertex before the exit
-            node = JM{ty - n, min(x, min(mz, d.M))};
+            node = JM{node_of[ty - n], min(x, min(mz, d.M))};
         }
-        ws.jm[0][x] = node;
+        ND[0][i] = node;
         ws.jls[1][x] = JLS{~(n + x), 0, 0};   // the exits' local state in both buffers
     }
     if (!grid_barrier(c, nblocks)) return;
     int nr = 0;
     for (int r = 0;; ++r) {
-        const JM *in = ws.jm[r & 1];
-        JM *out = ws.jm[(r + 1) & 1];
+        const JM *in = ND[r & 1];
+        JM *out = ND[(r + 1) & 1];
         int pend = 0;
-        for (int i = first + threadIdx.x; i < K_exit; i += stride) {
-            const int x = X[i];
-            const JM s = in[x];
-            if (s.J < 0) {
-                out[x] = s;
-                continue;
-            }
-            const JM t = in[s.J];
-            int root = -1;
-            if (t.J < 0) {
-                root = ~t.J;
-            } else if (r > 0 && t.M == ws.aprev[x]) {
-                root = t.M;   // the cycle's smallest vertex (it may lie inside a segment)
-                if (atomicExch(&ws.root_mark[root], stamp) != stamp) {
-                    const int pos = atomicAdd(&c->nrep, 1);
-                    ws.cyc_root[pos] = root;
+        for (int i0 = first + threadIdx.x; i0 < K_exit; i0 += kNU * stride) {
+            JM sn[kNU], tn[kNU];
+            int ap[kNU];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u) {
+                const int i = i0 + u * stride;
+                if (i < K_exit) {
+                    sn[u] = in[i];
+                    ap[u] = NAP[i];
                 }
             }
-            if (root >= 0) {
-                out[x] = JM{~root, 0};
-            } else {
-                out[x] = JM{t.J, min(s.M, t.M)};
-                ws.aprev[x] = t.M;
-                ++pend;
+#pragma unroll
+            for (int u = 0; u < kNU; ++u)
+                if (i0 + u * stride < K_exit && sn[u].J >= 0) tn[u] = in[sn[u].J];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u) {
+                const int i = i0 + u * stride;
+                if (i >= K_exit) continue;
+                if (sn[u].J < 0) {
+                    out[i] = sn[u];
+                    continue;
+                }
+                int root = -1;
+                if (tn[u].J < 0) {
+                    root = ~tn[u].J;
+                } else if (r > 0 && tn[u].M == ap[u]) {
+                    root = tn[u].M;   // the cycle's smallest vertex (it may lie inside a segment)
+                    if (atomicExch(&ws.root_mark[root], stamp) != stamp) {
+                        const int pos = atomicAdd(&c->nrep, 1);
+                        ws.cyc_root[pos] = root;
+                    }
+                }
+                if (root >= 0) {
+                    out[i] = JM{~root, 0};
+                } else {
+                    out[i] = JM{tn[u].J, min(sn[u].M, tn[u].M)};
+                    NAP[i] = tn[u].M;
+                    ++pend;
+                }
             }
         }
         bool ok;
@@ -1558,8 +1591,9 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     }
     if (!grid_barrier(c, nblocks)) return;
 
-    // ---- node graph: (len, S) of every exit to its root (the exits' entries
-    //      of jls[0] keep their local state until the jumping below)
+    // ---- node graph: (len, S) of every exit to its root, in node order; the
+    //      final states go back to the exits' entries of jls[0]
+    JLS *NV[2] = {reinterpret_cast<JLS *>(ws.rec), ws.jls[1]};
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         JLS node;
@@ -1574,44 +1608,50 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
                 node = JLS{~ty, len, S};
             } else {
                 const int xn = ty - n;
-                node = JLS{ws.rep[xn] == xn ? ~xn : xn, len, S};
+                node = JLS{ws.rep[xn] == xn ? ~xn : node_of[xn], len, S};
             }
         }
-        ws.jls[1][x] = node;
+        NV[0][i] = node;
     }
     if (!grid_barrier(c, nblocks)) return;
-    int FN = 1;
+    int FN = 0;
     for (int j = 1;; ++j) {
-        const JLS *in = ws.jls[j & 1];
-        JLS *out = ws.jls[(j + 1) & 1];
+        const JLS *in = NV[(j + 1) & 1];
+        JLS *out = NV[j & 1];
         int pend = 0;
-        for (int i = first + threadIdx.x; i < K_exit; i += stride) {
-            const int x = X[i];
-            const JLS s = in[x];
-            if (s.J < 0) {
-                out[x] = s;
-                continue;
+        for (int i0 = first + threadIdx.x; i0 < K_exit; i0 += kNU * stride) {
+            JLS sn[kNU], tn[kNU];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u)
+                if (i0 + u * stride < K_exit) sn[u] = in[i0 + u * stride];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u)
+                if (i0 + u * stride < K_exit && sn[u].J >= 0) tn[u] = in[sn[u].J];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u) {
+                const int i = i0 + u * stride;
+                if (i >= K_exit) continue;
+                if (sn[u].J < 0) {
+                    out[i] = sn[u];
+                    continue;
+                }
+                const JLS nu{tn[u].J, sn[u].len + tn[u].len, sn[u].S + tn[u].S};
+                out[i] = nu;
+                pend += nu.J >= 0;
             }
-            const JLS t = in[s.J];
-            const JLS nu{t.J, s.len + t.len, s.S + t.S};
-            out[x] = nu;
-            pend += nu.J >= 0;
         }
         bool ok;
         const int left = grid_sum_barrier(c, nblocks, pend, &ok);
         if (!ok) return;
         ++nr;
-        FN = (j + 1) & 1;
+        FN = j & 1;
         if (left == 0) break;
         if (j + 1 > max_node) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrValue);
             return;
         }
     }
-    for (int i = first + threadIdx.x; i < K_exit; i += stride) {
-        const int x = X[i];
-        ws.jls[FN ^ 1][x] = ws.jls[FN][x];
-    }
+    for (int i = first + threadIdx.x; i < K_exit; i += stride) ws.jls[0][X[i]] = NV[FN][i];
     if (!grid_barrier(c, nblocks)) return;
 
     // (the expansion of exit-bound vertices happens in the tail)
