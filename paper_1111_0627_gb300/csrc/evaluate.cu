@@ -1430,12 +1430,15 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         const JM *in = ND[r & 1];
         JM *out = ND[(r + 1) & 1];
         int pend = 0;
-        for (int i0 = first + threadIdx.x; i0 < K_exit; i0 += kNU * stride) {
+        // (warp-uniform trip counts: the roots met are marked with one atomic
+        // per distinct root and warp -- a cycle is met by most nodes at once)
+        const int lane = threadIdx.x & 31;
+        for (int i0 = first + (int)threadIdx.x - lane; i0 < K_exit; i0 += kNU * stride) {
             JM sn[kNU], tn[kNU];
             int ap[kNU];
 #pragma unroll
             for (int u = 0; u < kNU; ++u) {
-                const int i = i0 + u * stride;
+                const int i = i0 + lane + u * stride;
                 if (i < K_exit) {
                     sn[u] = in[i];
                     ap[u] = NAP[i];
@@ -1443,31 +1446,41 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
             }
 #pragma unroll
             for (int u = 0; u < kNU; ++u)
-                if (i0 + u * stride < K_exit && sn[u].J >= 0) tn[u] = in[sn[u].J];
+                if (i0 + lane + u * stride < K_exit && sn[u].J >= 0) tn[u] = in[sn[u].J];
 #pragma unroll
             for (int u = 0; u < kNU; ++u) {
-                const int i = i0 + u * stride;
-                if (i >= K_exit) continue;
-                if (sn[u].J < 0) {
-                    out[i] = sn[u];
-                    continue;
-                }
+                const int i = i0 + lane + u * stride;
                 int root = -1;
-                if (tn[u].J < 0) {
-                    root = ~tn[u].J;
-                } else if (r > 0 && tn[u].M == ap[u]) {
-                    root = tn[u].M;   // the cycle's smallest vertex (it may lie inside a segment)
-                    if (atomicExch(&ws.root_mark[root], stamp) != stamp) {
-                        const int pos = atomicAdd(&c->nrep, 1);
-                        ws.cyc_root[pos] = root;
+                bool win = false;   // the root of a cycle of the node graph, found here
+                if (i < K_exit) {
+                    if (sn[u].J < 0) {
+                        out[i] = sn[u];
+                    } else {
+                        if (tn[u].J < 0) {
+                            root = ~tn[u].J;
+                        } else if (r > 0 && tn[u].M == ap[u]) {
+                            root = tn[u].M;   // the cycle's smallest vertex (it may lie inside a segment)
+                            win = true;
+                        }
+                        if (root >= 0) {
+                            out[i] = JM{~root, 0};
+                        } else {
+                            out[i] = JM{tn[u].J, min(sn[u].M, tn[u].M)};
+                            NAP[i] = tn[u].M;
+                            ++pend;
+                        }
                     }
                 }
-                if (root >= 0) {
-                    out[i] = JM{~root, 0};
-                } else {
-                    out[i] = JM{tn[u].J, min(sn[u].M, tn[u].M)};
-                    NAP[i] = tn[u].M;
-                    ++pend;
+                unsigned m = __ballot_sync(0xffffffffu, win);
+                while (m) {
+                    const int leader = __ffs(m) - 1;
+                    const int r0 = __shfl_sync(0xffffffffu, root, leader);
+                    m &= ~__ballot_sync(0xffffffffu, win && root == r0);
+                    if (lane == leader && load_volatile(&ws.root_mark[r0]) != stamp &&
+                        atomicExch(&ws.root_mark[r0], stamp) != stamp) {
+                        const int pos = atomicAdd(&c->nrep, 1);
+                        ws.cyc_root[pos] = r0;
+                    }
                 }
             }
         }
