@@ -738,6 +738,23 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
 }
 
 // --------------------------------------------------------------- extract --
+// Appends item to a global list with one atomic per block (all threads of the
+// block call it; the order within the list is immaterial).
+static __device__ __forceinline__ void block_append_global(int *list, int *counter, bool pred,
+                                                           int item, int lane) {
+    __shared__ int s_cnt, s_base;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    int wbase = 0;
+    if (lane == 0 && mask) wbase = atomicAdd(&s_cnt, __popc(mask));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(counter, s_cnt) : 0;
+    __syncthreads();
+    if (pred) list[s_base + wbase + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
 // Critical cycle of root r* (length L*): its vertices are exactly the v with
 // root(v) = r*, len(v) < L* and succ^{L*}(v) = v; v sits at position
 // (L* - len(v)) mod L* counted from r*.  succ^{L*} is evaluated for all
@@ -758,8 +775,7 @@ extract_candidates_kernel(int n, Workspace ws) {
             cand = (~st.J == root) && st.len < L;
             if (cand) cur[v] = v;
         }
-        int pos = warp_append(&c->ncand, cand, lane);
-        if (cand) ws.list[0][pos] = v;
+        block_append_global(ws.list[0], &c->ncand, cand, v, lane);
     }
 }
 
@@ -1537,34 +1553,44 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         // the members: vertices of the roots' ranges tagged with a root's exit
         int *FL = ws.list[0];
         const long long span = (long long)k_new * R;
-        for (long long q = first + threadIdx.x; q < span; q += stride) {
-            const int ri = (int)(q / R);
-            const int rlo = (s_roots[ri] / R) * R;
-            bool seen = false;   // a range holding several roots is scanned once
-            for (int i = 0; i < ri; ++i) seen |= (s_roots[i] / R) * R == rlo;
-            const int v = rlo + (int)(q % R);
-            if (seen || v >= n) continue;
-            bool root = false, member = false;
-            const int tag = ~ws.jls[0][v].J;   // (a leaf: no tag, completed on read)
-            for (int i = 0; i < k_new; ++i) {
-                root |= s_roots[i] == v;
-                member |= s_tags[i] == tag;
+        // (warp-uniform trip counts: the members are listed with one atomic
+        // per warp)
+        const int lane = threadIdx.x & 31;
+        for (long long q0 = first + (int)threadIdx.x - lane; q0 < span; q0 += stride) {
+            const long long q = q0 + lane;
+            bool listed = false;
+            int v = 0;
+            if (q < span) {
+                const int ri = (int)(q / R);
+                const int rlo = (s_roots[ri] / R) * R;
+                bool seen = false;   // a range holding several roots is scanned once
+                for (int i = 0; i < ri; ++i) seen |= (s_roots[i] / R) * R == rlo;
+                v = rlo + (int)(q % R);
+                if (!seen && v < n) {
+                    bool root = false, member = false;
+                    const int tag = ~ws.jls[0][v].J;   // (a leaf: no tag, completed on read)
+                    for (int i = 0; i < k_new; ++i) {
+                        root |= s_roots[i] == v;
+                        member |= s_tags[i] == tag;
+                    }
+                    const int sv = ws.succ[v];
+                    if (root) {
+                        const JLS f{~v, 0, 0};
+                        ws.jls[0][v] = f;
+                        ws.jls[1][v] = f;
+                    } else if (member && sv >= rlo && sv < min(rlo + R, n)) {   // exits stay final
+                        const int ts = ws.rep[sv];
+                        const bool fin = ts == sv || ts == n + sv;
+                        const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
+                        ws.jls[0][v] = st;
+                        ws.jls[1][v] = st;
+                        if (fin) ws.rep[v] = ts;   // (its successor is a root or the exit)
+                        listed = !fin;
+                    }
+                }
             }
-            if (root) {
-                const JLS f{~v, 0, 0};
-                ws.jls[0][v] = f;
-                ws.jls[1][v] = f;
-                continue;
-            }
-            const int sv = ws.succ[v];
-            if (!member || sv < rlo || sv >= min(rlo + R, n)) continue;   // exits stay final
-            const int ts = ws.rep[sv];
-            const bool fin = ts == sv || ts == n + sv;
-            const JLS st{fin ? ~ts : sv, 1, (long long)ws.wpi[v]};
-            ws.jls[0][v] = st;
-            ws.jls[1][v] = st;
-            if (fin) ws.rep[v] = ts;   // (its successor is a root or the exit)
-            else FL[atomicAdd(&c->fix_cnt, 1)] = v;
+            const int pos = warp_append(&c->fix_cnt, listed, lane);
+            if (listed) FL[pos] = v;
         }
         if (!grid_barrier(c, nblocks)) return;
         const int K_fix = load_volatile(&c->fix_cnt);
