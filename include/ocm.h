@@ -234,6 +234,16 @@ typedef struct ocm_options {
  * with many more bands).  Same results. */
 #define OCM_FLAG_TEST_SMALL_BANDS 64
 
+/* Test-only: the frontier sweep after every evaluation but the first.  By
+ * default the record pass marks the records it changes when the sweep before
+ * it switched fewer than n/256 vertices, and the next sweep then skips the
+ * vertices none of whose out-edges' targets changed its record, when fewer
+ * than n/8 records changed (such a vertex would choose as in the last sweep);
+ * not in the single-lambda form, whose rebuild writes records itself.  With
+ * this flag the marks and the skipping happen whatever the counts.  Same
+ * results. */
+#define OCM_FLAG_TEST_FRONTIER 128
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
@@ -468,7 +478,8 @@ const char *ocm_status_string(int status);
  * test hook; 107: ocm_options.batch_small_vertices,
  * ocm_stats.batch_small_graphs; 108: OCM_FLAG_EVAL_LOCAL, OCM_FLAG_EVAL_GLOBAL,
  * OCM_FLAG_TEST_NO_BITMAP; 109: OCM_SWEEP_WINDOW, ocm_stats.sweep_kind; 110:
- * OCM_FLAG_TEST_SMALL_BANDS). */
+ * OCM_FLAG_TEST_SMALL_BANDS; 111: OCM_FLAG_TEST_FRONTIER and the frontier
+ * sweep). */
 int ocm_version(void);
 
 #ifdef __cplusplus

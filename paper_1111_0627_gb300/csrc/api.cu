@@ -48,6 +48,11 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.cyc_rank = static_cast<int *>(take(4 * N));
     w.cid_of_root = static_cast<int *>(take(4 * N));
     w.done = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
+    w.rec_dirty = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
+    w.scratch16 = static_cast<int4 *>(take(sizeof(int4) * N));
+    w.blk_tgt = static_cast<int2 *>(take(sizeof(int2) * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.rec_dirty_blk = static_cast<unsigned *>(
+        take(4 * (((N + kDirtyBlock - 1) / kDirtyBlock + 31) / 32)));
     w.sw_iter = static_cast<int *>(take(4 * N));
     w.cls_list = static_cast<int *>(take(4 * N));
     w.cls_hist = static_cast<int *>(take(4 * (size_t)kClassSlots * ((N + kClassifyBlock - 1) / kClassifyBlock)));
@@ -71,11 +76,12 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     return align_up(off, 256);
 }
 
-__global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns) {
+__global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns, int frontier) {
     Ctrl z;
     memset(&z, 0, sizeof z);
     z.bad_index = INT_MAX;
     z.wait_ns = wait_ns;
+    z.frontier = frontier;
     *c = z;
 }
 
@@ -505,7 +511,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 110; }
+int ocm_version(void) { return 111; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -581,7 +587,11 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     auto phase = [](const char *name) { nvtxRangePop(); nvtxRangePushA(name); };
     nvtxRangePushA("ocm:validate");
     struct PopOnExit { ~PopOnExit() { nvtxRangePop(); } } pop_phase;
-    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl, wait_ns);
+    // the frontier sweep: not in the single-lambda form, whose rebuild writes
+    // records after the record pass
+    const int frontier =
+        single ? 0 : (opt && (opt->flags & OCM_FLAG_TEST_FRONTIER)) ? 2 : 1;
+    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl, wait_ns, frontier);
     launch_check_row_ptr(row_ptr, n, m, ws.ctrl, st);
     launches += 2;
     if (bs) launches += launch_batch_prepare(n, m, b, ws, st);
@@ -827,7 +837,8 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (n < 1 || m < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA |
                                OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL |
-                               OCM_FLAG_TEST_NO_BITMAP | OCM_FLAG_TEST_SMALL_BANDS)))
+                               OCM_FLAG_TEST_NO_BITMAP | OCM_FLAG_TEST_SMALL_BANDS |
+                               OCM_FLAG_TEST_FRONTIER)))
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
         return OCM_ERR_INVALID_ARG;
@@ -853,7 +864,8 @@ int ocm_solve_batch(const int32_t *graph_vptr, const int32_t *row_ptr, const int
     if (!graph_vptr || !row_ptr || !col_idx || !w || !num || !den || !cycle_len || !cycle_out)
         return OCM_ERR_INVALID_ARG;
     if (G < 1 || N < G || M < 1 || (mode != OCM_MAX && mode != OCM_MIN)) return OCM_ERR_INVALID_ARG;
-    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_TEST_SMALL_BANDS)))
+    if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_TEST_SMALL_BANDS |
+                               OCM_FLAG_TEST_FRONTIER)))
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_WINDOW))
         return OCM_ERR_INVALID_ARG;

@@ -152,7 +152,29 @@ struct Ctrl {
     int fix_tag[32];          // and their tags before the fix (n + their exit)
     long long local_edges;    // edges whose target lies in the source's block range
     long long win_edges[kWinShapes];   // edges inside each window shape of the window sweep
+    // frontier sweep: 0 off (single-lambda form), 1 when few vertices switched,
+    // 2 (test) after every evaluation but the first
+    int frontier;
+    int dirty_on;             // the last record pass marked the records it changed
+    long long dirty_cnt;      // how many it changed
 };
+
+// The record pass marks the records it changes when the sweep before it
+// switched fewer than n >> kFrontierSwitchShift vertices, and the next sweep
+// then skips the vertices none of whose targets' records changed when fewer
+// than n >> kFrontierDirtyShift did (their choice would be the same as in the
+// last sweep).
+// A second bitmap marks blocks of kDirtyBlock vertices with a changed record
+// (a few KB, held in L1), and the sweep looks at a target's own bit only
+// where its block's bit is set; a whole block of kClassifyBlock vertices none
+// of whose edges reaches a changed block (by the range of target blocks the
+// initial pass records) is skipped without reading its edges.
+constexpr int kFrontierSwitchShift = 8;
+constexpr int kFrontierDirtyShift = 3;
+constexpr int kDirtyBlock = 1024;
+// A vertex whose block's targets span more than this many dirty-bitmap words
+// checks its edges one by one.
+constexpr int kFrontierRangeWords = 64;
 
 // Default limit of a device-side wait, and the one the test-only stall flag
 // uses unless the caller sets ocm_options.wait_limit_ms.
@@ -193,6 +215,13 @@ struct Workspace {
     int *cyc_rank;
     int *cid_of_root;
     unsigned *done;       // bitmap: vertex resolved and its state in both buffers
+    unsigned *rec_dirty;  // bitmap: the last record pass changed v's record (Ctrl::dirty_on)
+    int2 *blk_tgt;        // [n / kClassifyBlock] smallest and largest target block (of
+                          //     kDirtyBlock vertices) of the out-edges of each block of
+                          //     kClassifyBlock vertices (heavy vertices left out)
+    int4 *scratch16;      // [n] two-level evaluation: packed jump states, then node values
+                          //     (the records stay intact for the frontier comparison)
+    unsigned *rec_dirty_blk;  // bitmap: ... some record of v's block of kDirtyBlock vertices
     int *sw_iter;         // evaluation index after the sweep that last switched v
     int *cls_list;        // vertices grouped by degree class (stable within a class)
     int *cls_hist;        // per-block class counts, then their exclusive scan

@@ -232,6 +232,19 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     const int stride = gridDim.x * blockDim.x;
     const int first = blockIdx.x * blockDim.x;
     constexpr bool ratio = RATIO;
+    // frontier sweep: mark the records this pass changes?  (decided from the
+    // last sweep's switch count before block 0 clears it below)
+    const int fm = c->frontier;
+    const bool mark = fm != 0 && c->iter > 0 &&
+                      (fm == 2 || (long long)c->switched < ((long long)n >> kFrontierSwitchShift));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->dirty_on = mark ? 1 : 0;
+        c->dirty_cnt = 0;
+    }
+    if (mark && blockIdx.x == 0) {
+        const int words = ((n + kDirtyBlock - 1) / kDirtyBlock + 31) / 32;
+        for (int i = threadIdx.x; i < words; i += blockDim.x) ws.rec_dirty_blk[i] = 0u;
+    }
     // ------------------------------------------------------------ cycles
     // mean W/L, or for the cycle ratio W/T with T the cycle's transit time
     const int K = load_volatile(&c->nrep);
@@ -329,19 +342,51 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
         c->changed = 0;
         c->switched = 0;
     }
-    for (int v = first + threadIdx.x; v < n; v += stride) {
-        if (bs.G && bs.gconv[bs.gid[v]]) continue;
-        JLS st = LOCAL ? final_value(ws.jls[0], n, v) : ws.jls[F][v];
-        int i = ws.cid_of_root[~st.J];
-        long long p = ws.cyc_p[i];
-        int q = ws.cyc_q[i];
-        Rec rec;
-        const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
-        rec.V = (long long)q * st.S - p * T;
-        rec.rank = ws.cyc_rank[i];
-        rec.q = q;
-        ws.rec[v] = rec;
-        if (ratio) ws.recp[v] = p;
+    // (warp-uniform trip counts: a warp covers 32 consecutive vertices, one
+    // word of the change bitmap)
+    int changed = 0;
+    for (int base = first + (int)threadIdx.x - lane; base < n; base += stride) {
+        const int v = base + lane;
+        bool dirty = false;
+        if (v < n && !(bs.G && bs.gconv[bs.gid[v]])) {
+            JLS st = LOCAL ? final_value(ws.jls[0], n, v) : ws.jls[F][v];
+            int i = ws.cid_of_root[~st.J];
+            long long p = ws.cyc_p[i];
+            int q = ws.cyc_q[i];
+            Rec rec;
+            const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
+            rec.V = (long long)q * st.S - p * T;
+            rec.rank = ws.cyc_rank[i];
+            rec.q = q;
+            if (mark) {
+                const Rec old = ws.rec[v];
+                dirty = old.V != rec.V || old.rank != rec.rank || old.q != rec.q ||
+                        (ratio && ws.recp[v] != p);
+            }
+            ws.rec[v] = rec;
+            if (ratio) ws.recp[v] = p;
+        }
+        if (mark) {
+            const unsigned m = __ballot_sync(0xffffffffu, dirty);
+            if (lane == 0) {
+                ws.rec_dirty[base >> 5] = m;
+                changed += __popc(m);
+                if (m) {
+                    const int blk = base / kDirtyBlock;
+                    atomicOr(&ws.rec_dirty_blk[blk >> 5], 1u << (blk & 31));
+                }
+            }
+        }
+    }
+    if (mark) {
+        __shared__ int s_changed;
+        if (threadIdx.x == 0) s_changed = 0;
+        __syncthreads();
+        if (lane == 0 && changed) atomicAdd(&s_changed, changed);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_changed)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&c->dirty_cnt),
+                      (unsigned long long)s_changed);
     }
 }
 
@@ -892,8 +937,8 @@ namespace ocm {
 // The node graph is kept in dense node order (node i is the exit list[2][i]):
 // the exits' node indices, by vertex, and the detection buffers live in the
 // cycle-ratio buffers, which the two-level evaluation (the mean only) does not
-// use; the value buffers in the records (dead until the record pass) and the
-// second value buffer (dead once the root fix is done).
+// use; the value buffers in the 16-byte scratch and the second value buffer
+// (dead once the root fix is done).
 constexpr int kNU = 2;   // nodes per thread per pass of a node round
 
 static __device__ __forceinline__ int *node_index(const Workspace &ws) {
@@ -1141,8 +1186,8 @@ static __device__ bool local_phase(int lo, int hi, int n, bool rerun, bool list_
 // tags in a detection pass first and jumps for the values afterwards).  The
 // state is packed into 16 bytes: bits 0-20 the jump target, 21-41 the path
 // length (saturating), 42-62 the path minimum (local indices; all ones: none),
-// bit 63 finished, then the weight.  Ping-pong buffers: the records (dead
-// until this evaluation writes them again) and the second value buffer; a
+// bit 63 finished, then the weight.  Ping-pong buffers: the 16-byte scratch
+// and the second value buffer; a
 // finished vertex writes its final {~tag, len, S} to jls[0] and its
 // {~tag, path minimum} for the node graph once; rep holds n + x for an exit
 // x and -1 for the others (the tags are in jls[0]).  A path still unfinished after
@@ -1188,7 +1233,7 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
     const bool trim = nwords > 0 && 3 * nw <= nwords;
     unsigned *keep_bits = bits + nw;   // vertices with a predecessor that is no leaf
     unsigned *pref = bits + 2 * nw;    // set keep bits in the words before each word
-    PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.rec) + lo,
+    PackedState *P[2] = {reinterpret_cast<PackedState *>(ws.scratch16) + lo,
                          reinterpret_cast<PackedState *>(ws.jls[1]) + lo};
     int *orig = ws.aprev + lo;    // dense index -> vertex
     if (threadIdx.x == 0) *s_flag = 0;
@@ -1632,7 +1677,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
 
     // ---- node graph: (len, S) of every exit to its root, in node order; the
     //      final states go back to the exits' entries of jls[0]
-    JLS *NV[2] = {reinterpret_cast<JLS *>(ws.rec), ws.jls[1]};
+    JLS *NV[2] = {reinterpret_cast<JLS *>(ws.scratch16), ws.jls[1]};
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         JLS node;

@@ -147,6 +147,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         const int v = valid ? ws.cls_list[grp.y + idx] : 0;
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
         int a = 0, b = 0;
+        int tmin = INT_MAX, tmax = INT_MIN;   // this lane's targets
         if (valid) {
             a = __ldg(&row_ptr[v]);
             b = __ldg(&row_ptr[v + 1]);
@@ -166,6 +167,8 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     x = 0;
                 }
                 maxabs = max(maxabs, x < 0 ? -x : x);
+                tmin = min(tmin, t);
+                tmax = max(tmax, t);
                 if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
                 if (count_win) {
 #pragma unroll
@@ -193,6 +196,22 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 other.key = __shfl_xor_sync(0xffffffffu, best.key, o);
                 if (better(other, best)) best = other;
             }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            if (o < g) {
+                tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+                tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            }
+        }
+        if (valid && sub == 0 && tmin <= tmax && (unsigned)tmin < (unsigned)n &&
+            (unsigned)tmax < (unsigned)n) {
+            // the range of target blocks of v's block (the frontier sweep)
+            // (a plain read first: most vertices widen nothing)
+            int2 *bt = &ws.blk_tgt[v / kClassifyBlock];
+            const int2 cur = *bt;
+            if (tmin / kDirtyBlock < cur.x) atomicMin(&bt->x, tmin / kDirtyBlock);
+            if (tmax / kDirtyBlock > cur.y) atomicMax(&bt->y, tmax / kDirtyBlock);
         }
         if (valid && sub == 0) {
             int be = best.e;
@@ -275,6 +294,7 @@ classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, W
     if (v < n) atomicAdd(&s_cnt[degree_class(__ldg(&row_ptr[v + 1]) - __ldg(&row_ptr[v]), epl)], 1);
     __syncthreads();
     if (threadIdx.x < kClassSlots) ws.cls_hist[threadIdx.x * nb + blockIdx.x] = s_cnt[threadIdx.x];
+    if (threadIdx.x == 0) ws.blk_tgt[blockIdx.x] = make_int2(INT_MAX, INT_MIN);   // (initial pass)
 }
 
 // One block: exclusive scan of the class-major histogram (class c, block b at
@@ -493,11 +513,20 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
     return Cand{r.z, e, key};
 }
 
-template <bool RATIO, bool BANDED>
+// FRONTIER: the instance for the frontier form; both instances are launched
+// every step and the one whose form the control block does not ask for
+// returns at once (the choice is made on the device, inside the loop graph).
+template <bool RATIO, bool BANDED, bool FRONTIER>
 __global__ void __launch_bounds__(kSweepMaxThreads, 3)   // 40 registers: 48 warps per SM
 improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                const int *__restrict__ w, int sign, int n_vertices, int groups, ClassGrid cg,
                Workspace ws, BatchState bs) {
+    // the frontier form: the record pass marked the records it changed, and
+    // few changed (or the test flag asks for it)
+    const bool frontier =
+        ws.ctrl->dirty_on &&
+        (ws.ctrl->frontier == 2 || ws.ctrl->dirty_cnt < ((long long)n_vertices >> kFrontierDirtyShift));
+    if (frontier != FRONTIER) return;
     __shared__ int s_sw;
     const int tid = threadIdx.x;
     // a vertex switched here is "dirty" for the next evaluation
@@ -543,6 +572,48 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         // batched: a graph whose last sweep switched nothing never switches
         // again (its records do not change), so its vertices are skipped
         if (valid && bs.G && bs.gconv[bs.gid[v]]) valid = false;
+        if (FRONTIER) {
+            // a vertex none of whose targets' records changed since the last
+            // sweep chooses as it did then: skipped
+            // (four edges of the lane at a time, their loads independent)
+            bool any = false;
+            if (valid) {
+                // no changed block in the range of v's block's targets: skipped
+                const int2 rg = ws.blk_tgt[v / kClassifyBlock];
+                if (rg.x <= rg.y && (rg.y >> 5) - (rg.x >> 5) < kFrontierRangeWords) {
+                    bool near = false;
+                    for (int wd = rg.x >> 5; wd <= (rg.y >> 5) && !near; ++wd) {
+                        unsigned bits = ws.rec_dirty_blk[wd];
+                        if (wd == (rg.x >> 5)) bits &= ~0u << (rg.x & 31);
+                        if (wd == (rg.y >> 5)) bits &= ~0u >> (31 - (rg.y & 31));
+                        near = bits != 0u;
+                    }
+                    if (!near) valid = false;
+                }
+            }
+            if (valid) {
+                const int e_end = __ldg(&row_ptr[v + 1]);
+                for (int e = __ldg(&row_ptr[v]) + sub; e < e_end && !any; e += 4 * g) {
+                    int t[4];
+                    unsigned bw[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) t[u] = e + u * g < e_end ? __ldg(&col[e + u * g]) : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        bw[u] = t[u] >= 0 ? ws.rec_dirty_blk[(t[u] / kDirtyBlock) >> 5] : 0u;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int blk = t[u] / kDirtyBlock;
+                        if (t[u] >= 0 && ((bw[u] >> (blk & 31)) & 1u))
+                            any |= ((ws.rec_dirty[t[u] >> 5] >> (t[u] & 31)) & 1u) != 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1)
+                if (o < g) any |= __shfl_xor_sync(0xffffffffu, any, o) != 0;
+            valid = valid && any;
+        }
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
         Cand own{INT_MIN, INT_MAX, LLONG_MIN};   // the current policy edge, in one lane
         if (valid) {
@@ -765,7 +836,7 @@ static int classes_grid(int threads) {
     if (cached_dev[slot] != dev) {
         int sms = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel<RATIO, true>, threads,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, improve_kernel<RATIO, true, true>, threads,
                                                           0) != cudaSuccess ||
             sms <= 0 || per_sm <= 0)
             return 0;
@@ -928,19 +999,23 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
     if (blocks < 1) blocks = 1;   // block 0 also publishes the evaluation's best cycle
     prof_begin(kProfSweep, st);
     const int nb = (int)blocks;
-    if (ratio && banded)
-        improve_kernel<true, true><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
-                                                           ws, bs);
-    else if (ratio)
-        improve_kernel<true, false><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
-                                                            ws, bs);
-    else if (banded)
-        improve_kernel<false, true><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg,
-                                                            ws, bs);
-    else
-        improve_kernel<false, false><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups,
-                                                             cg, ws, bs);
-    int launches = 1;
+#define OCM_IMPROVE(R, B, F) \
+    improve_kernel<R, B, F><<<nb, threads, 0, st>>>(row_ptr, col, w, sign, n, groups, cg, ws, bs)
+    if (ratio && banded) {
+        OCM_IMPROVE(true, true, false);
+        OCM_IMPROVE(true, true, true);
+    } else if (ratio) {
+        OCM_IMPROVE(true, false, false);
+        OCM_IMPROVE(true, false, true);
+    } else if (banded) {
+        OCM_IMPROVE(false, true, false);
+        OCM_IMPROVE(false, true, true);
+    } else {
+        OCM_IMPROVE(false, false, false);
+        OCM_IMPROVE(false, false, true);
+    }
+#undef OCM_IMPROVE
+    int launches = 2;
     const int kh = launch_sweep_heavy(row_ptr, col, w, sign, ws, cls_cnt[kClasses], heavy_edges,
                                       bs, st);
     if (kh < 0) return -1;

@@ -29,6 +29,7 @@ OCM_FLAG_EVAL_LOCAL = 8     # force the two-level evaluation (include/ocm.h)
 OCM_FLAG_EVAL_GLOBAL = 16   # forbid it
 OCM_FLAG_TEST_NO_BITMAP = 32  # test only: the two-level evaluation without its bitmaps
 OCM_FLAG_TEST_SMALL_BANDS = 64  # test only: the class sweep's task order in 1,024-vertex bands
+OCM_FLAG_TEST_FRONTIER = 128  # test only: the frontier sweep after every evaluation but the first
 OCM_SWEEP_DEFAULT, OCM_SWEEP_CLASSES, OCM_SWEEP_TILES, OCM_SWEEP_WINDOW = 0, 1, 2, 3
 
 
