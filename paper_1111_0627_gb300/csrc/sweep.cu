@@ -18,8 +18,8 @@
 // warps of an SM keep many independent loads in flight.  A vertex with more
 // than kHeavyEdges out-edges takes the heavy path instead (chunks of its
 // edges, one block each, combined per vertex).  The initial policy (no
-// records yet) is a thread-per-vertex pass that also validates the input, with
-// the same heavy path for heavy vertices.
+// records yet) runs in the same lane groups and also validates the input,
+// with the same heavy path for heavy vertices.
 #include "common.cuh"
 
 namespace ocm {
@@ -614,6 +614,7 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 if (o < g) any |= __shfl_xor_sync(0xffffffffu, any, o) != 0;
             valid = valid && any;
         }
+        if (!__any_sync(0xffffffffu, valid)) continue;   // (a whole task skipped)
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
         Cand own{INT_MIN, INT_MAX, LLONG_MIN};   // the current policy edge, in one lane
         if (valid) {
