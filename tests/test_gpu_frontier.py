@@ -107,3 +107,18 @@ def test_default_frontier_on_the_2p20_locality_graph():
     assert (s.num, s.den) == (int(kv["num"]), int(kv["den"]))
     assert synth.digest(s.cycle.cpu().numpy().astype(np.int32)) == int(kv["cycle_digest"])
     assert s.stats["iterations"] == int(kv["iters"])
+
+
+def test_single_lambda_form_keeps_full_sweeps():
+    """The single-lambda rebuild writes records after the record pass, so the
+    frontier is off in that form even with the test flag; results stay exact."""
+    rng = np.random.default_rng(1111063130)
+    for trial in range(40):
+        g = synth.tiny_random(rng, int(rng.integers(2, 60)), max_extra=3, wlo=-20, whi=20,
+                              ring=True)
+        h = oracle.howard_single(g.row_ptr, g.col_idx, g.w, g.mode)
+        rp, col, w = _dev(g.row_ptr, g.col_idx, g.w)
+        s = ocm.solve(rp, col, w, g.mode, flags=OCM_FLAG_TEST_FRONTIER, single_lambda=True)
+        assert (s.num, s.den) == (h.num, h.den)
+        assert s.stats["iterations"] == h.iterations
+
