@@ -204,14 +204,30 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
             }
         }
-        if (valid && sub == 0 && tmin <= tmax && (unsigned)tmin < (unsigned)n &&
-            (unsigned)tmax < (unsigned)n) {
-            // the range of target blocks of v's block (the frontier sweep)
-            // (a plain read first: most vertices widen nothing)
-            int2 *bt = &ws.blk_tgt[v / kClassifyBlock];
-            const int2 cur = *bt;
-            if (tmin / kDirtyBlock < cur.x) atomicMin(&bt->x, tmin / kDirtyBlock);
-            if (tmax / kDirtyBlock > cur.y) atomicMax(&bt->y, tmax / kDirtyBlock);
+        {
+            // the range of target blocks of v's block (the frontier sweep): one
+            // update per warp when all its vertices lie in one block (a plain
+            // read first: most updates widen nothing)
+            const bool ok = valid && sub == 0 && tmin <= tmax && (unsigned)tmin < (unsigned)n &&
+                            (unsigned)tmax < (unsigned)n;
+            const int blk = ok ? v / kClassifyBlock : -1;
+            const unsigned okm = __ballot_sync(0xffffffffu, ok);
+            const int blk0 = okm ? __shfl_sync(0xffffffffu, blk, __ffs(okm) - 1) : -1;
+            const bool one = __all_sync(0xffffffffu, !ok || blk == blk0);
+            int lo = ok ? tmin / kDirtyBlock : INT_MAX, hi = ok ? tmax / kDirtyBlock : INT_MIN;
+            if (one) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+            }
+            if (ok && (!one || lane == __ffs(okm) - 1)) {
+                int2 *bt = &ws.blk_tgt[blk];
+                const int2 cur = *bt;
+                if (lo < cur.x) atomicMin(&bt->x, lo);
+                if (hi > cur.y) atomicMax(&bt->y, hi);
+            }
         }
         if (valid && sub == 0) {
             int be = best.e;
