@@ -151,8 +151,14 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         if (valid) {
             a = __ldg(&row_ptr[v]);
             b = __ldg(&row_ptr[v + 1]);
-            const int my_range = local_R ? v / local_R : 0;
+            // v's block range of the two-level evaluation, as bounds
+            const unsigned r_lo = local_R ? (unsigned)(v / local_R) * (unsigned)local_R : 0u;
+            const unsigned r_len = (unsigned)local_R;
             const int my_g = gid ? gid[v] : 0;
+            // (the lane's best as (key, edge): every key has rank 0 here, and
+            // the lane meets its edges in increasing order, so a strictly larger
+            // key is the only way to replace the incumbent)
+            int best_k = INT_MIN, best_e = INT_MAX;
             for (int e = a + sub; e < b; e += g) {
                 const int t = __ldg(&col[e]);
                 int x = __ldg(&w[e]);
@@ -169,7 +175,7 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                 maxabs = max(maxabs, x < 0 ? -x : x);
                 tmin = min(tmin, t);
                 tmax = max(tmax, t);
-                if (local_R) local += (unsigned)t / (unsigned)local_R == (unsigned)my_range;
+                if (local_R) local += (unsigned)t - r_lo < r_len;
                 if (count_win) {
 #pragma unroll
                     for (int j = 0; j < kWinShapes; ++j)
@@ -183,9 +189,13 @@ init_policy_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
                     }
                     maxt = max(maxt, te);
                 }
-                const Cand x0{0, e, (long long)sign * x};
-                if (better(x0, best)) best = x0;
+                const int k = sign * x;
+                if (k > best_k || best_e == INT_MAX) {
+                    best_k = k;
+                    best_e = e;
+                }
             }
+            if (best_e != INT_MAX) best = Cand{0, best_e, (long long)best_k};
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
