@@ -51,6 +51,8 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.rec_dirty = static_cast<unsigned *>(take(4 * ((N + 31) / 32)));
     w.scratch16 = static_cast<int4 *>(take(sizeof(int4) * N));
     w.blk_tgt = static_cast<int2 *>(take(sizeof(int2) * ((N + kClassifyBlock - 1) / kClassifyBlock)));
+    w.need_blk = static_cast<unsigned *>(
+        take(4 * (((N + kClassifyBlock - 1) / kClassifyBlock + 31) / 32)));
     w.rec_dirty_blk = static_cast<unsigned *>(
         take(4 * (((N + kDirtyBlock - 1) / kDirtyBlock + 31) / 32)));
     w.sw_iter = static_cast<int *>(take(4 * N));

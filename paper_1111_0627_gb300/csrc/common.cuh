@@ -216,6 +216,8 @@ struct Workspace {
     int *cid_of_root;
     unsigned *done;       // bitmap: vertex resolved and its state in both buffers
     unsigned *rec_dirty;  // bitmap: the last record pass changed v's record (Ctrl::dirty_on)
+    unsigned *need_blk;   // bitmap over blocks of kClassifyBlock vertices: some target of
+                          //     the block's edges lies in a block with a changed record
     int2 *blk_tgt;        // [n / kClassifyBlock] smallest and largest target block (of
                           //     kDirtyBlock vertices) of the out-edges of each block of
                           //     kClassifyBlock vertices (heavy vertices left out)

@@ -387,6 +387,26 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
         if (threadIdx.x == 0 && s_changed)
             atomicAdd(reinterpret_cast<unsigned long long *>(&c->dirty_cnt),
                       (unsigned long long)s_changed);
+        // the blocks of kClassifyBlock vertices whose edges reach a block with
+        // a changed record (by the initial pass's range of target blocks)
+        if (!grid_barrier(c, nblocks)) return;
+        const int nb = (n + kClassifyBlock - 1) / kClassifyBlock;
+        for (int base = first + (int)threadIdx.x - lane; base < nb; base += stride) {
+            const int i = base + lane;
+            bool need = false;
+            if (i < nb) {
+                const int2 rg = ws.blk_tgt[i];
+                need = rg.x > rg.y || (rg.y >> 5) - (rg.x >> 5) >= kFrontierRangeWords;
+                for (int wd = rg.x >> 5; !need && rg.x <= rg.y && wd <= (rg.y >> 5); ++wd) {
+                    unsigned bits = ws.rec_dirty_blk[wd];
+                    if (wd == (rg.x >> 5)) bits &= ~0u << (rg.x & 31);
+                    if (wd == (rg.y >> 5)) bits &= ~0u >> (31 - (rg.y & 31));
+                    need = bits != 0u;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, need);
+            if (lane == 0) ws.need_blk[base >> 5] = m;
+        }
     }
 }
 

@@ -520,6 +520,7 @@ int launch_classify(const int *row_ptr, int n, int epl, int band_blocks, Workspa
 // (same-address atomics per warp would serialise the whole sweep).
 struct ClassGrid {
     int task_off[kClasses + 1];  // first warp task of each class; [kClasses] = total
+    int band_blocks;             // classification blocks per band of the task order
 };
 
 // Candidate of edge e.  Cycle ratio (RATIO): the key also subtracts
@@ -537,6 +538,21 @@ static __device__ __forceinline__ Cand edge_cand(const int *__restrict__ col,
     long long key = (long long)r.w * (long long)(sign * x) + V;
     if (RATIO) key -= __ldg(&ws.recp[t]) * (long long)__ldg(&ws.transit[e]);
     return Cand{r.z, e, key};
+}
+
+// Whether some block of band b (of B classification blocks) has edges that
+// reach a block with a changed record.
+static __device__ __forceinline__ bool band_reaches_change(const Workspace &ws, int b, int B,
+                                                           int n) {
+    const int nbk = (n + kClassifyBlock - 1) / kClassifyBlock;
+    const int b0 = b * B, b1 = min(b0 + B, nbk) - 1;
+    for (int wd = b0 >> 5; wd <= (b1 >> 5); ++wd) {
+        unsigned bits = ws.need_blk[wd];
+        if (wd == (b0 >> 5)) bits &= ~0u << (b0 & 31);
+        if (wd == (b1 >> 5)) bits &= ~0u >> (31 - (b1 & 31));
+        if (bits) return true;
+    }
+    return false;
 }
 
 // FRONTIER: the instance for the frontier form; both instances are launched
@@ -566,16 +582,44 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
     const int4 *__restrict__ grp_tab = ws.band_grp;
     const int total = BANDED ? grp_tab[groups].x : cg.task_off[kClasses];
     int switched = 0;
+    int need_b = -1;    // (FRONTIER) the band band_need describes
+    const int gw = (blockIdx.x * blockDim.x + tid) >> 5;
+    bool band_need = true;
     int p = 0;          // the group holding the current task: grp_tab[p].x <= task
     int4 grp = BANDED ? grp_tab[0] : make_int4(0, 0, 0, 0);
     int next_start = (BANDED && groups > 1) ? grp_tab[1].x : total;
-    for (int task = (blockIdx.x * blockDim.x + tid) >> 5; task < total; task += warps) {
+    for (int task = gw; task < total; task += warps) {
         int c, first_task, list0, cnt;
         if (BANDED) {
             while (task >= next_start) {   // (the same steps in every lane)
                 ++p;
                 grp = grp_tab[p];
                 next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+            }
+            if (FRONTIER) {
+                // a band none of whose blocks reaches a changed record: the
+                // warp jumps to its first task in the next band that has one
+                // (no vertex loaded, no cursor step per group in between)
+                const int b = p / kClasses;
+                if (b != need_b) {
+                    need_b = b;
+                    band_need = band_reaches_change(ws, b, cg.band_blocks, n_vertices);
+                }
+                if (!band_need) {
+                    const int bands = groups / kClasses;
+                    int b2 = b + 1;
+                    while (b2 < bands && !band_reaches_change(ws, b2, cg.band_blocks, n_vertices))
+                        ++b2;
+                    if (b2 >= bands) break;   // (the same decision in every lane)
+                    const int ts = grp_tab[b2 * kClasses].x;
+                    p = b2 * kClasses;
+                    grp = grp_tab[p];
+                    next_start = p + 1 < groups ? grp_tab[p + 1].x : total;
+                    need_b = b2;
+                    band_need = true;
+                    task = ts + (((gw - ts) % warps) + warps) % warps - warps;   // (+ warps below)
+                    continue;
+                }
             }
             c = grp.w;
             first_task = grp.x;
@@ -604,18 +648,9 @@ improve_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
             // (four edges of the lane at a time, their loads independent)
             bool any = false;
             if (valid) {
-                // no changed block in the range of v's block's targets: skipped
-                const int2 rg = ws.blk_tgt[v / kClassifyBlock];
-                if (rg.x <= rg.y && (rg.y >> 5) - (rg.x >> 5) < kFrontierRangeWords) {
-                    bool near = false;
-                    for (int wd = rg.x >> 5; wd <= (rg.y >> 5) && !near; ++wd) {
-                        unsigned bits = ws.rec_dirty_blk[wd];
-                        if (wd == (rg.x >> 5)) bits &= ~0u << (rg.x & 31);
-                        if (wd == (rg.y >> 5)) bits &= ~0u >> (31 - (rg.y & 31));
-                        near = bits != 0u;
-                    }
-                    if (!near) valid = false;
-                }
+                // no changed block within reach of v's block's edges: skipped
+                const int blk = v / kClassifyBlock;
+                if (!((ws.need_blk[blk >> 5] >> (blk & 31)) & 1u)) valid = false;
             }
             if (valid) {
                 const int e_end = __ldg(&row_ptr[v + 1]);
@@ -1013,6 +1048,7 @@ int launch_sweep(const int *row_ptr, const int *col, const int *w, int sign, int
         tasks += (((long long)cls_cnt[c] << c) + 31) / 32;
     }
     cg.task_off[kClasses] = (int)tasks;
+    cg.band_blocks = band_blocks;
     const int groups = sweep_groups(n, band_blocks);
     const bool banded = groups > kClasses;
     if (banded) tasks += groups;
