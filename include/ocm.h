@@ -236,7 +236,7 @@ typedef struct ocm_options {
 
 /* Test-only: the frontier sweep after every evaluation but the first.  By
  * default the record pass marks the records it changes when the sweep before
- * it switched fewer than n/256 vertices, and the next sweep then skips the
+ * it switched fewer than n/512 vertices, and the next sweep then skips the
  * vertices none of whose out-edges' targets changed its record, when fewer
  * than n/8 records changed (such a vertex would choose as in the last sweep);
  * not in the single-lambda form, whose rebuild writes records itself.  With

@@ -169,7 +169,7 @@ struct Ctrl {
 // where its block's bit is set; a whole block of kClassifyBlock vertices none
 // of whose edges reaches a changed block (by the range of target blocks the
 // initial pass records) is skipped without reading its edges.
-constexpr int kFrontierSwitchShift = 8;
+constexpr int kFrontierSwitchShift = 9;
 constexpr int kFrontierDirtyShift = 3;
 constexpr int kDirtyBlock = 1024;
 // A vertex whose block's targets span more than this many dirty-bitmap words

@@ -371,9 +371,10 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
             if (lane == 0) {
                 ws.rec_dirty[base >> 5] = m;
                 changed += __popc(m);
-                if (m) {
+                if (m) {   // (a plain read first: the 32 warps of a block share the bit)
                     const int blk = base / kDirtyBlock;
-                    atomicOr(&ws.rec_dirty_blk[blk >> 5], 1u << (blk & 31));
+                    const unsigned bit = 1u << (blk & 31);
+                    if (!(ws.rec_dirty_blk[blk >> 5] & bit)) atomicOr(&ws.rec_dirty_blk[blk >> 5], bit);
                 }
             }
         }
