@@ -973,11 +973,15 @@ namespace ocm {
 //           weight and smallest vertex); detection by window minima on it
 //           finds the roots of the cycles that cross ranges (the smallest
 //           segment minimum on the node cycle is the cycle's smallest vertex);
-//   fix:    a block whose range holds such a root repeats its local phase with
-//           the root as one more terminal, so that every path reaching it
-//           stops at its first occurrence;
+//   fix:    the vertices of such a root's range whose local path ends at the
+//           root's former exit repeat their value jumping, spread over the
+//           whole grid, with the root as one more terminal, so that every path
+//           reaching it stops at its first occurrence (with many such roots,
+//           the blocks holding one repeat their whole local phase instead);
 //   values: (len, S) of every exit to its root by jumping on the node graph;
-//   expand: each vertex adds its local part to its exit's value.
+//   expand: each vertex adds its local part to its exit's value where it is
+//           read (final_value), a leaf first following its one or two steps
+//           to a vertex with a state of its own (local_state).
 // The local rounds are O(log) of the path length inside a range instead of
 // the whole depth and cycle length, and need no grid barrier.
 // ---------------------------------------------------------------------------
