@@ -135,7 +135,8 @@ static __device__ __forceinline__ int block_scan_incl(int x, int *s_warp) {
 // best (rank, INT_MAX - root) in *s_best.  Returns false on an error
 // (recorded in the control block).
 static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *s_red, int *s_k,
-                                      unsigned long long *s_best, unsigned *bits, int nwords) {
+                                      unsigned long long *s_best, unsigned *bits, int nwords,
+                                      unsigned *dirty, int *n_dirty) {
     const int n = v1 - v0;
     int lg = 0;
     while ((1 << lg) < n) ++lg;
@@ -235,7 +236,7 @@ static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *
         if (r + 1 > lg + 4) { if (threadIdx.x == 0) atomicOr(&c->err, kErrDetect); return false; }
     }
     // ---- values on the dense space, the root terminal (final J = ~root)
-    JLS *A = ws.jls[1] + v0, *B = reinterpret_cast<JLS *>(ws.rec) + v0;
+    JLS *A = ws.jls[1] + v0, *B = reinterpret_cast<JLS *>(ws.scratch16) + v0;
     for (int d = (int)threadIdx.x; d < nk; d += Wt) {
         const int v = orig[d];
         const int root = ws.rep[v];
@@ -320,7 +321,14 @@ static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *
         atomicMax(s_best, packed);
     }
     __syncthreads();
-    // ---- materialise the records the sweep gathers
+    // ---- materialise the records the sweep gathers (with dirty != nullptr,
+    //      marking those that change: the next sweep looks only at vertices
+    //      with a changed target)
+    if (dirty) {
+        for (int i = threadIdx.x; i < (n + 31) / 32; i += W) dirty[i] = 0u;
+        __syncthreads();
+    }
+    int changed = 0;
     for (int v = v0 + (int)threadIdx.x; v < v1; v += W) {
         const JLS st = A[v];
         const int i = ws.cid_of_root[~st.J];
@@ -330,9 +338,17 @@ static __device__ bool small_evaluate(int v0, int v1, const Workspace &ws, int *
         rec.V = (long long)q * st.S - p * (long long)st.len;
         rec.rank = ws.cyc_rank[i];
         rec.q = q;
+        if (dirty) {
+            const Rec old = ws.rec[v];
+            if (old.V != rec.V || old.rank != rec.rank || old.q != rec.q) {
+                atomicOr(&dirty[(v - v0) >> 5], 1u << ((v - v0) & 31));
+                ++changed;
+            }
+        }
         ws.rec[v] = rec;
     }
-    __syncthreads();
+    if (dirty) *n_dirty = block_sum(changed, s_red);   // (its barriers end the pass)
+    else __syncthreads();
     return true;
 }
 
@@ -366,9 +382,17 @@ static __device__ __forceinline__ Cand small_cand(const int *__restrict__ col,
 // improve_kernel): a thread per vertex of out-degree <= 32, a warp per vertex
 // with more (lanes stride its edges, shuffles combine); returns the number of
 // switches.
+static __device__ __forceinline__ bool target_changed(const unsigned *dirty, int v0, int t) {
+    return (dirty[(t - v0) >> 5] >> ((t - v0) & 31)) & 1u;
+}
+
+// dirty != nullptr: the frontier form -- a vertex none of whose targets'
+// records changed in the last evaluation would choose as in the last sweep,
+// and is skipped.
 static __device__ int small_sweep(int v0, int v1, const int *__restrict__ row_ptr,
                                   const int *__restrict__ col, const int *__restrict__ w,
-                                  int sign, const Workspace &ws, int *s_red) {
+                                  int sign, const Workspace &ws, int *s_red,
+                                  const unsigned *dirty) {
     int sw = 0;
     bool heavy_seen = false;
     for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
@@ -376,6 +400,11 @@ static __device__ int small_sweep(int v0, int v1, const int *__restrict__ row_pt
         if (b - a > 32) {
             heavy_seen = true;
             continue;
+        }
+        if (dirty) {
+            bool any = false;
+            for (int e = a; e < b && !any; ++e) any = target_changed(dirty, v0, col[e]);
+            if (!any) continue;
         }
         const int pv = ws.pi[v];
         Cand best{INT_MIN, INT_MAX, LLONG_MIN};
@@ -393,6 +422,12 @@ static __device__ int small_sweep(int v0, int v1, const int *__restrict__ row_pt
         for (int v = v0 + (int)(threadIdx.x >> 5); v < v1; v += nw) {
             const int a = row_ptr[v], b = row_ptr[v + 1];
             if (b - a <= 32) continue;   // the same decision in every lane
+            if (dirty) {
+                bool any = false;
+                for (int e = a + lane; e < b && !any; e += 32)
+                    any = target_changed(dirty, v0, col[e]);
+                if (!__any_sync(0xffffffffu, any)) continue;
+            }
             const int pv = ws.pi[v];
             Cand best{INT_MIN, INT_MAX, LLONG_MIN};
             Cand own{INT_MIN, INT_MAX, LLONG_MIN};
@@ -440,12 +475,26 @@ small_graph_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col,
         const int v0 = bs.vptr[g], v1 = bs.vptr[g + 1];
         long long it = 0;
         bool ok = true;
+        // the frontier form: once the last sweep switched fewer than n/8
+        // vertices, the record pass marks the records it changes (a bitmap in
+        // shared memory after the leaf bitmaps, when both fit), and the sweep
+        // looks only at vertices with a changed target when fewer than n/4
+        // changed
+        const int ng = v1 - v0;
+        unsigned *dirty_bits = 4 * ((ng + 31) / 32) <= nwords ? s_bits + 3 * ((ng + 31) / 32)
+                                                              : nullptr;
+        int last_sw = ng;
         for (;;) {
-            if (!small_evaluate(v0, v1, ws, s_red, &s_k, &s_best, s_bits, nwords)) {
+            unsigned *mark = (dirty_bits && it > 0 && last_sw < (ng >> 3)) ? dirty_bits : nullptr;
+            int n_dirty = ng;
+            if (!small_evaluate(v0, v1, ws, s_red, &s_k, &s_best, s_bits, nwords, mark,
+                                &n_dirty)) {
                 ok = false;
                 break;
             }
-            const int sw = small_sweep(v0, v1, row_ptr, col, w, sign, ws, s_red);
+            const int sw = small_sweep(v0, v1, row_ptr, col, w, sign, ws, s_red,
+                                       (mark && n_dirty < (ng >> 2)) ? mark : nullptr);
+            last_sw = sw;
             if (sw == 0) break;
             if (++it >= max_iters) {
                 if (threadIdx.x == 0) c->not_converged = 1;
