@@ -244,6 +244,21 @@ typedef struct ocm_options {
  * results. */
 #define OCM_FLAG_TEST_FRONTIER 128
 
+/* Test-only: the local phase of the two-level evaluation.  By default every
+ * block resolves its range in chunks of 4,096 vertices from the top of the
+ * range down: a vertex whose successor lies in a chunk done before starts
+ * from that vertex's finished state, the paths inside a chunk are resolved by
+ * pointer jumping in shared memory, and the paths that go back to a lower
+ * chunk are finished by jumping over the range at the end (on a graph whose
+ * edges point forward there are none, and each range costs one streaming
+ * pass).  Once a range leaves more than an eighth of its vertices to that
+ * last step, the solve's later evaluations use leaf-trimmed jump rounds over
+ * the whole range instead.  OCM_FLAG_TEST_LOCAL_CHUNKS keeps the chunks in
+ * every evaluation, OCM_FLAG_TEST_NO_LOCAL_CHUNKS never uses them (setting
+ * both is OCM_ERR_INVALID_ARG).  Same results. */
+#define OCM_FLAG_TEST_LOCAL_CHUNKS 256
+#define OCM_FLAG_TEST_NO_LOCAL_CHUNKS 512
+
 /* Counters of one solve (host struct, filled when a pointer is given). */
 typedef struct ocm_stats {
     int32_t iterations;     /* improvement sweeps that changed the policy           */
@@ -479,7 +494,8 @@ const char *ocm_status_string(int status);
  * ocm_stats.batch_small_graphs; 108: OCM_FLAG_EVAL_LOCAL, OCM_FLAG_EVAL_GLOBAL,
  * OCM_FLAG_TEST_NO_BITMAP; 109: OCM_SWEEP_WINDOW, ocm_stats.sweep_kind; 110:
  * OCM_FLAG_TEST_SMALL_BANDS; 111: OCM_FLAG_TEST_FRONTIER and the frontier
- * sweep). */
+ * sweep; 112: OCM_FLAG_TEST_LOCAL_CHUNKS, OCM_FLAG_TEST_NO_LOCAL_CHUNKS and
+ * the chunked local phase). */
 int ocm_version(void);
 
 #ifdef __cplusplus

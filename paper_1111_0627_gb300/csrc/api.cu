@@ -78,12 +78,13 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     return align_up(off, 256);
 }
 
-__global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns, int frontier) {
+__global__ void ctrl_init_kernel(Ctrl *c, long long wait_ns, int frontier, int local_chunks) {
     Ctrl z;
     memset(&z, 0, sizeof z);
     z.bad_index = INT_MAX;
     z.wait_ns = wait_ns;
     z.frontier = frontier;
+    z.local_chunks = local_chunks;
     *c = z;
 }
 
@@ -513,7 +514,7 @@ const char *ocm_status_string(int status) {
     }
 }
 
-int ocm_version(void) { return 111; }
+int ocm_version(void) { return 112; }
 
 int ocm_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;
@@ -593,7 +594,11 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     // records after the record pass
     const int frontier =
         single ? 0 : (opt && (opt->flags & OCM_FLAG_TEST_FRONTIER)) ? 2 : 1;
-    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl, wait_ns, frontier);
+    const int local_chunks = !opt                                         ? 1
+                             : (opt->flags & OCM_FLAG_TEST_NO_LOCAL_CHUNKS) ? 0
+                             : (opt->flags & OCM_FLAG_TEST_LOCAL_CHUNKS)    ? 2
+                                                                           : 1;
+    ctrl_init_kernel<<<1, 1, 0, st>>>(ws.ctrl, wait_ns, frontier, local_chunks);
     launch_check_row_ptr(row_ptr, n, m, ws.ctrl, st);
     launches += 2;
     if (bs) launches += launch_batch_prepare(n, m, b, ws, st);
@@ -840,9 +845,13 @@ int ocm_solve(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, 
     if (opt && (opt->flags & ~(OCM_FLAG_TEST_STALL | OCM_FLAG_HOST_LOOP | OCM_FLAG_SINGLE_LAMBDA |
                                OCM_FLAG_EVAL_LOCAL | OCM_FLAG_EVAL_GLOBAL |
                                OCM_FLAG_TEST_NO_BITMAP | OCM_FLAG_TEST_SMALL_BANDS |
-                               OCM_FLAG_TEST_FRONTIER)))
+                               OCM_FLAG_TEST_FRONTIER | OCM_FLAG_TEST_LOCAL_CHUNKS |
+                               OCM_FLAG_TEST_NO_LOCAL_CHUNKS)))
         return OCM_ERR_INVALID_ARG;
     if (opt && (opt->flags & OCM_FLAG_EVAL_LOCAL) && (opt->flags & OCM_FLAG_EVAL_GLOBAL))
+        return OCM_ERR_INVALID_ARG;
+    if (opt && (opt->flags & OCM_FLAG_TEST_LOCAL_CHUNKS) &&
+        (opt->flags & OCM_FLAG_TEST_NO_LOCAL_CHUNKS))
         return OCM_ERR_INVALID_ARG;
     const bool single = opt && (opt->flags & OCM_FLAG_SINGLE_LAMBDA);
     if (opt && (opt->sweep_kind < OCM_SWEEP_DEFAULT || opt->sweep_kind > OCM_SWEEP_WINDOW))

@@ -156,6 +156,11 @@ struct Ctrl {
     // 2 (test) after every evaluation but the first
     int frontier;
     int dirty_on;             // the last record pass marked the records it changed
+    // two-level evaluation: chunked local pass (0 off, 1 on until a range
+    // leaves more than an eighth of its vertices pending, 2 always), and the
+    // report of such a range
+    int local_chunks;
+    int chunk_bad;
     long long dirty_cnt;      // how many it changed
 };
 

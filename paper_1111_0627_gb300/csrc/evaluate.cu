@@ -743,6 +743,13 @@ __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       int nwords, Workspace ws, BatchState bs);
 constexpr int kLocalBitmapWords = 40960;   // 160 KB: the bitmaps of ranges up to 436,906 vertices
+// chunked local pass: vertices per chunk, and its two shared-memory buffers of
+// 16-byte packed states
+constexpr int kLocalChunkPerThread = 4;
+constexpr int kLocalChunk = kLocalChunkPerThread * kEvalThreads;
+constexpr int kPackedStateBytes = 16;
+constexpr int kLocalChunkBytes = 2 * kLocalChunk * kPackedStateBytes;
+static_assert(kLocalChunkBytes <= kLocalBitmapWords * 4, "chunk buffers within the opt-in size");
 int evaluate_local_blocks(int n);
 
 // One policy evaluation = one cooperative launch; returns 1, or -1 on a
@@ -760,7 +767,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
         cfg.blockDim = dim3(kEvalThreads);
-        cfg.dynamicSmemBytes = (size_t)nwords * 4;
+        cfg.dynamicSmemBytes = (size_t)(nwords * 4 > kLocalChunkBytes ? nwords * 4 : kLocalChunkBytes);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -1460,12 +1467,236 @@ static __device__ int local_onepass(int lo, int hi, int n, int max_rounds, const
     return 1;
 }
 
+// Path v -> J(s) followed by the path J(s) -> J(t): target, length
+// (saturating), minimum and finished bit of t's end, weights added.
+static __device__ __forceinline__ PackedState pk_compose(const PackedState &s,
+                                                         const PackedState &t) {
+    const unsigned len = min((unsigned)((s.a >> 21) & kPkMask) + (unsigned)((t.a >> 21) & kPkMask),
+                             (unsigned)kPkNone);
+    const unsigned M = min((unsigned)((s.a >> 42) & kPkMask), (unsigned)((t.a >> 42) & kPkMask));
+    return pk_make((unsigned)(t.a & kPkMask), len, M, (t.a >> 63) != 0, s.S + t.S);
+}
+
+// Chunked local phase.  On graphs whose edges mostly point to higher vertices
+// (the synthetic locality graph: every edge goes forward) a policy path
+// inside a block range only climbs, so the range can be taken in chunks of
+// kLocalChunk vertices from its top down, each chunk finishing its vertices
+// from the states of the chunks above it:
+//   states: a vertex whose successor lies outside the range is an exit; one
+//           whose successor lies in a chunk done before starts from that
+//           vertex's state (finished: its exit, or pending: a path that goes
+//           back below); the others start with the one step;
+//   jumping inside the chunk in shared memory (two buffers of packed states)
+//           until no path ends inside the chunk (a path of as many steps as
+//           the chunk has vertices that still does lies in the basin of a
+//           cycle inside the range);
+//   writes: finished vertices get their final state {~(n + exit), len, S}
+//           (jls[0]) and path minimum (jm[1]); a vertex whose path goes back
+//           to a lower chunk is pending (its packed state in the 16-byte
+//           scratch, J >= 0 in jls[0]) and listed; the chunk's exits are
+//           listed with one global atomic.
+// The pending vertices are finished at the end by jumping over the range
+// (none on the locality graph).  Every vertex ends with a final state, so the
+// readers have no leaves to complete.  Returns 1 done, 0 a cycle inside the
+// range (every exit listed; the two-pass phase takes over), -1 an error;
+// *pending_out is the number of vertices the chunks left pending.
+static_assert(sizeof(PackedState) == kPackedStateBytes, "packed state size");
+
+// State of vertex u (lo <= u < hi) of a chunk done before: final in jls[0]
+// (J < 0, with its path minimum in jm[1]) or pending in P.
+static __device__ __forceinline__ PackedState chunk_done_state(const Workspace &ws,
+                                                               const PackedState *P, int lo,
+                                                               int n, int u) {
+    const JLS f = ws.jls[0][u];
+    const JM d = ws.jm[1][u];
+    if (f.J >= 0) return P[u - lo];
+    return pk_make((unsigned)(~f.J - n - lo), (unsigned)f.len,
+                   d.M == INT_MAX ? (unsigned)kPkNone : (unsigned)(d.M - lo), true, f.S);
+}
+
+static __device__ __forceinline__ void chunk_write_final(const Workspace &ws, int lo, int n,
+                                                         int v, const PackedState &s) {
+    const int tag = n + lo + (int)(s.a & kPkMask);
+    const unsigned M = (unsigned)((s.a >> 42) & kPkMask);
+    ws.jls[0][v] = JLS{~tag, (int)((s.a >> 21) & kPkMask), s.S};
+    ws.jm[1][v] = JM{~tag, M == kPkNone ? INT_MAX : lo + (int)M};
+}
+
+static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const Workspace &ws,
+                                    int *LA, int *s_cnt, int *s_red, int *s_flag,
+                                    PackedState *sm, int *pending_out, int *work_total) {
+    Ctrl *c = ws.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int W = blockDim.x;   // kEvalThreads
+    const int nv = hi - lo;
+    PackedState *Pg = reinterpret_cast<PackedState *>(ws.scratch16) + lo;
+    __shared__ int s_xcnt, s_xbase;
+    if (threadIdx.x == 0) {
+        *s_flag = 0;
+        s_xcnt = 0;
+    }
+    __syncthreads();
+    for (int c_hi = hi; c_hi > lo; c_hi -= kLocalChunk) {
+        const int c_lo = max(lo, c_hi - kLocalChunk);
+        const int cn = c_hi - c_lo;
+        const int off = c_lo - lo;   // local index of the chunk's first vertex
+        // ---- the chunk's states
+        bool ex[kLocalChunkPerThread];
+        unsigned xb[kLocalChunkPerThread];
+        int xw = 0;
+#pragma unroll
+        for (int u = 0; u < kLocalChunkPerThread; ++u) {
+            const int k = (int)threadIdx.x + u * W;
+            ex[u] = false;
+            if (k < cn) {
+                const int v = c_lo + k;
+                const int sv = ws.succ[v];
+                PackedState s;
+                if (sv < lo || sv >= hi) {
+                    ex[u] = true;
+                    s = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
+                } else {
+                    s = pk_make((unsigned)(sv - lo), 1, (unsigned)(v - lo), false,
+                                (long long)ws.wpi[v]);
+                    if (sv >= c_hi) s = pk_compose(s, chunk_done_state(ws, Pg, lo, n, sv));
+                }
+                sm[k] = s;
+            }
+            xb[u] = __ballot_sync(0xffffffffu, ex[u]);
+            xw += __popc(xb[u]);
+        }
+        int woff = 0;
+        if (lane == 0 && xw) woff = atomicAdd(&s_xcnt, xw);
+        woff = __shfl_sync(0xffffffffu, woff, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) {   // (read after the round barriers below)
+            s_xbase = s_xcnt ? atomicAdd(&c->node_cnt, s_xcnt) : 0;
+            s_xcnt = 0;
+        }
+        // ---- jumping inside the chunk
+        int fb = 0;   // the buffer with the chunk's current states
+        for (int r = 0;; ++r) {
+            const PackedState *in = sm + fb * kLocalChunk;
+            PackedState *out = sm + (fb ^ 1) * kLocalChunk;
+            bool more = false;
+#pragma unroll
+            for (int u = 0; u < kLocalChunkPerThread; ++u) {
+                const int k = (int)threadIdx.x + u * W;
+                if (k >= cn) continue;
+                PackedState s = in[k];
+                const int j = (int)(s.a & kPkMask) - off;
+                if (!(s.a >> 63) && j >= 0 && j < cn) {
+                    s = pk_compose(s, in[j]);
+                    const int j2 = (int)(s.a & kPkMask) - off;
+                    if (!(s.a >> 63) && j2 >= 0 && j2 < cn) {
+                        more = true;
+                        if ((int)((s.a >> 21) & kPkMask) >= cn) *s_flag = 1;   // a cycle here
+                    }
+                }
+                out[k] = s;
+            }
+            fb ^= 1;
+            if (!__syncthreads_or(more) || *s_flag) break;
+            if (r + 1 > max_rounds) {
+                if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+                return -1;
+            }
+        }
+        // ---- write the chunk out
+        const PackedState *fin = sm + fb * kLocalChunk;
+        int xrun = 0;   // exits of the warp in the slots before u
+#pragma unroll
+        for (int u = 0; u < kLocalChunkPerThread; ++u) {
+            const int k = (int)threadIdx.x + u * W;
+            bool pend = false;
+            if (k < cn) {
+                const int v = c_lo + k;
+                if (ex[u]) {
+                    const int pos = s_xbase + woff + xrun + __popc(xb[u] & ((1u << lane) - 1u));
+                    ws.jls[0][v] = JLS{~(n + v), 0, 0};
+                    ws.jm[1][v] = JM{~(n + v), INT_MAX};
+                    ws.rep[v] = n + v;
+                    node_index(ws)[v] = pos;
+                    ws.list[2][pos] = v;
+                } else {
+                    const PackedState s = fin[k];
+                    ws.rep[v] = -1;   // no root, no exit (the root fix sets the roots)
+                    if (s.a >> 63) {
+                        chunk_write_final(ws, lo, n, v, s);
+                    } else {
+                        Pg[v - lo] = s;
+                        ws.jls[0][v] = JLS{lo + (int)(s.a & kPkMask), 0, 0};   // pending
+                        pend = true;
+                    }
+                }
+            }
+            xrun += __popc(xb[u]);
+            block_append(LA, s_cnt, pend, off + k, lane);
+        }
+        __syncthreads();
+    }
+    const int np = *s_cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_cnt = 0;
+    *pending_out = np;
+    int work = nv;
+    if (*s_flag) {
+        *work_total += work;
+        return 0;
+    }
+    if (np > 0) {
+        // ---- the paths going back to a lower chunk: jumping over the range
+        //      (their targets' states: final in jls[0], or pending in the
+        //      round's input buffer)
+        PackedState *P[2] = {Pg, reinterpret_cast<PackedState *>(ws.jls[1]) + lo};
+        int f = 0;
+        for (int r = 0;; ++r) {
+            const PackedState *in = P[f];
+            PackedState *out = P[f ^ 1];
+            int still = 0;
+            for (int i = threadIdx.x; i < np; i += W) {
+                const int d = LA[i];
+                PackedState s = in[d];
+                if (!(s.a >> 63)) {
+                    s = pk_compose(s, chunk_done_state(ws, in, lo, n, lo + (int)(s.a & kPkMask)));
+                    if (!(s.a >> 63)) {
+                        ++still;
+                        if ((int)((s.a >> 21) & kPkMask) >= nv) *s_flag = 1;   // a cycle here
+                    }
+                }
+                out[d] = s;
+            }
+            f ^= 1;
+            work += np;
+            const int left = block_sum_int(still, s_red);
+            if (*s_flag) {
+                *work_total += work;
+                return 0;
+            }
+            if (left == 0) break;
+            if (r + 1 > max_rounds) {
+                if (threadIdx.x == 0) atomicOr(&c->err, kErrValue);
+                return -1;
+            }
+        }
+        for (int i = threadIdx.x; i < np; i += W) {
+            const int d = LA[i];
+            chunk_write_final(ws, lo, n, lo + d, P[f][d]);
+        }
+        __syncthreads();
+    }
+    *work_total += work;
+    return 1;
+}
+
 constexpr int kRerunMaxRoots = 32;   // roots on the node graph fixed by the grid-wide rerun
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       int nwords, Workspace ws, BatchState bs) {
-    extern __shared__ unsigned s_bits[];   // nwords: the local predecessor bitmap
+    // nwords: the local predecessor bitmaps, or the chunked pass's two state
+    // buffers (kLocalChunkBytes)
+    extern __shared__ __align__(16) unsigned s_bits[];
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     __shared__ int s_red[kEvalThreads / 32];
@@ -1495,10 +1726,23 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     //      two where the range holds a cycle of its own
     int work = 0;
     {
-        const int one = (hi - lo <= kMaxOnePassRange)
-                            ? local_onepass(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red,
-                                            &s_rerun, s_bits, nwords, &work)
-                            : 0;
+        // the chunked pass (0: off, 1: on while no range leaves more than an
+        // eighth of its vertices pending, 2: always); read by every block
+        // before the barrier after which block 0 may turn it off
+        const int chunks = load_volatile(&c->local_chunks);
+        int one = 0;
+        if (hi - lo <= kMaxOnePassRange) {
+            if (chunks) {
+                int np = 0;
+                one = local_chunked(lo, hi, n, max_local, ws, LA, &s_cnt, s_red, &s_rerun,
+                                    reinterpret_cast<PackedState *>(s_bits), &np, &work);
+                if (threadIdx.x == 0 && chunks == 1 && np > (hi - lo) / 8)
+                    atomicOr(&c->chunk_bad, 1);
+            } else {
+                one = local_onepass(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red, &s_rerun,
+                                    s_bits, nwords, &work);
+            }
+        }
         if (one < 0) return;
         if (one == 0 &&
             !local_phase(lo, hi, n, false, hi - lo > kMaxOnePassRange, max_local, ws, LA, LB,
@@ -1506,6 +1750,9 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
             return;
     }
     if (!grid_barrier(c, nblocks)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c->local_chunks == 1 &&
+        load_volatile(&c->chunk_bad))
+        c->local_chunks = 0;   // the paths mostly go backwards: leaf-trimmed rounds from now on
     const int K_exit = load_volatile(&c->node_cnt);
     const int K_local = load_volatile(&c->nrep);
     const int *X = ws.list[2];

@@ -30,6 +30,8 @@ OCM_FLAG_EVAL_GLOBAL = 16   # forbid it
 OCM_FLAG_TEST_NO_BITMAP = 32  # test only: the two-level evaluation without its bitmaps
 OCM_FLAG_TEST_SMALL_BANDS = 64  # test only: the class sweep's task order in 1,024-vertex bands
 OCM_FLAG_TEST_FRONTIER = 128  # test only: the frontier sweep after every evaluation but the first
+OCM_FLAG_TEST_LOCAL_CHUNKS = 256     # test only: the chunked local phase in every evaluation
+OCM_FLAG_TEST_NO_LOCAL_CHUNKS = 512  # test only: never the chunked local phase
 OCM_SWEEP_DEFAULT, OCM_SWEEP_CLASSES, OCM_SWEEP_TILES, OCM_SWEEP_WINDOW = 0, 1, 2, 3
 
 

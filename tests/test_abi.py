@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_only_entry_points():
     lib = ocm.load()
-    assert lib.ocm_version() == 111
+    assert lib.ocm_version() == 112
     assert lib.ocm_workspace_size(0, 5) == 0
     assert lib.ocm_workspace_size(5, 0) == 0
     small = lib.ocm_workspace_size(1000, 4000)
@@ -69,7 +69,11 @@ def test_argument_errors_are_reported_before_any_device_work():
                        ctypes.byref(clen), ctypes.c_void_p(256 + 8), 10**9, None, None, None)
     assert rc == -7                                      # workspace misaligned
     opt = _native.OcmOptions()
-    opt.flags = 256                                      # no such flag
+    opt.flags = 1024                                     # no such flag
+    rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
+                       ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
+    assert rc == -1
+    opt.flags = 256 | 512                                # chunks forced on and off at once
     rc = lib.ocm_solve(fake, fake, fake, 4, 4, 0, ctypes.byref(num), ctypes.byref(den), fake,
                        ctypes.byref(clen), fake, 10**9, None, ctypes.byref(opt), None)
     assert rc == -1
