@@ -1523,56 +1523,85 @@ static __device__ __forceinline__ void chunk_write_final(const Workspace &ws, in
 }
 
 static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const Workspace &ws,
-                                    int *LA, int *s_cnt, int *s_red, int *s_flag,
+                                    int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
                                     PackedState *sm, int *pending_out, int *work_total) {
     Ctrl *c = ws.ctrl;
     const int lane = threadIdx.x & 31;
     const int W = blockDim.x;   // kEvalThreads
     const int nv = hi - lo;
     PackedState *Pg = reinterpret_cast<PackedState *>(ws.scratch16) + lo;
-    __shared__ int s_xcnt, s_xbase;
+    __shared__ int s_xcnt;
     if (threadIdx.x == 0) {
         *s_flag = 0;
         s_xcnt = 0;
+    }
+    // successors and weights of the next chunk, loaded while the one before
+    // it is resolved
+    int nsv[kLocalChunkPerThread], nwv[kLocalChunkPerThread];
+    {
+        const int c_lo = max(lo, hi - kLocalChunk);
+#pragma unroll
+        for (int u = 0; u < kLocalChunkPerThread; ++u) {
+            const int v = c_lo + (int)threadIdx.x + u * W;
+            nsv[u] = v < hi ? ws.succ[v] : -1;
+            nwv[u] = v < hi ? ws.wpi[v] : 0;
+        }
     }
     __syncthreads();
     for (int c_hi = hi; c_hi > lo; c_hi -= kLocalChunk) {
         const int c_lo = max(lo, c_hi - kLocalChunk);
         const int cn = c_hi - c_lo;
         const int off = c_lo - lo;   // local index of the chunk's first vertex
-        // ---- the chunk's states
+        // ---- the chunk's states: the targets in chunks done before first
+        //      (all gathers in flight at once), then the states
         bool ex[kLocalChunkPerThread];
-        unsigned xb[kLocalChunkPerThread];
-        int xw = 0;
+        JLS tf[kLocalChunkPerThread];
+        JM td[kLocalChunkPerThread];
 #pragma unroll
         for (int u = 0; u < kLocalChunkPerThread; ++u) {
             const int k = (int)threadIdx.x + u * W;
-            ex[u] = false;
-            if (k < cn) {
-                const int v = c_lo + k;
-                const int sv = ws.succ[v];
-                PackedState s;
-                if (sv < lo || sv >= hi) {
-                    ex[u] = true;
-                    s = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
-                } else {
-                    s = pk_make((unsigned)(sv - lo), 1, (unsigned)(v - lo), false,
-                                (long long)ws.wpi[v]);
-                    if (sv >= c_hi) s = pk_compose(s, chunk_done_state(ws, Pg, lo, n, sv));
-                }
-                sm[k] = s;
+            const int sv = nsv[u];
+            ex[u] = k < cn && (sv < lo || sv >= hi);
+            tf[u].J = INT_MIN;
+            if (k < cn && sv >= c_hi && sv < hi) {
+                tf[u] = ws.jls[0][sv];
+                td[u] = ws.jm[1][sv];
             }
-            xb[u] = __ballot_sync(0xffffffffu, ex[u]);
-            xw += __popc(xb[u]);
         }
-        int woff = 0;
-        if (lane == 0 && xw) woff = atomicAdd(&s_xcnt, xw);
-        woff = __shfl_sync(0xffffffffu, woff, 0);
+#pragma unroll
+        for (int u = 0; u < kLocalChunkPerThread; ++u) {
+            const int k = (int)threadIdx.x + u * W;
+            if (k >= cn) continue;
+            const int v = c_lo + k;
+            const int sv = nsv[u];
+            PackedState s;
+            if (ex[u]) {
+                s = pk_make((unsigned)(v - lo), 0, (unsigned)kPkNone, true, 0);
+            } else {
+                s = pk_make((unsigned)(sv - lo), 1, (unsigned)(v - lo), false, (long long)nwv[u]);
+                if (tf[u].J != INT_MIN) {   // the successor's chunk is done
+                    const PackedState t =
+                        tf[u].J >= 0
+                            ? Pg[sv - lo]   // pending: its path goes back to a lower chunk
+                            : pk_make((unsigned)(~tf[u].J - n - lo), (unsigned)tf[u].len,
+                                      td[u].M == INT_MAX ? (unsigned)kPkNone
+                                                         : (unsigned)(td[u].M - lo),
+                                      true, tf[u].S);
+                    s = pk_compose(s, t);
+                }
+            }
+            sm[k] = s;
+        }
+        {   // prefetch the next chunk
+            const int n_lo = max(lo, c_lo - kLocalChunk);
+#pragma unroll
+            for (int u = 0; u < kLocalChunkPerThread; ++u) {
+                const int v = n_lo + (int)threadIdx.x + u * W;
+                nsv[u] = v < c_lo ? ws.succ[v] : -1;
+                nwv[u] = v < c_lo ? ws.wpi[v] : 0;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {   // (read after the round barriers below)
-            s_xbase = s_xcnt ? atomicAdd(&c->node_cnt, s_xcnt) : 0;
-            s_xcnt = 0;
-        }
         // ---- jumping inside the chunk
         int fb = 0;   // the buffer with the chunk's current states
         for (int r = 0;; ++r) {
@@ -1602,9 +1631,8 @@ static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const
                 return -1;
             }
         }
-        // ---- write the chunk out
+        // ---- write the chunk out (the exits are listed in LB, in block order)
         const PackedState *fin = sm + fb * kLocalChunk;
-        int xrun = 0;   // exits of the warp in the slots before u
 #pragma unroll
         for (int u = 0; u < kLocalChunkPerThread; ++u) {
             const int k = (int)threadIdx.x + u * W;
@@ -1612,12 +1640,9 @@ static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const
             if (k < cn) {
                 const int v = c_lo + k;
                 if (ex[u]) {
-                    const int pos = s_xbase + woff + xrun + __popc(xb[u] & ((1u << lane) - 1u));
                     ws.jls[0][v] = JLS{~(n + v), 0, 0};
                     ws.jm[1][v] = JM{~(n + v), INT_MAX};
                     ws.rep[v] = n + v;
-                    node_index(ws)[v] = pos;
-                    ws.list[2][pos] = v;
                 } else {
                     const PackedState s = fin[k];
                     ws.rep[v] = -1;   // no root, no exit (the root fix sets the roots)
@@ -1630,10 +1655,21 @@ static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const
                     }
                 }
             }
-            xrun += __popc(xb[u]);
             block_append(LA, s_cnt, pend, off + k, lane);
+            block_append(LB, &s_xcnt, ex[u], c_lo + k, lane);
         }
         __syncthreads();
+    }
+    {   // the node list: the range's exits, one global atomic
+        __shared__ int s_xbase;
+        const int nx = s_xcnt;
+        if (threadIdx.x == 0) s_xbase = nx ? atomicAdd(&c->node_cnt, nx) : 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx; i += W) {
+            const int v = LB[i];
+            ws.list[2][s_xbase + i] = v;
+            node_index(ws)[v] = s_xbase + i;
+        }
     }
     const int np = *s_cnt;
     __syncthreads();
@@ -1734,7 +1770,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         if (hi - lo <= kMaxOnePassRange) {
             if (chunks) {
                 int np = 0;
-                one = local_chunked(lo, hi, n, max_local, ws, LA, &s_cnt, s_red, &s_rerun,
+                one = local_chunked(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red, &s_rerun,
                                     reinterpret_cast<PackedState *>(s_bits), &np, &work);
                 if (threadIdx.x == 0 && chunks == 1 && np > (hi - lo) / 8)
                     atomicOr(&c->chunk_bad, 1);
