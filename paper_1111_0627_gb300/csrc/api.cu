@@ -72,6 +72,7 @@ size_t carve_workspace(void *base, int n, int m, Workspace *ws) {
     w.jt[1] = static_cast<long long *>(take(8 * N));
     w.recp = static_cast<long long *>(take(8 * N));
     w.root_mark = static_cast<int *>(take(4 * N));
+    w.chunk_info = static_cast<int2 *>(take(sizeof(int2) * (N / kEvalThreads + 2)));
     w.transit = nullptr;
     w.ctrl = static_cast<Ctrl *>(take(sizeof(Ctrl)));
     if (ws) *ws = w;

@@ -253,6 +253,7 @@ struct Workspace {
     long long *jt[2];     // [n] value jumping: transit time of the path from v to J
     long long *recp;      // [n] numerator p of the ratio of v's cycle (gathered by the sweep)
     int *root_mark;       // [n] two-level evaluation: evaluation stamp of a root found on the node graph
+    int2 *chunk_info;     // [n / 1024 + 2] chunked local pass, per block range: (status, exits)
     Ctrl *ctrl;
 };
 

@@ -750,11 +750,14 @@ constexpr int kLocalChunk = kLocalChunkPerThread * kEvalThreads;
 constexpr int kPackedStateBytes = 16;
 constexpr int kLocalChunkBytes = 2 * kLocalChunk * kPackedStateBytes;
 static_assert(kLocalChunkBytes <= kLocalBitmapWords * 4, "chunk buffers within the opt-in size");
+__global__ void __launch_bounds__(kEvalThreads, 1)
+local_chunk_kernel(int n, int max_local, Workspace ws);
 int evaluate_local_blocks(int n);
 
-// One policy evaluation = one cooperative launch; returns 1, or -1 on a
-// launch failure.  local: the two-level evaluation (single graphs without
-// transit times only).
+// One policy evaluation = one cooperative launch (the two-level form: the
+// chunked local pass first, then the cooperative launch); returns the number
+// of launches, or -1 on a launch failure.  local: the two-level evaluation
+// (single graphs without transit times only).
 int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchState bs,
                     cudaStream_t st, bool local, bool no_bitmap) {
     const bool ratio = ws.transit != nullptr;
@@ -767,7 +770,7 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(blocks);
         cfg.blockDim = dim3(kEvalThreads);
-        cfg.dynamicSmemBytes = (size_t)(nwords * 4 > kLocalChunkBytes ? nwords * 4 : kLocalChunkBytes);
+        cfg.dynamicSmemBytes = (size_t)nwords * 4;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -775,11 +778,15 @@ int launch_evaluate(int n, long long N2, Workspace ws, int stall_test, BatchStat
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         prof_begin(kProfEvaluate, st);
+        // (a kernel of its own: the cooperative kernel's register budget would
+        // spill the pass's state; it returns at once when the pass is off)
+        local_chunk_kernel<<<blocks, kEvalThreads, kLocalChunkBytes, st>>>(n, ceil_log2(R) + 4, ws);
+        const cudaError_t e0 = cudaGetLastError();
         const cudaError_t e = cudaLaunchKernelEx(&cfg, evaluate_local_kernel, n, N2,
                                                  ceil_log2(R) + 4, ceil_log2(n) + 4, stall_test,
                                                  nwords, ws, bs);
         prof_end(kProfEvaluate, st);
-        return e == cudaSuccess ? 1 : -1;
+        return (e0 == cudaSuccess && e == cudaSuccess) ? 2 : -1;
     }
     int blocks = ratio ? evaluate_grid<true>() : evaluate_grid<false>();
     if (blocks <= 0) return -1;
@@ -1524,7 +1531,8 @@ static __device__ __forceinline__ void chunk_write_final(const Workspace &ws, in
 
 static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const Workspace &ws,
                                     int *LA, int *LB, int *s_cnt, int *s_red, int *s_flag,
-                                    PackedState *sm, int *pending_out, int *work_total) {
+                                    PackedState *sm, int *pending_out, int *exits_out,
+                                    int *work_total) {
     Ctrl *c = ws.ctrl;
     const int lane = threadIdx.x & 31;
     const int W = blockDim.x;   // kEvalThreads
@@ -1660,17 +1668,7 @@ static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const
         }
         __syncthreads();
     }
-    {   // the node list: the range's exits, one global atomic
-        __shared__ int s_xbase;
-        const int nx = s_xcnt;
-        if (threadIdx.x == 0) s_xbase = nx ? atomicAdd(&c->node_cnt, nx) : 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < nx; i += W) {
-            const int v = LB[i];
-            ws.list[2][s_xbase + i] = v;
-            node_index(ws)[v] = s_xbase + i;
-        }
-    }
+    *exits_out = s_xcnt;
     const int np = *s_cnt;
     __syncthreads();
     if (threadIdx.x == 0) *s_cnt = 0;
@@ -1725,14 +1723,47 @@ static __device__ int local_chunked(int lo, int hi, int n, int max_rounds, const
     return 1;
 }
 
+// The chunked local pass of every block range of the two-level evaluation
+// (same grid and ranges as evaluate_local_kernel, which follows it): per
+// range, (status, exits) in chunk_info -- status 1 done, 0 a cycle inside the
+// range (the two-pass phase takes over), -1 an error, 2 not run (ranges too
+// large for the packed state) -- and the range's exits in list[1].  Returns
+// at once when the pass is off.
+__global__ void __launch_bounds__(kEvalThreads, 1)
+local_chunk_kernel(int n, int max_local, Workspace ws) {
+    extern __shared__ __align__(16) unsigned s_chunk[];
+    __shared__ int s_cnt, s_flag;
+    __shared__ int s_red[kEvalThreads / 32];
+    Ctrl *c = ws.ctrl;
+    const int chunks = load_volatile(&c->local_chunks);
+    if (!chunks) return;
+    const int R = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = min((int)blockIdx.x * R, n), hi = min(lo + R, n);
+    if (hi - lo > kMaxOnePassRange) {
+        if (threadIdx.x == 0) ws.chunk_info[blockIdx.x] = make_int2(2, 0);
+        return;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int np = 0, nx = 0, work = 0;
+    const int st = local_chunked(lo, hi, n, max_local, ws, ws.list[0] + lo, ws.list[1] + lo,
+                                 &s_cnt, s_red, &s_flag, reinterpret_cast<PackedState *>(s_chunk),
+                                 &np, &nx, &work);
+    if (threadIdx.x == 0) {
+        ws.chunk_info[blockIdx.x] = make_int2(st, nx);
+        if (chunks == 1 && np > (hi - lo) / 8) atomicOr(&c->chunk_bad, 1);
+        if (work)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&c->items_detect),
+                      (unsigned long long)work);
+    }
+}
+
 constexpr int kRerunMaxRoots = 32;   // roots on the node graph fixed by the grid-wide rerun
 
 __global__ void __launch_bounds__(kEvalThreads, 1)
 evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stall_test,
                       int nwords, Workspace ws, BatchState bs) {
-    // nwords: the local predecessor bitmaps, or the chunked pass's two state
-    // buffers (kLocalChunkBytes)
-    extern __shared__ __align__(16) unsigned s_bits[];
+    extern __shared__ unsigned s_bits[];   // nwords: the local predecessor bitmaps
     __shared__ long long s_key[kRankTile];
     __shared__ int s_cnt;
     __shared__ int s_red[kEvalThreads / 32];
@@ -1769,11 +1800,18 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
         int one = 0;
         if (hi - lo <= kMaxOnePassRange) {
             if (chunks) {
-                int np = 0;
-                one = local_chunked(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red, &s_rerun,
-                                    reinterpret_cast<PackedState *>(s_bits), &np, &work);
-                if (threadIdx.x == 0 && chunks == 1 && np > (hi - lo) / 8)
-                    atomicOr(&c->chunk_bad, 1);
+                // done by local_chunk_kernel: list the range's exits (in
+                // list[1]) as nodes, one global atomic
+                const int2 info = ws.chunk_info[blockIdx.x];
+                __shared__ int s_xbase;
+                if (threadIdx.x == 0) s_xbase = info.y ? atomicAdd(&c->node_cnt, info.y) : 0;
+                __syncthreads();
+                for (int i = threadIdx.x; i < info.y; i += blockDim.x) {
+                    const int v = LB[i];
+                    ws.list[2][s_xbase + i] = v;
+                    node_index(ws)[v] = s_xbase + i;
+                }
+                one = info.x;
             } else {
                 one = local_onepass(lo, hi, n, max_local, ws, LA, LB, &s_cnt, s_red, &s_rerun,
                                     s_bits, nwords, &work);
@@ -2096,6 +2134,8 @@ static int evaluate_local_grid() {
     // co-resident with the largest bitmap any launch uses
     if (cudaFuncSetAttribute(evaluate_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kLocalBitmapWords * 4) != cudaSuccess ||
+        cudaFuncSetAttribute(local_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kLocalChunkBytes) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_local_kernel,
                                                       kEvalThreads, kLocalBitmapWords * 4) !=
             cudaSuccess ||
