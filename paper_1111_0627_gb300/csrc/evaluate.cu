@@ -841,26 +841,28 @@ static __device__ __forceinline__ void block_append_global(int *list, int *count
 // candidates at once by binary lifting over the bits of L* (the candidate set
 // is closed under succ, so the jump tables never leave it).
 //
-// After the two-level evaluation the leaves of the local phase (a one-step
-// state in jls[0], J >= 0) lie on no cycle unless their cycle predecessor is
-// in another range: a cycle leaf is an entry (the successor of an exit) or
-// the successor of a leaf entry.  Those are marked (the change bitmap of the
-// frontier sweep is free once the loop has ended) and the other leaves are no
-// candidates; the set stays closed under succ (a kept vertex's successor is
-// kept or an exit, an exit's is an entry, a leaf entry's is marked, and a
-// marked second-level vertex's successor is kept).
+// Candidates are also restricted to the vertices at the end of a policy path
+// of two edges (a vertex of a cycle is: its cycle predecessor has one too),
+// marked in two passes over succ (A: has a predecessor, B: has a predecessor
+// in A).  The set stays closed under succ (v in B makes succ(v)'s predecessor
+// v in A) and loses the policy tree's leaves and their successors that no
+// other vertex reaches, about half of a random policy graph.  Bitmaps: the
+// frontier sweep's change bitmap and the spare done bitmap, both free once
+// the loop has ended.
 __global__ void __launch_bounds__(kThreads) extract_clear_kernel(int words, Workspace ws) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
         ws.rec_dirty[i] = 0u;
+        ws.done[i] = 0u;
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) extract_mark_kernel(Workspace ws) {
-    const int K = ws.ctrl->node_cnt;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
-        const int y = ws.succ[ws.list[2][i]];
-        atomicOr(&ws.rec_dirty[y >> 5], 1u << (y & 31));
-        const JLS f = ws.jls[0][y];
-        if (f.J >= 0) atomicOr(&ws.rec_dirty[f.J >> 5], 1u << (f.J & 31));
+// to[succ(v)] for every v (from == nullptr) or every v marked in from.
+__global__ void __launch_bounds__(kThreads)
+extract_pred_kernel(int n, const unsigned *from, unsigned *to, Workspace ws) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (from && !((from[v >> 5] >> (v & 31)) & 1u)) continue;
+        const int t = ws.succ[v];
+        atomicOr(&to[t >> 5], 1u << (t & 31));
     }
 }
 
@@ -876,8 +878,7 @@ extract_candidates_kernel(int n, Workspace ws) {
         bool cand = false;
         if (v < n) {
             const JLS st = final_value(ws.jls[0], n, v);
-            cand = (~st.J == root) && st.len < L &&
-                   (ws.jls[0][v].J < 0 || ((ws.rec_dirty[v >> 5] >> (v & 31)) & 1u));
+            cand = (~st.J == root) && st.len < L && ((ws.done[v >> 5] >> (v & 31)) & 1u);
             if (cand) cur[v] = v;
         }
         block_append_global(ws.list[0], &c->ncand, cand, v, lane);
@@ -931,9 +932,10 @@ int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cud
     prof_begin(kProfExtract, st);
     extract_reset_kernel<<<1, 1, 0, st>>>(ws);
     extract_clear_kernel<<<grid, kThreads, 0, st>>>((n + 31) / 32, ws);
-    extract_mark_kernel<<<grid, kThreads, 0, st>>>(ws);
+    extract_pred_kernel<<<grid, kThreads, 0, st>>>(n, nullptr, ws.rec_dirty, ws);
+    extract_pred_kernel<<<grid, kThreads, 0, st>>>(n, ws.rec_dirty, ws.done, ws);
     extract_candidates_kernel<<<grid, kThreads, 0, st>>>(n, ws);
-    int launches = 4;
+    int launches = 5;
     int bits = 0;
     while ((1LL << bits) <= Lstar) ++bits;
     for (int b = 0; b < bits; ++b, ++launches) extract_round_kernel<<<grid, kThreads, 0, st>>>(b, ws);
