@@ -983,7 +983,12 @@ namespace ocm {
 //           the range (an "exit") being terminal: each vertex ends with the
 //           root of a cycle inside the range, or with the exit its path
 //           leaves by, the path's length and weight to it, and the smallest
-//           vertex on the way;
+//           vertex on the way.  By default a kernel of its own does it chunk
+//           by chunk from the top of the range down (local_chunked: one
+//           streaming pass when the paths climb, as on the locality graph);
+//           a range with a cycle of its own, and every range once paths that
+//           go back dominate, take the jump rounds of local_onepass or the
+//           two-pass local_phase inside the cooperative kernel;
 //   nodes:  the exits form a functional graph of their own (exit x -> the
 //           exit that succ(x)'s local path ends at, with the segment's length,
 //           weight and smallest vertex); detection by window minima on it
@@ -996,8 +1001,9 @@ namespace ocm {
 //           the blocks holding one repeat their whole local phase instead);
 //   values: (len, S) of every exit to its root by jumping on the node graph;
 //   expand: each vertex adds its local part to its exit's value where it is
-//           read (final_value), a leaf first following its one or two steps
-//           to a vertex with a state of its own (local_state).
+//           read (final_value), a leaf of local_onepass first following its
+//           one or two steps to a vertex with a state of its own
+//           (local_state).
 // The local rounds are O(log) of the path length inside a range instead of
 // the whole depth and cycle length, and need no grid barrier.
 // ---------------------------------------------------------------------------
