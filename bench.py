@@ -198,16 +198,6 @@ def algorithmic_bytes(cls: str, n: int, m: int, launches: int) -> float:
     return 0.0
 
 
-def round_bytes(n: int, st_total: dict, launches: int) -> float:
-    """Bytes the pointer-jumping evaluation moves by its own count: 40 B per
-    vertex-round of cycle detection (own state 8, target state 8, previous
-    window minimum 4 + 4, new state 8, done bitmap and succ 8), 48 B per
-    vertex-round of value propagation (own 16, target 16, new 16), and 68 B
-    per vertex per evaluation (value set-up and materialisation)."""
-    return (40.0 * st_total["detect_items"] + 48.0 * st_total["value_items"]
-            + 68.0 * n * launches)
-
-
 CLASSES = ["init", "sweep", "evaluate", "extract"]
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
@@ -220,10 +210,12 @@ CLASSES = ["init", "sweep", "evaluate", "extract"]
 KERNEL_SOURCES = {"evaluate": ("evaluate.cu", "grid_sync.cuh", "common.cuh"),
                   "sweep": ("sweep.cu", "common.cuh")}
 TRAFFIC = {
-    # n = 2^23 capture (launches from the middle of a solve, mean; the sweep's
-    # full instance) x 4
-    ("locality32m", "evaluate"): (4 * (0.587198e9 + 0.681805e9), "f0833845eac2641d"),
-    ("locality32m", "sweep"): (4 * (0.862521e9 + 0.122266e9), "cbd4a579ab6ce80b"),
+    # n = 2^23 capture (launches from the middle of a solve, mean; the
+    # evaluation's two launches, local_chunk_kernel + evaluate_local_kernel;
+    # the sweep's full instance) x 4
+    ("locality32m", "evaluate"): (4 * (0.067934e9 + 0.174014e9 + 0.191952e9 + 0.137857e9),
+                                  "a71cf8ae7486b1e7"),
+    ("locality32m", "sweep"): (4 * (0.861710e9 + 0.122202e9), "58329d72b625e079"),
 }
 
 
@@ -370,12 +362,9 @@ def run_ours(args, g, desc):
     prof_steps = max(1, min(args.steps, 5))
     lib.ocm_profile_enable(1)
     lib.ocm_profile_collect(None, None)
-    st_total = {"switched": 0, "detect_items": 0, "value_items": 0}
     for k in range(prof_steps):
         flush.fill_(k & 0xFF)
-        s = solve()
-        for key in st_total:
-            st_total[key] += s.stats[key]
+        solve()
     ms_arr = (ctypes.c_double * len(CLASSES))()
     n_arr = (ctypes.c_int64 * len(CLASSES))()
     lib.ocm_profile_collect(ms_arr, n_arr)
@@ -399,15 +388,16 @@ def run_ours(args, g, desc):
                 "avg_launch_us": d["ms_total"] * 1e3 / max(d["launches"], 1),
                 "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / max(d["launches"], 1)}
 
-    roofline = kernel_roofline(dom)
-    n_eval = max(classes["evaluate"]["launches"], 1)
-    eval_rounds = round_bytes(g.n, st_total, classes["evaluate"]["launches"])
-    roofline["eval_round_bytes_per_launch"] = eval_rounds / n_eval
-    roofline["eval_bytes_over_floor"] = eval_rounds / (40.0 * g.n * n_eval)
-    roofline_sweep = kernel_roofline("sweep")
-    roofline_sweep["note"] = ("averaged over every sweep of the solve: the frontier sweeps of the "
-                              "last iterations, which skip most vertices, count at the full "
-                              "sweep's algorithmic bytes; traffic is the full sweep's")
+    # the dominant class, and the other of the two per-step classes beside it
+    other = "sweep" if dom != "sweep" else "evaluate"
+    rooflines = {dom: kernel_roofline(dom), other: kernel_roofline(other)}
+    rooflines["sweep"]["note"] = ("averaged over every sweep of the solve: the frontier sweeps of "
+                                  "the last iterations, which skip most vertices, count at the "
+                                  "full sweep's algorithmic bytes; traffic is the full sweep's")
+    if "evaluate" in rooflines:
+        rooflines["evaluate"]["note"] = ("algorithmic bytes: the 40 B per vertex floor of one "
+                                         "evaluation; both launches of the two-level form")
+    roofline = rooflines[dom]
     share = {c: round(v["ms_total"] / max(sum(x["ms_total"] for x in classes.values()), 1e-12), 4)
              for c, v in classes.items()}
 
@@ -480,7 +470,7 @@ def run_ours(args, g, desc):
                        "iteration": ("single-lambda (Alg. 1 rebuild around the chosen cycle)"
                                      if single else "multichain (one mean per policy cycle)")},
             "roofline": roofline,
-            "roofline_sweep": roofline_sweep,
+            "roofline_" + other: rooflines[other],
             "kernel_share": share,
             "kernels": {c: {"ms_per_solve": v["ms_total"] / prof_steps,
                             "launches_per_solve": v["launches"] / prof_steps,
