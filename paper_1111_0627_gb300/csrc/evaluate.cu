@@ -343,38 +343,73 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
         c->switched = 0;
     }
     // (warp-uniform trip counts: a warp covers 32 consecutive vertices, one
-    // word of the change bitmap)
+    // word of the change bitmap, in each of its kMU slots; the slots' loads
+    // are issued together, stage by stage)
+    constexpr int kMU = 2;
     int changed = 0;
-    for (int base = first + (int)threadIdx.x - lane; base < n; base += stride) {
-        const int v = base + lane;
-        bool dirty = false;
-        if (v < n && !(bs.G && bs.gconv[bs.gid[v]])) {
-            JLS st = LOCAL ? final_value(ws.jls[0], n, v) : ws.jls[F][v];
-            int i = ws.cid_of_root[~st.J];
-            long long p = ws.cyc_p[i];
-            int q = ws.cyc_q[i];
-            Rec rec;
-            const long long T = ratio ? ws.jt[F][v] : (long long)st.len;
-            rec.V = (long long)q * st.S - p * T;
-            rec.rank = ws.cyc_rank[i];
-            rec.q = q;
-            if (mark) {
-                const Rec old = ws.rec[v];
-                dirty = old.V != rec.V || old.rank != rec.rank || old.q != rec.q ||
-                        (ratio && ws.recp[v] != p);
-            }
-            ws.rec[v] = rec;
-            if (ratio) ws.recp[v] = p;
+    for (int base0 = first + (int)threadIdx.x - lane; base0 < n; base0 += kMU * stride) {
+        JLS st[kMU];
+        bool ok[kMU];
+#pragma unroll
+        for (int u = 0; u < kMU; ++u) {
+            const int v = base0 + u * stride + lane;
+            ok[u] = v < n && !(bs.G && bs.gconv[bs.gid[v]]);
+            if (ok[u]) st[u] = LOCAL ? ws.jls[0][v] : ws.jls[F][v];
         }
-        if (mark) {
-            const unsigned m = __ballot_sync(0xffffffffu, dirty);
-            if (lane == 0) {
-                ws.rec_dirty[base >> 5] = m;
-                changed += __popc(m);
-                if (m) {   // (a plain read first: the 32 warps of a block share the bit)
-                    const int blk = base / kDirtyBlock;
-                    const unsigned bit = 1u << (blk & 31);
-                    if (!(ws.rec_dirty_blk[blk >> 5] & bit)) atomicOr(&ws.rec_dirty_blk[blk >> 5], bit);
+        if (LOCAL) {   // final_value: a leaf's steps, then the exit's value
+#pragma unroll
+            for (int u = 0; u < kMU; ++u) {
+                if (!ok[u]) continue;
+                for (int k = 0; k < 2 && st[u].J >= 0; ++k) {
+                    const JLS nx = ws.jls[0][st[u].J];
+                    st[u] = JLS{nx.J, st[u].len + nx.len, st[u].S + nx.S};
+                }
+            }
+            JLS xf[kMU];
+#pragma unroll
+            for (int u = 0; u < kMU; ++u)
+                if (ok[u] && ~st[u].J >= n) xf[u] = ws.jls[0][~st[u].J - n];
+#pragma unroll
+            for (int u = 0; u < kMU; ++u)
+                if (ok[u] && ~st[u].J >= n)
+                    st[u] = JLS{xf[u].J, st[u].len + xf[u].len, st[u].S + xf[u].S};
+        }
+        int ci[kMU];
+#pragma unroll
+        for (int u = 0; u < kMU; ++u) ci[u] = ok[u] ? ws.cid_of_root[~st[u].J] : 0;
+#pragma unroll
+        for (int u = 0; u < kMU; ++u) {
+            const int v = base0 + u * stride + lane;
+            bool dirty = false;
+            if (ok[u]) {
+                const int i = ci[u];
+                const long long p = ws.cyc_p[i];
+                const int q = ws.cyc_q[i];
+                Rec rec;
+                const long long T = ratio ? ws.jt[F][v] : (long long)st[u].len;
+                rec.V = (long long)q * st[u].S - p * T;
+                rec.rank = ws.cyc_rank[i];
+                rec.q = q;
+                if (mark) {
+                    const Rec old = ws.rec[v];
+                    dirty = old.V != rec.V || old.rank != rec.rank || old.q != rec.q ||
+                            (ratio && ws.recp[v] != p);
+                }
+                ws.rec[v] = rec;
+                if (ratio) ws.recp[v] = p;
+            }
+            const int base = base0 + u * stride;
+            if (mark && base < n) {
+                const unsigned m = __ballot_sync(0xffffffffu, dirty);
+                if (lane == 0) {
+                    ws.rec_dirty[base >> 5] = m;
+                    changed += __popc(m);
+                    if (m) {   // (a plain read first: the 32 warps of a block share the bit)
+                        const int blk = base / kDirtyBlock;
+                        const unsigned bit = 1u << (blk & 31);
+                        if (!(ws.rec_dirty_blk[blk >> 5] & bit))
+                            atomicOr(&ws.rec_dirty_blk[blk >> 5], bit);
+                    }
                 }
             }
         }
