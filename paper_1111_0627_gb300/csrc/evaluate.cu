@@ -345,7 +345,7 @@ static __device__ void evaluate_tail(int n, long long N2, int F, const Workspace
     // (warp-uniform trip counts: a warp covers 32 consecutive vertices, one
     // word of the change bitmap, in each of its kMU slots; the slots' loads
     // are issued together, stage by stage)
-    constexpr int kMU = 2;
+    constexpr int kMU = 4;
     int changed = 0;
     for (int base0 = first + (int)threadIdx.x - lane; base0 < n; base0 += kMU * stride) {
         JLS st[kMU];
