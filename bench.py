@@ -213,9 +213,9 @@ TRAFFIC = {
     # n = 2^23 capture (launches from the middle of a solve, mean; the
     # evaluation's two launches, local_chunk_kernel + evaluate_local_kernel;
     # the sweep's full instance) x 4
-    ("locality32m", "evaluate"): (4 * (0.067934e9 + 0.174014e9 + 0.191952e9 + 0.137857e9),
-                                  "a71cf8ae7486b1e7"),
-    ("locality32m", "sweep"): (4 * (0.861710e9 + 0.122202e9), "58329d72b625e079"),
+    ("locality32m", "evaluate"): (4 * (0.067928e9 + 0.173937e9 + 0.191412e9 + 0.133667e9),
+                                  "4bb4fb85ecd77e7a"),
+    ("locality32m", "sweep"): (4 * (0.861859e9 + 0.122140e9), "58329d72b625e079"),
 }
 
 
