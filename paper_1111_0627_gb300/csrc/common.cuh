@@ -348,12 +348,14 @@ __device__ __forceinline__ void publish_result(const Workspace &ws, int n) {
     }
 }
 
-// Local state of v after the two-level evaluation's local phase.  A vertex
-// that no vertex of its range jumps to (a "leaf": no predecessor in the
-// range, or leaves only) keeps the one step to its successor, J = succ(v) >= 0,
-// len 1 and its edge weight, and is completed here by following those steps:
-// at most two, since the successor of a leaf whose predecessors are all
-// leaves has a state of its own.  Every other state is returned as stored.
+// Local state of v after the two-level evaluation's local phase.  After the
+// leaf-trimmed rounds (local_onepass) a vertex that no vertex of its range
+// jumps to (a "leaf": no predecessor in the range, or leaves only) keeps the
+// one step to its successor, J = succ(v) >= 0, len 1 and its edge weight,
+// and is completed here by following those steps: at most two, since the
+// successor of a leaf whose predecessors are all leaves has a state of its
+// own.  Every other state (all of them after the chunked pass) is returned
+// as stored.
 __device__ __forceinline__ JLS local_state(const JLS *jls0, int v) {
     JLS st = jls0[v];
 #pragma unroll

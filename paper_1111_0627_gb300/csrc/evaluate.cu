@@ -1543,13 +1543,14 @@ static __device__ __forceinline__ PackedState pk_compose(const PackedState &s,
 //   writes: finished vertices get their final state {~(n + exit), len, S}
 //           (jls[0]) and path minimum (jm[1]); a vertex whose path goes back
 //           to a lower chunk is pending (its packed state in the 16-byte
-//           scratch, J >= 0 in jls[0]) and listed; the chunk's exits are
-//           listed with one global atomic.
+//           scratch, J >= 0 in jls[0]) and listed in LA; the exits are listed
+//           in LB (the cooperative kernel makes them nodes).
 // The pending vertices are finished at the end by jumping over the range
 // (none on the locality graph).  Every vertex ends with a final state, so the
 // readers have no leaves to complete.  Returns 1 done, 0 a cycle inside the
 // range (every exit listed; the two-pass phase takes over), -1 an error;
-// *pending_out is the number of vertices the chunks left pending.
+// *pending_out is the number of vertices the chunks left pending,
+// *exits_out the number of exits listed.
 static_assert(sizeof(PackedState) == kPackedStateBytes, "packed state size");
 
 // State of vertex u (lo <= u < hi) of a chunk done before: final in jls[0]
@@ -1881,8 +1882,9 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
     for (int i = first + threadIdx.x; i < K_exit; i += stride) {
         const int x = X[i];
         const int y = ws.succ[x];
-        // y's local result: through a leaf's steps to the first vertex with a
-        // state of its own (the leaves passed count for the path minimum)
+        // y's local result: through a leaf's steps (local_onepass) to the
+        // first vertex with a state of its own (the leaves passed count for
+        // the path minimum)
         int z = y, mz = INT_MAX;
         JLS f = ws.jls[0][z];
         for (int k = 0; k < 2 && f.J >= 0; ++k) {
@@ -2029,7 +2031,7 @@ evaluate_local_kernel(int n, long long N2, int max_local, int max_node, int stal
                 v = rlo + (int)(q % R);
                 if (!seen && v < n) {
                     bool root = false, member = false;
-                    const int tag = ~ws.jls[0][v].J;   // (a leaf: no tag, completed on read)
+                    const int tag = ~ws.jls[0][v].J;   // (a leaf of local_onepass: no tag)
                     for (int i = 0; i < k_new; ++i) {
                         root |= s_roots[i] == v;
                         member |= s_tags[i] == tag;
