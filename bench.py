@@ -213,9 +213,9 @@ TRAFFIC = {
     # n = 2^23 capture (launches from the middle of a solve, mean; the
     # evaluation's two launches, local_chunk_kernel + evaluate_local_kernel;
     # the sweep's full instance) x 4
-    ("locality32m", "evaluate"): (4 * (0.067928e9 + 0.173937e9 + 0.191412e9 + 0.133667e9),
-                                  "4bb4fb85ecd77e7a"),
-    ("locality32m", "sweep"): (4 * (0.861859e9 + 0.122140e9), "58329d72b625e079"),
+    ("locality32m", "evaluate"): (4 * (0.067995e9 + 0.174004e9 + 0.191367e9 + 0.133739e9),
+                                  "0f2efe8677211bac"),
+    ("locality32m", "sweep"): (4 * (0.861799e9 + 0.122377e9), "e09584c8859bd923"),
 }
 
 
