@@ -215,7 +215,7 @@ TRAFFIC = {
     # the sweep's full instance) x 4
     ("locality32m", "evaluate"): (4 * (0.067995e9 + 0.174004e9 + 0.191367e9 + 0.133739e9),
                                   "0f2efe8677211bac"),
-    ("locality32m", "sweep"): (4 * (0.861799e9 + 0.122377e9), "e09584c8859bd923"),
+    ("locality32m", "sweep"): (4 * (0.861834e9 + 0.122357e9), "b83c7b639091d1b5"),
 }
 
 

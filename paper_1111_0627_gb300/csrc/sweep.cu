@@ -326,45 +326,46 @@ classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, W
 // One block: exclusive scan of the class-major histogram (class c, block b at
 // c * nb + b), so every (class, block) pair gets its first list position.
 __global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace ws) {
+    // (one block: each thread sums a contiguous piece, a block scan of the
+    // piece sums gives each piece its offset, each thread writes its prefixes)
     __shared__ int s_warp[32];
-    __shared__ int s_carry;
+    __shared__ int s_total;
     const int total = kClassSlots * nb;
-    if (threadIdx.x == 0) s_carry = 0;
+    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min(total, (int)threadIdx.x * per), i1 = min(total, i0 + per);
+    int sum = 0;
+    for (int i = i0; i < i1; ++i) sum += ws.cls_hist[i];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((threadIdx.x & 31) >= o) incl += y;
+    }
+    if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
     __syncthreads();
-    for (int base = 0; base < total; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int x = i < total ? ws.cls_hist[i] : 0;
-        int incl = x;
+    if (threadIdx.x < 32) {
+        int wv = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((threadIdx.x & 31) >= o) incl += y;
+            const int y = __shfl_up_sync(0xffffffffu, wv, o);
+            if (threadIdx.x >= o) wv += y;
         }
-        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int wv = s_warp[threadIdx.x];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, wv, o);
-                if (threadIdx.x >= o) wv += y;
-            }
-            s_warp[threadIdx.x] = wv;
-        }
-        __syncthreads();
-        const int warp_prefix = (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
-        const int excl = s_carry + warp_prefix + incl - x;
-        if (i < total) {
-            ws.cls_hist[i] = excl;
-            if (i % nb == 0) ws.ctrl->cls_off[i / nb] = excl;
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry += warp_prefix + incl;
-        __syncthreads();
+        s_warp[threadIdx.x] = wv;
     }
+    __syncthreads();
+    incl += (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+    int run = incl - sum;   // exclusive prefix of this thread's piece
+    for (int i = i0; i < i1; ++i) {
+        const int x = ws.cls_hist[i];
+        ws.cls_hist[i] = run;
+        if (i % nb == 0) ws.ctrl->cls_off[i / nb] = run;
+        run += x;
+    }
+    if (threadIdx.x == blockDim.x - 1) s_total = incl;
+    __syncthreads();
     if (threadIdx.x < kClassSlots) {
         const int c = threadIdx.x;
-        const int next = (c + 1 < kClassSlots) ? ws.ctrl->cls_off[c + 1] : s_carry;
+        const int next = (c + 1 < kClassSlots) ? ws.ctrl->cls_off[c + 1] : s_total;
         ws.ctrl->cls_cnt[c] = next - ws.ctrl->cls_off[c];
     }
 }
@@ -866,10 +867,30 @@ heavy_init_final_kernel(const int *__restrict__ row_ptr, const int *__restrict__
     }
 }
 
+// Co-resident blocks of the initial pass on the current device.
+static int init_grid() {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != cached_dev) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, init_policy_kernel,
+                                                          kSweepMaxThreads, 0) != cudaSuccess)
+            return 0;
+        cached_dev = dev;
+        cached = sms * per_sm;
+    }
+    return cached;
+}
+
 void launch_init_policy(const int *row_ptr, const int *col, const int *w, int sign, int n, int m,
                         const int *init, Workspace ws, const BatchState *bs, cudaStream_t st,
                         int local_R, int count_win, int band_blocks) {
+    // one wave of co-resident blocks (the tasks are taken grid-stride)
     int blocks = (n + kSweepMaxThreads - 1) / kSweepMaxThreads;
+    const int resident = init_grid();
+    if (resident > 0 && blocks > resident) blocks = resident;
     if (blocks > 1024) blocks = 1024;
     const int groups = sweep_groups(n, band_blocks);
     prof_begin(kProfInit, st);
