@@ -213,9 +213,9 @@ TRAFFIC = {
     # n = 2^23 capture (launches from the middle of a solve, mean; the
     # evaluation's two launches, local_chunk_kernel + evaluate_local_kernel;
     # the sweep's full instance) x 4
-    ("locality32m", "evaluate"): (4 * (0.067995e9 + 0.174004e9 + 0.191367e9 + 0.133739e9),
-                                  "0f2efe8677211bac"),
-    ("locality32m", "sweep"): (4 * (0.861834e9 + 0.122357e9), "b83c7b639091d1b5"),
+    ("locality32m", "evaluate"): (4 * (0.067920e9 + 0.174084e9 + 0.191438e9 + 0.133894e9),
+                                  "d516308f4f43a93f"),
+    ("locality32m", "sweep"): (4 * (0.861792e9 + 0.122247e9), "71b96b750f0f6a14"),
 }
 
 

@@ -768,7 +768,14 @@ static int solve_impl(const int32_t *row_ptr, const int32_t *col_idx, const int3
     } else {
         Lstar = h.res_len;
         if (Lstar < 1 || Lstar > n) return OCM_ERR_INTERNAL;
-        launches += launch_extract(n, Lstar, ws, out.cycle_out, grid, st);
+        // (after the two-level evaluation: its block range size, for the
+        // segment walk along the cycle)
+        int local_R = 0;
+        if (sa.local) {
+            const int eb = evaluate_local_blocks(n);
+            if (eb > 0) local_R = (n + eb - 1) / eb;
+        }
+        launches += launch_extract(n, Lstar, ws, out.cycle_out, grid, local_R, st);
     }
     if (opt && (opt->eta_num || opt->eta_den || opt->potential || opt->policy)) {
         launch_outputs(n, ws, opt->eta_num, opt->eta_den, opt->potential, opt->policy, st);

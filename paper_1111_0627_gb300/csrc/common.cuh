@@ -161,6 +161,7 @@ struct Ctrl {
     // report of such a range
     int local_chunks;
     int chunk_bad;
+    int walk_ok;              // extraction: the segment walk found the critical cycle
     long long dirty_cnt;      // how many it changed
 };
 
@@ -473,7 +474,8 @@ int launch_batch_small(const int *row_ptr, const int *col, const int *w, int sig
 int launch_batch_finish(int N, int sign, int Lbits, BatchState bs, Workspace ws, int64_t *num,
                         int32_t *den, int32_t *cycle_len, int32_t *cycle_out, int grid,
                         cudaStream_t st);
-int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st);
+int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, int local_R,
+                   cudaStream_t st);
 // Transposed CSR (scc.cu); returns the number of kernels launched.
 int launch_csc(const int *row_ptr, const int *col, int n, int m, int *in_ptr, int *in_src,
                int *cursor, int *bsum, cudaStream_t st);

@@ -884,7 +884,86 @@ static __device__ __forceinline__ void block_append_global(int *list, int *count
 // other vertex reaches, about half of a random policy graph.  Bitmaps: the
 // frontier sweep's change bitmap and the spare done bitmap, both free once
 // the loop has ended.
+//
+// After the two-level evaluation the cycle can be walked instead, segment by
+// segment (extract_walk_kernel): from r*, a vertex's local state names the exit
+// its path leaves its block range by (or r* itself, for the vertices of r*'s
+// range that reach it first), so one thread follows the cycle from exit to
+// exit, noting each segment's first vertex, length and position, and the
+// block's threads then walk the segments at once.  It gives up (and the
+// lifting runs) when the cycle has more than kWalkSegs segments or a segment
+// more than kWalkSegLen vertices; the lifting kernels return at once when it
+// succeeded.
+constexpr int kWalkSegs = 1024;
+constexpr int kWalkSegLen = 4096;
+
+__global__ void __launch_bounds__(1024)
+extract_walk_kernel(int n, int R, Workspace ws, int *cycle_out) {
+    __shared__ int s_first[kWalkSegs], s_pos[kWalkSegs], s_len[kWalkSegs];
+    __shared__ int s_k, s_ok;
+    Ctrl *c = ws.ctrl;
+    const int r = c->res_root, L = c->res_len;
+    if (threadIdx.x == 0) {
+        int ok = 1, k = 0, pos = 1;
+        int y = ws.succ[r];
+        while (y != r) {
+            if (k >= kWalkSegs || y < 0 || y >= n) {
+                ok = 0;
+                break;
+            }
+            const int lo = (y / R) * R, hi = min(lo + R, n);
+            const int sy = ws.succ[y];
+            int cnt, next;
+            if (sy < lo || sy >= hi) {   // y is an exit (its state is its value)
+                cnt = 1;
+                next = sy;
+            } else {
+                const JLS st = local_state(ws.jls[0], y);
+                const int tag = ~st.J;
+                if (tag == r) {            // y's path reaches r* inside the range
+                    cnt = st.len;
+                    next = r;
+                } else if (tag >= n && tag - n < n) {   // ... or leaves it by an exit
+                    cnt = st.len + 1;
+                    next = ws.succ[tag - n];
+                } else {
+                    ok = 0;
+                    break;
+                }
+            }
+            if (cnt < 1 || cnt > kWalkSegLen || pos + cnt > L) {
+                ok = 0;
+                break;
+            }
+            s_first[k] = y;
+            s_pos[k] = pos;
+            s_len[k] = cnt;
+            pos += cnt;
+            ++k;
+            y = next;
+        }
+        s_k = k;
+        s_ok = ok && pos == L;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    if (threadIdx.x == 0) cycle_out[0] = ws.pi[r];
+    for (int j = threadIdx.x; j < s_k; j += blockDim.x) {
+        int v = s_first[j];
+        const int p = s_pos[j];
+        for (int q = 0; q < s_len[j]; ++q) {
+            cycle_out[p + q] = ws.pi[v];
+            v = ws.succ[v];
+        }
+    }
+    if (threadIdx.x == 0) {
+        c->cnt[0] = L;
+        c->walk_ok = 1;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) extract_clear_kernel(int words, Workspace ws) {
+    if (load_volatile(&ws.ctrl->walk_ok)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
         ws.rec_dirty[i] = 0u;
         ws.done[i] = 0u;
@@ -894,6 +973,7 @@ __global__ void __launch_bounds__(kThreads) extract_clear_kernel(int words, Work
 // to[succ(v)] for every v (from == nullptr) or every v marked in from.
 __global__ void __launch_bounds__(kThreads)
 extract_pred_kernel(int n, const unsigned *from, unsigned *to, Workspace ws) {
+    if (load_volatile(&ws.ctrl->walk_ok)) return;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (from && !((from[v >> 5] >> (v & 31)) & 1u)) continue;
         const int t = ws.succ[v];
@@ -904,6 +984,7 @@ extract_pred_kernel(int n, const unsigned *from, unsigned *to, Workspace ws) {
 __global__ void __launch_bounds__(kThreads)
 extract_candidates_kernel(int n, Workspace ws) {
     Ctrl *c = ws.ctrl;
+    if (load_volatile(&c->walk_ok)) return;   // (no candidates: the rounds have nothing to do)
     const int root = c->res_root, L = c->res_len;
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -959,18 +1040,27 @@ extract_scatter_kernel(int n, Workspace ws, int *cycle_out) {
 __global__ void extract_reset_kernel(Workspace ws) {
     ws.ctrl->ncand = 0;
     ws.ctrl->cnt[0] = 0;
+    ws.ctrl->walk_ok = 0;
 }
 
 // Extracts the critical cycle (root and length already in ctrl->res_*);
-// returns the number of kernel launches.
-int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, cudaStream_t st) {
+// returns the number of kernel launches.  local_R: the block range size of
+// the two-level evaluation the loop used (0: the one-level evaluation, no
+// segment walk).
+int launch_extract(int n, int Lstar, Workspace ws, int *cycle_out, int grid, int local_R,
+                   cudaStream_t st) {
     prof_begin(kProfExtract, st);
     extract_reset_kernel<<<1, 1, 0, st>>>(ws);
+    int walk = 0;
+    if (local_R > 0) {
+        extract_walk_kernel<<<1, 1024, 0, st>>>(n, local_R, ws, cycle_out);
+        walk = 1;
+    }
     extract_clear_kernel<<<grid, kThreads, 0, st>>>((n + 31) / 32, ws);
     extract_pred_kernel<<<grid, kThreads, 0, st>>>(n, nullptr, ws.rec_dirty, ws);
     extract_pred_kernel<<<grid, kThreads, 0, st>>>(n, ws.rec_dirty, ws.done, ws);
     extract_candidates_kernel<<<grid, kThreads, 0, st>>>(n, ws);
-    int launches = 5;
+    int launches = 5 + walk;
     int bits = 0;
     while ((1LL << bits) <= Lstar) ++bits;
     for (int b = 0; b < bits; ++b, ++launches) extract_round_kernel<<<grid, kThreads, 0, st>>>(b, ws);
