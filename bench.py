@@ -215,7 +215,7 @@ TRAFFIC = {
     # the sweep's full instance) x 4
     ("locality32m", "evaluate"): (4 * (0.067920e9 + 0.174084e9 + 0.191438e9 + 0.133894e9),
                                   "d516308f4f43a93f"),
-    ("locality32m", "sweep"): (4 * (0.861792e9 + 0.122247e9), "71b96b750f0f6a14"),
+    ("locality32m", "sweep"): (4 * (0.862757e9 + 0.122895e9), "7327f46a463627d3"),
 }
 
 

@@ -326,42 +326,50 @@ classify_count_kernel(const int *__restrict__ row_ptr, int n, int nb, int epl, W
 // One block: exclusive scan of the class-major histogram (class c, block b at
 // c * nb + b), so every (class, block) pair gets its first list position.
 __global__ void __launch_bounds__(1024) classify_scan_kernel(int nb, Workspace ws) {
-    // (one block: each thread sums a contiguous piece, a block scan of the
-    // piece sums gives each piece its offset, each thread writes its prefixes)
+    // (warp w scans the contiguous piece [w * per, (w + 1) * per) in strips
+    // of 32 consecutive entries: the pieces' sums first, then, offset by a
+    // scan of those sums, the prefixes)
     __shared__ int s_warp[32];
     __shared__ int s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const int total = kClassSlots * nb;
-    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int i0 = min(total, (int)threadIdx.x * per), i1 = min(total, i0 + per);
+    const int per = ((total + nwarps - 1) / nwarps + 31) & ~31;
+    const int i0 = min(total, warp * per), i1 = min(total, i0 + per);
     int sum = 0;
-    for (int i = i0; i < i1; ++i) sum += ws.cls_hist[i];
-    int incl = sum;
+    for (int i = i0 + lane; i < i1; i += 32) sum += ws.cls_hist[i];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((threadIdx.x & 31) >= o) incl += y;
-    }
-    if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) s_warp[warp] = sum;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        int wv = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
+    if (warp == 0) {
+        int wv = lane < nwarps ? s_warp[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, wv, o);
-            if (threadIdx.x >= o) wv += y;
+            if (lane >= o) wv += y;
         }
-        s_warp[threadIdx.x] = wv;
+        s_warp[lane] = wv;   // inclusive
     }
     __syncthreads();
-    incl += (threadIdx.x >= 32) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
-    int run = incl - sum;   // exclusive prefix of this thread's piece
-    for (int i = i0; i < i1; ++i) {
-        const int x = ws.cls_hist[i];
-        ws.cls_hist[i] = run;
-        if (i % nb == 0) ws.ctrl->cls_off[i / nb] = run;
-        run += x;
+    int run = warp > 0 ? s_warp[warp - 1] : 0;   // the piece's offset
+    for (int base = i0; base < i1; base += 32) {   // (warp-uniform trip count)
+        const int i = base + lane;
+        const int x = i < i1 ? ws.cls_hist[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < i1) {
+            const int excl = run + incl - x;
+            ws.cls_hist[i] = excl;
+            if (i % nb == 0) ws.ctrl->cls_off[i / nb] = excl;
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (threadIdx.x == blockDim.x - 1) s_total = incl;
+    if (threadIdx.x == 0) s_total = s_warp[nwarps - 1];
     __syncthreads();
     if (threadIdx.x < kClassSlots) {
         const int c = threadIdx.x;
